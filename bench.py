@@ -1,0 +1,346 @@
+"""Benchmark of the MMGaP hot path on GB300: one step = one 100 MHz / 30 kHz
+uplink slot (3276 subcarriers x 14 OFDM symbols = 45,864 detection problems)
+of 16x16 16-QAM through build -> CIM-CAC solve -> decode.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mmgap|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank detects its own slot
+(weak scaling: fixed work per GPU, no collective on the data path); the step
+time is the max over ranks.  --impl reference times the CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "detections/s (subcarrier-problems, 16x16 16-QAM) at equal BER; p99 slot latency"
+UNIT = "problems/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+WORKLOADS = {
+    # name: (n_r, n_t, mod_bits, model, hold, snr_db)
+    "ul16x16_16qam_slot": (16, 16, 4, "iid", "subcarrier", 16.0),
+    "ul8x8_16qam_slot_kron_prb": (8, 8, 4, "kron", "prb", 15.0),
+}
+
+
+def solver_flops(P: int, n_t: int, runs: int, steps: int, f_mvm: int) -> float:
+    """Algorithmic FP32 work of the anneals (FMA = 2 flops): per anneal,
+    ceil(S/f) field refreshes of 2n^2 + 9n flops (u, m = A u, b^T u, c, mu1,
+    mu2) and S Euler steps of 9 flops for each of the 2n+1 spins."""
+    n = 2 * n_t
+    N = 2 * n + 1
+    refresh = math.ceil(steps / f_mvm) if steps else 0
+    return float(P) * runs * (refresh * (2 * n * n + 9 * n) + 9 * N * steps)
+
+
+def alu_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(name: str, seed: int):
+    n_r, n_t, mb, model, hold, snr = WORKLOADS[name]
+    return synth.uplink(seed, n_r, n_t, mb, snr_db=snr, model=model, hold=hold)
+
+
+def cpu_baseline(w, prm_fields: dict, seed: int, budget_s: float = 12.0, min_problems: int = 4):
+    """Time the CPU oracle (single thread, as it stands) on a bounded sample of
+    the workload; returns (problems/s, sample description, problems done)."""
+    import oracle
+    op = oracle.Params(**prm_fields)
+    n_t, mb = w["n_t"], w["mod_bits"]
+    L = (1 << (mb // 2)) - 1
+    P = w["y"].shape[0]
+    rng = np.random.default_rng(seed)
+    idx = rng.permutation(P)
+    t0 = time.perf_counter()
+    done = 0
+    for p in idx:
+        c = int(w["chan_index"][p])
+        b = oracle.build_detect32(w["H"][c], w["y"][p], w["noise_var"][p], mb)
+        r = oracle.cac_solve(b["Aq"], b["hq"], b["g"], L, op, seed, int(p))
+        oracle.decode_detect(n_t, mb, b["g"], r["d"])
+        done += 1
+        if done >= min_problems and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, f"{done} random problems of the slot, oracle build+solve+decode, 1 thread", done
+
+
+def run_reference(args, rank: int):
+    """CPU oracle as the reference arm (host cores, bounded sample per step)."""
+    if rank != 0:
+        return
+    w = make_workload(args.workload, 2025)
+    fields = dict(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm, dt=0.02, p=1.2, a=1.0, zeta=3.0,
+                  eps=0.5, sigma0=0.1, x_max=1000.0)
+    per_step = []
+    total, tdone = 0.0, 0
+    for i in range(args.warmup + args.steps):
+        v, sample, done = cpu_baseline(w, fields, 1000 + i, budget_s=args.ref_budget, min_problems=2)
+        if i >= args.warmup:
+            per_step.append(done / v)
+            total += done / v
+            tdone += done
+    value = tdone / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "runs": args.runs, "solver_steps": args.solver_steps,
+                       "f_mvm": args.f_mvm, "sample_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mmgap", choices=["mmgap", "reference"])
+    ap.add_argument("--workload", default="ul16x16_16qam_slot", choices=sorted(WORKLOADS))
+    ap.add_argument("--runs", type=int, default=32)
+    ap.add_argument("--solver-steps", type=int, default=200)
+    ap.add_argument("--f-mvm", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=6.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2510_01579_gb300 import Context, Params
+
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # each rank detects its own slot (different seed): weak scaling
+    w = make_workload(args.workload, 2025 + rank)
+    P = w["y"].shape[0]
+    n_t, mb = w["n_t"], w["mod_bits"]
+    prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
+    H = torch.from_numpy(w["H"]).to(dev)
+    y = torch.from_numpy(w["y"]).to(dev)
+    nv = torch.from_numpy(w["noise_var"]).to(dev)
+    ci = torch.from_numpy(w["chan_index"]).to(dev)
+    ctx = Context(local, workspace_bytes=512 << 20)
+    out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
+           "energy": torch.empty(P, dtype=torch.int32, device=dev),
+           "guess": torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)}
+    job = ctx.detect_job(H, y, nv, mb, 77, out, ci)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+    ctx.set_timing(True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.detect_jobs([job], prm)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, each bracketed by events; L2 flushed between steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    solve_ms, build_ms, chunks = [], [], 0
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+        b, s, _, _, nch = ctx.stage_times()
+        build_ms.append(b)
+        solve_ms.append(s)
+        chunks += nch
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * P * args.steps / (total_ms / 1e3)
+
+    # BER of this slot against the transmitted symbols, and of the MMSE guess
+    sym = out["sym"].cpu().numpy()
+    g = out["guess"].cpu().numpy().astype(int)
+    side = 1 << (mb // 2)
+    Lm = side - 1
+    mmse_sym = ((g[:, :n_t] + Lm) // 2) * side + (g[:, n_t:] + Lm) // 2
+    nbits = P * n_t * mb
+    ber = synth.bit_errors(sym, w["sym"], mb) / nbits
+    ber_mmse = synth.bit_errors(mmse_sym, w["sym"], mb) / nbits
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        hH, hy, hnv, hci = (torch.from_numpy(a).pin_memory() for a in (w["H"], w["y"], w["noise_var"],
+                                                                        w["chan_index"]))
+        hsym = torch.empty((P, n_t), dtype=torch.uint8).pin_memory()
+        dH, dy, dnv, dci = (torch.empty_like(a, device=dev) for a in (hH, hy, hnv, hci))
+        e_out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev)}
+        ejob = ctx.detect_job(dH, dy, dnv, mb, 77, e_out, dci)
+        h2d = sum(a.numel() * a.element_size() for a in (hH, hy, hnv, hci))
+        d2h = hsym.numel() * hsym.element_size()
+
+        def e2e_step():
+            for d_, h_ in ((dH, hH), (dy, hy), (dnv, hnv), (dci, hci)):
+                d_.copy_(h_, non_blocking=True)
+            ctx.detect_jobs([ejob], prm)
+            hsym.copy_(e_out["sym"], non_blocking=True)
+
+        for _ in range(args.warmup):
+            flush.zero_()
+            e2e_step()
+        torch.cuda.synchronize()
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            es[i].record(stream)
+            e2e_step()
+            ee[i].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_total = sum(es[i].elapsed_time(ee[i]) for i in range(args.steps))
+        if world > 1:
+            t = torch.tensor([e_total], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_total = float(t.item())
+        if not torch.equal(hsym, out["sym"].cpu()):
+            raise RuntimeError("host-buffer path disagrees with the device-resident path")
+        e2e = {"value": world * P * args.steps / (e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_total / args.steps}
+
+    # roofline of the dominant kernel (the CIM-CAC solver), from the library's
+    # own CUDA events on the launching stream
+    flops = solver_flops(P, n_t, args.runs, args.solver_steps, args.f_mvm)
+    solve_avg = statistics.mean(solve_ms)
+    achieved = flops / (solve_avg / 1e3) / 1e12
+    peak = alu_peak_tflops()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "cac_solve_kernel<16,2>",
+                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts and max clock)",
+                "flops_per_launch": flops, "avg_launch_ms": solve_avg}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        fields = {f: getattr(prm, f) for f in ("runs", "steps", "f_mvm", "dt", "p", "a", "zeta", "eps", "sigma0",
+                                              "x_max")}
+        v, sample, _ = cpu_baseline(w, fields, 77)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    srt = sorted(step_ms)
+    p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "problems_per_step": P, "n_r": w["n_r"], "n_t": n_t,
+                       "mod_bits": mb, "runs": args.runs, "solver_steps": args.solver_steps, "f_mvm": args.f_mvm,
+                       "dt": 0.02, "channel": WORKLOADS[args.workload][3], "hold": WORKLOADS[args.workload][4],
+                       "snr_db": WORKLOADS[args.workload][5], "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"{world} rank(s), one slot per rank"},
+            "slot_latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "max": max(step_ms)},
+            "stage_ms": {"build": statistics.mean(build_ms), "solve": solve_avg},
+            "ber": {"mmgap": ber, "mmse": ber_mmse},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 2 * chunks, "clocks": clk, "wall_s": wall}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * mmgap.h -- C ABI of the GB300 (sm_103a) MMGaP hot path.
+ *
+ * MMGaP (Singh & Jamieson, "Multi-User MIMO Detection and Precoding using
+ * GPU-assisted Physics-inspired Computation") turns every subcarrier's
+ * uplink ML detection problem (Sec. 2.1, Eq. 2) and every downlink
+ * vector-perturbation precoding problem (Sec. 2.2 Eq. 8, Sec. 3.3 Eq. 13)
+ * into a delta-Ising problem around a guess (Sec. 2.3 Eq. 9, Sec. 3.2.1,
+ * Fig. 5), runs many CIM-CAC anneals on it (Eqs. 10-11, Sec. 3.2) and keeps
+ * the lowest-energy candidate.  The paper's three kernels (pre-processing,
+ * solver, post-processing; Sec. 3.2, Fig. 4) map to: a batched builder
+ * (Gram, matched filter, MMSE guess, field, Q14 quantisation), the CIM-CAC
+ * solver with the arg-min folded in, and a decoder.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, unless stated
+ *     otherwise.  Complex arrays are interleaved float32 (re, im) pairs, row
+ *     major.  Pointers must be 4-byte aligned (complex: 8-byte).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; the caller synchronises.
+ *   - Argument errors are reported synchronously (MMGAP_EINVAL /
+ *     MMGAP_EUNSUPPORTED / MMGAP_ENOMEM) before anything is launched.  A CUDA
+ *     launch error returns MMGAP_ECUDA; asynchronous device faults surface on
+ *     the caller's next synchronisation.  mmgap_last_error() describes the
+ *     last failure.  No C++ exception crosses this boundary.
+ *   - Determinism: results depend only on the inputs, the parameters, the job
+ *     seed and the problem's index within its job, never on batch position,
+ *     chunking or stream.  For identical inputs the integer outputs (guesses,
+ *     quantised couplings, offsets, symbols, energies) equal the CPU oracle's
+ *     bit for bit.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef MMGAP_H
+#define MMGAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mmgap_ctx mmgap_ctx;
+
+typedef enum {
+    MMGAP_OK = 0,
+    MMGAP_EINVAL = 1,       /* bad argument (NULL pointer, size out of range) */
+    MMGAP_ENOMEM = 2,       /* workspace too small for one problem / allocation failed */
+    MMGAP_ECUDA = 3,        /* CUDA runtime error */
+    MMGAP_ETIMEOUT = 4,     /* a bounded wait expired */
+    MMGAP_EUNSUPPORTED = 5, /* size or option not compiled in */
+    MMGAP_EBUSY = 6         /* resource in use */
+} mmgap_status;
+
+/*
+ * Solver parameters.  dt, f_mvm: Appendix A (the paper uses dt = 0.02,
+ * f_mvm = 2); p, a, zeta, eps: the free parameters of Eqs. 10-11 (the paper
+ * prints no values); runs: N_a anneals per problem (Sec. 2.3, Sec. 3.2;
+ * the paper uses 32, one warp); steps: N_I Euler steps per anneal.
+ * sigma0: initial amplitudes are uniform in [-sigma0, sigma0) (Sec. 2.3:
+ * random initialisation); x_max: an anneal whose final |x| exceeds x_max, is
+ * not finite, or whose error variable left (0, inf) is counted as diverged
+ * (Appendix A, P_diverge) and replaced by the guess.
+ * Limits: runs in {32, 64, 96, 128}; steps in [0, 1<<20]; f_mvm in [1, 64];
+ * dt > 0.
+ */
+typedef struct {
+    int32_t runs;
+    int32_t steps;
+    int32_t f_mvm;
+    float dt, p, a, zeta, eps;
+    float sigma0;
+    float x_max;
+} mmgap_params;
+
+/*
+ * One uplink detection job: n_problems problems (resource elements) of the
+ * same size (Sec. 3.2: inputs are H and y per problem, Fig. 4).
+ *   n_t in {1, 2, 3, 4, 8, 16} users, n_r in [1, 64] antennas,
+ *   mod_bits in {2, 4, 6} (QPSK, 16-QAM, 64-QAM; symbol index q maps to the
+ *   lattice point (2 (q / sqrt(M)) - L) + i (2 (q % sqrt(M)) - L),
+ *   L = sqrt(M) - 1, scaled by 1/sqrt(2 (M - 1) / 3)).
+ *   H:         complex [n_chan][n_r][n_t]
+ *   chan_index: int32 [n_problems], channel of each problem; NULL = identity
+ *              (then n_chan >= n_problems)
+ *   y:         complex [n_problems][n_r]
+ *   noise_var: float [n_problems], noise variance per receive antenna
+ *              (rho of Eq. 3 with unit symbol energy)
+ *   seed:      Philox4x32-10 key; problem k of the job draws from counter
+ *              space (., run, k).
+ * Outputs (NULL = not wanted, except sym_out):
+ *   sym_out:    uint8 [n_problems][n_t] detected QAM symbol indices
+ *   energy_out: int32 [n_problems] selected quantised energy (<= 0; 0 = guess)
+ *   guess_out:  int8 [n_problems][2 n_t] MMSE lattice guess (re block, im block)
+ *   offset_out: int8 [n_problems][2 n_t] selected offset d in {-1, 0, 1}
+ *   ndiv_out:   int32 [n_problems] diverged anneals
+ */
+typedef struct {
+    int32_t n_r, n_t, mod_bits;
+    int32_t n_problems, n_chan;
+    const int32_t* chan_index;
+    const float* H;
+    const float* y;
+    const float* noise_var;
+    uint64_t seed;
+    uint8_t* sym_out;
+    int32_t* energy_out;
+    int8_t* guess_out;
+    int8_t* offset_out;
+    int32_t* ndiv_out;
+} mmgap_detect_job;
+
+/*
+ * One downlink VPP job (Sec. 2.2, Sec. 3.3): n_u users, n_t antennas.
+ *   n_u in {1, 2, 3, 4, 8, 16}, n_t in [n_u, 64], mod_bits in {2, 4, 6}.
+ *   H:     complex [n_chan][n_u][n_t] (users' channels)
+ *   chan_index: as above
+ *   u_sym: uint8 [n_problems][n_u] intended QAM symbol indices
+ *   seed:  as above
+ * Outputs:
+ *   v_out:      int8 [n_problems][n_u][2] Gaussian-integer perturbation
+ *               (re, im), each in {-1, 0, 1}
+ *   x_out:      complex [n_problems][n_t] transmit vector W (u + tau v),
+ *               unnormalised (Eq. 6 scales it to power P); may be NULL
+ *   power_out:  float [n_problems] ||W (u + tau v)||^2; may be NULL
+ *   energy_out, ndiv_out: as for detection; may be NULL
+ * tau = 2 sqrt(M) in lattice units (2 (c_max + Delta / 2), Delta = 2).
+ * W = H^H (H H^H)^-1 (Eq. 5) is formed through Q = (H H^H)^-1 in FP64.
+ */
+typedef struct {
+    int32_t n_u, n_t, mod_bits;
+    int32_t n_problems, n_chan;
+    const int32_t* chan_index;
+    const float* H;
+    const uint8_t* u_sym;
+    uint64_t seed;
+    int8_t* v_out;
+    float* x_out;
+    float* power_out;
+    int32_t* energy_out;
+    int32_t* ndiv_out;
+} mmgap_precode_job;
+
+/* Fill *p with the library defaults: runs 32, steps 200, f_mvm 2, dt 0.02,
+ * p 1.2, a 1.0, zeta 3.0, eps 0.5, sigma0 0.1, x_max 1000.  p/a/zeta/eps were
+ * chosen on the CPU oracle (the paper does not print them). */
+mmgap_status mmgap_default_params(mmgap_params* p);
+
+/* Create a context on CUDA device `device` owning `workspace_bytes` of device
+ * memory (0 = 256 MiB) for per-problem Ising coefficients.  Jobs larger than
+ * the workspace are processed in chunks.  *ctx = NULL on failure. */
+mmgap_status mmgap_create(mmgap_ctx** ctx, int device, size_t workspace_bytes);
+
+/* Destroy a context and free its workspace.  Synchronises the device first.
+ * NULL is accepted. */
+mmgap_status mmgap_destroy(mmgap_ctx* ctx);
+
+/* Message describing the last error on this context ("" if none).  Owned by
+ * the context; valid until the next call on it. */
+const char* mmgap_last_error(const mmgap_ctx* ctx);
+
+/* Uplink MIMO detection (Sec. 3.2): for each job, build the delta-Ising
+ * problem of every resource element around its MMSE guess, run
+ * params->runs anneals, keep the lowest-energy candidate (the guess if no
+ * anneal is better) and decode it to symbols. */
+mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job* jobs, int n_jobs,
+                          void* stream);
+
+/* Downlink vector-perturbation precoding (Sec. 3.3): the same solver on the
+ * detection form y~ = W u, H_p = -tau W / 2, guess 0. */
+mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_precode_job* jobs, int n_jobs,
+                           void* stream);
+
+/*
+ * Solver boundary (Sec. 2.3, Sec. 3.2): anneal n_problems quantised
+ * delta-Ising problems of half-size n (2n + 1 spins, n = 2 n_t,
+ * n in {2, 4, 6, 8, 16, 32}).
+ *   A_q: int16 [n_problems][n][n] symmetric Q14 half-size block A = -G
+ *        (Fig. 5(a): J = [[A~, A, b], [A, A~, b], [b^T, b^T, 0]])
+ *   h_q: int16 [n_problems][n] Q14 auxiliary block b
+ *   g:   int8 [n_problems][n] lattice guess, or NULL (then level_max must be 0)
+ *   level_max: offsets d_i with |g_i + 2 d_i| > level_max are set to 0
+ *              before scoring (0 = no clipping)
+ *   seed: Philox key; problem k draws from counter space (., run, k).
+ * Outputs: d_out int8 [n_problems][n] (required), E_out int32 [n_problems],
+ * run_out int32 [n_problems] (index of the winning anneal), ndiv_out int32
+ * [n_problems]; the last three may be NULL.
+ */
+mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n, int n_problems,
+                               const int16_t* A_q, const int16_t* h_q, const int8_t* g, int level_max, uint64_t seed,
+                               int8_t* d_out, int32_t* E_out, int32_t* run_out, int32_t* ndiv_out, void* stream);
+
+/*
+ * Builder boundary (Sec. 3.2 pre-processing, Eq. 3, Fig. 5): the delta-Ising
+ * coefficients of one detection job, without solving.
+ * Outputs (device): A_q int16 [P][n][n], h_q int16 [P][n], g int8 [P][n]
+ * (required); optional G_out float [P][n][n] and h_out float [P][n] (real-form
+ * Gram and field in lattice units before quantisation), sigma_exp_out int32
+ * [P] (normaliser 2^sigma_exp).  job->sym_out etc. are ignored.
+ */
+mmgap_status mmgap_build_detect(mmgap_ctx* ctx, const mmgap_detect_job* job, int16_t* A_q_out, int16_t* h_q_out,
+                                int8_t* g_out, float* G_out, float* h_out, int32_t* sigma_exp_out, void* stream);
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing of later detect /
+ * precode calls on this context. */
+mmgap_status mmgap_set_timing(mmgap_ctx* ctx, int enable);
+
+/* Device time in ms of each stage of the last timed detect / precode call,
+ * summed over its chunks: ms_out[0] build, [1] solve, [2] output
+ * (precode only; 0 for detect), [3] whole call.  Synchronises on the call's
+ * events.  *n_chunks_out (may be NULL) receives the number of chunks. */
+mmgap_status mmgap_stage_times(mmgap_ctx* ctx, float ms_out[4], int* n_chunks_out);
+
+/* Device-side error word of this context (bit 0: a channel index outside
+ * [0, n_chan) was met; the problem was computed as all-zero couplings).
+ * Synchronises the device; clears the word if `clear` is non-zero. */
+mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMGAP_H */

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of the MMGaP C ABI (include/mmgap.h).
+
+Argument marshalling only: torch CUDA tensors are checked (device, dtype,
+shape, contiguity) and passed as raw device pointers together with the
+current torch stream.  Every step of the detection / precoding path runs in
+the library's CUDA kernels; there is no CPU fallback.  If libmmgap.so is
+missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmmgap.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libmmgap.so not built at {LIB_PATH}; run __graft_entry__.build() "
+                      "or python -m paper_2510_01579_gb300.build")
+_lib = C.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EBUSY = range(7)
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED", 6: "EBUSY"}
+
+SUPPORTED_NT = (1, 2, 3, 4, 8, 16)
+
+
+class MMGaPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Params(C.Structure):
+    _fields_ = [("runs", C.c_int32), ("steps", C.c_int32), ("f_mvm", C.c_int32), ("dt", C.c_float),
+                ("p", C.c_float), ("a", C.c_float), ("zeta", C.c_float), ("eps", C.c_float),
+                ("sigma0", C.c_float), ("x_max", C.c_float)]
+
+
+class _DetectJob(C.Structure):
+    _fields_ = [("n_r", C.c_int32), ("n_t", C.c_int32), ("mod_bits", C.c_int32), ("n_problems", C.c_int32),
+                ("n_chan", C.c_int32), ("chan_index", C.c_void_p), ("H", C.c_void_p), ("y", C.c_void_p),
+                ("noise_var", C.c_void_p), ("seed", C.c_uint64), ("sym_out", C.c_void_p),
+                ("energy_out", C.c_void_p), ("guess_out", C.c_void_p), ("offset_out", C.c_void_p),
+                ("ndiv_out", C.c_void_p)]
+
+
+class _PrecodeJob(C.Structure):
+    _fields_ = [("n_u", C.c_int32), ("n_t", C.c_int32), ("mod_bits", C.c_int32), ("n_problems", C.c_int32),
+                ("n_chan", C.c_int32), ("chan_index", C.c_void_p), ("H", C.c_void_p), ("u_sym", C.c_void_p),
+                ("seed", C.c_uint64), ("v_out", C.c_void_p), ("x_out", C.c_void_p), ("power_out", C.c_void_p),
+                ("energy_out", C.c_void_p), ("ndiv_out", C.c_void_p)]
+
+
+_vp = C.c_void_p
+_lib.mmgap_default_params.argtypes = [C.POINTER(_Params)]
+_lib.mmgap_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_size_t]
+_lib.mmgap_destroy.argtypes = [_vp]
+_lib.mmgap_last_error.argtypes = [_vp]
+_lib.mmgap_last_error.restype = C.c_char_p
+_lib.mmgap_detect.argtypes = [_vp, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int, _vp]
+_lib.mmgap_precode.argtypes = [_vp, C.POINTER(_Params), C.POINTER(_PrecodeJob), C.c_int, _vp]
+_lib.mmgap_solve_ising.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, C.c_uint64,
+                                   _vp, _vp, _vp, _vp, _vp]
+_lib.mmgap_build_detect.argtypes = [_vp, C.POINTER(_DetectJob), _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.mmgap_set_timing.argtypes = [_vp, C.c_int]
+_lib.mmgap_stage_times.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)]
+_lib.mmgap_device_errors.argtypes = [_vp, C.POINTER(C.c_int), C.c_int]
+for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
+           "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
+           "mmgap_device_errors"):
+    getattr(_lib, _f).restype = C.c_int
+
+ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
+               "mmgap_precode", "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing",
+               "mmgap_stage_times", "mmgap_device_errors")
+
+
+@dataclasses.dataclass
+class Params:
+    """Solver parameters (mmgap_params); defaults from mmgap_default_params."""
+    runs: int
+    steps: int
+    f_mvm: int
+    dt: float
+    p: float
+    a: float
+    zeta: float
+    eps: float
+    sigma0: float
+    x_max: float
+
+    @classmethod
+    def default(cls, **overrides) -> "Params":
+        c = _Params()
+        _lib.mmgap_default_params(C.byref(c))
+        kw = {f: getattr(c, f) for f, _ in _Params._fields_}
+        kw.update(overrides)
+        return cls(**kw)
+
+    def _c(self) -> _Params:
+        return _Params(self.runs, self.steps, self.f_mvm, self.dt, self.p, self.a, self.zeta, self.eps,
+                       self.sigma0, self.x_max)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check(t, name, dtype, shape, device):
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Context:
+    """An mmgap_ctx on one CUDA device (owns the device workspace)."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        self.device = torch.device("cuda", device)
+        h = C.c_void_p()
+        st = _lib.mmgap_create(C.byref(h), device, workspace_bytes)
+        if st != OK:
+            raise MMGaPError(st, "mmgap_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mmgap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _stream(self):
+        return C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _raise(self, st):
+        if st != OK:
+            raise MMGaPError(st, _lib.mmgap_last_error(self._h).decode())
+
+    # ------------------------------------------------------------------ API
+    def detect(self, H, y, noise_var, mod_bits: int, params: Params, seed: int, chan_index=None,
+               want_energy=False, want_guess=False, want_offset=False, want_ndiv=False):
+        """Uplink detection of P problems.  H: complex64 (n_chan, n_r, n_t),
+        y: complex64 (P, n_r), noise_var: float32 (P,), chan_index: int32 (P,)
+        or None.  Returns a dict of CUDA tensors (sym uint8 (P, n_t), ...)."""
+        n_chan, n_r, n_t = H.shape
+        P = y.shape[0]
+        dev = self.device
+        _check(H, "H", torch.complex64, (n_chan, n_r, n_t), dev)
+        _check(y, "y", torch.complex64, (P, n_r), dev)
+        _check(noise_var, "noise_var", torch.float32, (P,), dev)
+        _check(chan_index, "chan_index", torch.int32, (P,), dev)
+        out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev)}
+        if want_energy:
+            out["energy"] = torch.empty(P, dtype=torch.int32, device=dev)
+        if want_guess:
+            out["guess"] = torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)
+        if want_offset:
+            out["offset"] = torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)
+        if want_ndiv:
+            out["ndiv"] = torch.empty(P, dtype=torch.int32, device=dev)
+        job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index)
+        self.detect_jobs([job], params)
+        return out
+
+    def detect_job(self, H, y, noise_var, mod_bits, seed, out, chan_index=None) -> _DetectJob:
+        n_chan, n_r, n_t = H.shape
+        return _DetectJob(n_r, n_t, mod_bits, y.shape[0], n_chan, _ptr(chan_index), _ptr(H), _ptr(y),
+                          _ptr(noise_var), seed, _ptr(out["sym"]), _ptr(out.get("energy")), _ptr(out.get("guess")),
+                          _ptr(out.get("offset")), _ptr(out.get("ndiv")))
+
+    def detect_jobs(self, jobs, params: Params, stream=None):
+        arr = (_DetectJob * len(jobs))(*jobs)
+        cp = params._c()
+        s = self._stream() if stream is None else C.c_void_p(stream.cuda_stream)
+        self._raise(_lib.mmgap_detect(self._h, C.byref(cp), arr, len(jobs), s))
+
+    def precode(self, H, u_sym, mod_bits: int, params: Params, seed: int, chan_index=None, want_x=True,
+                want_power=True, want_energy=False, want_ndiv=False):
+        """Downlink VPP of P problems.  H: complex64 (n_chan, n_u, n_t), u_sym: uint8 (P, n_u)."""
+        n_chan, n_u, n_t = H.shape
+        P = u_sym.shape[0]
+        dev = self.device
+        _check(H, "H", torch.complex64, (n_chan, n_u, n_t), dev)
+        _check(u_sym, "u_sym", torch.uint8, (P, n_u), dev)
+        _check(chan_index, "chan_index", torch.int32, (P,), dev)
+        out = {"v": torch.empty((P, n_u, 2), dtype=torch.int8, device=dev)}
+        if want_x:
+            out["x"] = torch.empty((P, n_t), dtype=torch.complex64, device=dev)
+        if want_power:
+            out["power"] = torch.empty(P, dtype=torch.float32, device=dev)
+        if want_energy:
+            out["energy"] = torch.empty(P, dtype=torch.int32, device=dev)
+        if want_ndiv:
+            out["ndiv"] = torch.empty(P, dtype=torch.int32, device=dev)
+        job = _PrecodeJob(n_u, n_t, mod_bits, P, n_chan, _ptr(chan_index), _ptr(H), _ptr(u_sym), seed,
+                          _ptr(out["v"]), _ptr(out.get("x")), _ptr(out.get("power")), _ptr(out.get("energy")),
+                          _ptr(out.get("ndiv")))
+        cp = params._c()
+        arr = (_PrecodeJob * 1)(job)
+        self._raise(_lib.mmgap_precode(self._h, C.byref(cp), arr, 1, self._stream()))
+        return out
+
+    def solve_ising(self, A_q, h_q, params: Params, seed: int, g=None, level_max: int = 0):
+        """Anneal P quantised delta-Ising problems: A_q int16 (P, n, n), h_q int16 (P, n),
+        g int8 (P, n) or None.  Returns d int8 (P, n), E, run, ndiv int32 (P,)."""
+        P, n, _ = A_q.shape
+        dev = self.device
+        _check(A_q, "A_q", torch.int16, (P, n, n), dev)
+        _check(h_q, "h_q", torch.int16, (P, n), dev)
+        _check(g, "g", torch.int8, (P, n), dev)
+        d = torch.empty((P, n), dtype=torch.int8, device=dev)
+        E = torch.empty(P, dtype=torch.int32, device=dev)
+        run = torch.empty(P, dtype=torch.int32, device=dev)
+        nd = torch.empty(P, dtype=torch.int32, device=dev)
+        cp = params._c()
+        self._raise(_lib.mmgap_solve_ising(self._h, C.byref(cp), n, P, _ptr(A_q), _ptr(h_q), _ptr(g), level_max,
+                                           seed, _ptr(d), _ptr(E), _ptr(run), _ptr(nd), self._stream()))
+        return dict(d=d, E=E, run=run, ndiv=nd)
+
+    def build_detect(self, H, y, noise_var, mod_bits: int, chan_index=None, want_float=True):
+        """Builder only: quantised delta-Ising coefficients of P detection problems."""
+        n_chan, n_r, n_t = H.shape
+        P = y.shape[0]
+        n = 2 * n_t
+        dev = self.device
+        _check(H, "H", torch.complex64, (n_chan, n_r, n_t), dev)
+        _check(y, "y", torch.complex64, (P, n_r), dev)
+        _check(noise_var, "noise_var", torch.float32, (P,), dev)
+        _check(chan_index, "chan_index", torch.int32, (P,), dev)
+        out = dict(A_q=torch.empty((P, n, n), dtype=torch.int16, device=dev),
+                   h_q=torch.empty((P, n), dtype=torch.int16, device=dev),
+                   g=torch.empty((P, n), dtype=torch.int8, device=dev))
+        if want_float:
+            out["G"] = torch.empty((P, n, n), dtype=torch.float32, device=dev)
+            out["h"] = torch.empty((P, n), dtype=torch.float32, device=dev)
+            out["sigma_exp"] = torch.empty(P, dtype=torch.int32, device=dev)
+        job = _DetectJob(n_r, n_t, mod_bits, P, n_chan, _ptr(chan_index), _ptr(H), _ptr(y), _ptr(noise_var), 0,
+                         None, None, None, None, None)
+        self._raise(_lib.mmgap_build_detect(self._h, C.byref(job), _ptr(out["A_q"]), _ptr(out["h_q"]),
+                                            _ptr(out["g"]), _ptr(out.get("G")), _ptr(out.get("h")),
+                                            _ptr(out.get("sigma_exp")), self._stream()))
+        return out
+
+    def set_timing(self, enable: bool):
+        self._raise(_lib.mmgap_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self):
+        """(build_ms, solve_ms, output_ms, total_ms, n_chunks) of the last timed call."""
+        ms = (C.c_float * 4)()
+        nc = C.c_int()
+        self._raise(_lib.mmgap_stage_times(self._h, ms, C.byref(nc)))
+        return (ms[0], ms[1], ms[2], ms[3], nc.value)
+
+    def device_errors(self, clear: bool = True) -> int:
+        f = C.c_int()
+        self._raise(_lib.mmgap_device_errors(self._h, C.byref(f), 1 if clear else 0))
+        return f.value

@@ -1,0 +1,507 @@
+// C-ABI front end of the MMGaP hot path: argument checking, workspace
+// chunking, size dispatch and per-stage timing.  All arithmetic of the path
+// runs in the kernels of kernels.cuh.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mmgap.h"
+#include "internal.h"
+
+using namespace mmgap;
+
+struct mmgap_ctx {
+    int device = 0;
+    char* ws = nullptr;         // device workspace
+    size_t ws_bytes = 0;
+    int* dev_err = nullptr;     // device error word
+    std::string err;
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // 4 per chunk: start, built, solved, output
+    int n_chunks = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+mmgap_status fail(mmgap_ctx* ctx, mmgap_status st, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+mmgap_status fail(mmgap_ctx* ctx, mmgap_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+mmgap_status cuda_fail(mmgap_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, MMGAP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool nt_supported(int nt) { return nt == 1 || nt == 2 || nt == 3 || nt == 4 || nt == 8 || nt == 16; }
+
+// Constants of the Euler discretisation of Eqs. 10-11, each computed in
+// double from the float parameters and rounded once to float.
+EulerConsts euler_consts(const mmgap_params& P) {
+    const double dt = P.dt, p = P.p, a = P.a, zeta = P.zeta, eps = P.eps;
+    EulerConsts k;
+    k.c1 = (float)(1.0 + dt * (p - 1.0));
+    k.cdt = (float)(-dt);
+    k.cz = (float)(-(dt * zeta));
+    k.c2 = (float)(1.0 + (dt * zeta) * a);
+    k.ce = (float)(eps * dt);
+    k.xs = (float)((double)P.sigma0 * 0x1p-23);
+    k.x_max = P.x_max;
+    return k;
+}
+
+mmgap_status check_params(mmgap_ctx* ctx, const mmgap_params* P) {
+    if (!P) return fail(ctx, MMGAP_EINVAL, "params is NULL");
+    if (!(P->runs == 32 || P->runs == 64 || P->runs == 96 || P->runs == 128))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "runs=%d: supported 32, 64, 96, 128", P->runs);
+    if (P->steps < 0 || P->steps > (1 << 20)) return fail(ctx, MMGAP_EINVAL, "steps=%d out of [0, 2^20]", P->steps);
+    if (P->f_mvm < 1 || P->f_mvm > 64) return fail(ctx, MMGAP_EINVAL, "f_mvm=%d out of [1, 64]", P->f_mvm);
+    if (!(P->dt > 0.0f) || !std::isfinite(P->dt)) return fail(ctx, MMGAP_EINVAL, "dt must be positive and finite");
+    if (!std::isfinite(P->p) || !std::isfinite(P->a) || !std::isfinite(P->zeta) || !std::isfinite(P->eps) ||
+        !std::isfinite(P->sigma0) || !(P->x_max > 0.0f))
+        return fail(ctx, MMGAP_EINVAL, "non-finite solver parameter or x_max <= 0");
+    return MMGAP_OK;
+}
+
+template <template <int> class Op, class... Args>
+cudaError_t dispatch_nt(int nt, Args&&... args) {
+    switch (nt) {
+    case 1: return Op<1>::run(args...);
+    case 2: return Op<2>::run(args...);
+    case 3: return Op<3>::run(args...);
+    case 4: return Op<4>::run(args...);
+    case 8: return Op<8>::run(args...);
+    case 16: return Op<16>::run(args...);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NT> struct OpBuild { static cudaError_t run(const BuildArgs& a, cudaStream_t s) { return launch_build_detect<NT>(a, s); } };
+template <int NT> struct OpSolve { static cudaError_t run(const SolveArgs& a, int r, cudaStream_t s) { return launch_solve<NT>(a, r, s); } };
+template <int NT> struct OpVppInv { static cudaError_t run(const VppInvArgs& a, cudaStream_t s) { return launch_vpp_inverse<NT>(a, s); } };
+template <int NT> struct OpVppBuild { static cudaError_t run(const VppBuildArgs& a, cudaStream_t s) { return launch_vpp_build<NT>(a, s); } };
+template <int NT> struct OpVppOut { static cudaError_t run(const VppOutArgs& a, cudaStream_t s) { return launch_vpp_output<NT>(a, s); } };
+
+// QAM normalisation kappa = 1/sqrt(2 (M-1)/3) and kappa^2, rounded once to float.
+void qam_kappa(int mod_bits, float* kappa, float* kappa2) {
+    const double M = (double)(1 << mod_bits);
+    *kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
+    *kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
+}
+
+struct CurrentDevice {
+    int prev = -1;
+    explicit CurrentDevice(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~CurrentDevice() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+mmgap_status timing_begin(mmgap_ctx* ctx) {
+    ctx->n_chunks = 0;
+    return MMGAP_OK;
+}
+
+// Record stage event `stage` (0..3) of the current chunk.
+mmgap_status timing_mark(mmgap_ctx* ctx, int stage, cudaStream_t s) {
+    if (!ctx->timing) return MMGAP_OK;
+    const size_t idx = (size_t)ctx->n_chunks * 4 + stage;
+    while (ctx->events.size() <= idx) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+        ctx->events.push_back(ev);
+    }
+    cudaError_t e = cudaEventRecord(ctx->events[idx], s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
+    if (stage == 3) ctx->n_chunks++;
+    return MMGAP_OK;
+}
+
+mmgap_status check_detect_job(mmgap_ctx* ctx, const mmgap_detect_job& j, bool need_sym) {
+    if (!nt_supported(j.n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d: supported 1, 2, 3, 4, 8, 16", j.n_t);
+    if (j.n_r < 1 || j.n_r > kMaxNr) return fail(ctx, MMGAP_EUNSUPPORTED, "n_r=%d out of [1, %d]", j.n_r, kMaxNr);
+    if (!(j.mod_bits == 2 || j.mod_bits == 4 || j.mod_bits == 6))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "mod_bits=%d: supported 2, 4, 6", j.mod_bits);
+    if (j.n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
+    if (j.n_problems == 0) return MMGAP_OK;
+    if (!j.H || !j.y || !j.noise_var || (need_sym && !j.sym_out))
+        return fail(ctx, MMGAP_EINVAL, "NULL H, y, noise_var or sym_out");
+    if (j.n_chan < 1) return fail(ctx, MMGAP_EINVAL, "n_chan < 1");
+    if (!j.chan_index && j.n_chan < j.n_problems)
+        return fail(ctx, MMGAP_EINVAL, "chan_index NULL needs n_chan >= n_problems");
+    return MMGAP_OK;
+}
+
+mmgap_status check_precode_job(mmgap_ctx* ctx, const mmgap_precode_job& j) {
+    if (!nt_supported(j.n_u)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_u=%d: supported 1, 2, 3, 4, 8, 16", j.n_u);
+    if (j.n_t < j.n_u || j.n_t > kMaxNr)
+        return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d out of [n_u, %d]", j.n_t, kMaxNr);
+    if (!(j.mod_bits == 2 || j.mod_bits == 4 || j.mod_bits == 6))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "mod_bits=%d: supported 2, 4, 6", j.mod_bits);
+    if (j.n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
+    if (j.n_problems == 0) return MMGAP_OK;
+    if (!j.H || !j.u_sym || !j.v_out) return fail(ctx, MMGAP_EINVAL, "NULL H, u_sym or v_out");
+    if (j.n_chan < 1) return fail(ctx, MMGAP_EINVAL, "n_chan < 1");
+    if (!j.chan_index && j.n_chan < j.n_problems)
+        return fail(ctx, MMGAP_EINVAL, "chan_index NULL needs n_chan >= n_problems");
+    return MMGAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mmgap_status mmgap_default_params(mmgap_params* p) {
+    if (!p) return MMGAP_EINVAL;
+    p->runs = 32;
+    p->steps = 200;
+    p->f_mvm = 2;
+    p->dt = 0.02f;
+    p->p = 1.2f;
+    p->a = 1.0f;
+    p->zeta = 3.0f;
+    p->eps = 0.5f;
+    p->sigma0 = 0.1f;
+    p->x_max = 1000.0f;
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_create(mmgap_ctx** out, int device, size_t workspace_bytes) {
+    if (!out) return MMGAP_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MMGAP_EINVAL;
+    auto* ctx = new (std::nothrow) mmgap_ctx();
+    if (!ctx) return MMGAP_ENOMEM;
+    ctx->device = device;
+    CurrentDevice cd(device);
+    ctx->ws_bytes = workspace_bytes ? workspace_bytes : ((size_t)256 << 20);
+    if (cudaMalloc(&ctx->ws, ctx->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return MMGAP_ENOMEM;
+    }
+    if (cudaMalloc(&ctx->dev_err, 256) != cudaSuccess || cudaMemset(ctx->dev_err, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->ws);
+        delete ctx;
+        return MMGAP_ENOMEM;
+    }
+    *out = ctx;
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_destroy(mmgap_ctx* ctx) {
+    if (!ctx) return MMGAP_OK;
+    CurrentDevice cd(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto ev : ctx->events) cudaEventDestroy(ev);
+    cudaFree(ctx->ws);
+    cudaFree(ctx->dev_err);
+    delete ctx;
+    return MMGAP_OK;
+}
+
+const char* mmgap_last_error(const mmgap_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+mmgap_status mmgap_set_timing(mmgap_ctx* ctx, int enable) {
+    if (!ctx) return MMGAP_EINVAL;
+    ctx->timing = enable != 0;
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_stage_times(mmgap_ctx* ctx, float ms_out[4], int* n_chunks_out) {
+    if (!ctx || !ms_out) return MMGAP_EINVAL;
+    for (int i = 0; i < 4; ++i) ms_out[i] = 0.0f;
+    if (n_chunks_out) *n_chunks_out = ctx->n_chunks;
+    if (ctx->n_chunks == 0) return MMGAP_OK;
+    CurrentDevice cd(ctx->device);
+    const int last = ctx->n_chunks * 4 - 1;
+    cudaError_t e = cudaEventSynchronize(ctx->events[last]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventSynchronize");
+    for (int c = 0; c < ctx->n_chunks; ++c) {
+        for (int s = 0; s < 3; ++s) {
+            float ms = 0.0f;
+            e = cudaEventElapsedTime(&ms, ctx->events[c * 4 + s], ctx->events[c * 4 + s + 1]);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventElapsedTime");
+            ms_out[s] += ms;
+        }
+    }
+    float all = 0.0f;
+    e = cudaEventElapsedTime(&all, ctx->events[0], ctx->events[last]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventElapsedTime");
+    ms_out[3] = all;
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear) {
+    if (!ctx || !flags_out) return MMGAP_EINVAL;
+    CurrentDevice cd(ctx->device);
+    cudaError_t e = cudaMemcpy(flags_out, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the device error word");
+    if (clear) {
+        e = cudaMemset(ctx->dev_err, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clearing the device error word");
+    }
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_build_detect(mmgap_ctx* ctx, const mmgap_detect_job* job, int16_t* A_q_out, int16_t* h_q_out,
+                                int8_t* g_out, float* G_out, float* h_out, int32_t* sigma_exp_out, void* stream) {
+    if (!ctx) return MMGAP_EINVAL;
+    if (!job) return fail(ctx, MMGAP_EINVAL, "job is NULL");
+    mmgap_status st = check_detect_job(ctx, *job, false);
+    if (st != MMGAP_OK) return st;
+    if (job->n_problems == 0) return MMGAP_OK;
+    if (!A_q_out || !h_q_out || !g_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q_out, h_q_out or g_out");
+    CurrentDevice cd(ctx->device);
+    BuildArgs a{};
+    a.H = job->H;
+    a.chan_index = job->chan_index;
+    a.y = job->y;
+    a.noise_var = job->noise_var;
+    a.n_r = job->n_r;
+    a.mod_bits = job->mod_bits;
+    a.n_problems = job->n_problems;
+    a.n_chan = job->n_chan;
+    qam_kappa(job->mod_bits, &a.kappa, &a.kappa2);
+    a.err = ctx->dev_err;
+    a.Aq = A_q_out;
+    a.hq = h_q_out;
+    a.g = g_out;
+    a.G32 = G_out;
+    a.h32 = h_out;
+    a.sigma_exp = sigma_exp_out;
+    cudaError_t e = dispatch_nt<OpBuild>(job->n_t, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build_detect launch");
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n, int n_problems, const int16_t* A_q,
+                               const int16_t* h_q, const int8_t* g, int level_max, uint64_t seed, int8_t* d_out,
+                               int32_t* E_out, int32_t* run_out, int32_t* ndiv_out, void* stream) {
+    if (!ctx) return MMGAP_EINVAL;
+    mmgap_status st = check_params(ctx, params);
+    if (st != MMGAP_OK) return st;
+    if (n < 2 || (n & 1) || !nt_supported(n / 2))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "n=%d: supported 2, 4, 6, 8, 16, 32", n);
+    if (n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
+    if (n_problems == 0) return MMGAP_OK;
+    if (!A_q || !h_q || !d_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q, h_q or d_out");
+    if (level_max < 0 || (level_max > 0 && !g)) return fail(ctx, MMGAP_EINVAL, "level_max needs g");
+    CurrentDevice cd(ctx->device);
+    SolveArgs a{};
+    a.Aq = A_q;
+    a.hq = h_q;
+    a.g = g;
+    a.level_max = level_max;
+    a.n_problems = n_problems;
+    a.steps = params->steps;
+    a.f_mvm = params->f_mvm;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.problem_offset = 0;
+    a.k = euler_consts(*params);
+    a.d_out = d_out;
+    a.E_out = E_out;
+    a.run_out = run_out;
+    a.ndiv_out = ndiv_out;
+    cudaError_t e = dispatch_nt<OpSolve>(n / 2, a, params->runs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job* jobs, int n_jobs,
+                          void* stream) {
+    if (!ctx) return MMGAP_EINVAL;
+    mmgap_status st = check_params(ctx, params);
+    if (st != MMGAP_OK) return st;
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, MMGAP_EINVAL, "bad jobs array");
+    for (int j = 0; j < n_jobs; ++j)
+        if ((st = check_detect_job(ctx, jobs[j], true)) != MMGAP_OK) return st;
+    CurrentDevice cd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const EulerConsts k = euler_consts(*params);
+    timing_begin(ctx);
+    for (int j = 0; j < n_jobs; ++j) {
+        const mmgap_detect_job& J = jobs[j];
+        if (J.n_problems == 0) continue;
+        const int n = 2 * J.n_t;
+        const size_t per = align_up((size_t)n * n * 2) + align_up((size_t)n * 2) + align_up((size_t)n);
+        // chunk so that three aligned regions of chunk size fit the workspace
+        long long chunk = (long long)(ctx->ws_bytes / (per + 3 * kAlign));
+        if (chunk < 1) return fail(ctx, MMGAP_ENOMEM, "workspace of %zu bytes holds no problem", ctx->ws_bytes);
+        if (chunk > J.n_problems) chunk = J.n_problems;
+        for (long long p0 = 0; p0 < J.n_problems; p0 += chunk) {
+            const int P = (int)std::min<long long>(chunk, J.n_problems - p0);
+            int16_t* Aq = (int16_t*)ctx->ws;
+            int16_t* hq = (int16_t*)(ctx->ws + align_up((size_t)P * n * n * 2));
+            int8_t* g = (int8_t*)((char*)hq + align_up((size_t)P * n * 2));
+            if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
+            BuildArgs b{};
+            b.H = J.chan_index ? J.H : J.H + (size_t)p0 * 2 * J.n_r * J.n_t;
+            b.chan_index = J.chan_index ? J.chan_index + p0 : nullptr;
+            b.y = J.y + (size_t)p0 * 2 * J.n_r;
+            b.noise_var = J.noise_var + p0;
+            b.n_r = J.n_r;
+            b.mod_bits = J.mod_bits;
+            b.n_problems = P;
+            b.n_chan = J.chan_index ? J.n_chan : P;
+            qam_kappa(J.mod_bits, &b.kappa, &b.kappa2);
+            b.err = ctx->dev_err;
+            b.Aq = Aq;
+            b.hq = hq;
+            b.g = g;
+            cudaError_t e = dispatch_nt<OpBuild>(J.n_t, b, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "build_detect launch");
+            if ((st = timing_mark(ctx, 1, s)) != MMGAP_OK) return st;
+            SolveArgs a{};
+            a.Aq = Aq;
+            a.hq = hq;
+            a.g = g;
+            a.level_max = (1 << (J.mod_bits >> 1)) - 1;
+            a.n_problems = P;
+            a.steps = params->steps;
+            a.f_mvm = params->f_mvm;
+            a.key0 = (uint32_t)J.seed;
+            a.key1 = (uint32_t)(J.seed >> 32);
+            a.problem_offset = (uint64_t)p0;
+            a.k = k;
+            a.d_out = J.offset_out ? J.offset_out + (size_t)p0 * n : nullptr;
+            a.E_out = J.energy_out ? J.energy_out + p0 : nullptr;
+            a.run_out = nullptr;
+            a.ndiv_out = J.ndiv_out ? J.ndiv_out + p0 : nullptr;
+            a.sym_out = J.sym_out + (size_t)p0 * J.n_t;
+            a.mod_bits = J.mod_bits;
+            e = dispatch_nt<OpSolve>(J.n_t, a, params->runs, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
+            if (J.guess_out) {
+                e = cudaMemcpyAsync(J.guess_out + (size_t)p0 * n, g, (size_t)P * n, cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "guess copy");
+            }
+            if ((st = timing_mark(ctx, 2, s)) != MMGAP_OK) return st;
+            if ((st = timing_mark(ctx, 3, s)) != MMGAP_OK) return st;
+        }
+    }
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_precode_job* jobs, int n_jobs,
+                           void* stream) {
+    if (!ctx) return MMGAP_EINVAL;
+    mmgap_status st = check_params(ctx, params);
+    if (st != MMGAP_OK) return st;
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, MMGAP_EINVAL, "bad jobs array");
+    for (int j = 0; j < n_jobs; ++j)
+        if ((st = check_precode_job(ctx, jobs[j])) != MMGAP_OK) return st;
+    CurrentDevice cd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const EulerConsts k = euler_consts(*params);
+    timing_begin(ctx);
+    for (int j = 0; j < n_jobs; ++j) {
+        const mmgap_precode_job& J = jobs[j];
+        if (J.n_problems == 0) continue;
+        const int n = 2 * J.n_u;
+        // channels whose inverse this job needs
+        const int n_chan = J.chan_index ? J.n_chan : J.n_problems;
+        const size_t qbytes = align_up((size_t)n_chan * J.n_u * J.n_u * 16) + align_up((size_t)n_chan * 4);
+        const size_t per = align_up((size_t)n * n * 2) + align_up((size_t)n * 2) + align_up((size_t)n);
+        if (qbytes + per + 3 * kAlign > ctx->ws_bytes)
+            return fail(ctx, MMGAP_ENOMEM, "workspace of %zu bytes too small for %d channel inverses", ctx->ws_bytes,
+                        n_chan);
+        long long chunk = (long long)((ctx->ws_bytes - qbytes) / (per + 3 * kAlign));
+        if (chunk > J.n_problems) chunk = J.n_problems;
+        double* Q = (double*)ctx->ws;
+        int32_t* qstat = (int32_t*)(ctx->ws + align_up((size_t)n_chan * J.n_u * J.n_u * 16));
+        char* base = ctx->ws + qbytes;
+        VppInvArgs vi{};
+        vi.H = J.H;
+        vi.n_t = J.n_t;
+        vi.n_chan = n_chan;
+        vi.Q = Q;
+        vi.status = qstat;
+        if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
+        cudaError_t e = dispatch_nt<OpVppInv>(J.n_u, vi, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_inverse launch");
+        for (long long p0 = 0; p0 < J.n_problems; p0 += chunk) {
+            const int P = (int)std::min<long long>(chunk, J.n_problems - p0);
+            int16_t* Aq = (int16_t*)base;
+            int16_t* hq = (int16_t*)(base + align_up((size_t)P * n * n * 2));
+            int8_t* d = (int8_t*)((char*)hq + align_up((size_t)P * n * 2));
+            if (p0 > 0 && (st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
+            VppBuildArgs b{};
+            b.Q = J.chan_index ? Q : Q + (size_t)p0 * 2 * J.n_u * J.n_u;
+            b.chan_index = J.chan_index ? J.chan_index + p0 : nullptr;
+            b.u_sym = J.u_sym + (size_t)p0 * J.n_u;
+            b.mod_bits = J.mod_bits;
+            b.n_problems = P;
+            b.n_chan = J.chan_index ? n_chan : P;
+            b.err = ctx->dev_err;
+            b.Aq = Aq;
+            b.hq = hq;
+            e = dispatch_nt<OpVppBuild>(J.n_u, b, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_build launch");
+            if ((st = timing_mark(ctx, 1, s)) != MMGAP_OK) return st;
+            SolveArgs a{};
+            a.Aq = Aq;
+            a.hq = hq;
+            a.g = nullptr;
+            a.level_max = 0;
+            a.n_problems = P;
+            a.steps = params->steps;
+            a.f_mvm = params->f_mvm;
+            a.key0 = (uint32_t)J.seed;
+            a.key1 = (uint32_t)(J.seed >> 32);
+            a.problem_offset = (uint64_t)p0;
+            a.k = k;
+            a.d_out = d;
+            a.E_out = J.energy_out ? J.energy_out + p0 : nullptr;
+            a.ndiv_out = J.ndiv_out ? J.ndiv_out + p0 : nullptr;
+            e = dispatch_nt<OpSolve>(J.n_u, a, params->runs, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
+            if ((st = timing_mark(ctx, 2, s)) != MMGAP_OK) return st;
+            VppOutArgs o{};
+            o.H = J.chan_index ? J.H : J.H + (size_t)p0 * 2 * J.n_u * J.n_t;
+            o.Q = b.Q;
+            o.chan_index = b.chan_index;
+            o.u_sym = b.u_sym;
+            o.d = d;
+            o.n_t = J.n_t;
+            o.mod_bits = J.mod_bits;
+            o.n_problems = P;
+            o.n_chan = b.n_chan;
+            o.err = ctx->dev_err;
+            o.v_out = J.v_out + (size_t)p0 * n;
+            o.x_out = J.x_out ? J.x_out + (size_t)p0 * 2 * J.n_t : nullptr;
+            o.power_out = J.power_out ? J.power_out + p0 : nullptr;
+            e = dispatch_nt<OpVppOut>(J.n_u, o, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_output launch");
+            if ((st = timing_mark(ctx, 3, s)) != MMGAP_OK) return st;
+        }
+    }
+    return MMGAP_OK;
+}
+
+}  // extern "C"

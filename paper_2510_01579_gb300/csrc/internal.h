@@ -1,0 +1,113 @@
+// Internal (C++) interface between the C-ABI front end (api.cu) and the
+// per-size kernel translation units (inst_nt*.cu).  Not part of the ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace mmgap {
+
+// Derived constants of the Euler discretisation of Eqs. 10-11, each rounded
+// once to FP32 from a double expression of the float parameters.
+struct EulerConsts {
+    float c1;   // 1 + dt (p - 1)
+    float cdt;  // -dt
+    float cz;   // -dt zeta
+    float c2;   // 1 + dt zeta a
+    float ce;   // eps dt, folded into the couplings
+    float xs;   // sigma0 2^-23 (initial-amplitude scale)
+    float x_max;
+};
+
+struct SolveArgs {
+    const int16_t* Aq;   // [P][n][n]
+    const int16_t* hq;   // [P][n]
+    const int8_t* g;     // [P][n] or nullptr
+    int level_max;
+    int n_problems;
+    int steps;
+    int f_mvm;
+    uint32_t key0, key1;       // Philox key (seed)
+    uint64_t problem_offset;   // job-local index of problem 0 of this launch
+    EulerConsts k;
+    // outputs (solver boundary)
+    int8_t* d_out;             // [P][n] or nullptr
+    int32_t* E_out;
+    int32_t* run_out;
+    int32_t* ndiv_out;
+    // fused uplink decode (detect): symbols of g + 2 d
+    uint8_t* sym_out;          // [P][n_t] or nullptr
+    int mod_bits;
+};
+
+struct BuildArgs {
+    const float* H;            // complex [n_chan][n_r][n_t]
+    const int32_t* chan_index; // [P] or nullptr (identity)
+    const float* y;            // complex [P][n_r]
+    const float* noise_var;    // [P]
+    int n_r;
+    int mod_bits;
+    int n_problems;
+    int n_chan;                // channels addressable through chan_index
+    float kappa, kappa2;
+    int* err;                  // device error word (bit 0: channel index out of range)
+    // outputs
+    int16_t* Aq;               // [P][n][n]
+    int16_t* hq;               // [P][n]
+    int8_t* g;                 // [P][n]
+    float* G32;                // [P][n][n] or nullptr
+    float* h32;                // [P][n] or nullptr
+    int32_t* sigma_exp;        // [P] or nullptr
+};
+
+struct VppInvArgs {
+    const float* H;   // complex [n_chan][n_u][n_t]
+    int n_t;
+    int n_chan;
+    double* Q;        // complex [n_chan][n_u][n_u]
+    int32_t* status;  // [n_chan] 0 ok, 1 not positive definite
+};
+
+struct VppBuildArgs {
+    const double* Q;           // complex [n_chan][n_u][n_u]
+    const int32_t* chan_index; // [P] or nullptr
+    const uint8_t* u_sym;      // [P][n_u]
+    int mod_bits;
+    int n_problems;
+    int n_chan;
+    int* err;
+    int16_t* Aq;
+    int16_t* hq;
+};
+
+struct VppOutArgs {
+    const float* H;            // complex [n_chan][n_u][n_t]
+    const double* Q;
+    const int32_t* chan_index;
+    const uint8_t* u_sym;
+    const int8_t* d;           // [P][n]
+    int n_t;
+    int mod_bits;
+    int n_problems;
+    int n_chan;
+    int* err;
+    int8_t* v_out;
+    float* x_out;
+    float* power_out;
+};
+
+// Launchers, one set per n_t (defined in inst_nt<N>.cu).  Return the launch
+// error (cudaSuccess on success).
+template <int NT> cudaError_t launch_build_detect(const BuildArgs& a, cudaStream_t s);
+template <int NT> cudaError_t launch_solve(const SolveArgs& a, int runs, cudaStream_t s);
+template <int NT> cudaError_t launch_vpp_inverse(const VppInvArgs& a, cudaStream_t s);
+template <int NT> cudaError_t launch_vpp_build(const VppBuildArgs& a, cudaStream_t s);
+template <int NT> cudaError_t launch_vpp_output(const VppOutArgs& a, cudaStream_t s);
+
+constexpr int kMaxNr = 64;
+
+// Bits of the device error word.
+constexpr int kErrChanIndex = 1;
+
+}  // namespace mmgap

@@ -1,0 +1,907 @@
+// MMGaP hot-path kernels for sm_103a.
+//
+// Three stages (Sec. 3.2, Fig. 4: pre-processing, solver, post-processing):
+//   build_detect_kernel  -- Gram + matched filter + MMSE guess + field +
+//                           Q14 quantisation, one warp per resource element
+//   cac_solve_kernel     -- CIM-CAC anneals (Eqs. 10-11) with the half-size
+//                           coupling field of Fig. 5, one thread per anneal,
+//                           warp shuffles for the arg-min, fused decode
+//   vpp_* kernels        -- downlink VPP (Sec. 3.3) in FP64
+//
+// Every floating-point operation that decides an integer result is written
+// with an explicit IEEE round-to-nearest intrinsic (__fmaf_rn, __fmul_rn,
+// __fadd_rn, __fdiv_rn, __fsqrt_rn and their double forms) in a fixed order,
+// so that guesses, quantised couplings, spins and symbols are reproducible
+// bit for bit by a sequential CPU implementation of the same order.  The
+// translation units are compiled with -fmad=false as a second guard.
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace mmgap {
+
+constexpr int kQBits = 14;
+
+// ----------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+// multiplies with the Weyl key schedule between rounds.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+        const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += W0;
+        k1 += W1;
+    }
+    return c;
+}
+
+// ------------------------------------------------------------ FP helpers
+__device__ __forceinline__ float fmarn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float mulrn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float addrn(float a, float b) { return __fadd_rn(a, b); }
+
+// exponent e of the smallest power of two 2^e >= mx (mx > 0 finite), else 0
+__device__ __forceinline__ int sigma_exp_f(float mx) {
+    if (!(mx > 0.0f) || isinf(mx)) return 0;
+    int E;
+    const float f = frexpf(mx, &E);
+    return (f == 0.5f) ? E - 1 : E;
+}
+__device__ __forceinline__ int sigma_exp_d(double mx) {
+    if (!(mx > 0.0) || isinf(mx)) return 0;
+    int E;
+    const double f = frexp(mx, &E);
+    return (f == 0.5) ? E - 1 : E;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// =========================================================================
+// Builder: one warp per problem (resource element).
+// =========================================================================
+constexpr int kBuildWarps = 4;
+
+template <int NT>
+__host__ __device__ constexpr int build_smem_floats(int n_r) {
+    // Hs [n_r][NT] c, Gc [NT][NT] c, L [NT][NT] c, y [n_r] c, z [n_r] c, m [NT] c, g [2NT], flag
+    return 2 * n_r * NT + 4 * NT * NT + 4 * n_r + 4 * NT + 4;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kBuildWarps * 32) build_detect_kernel(BuildArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    constexpr int n = 2 * NT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * kBuildWarps + warp;
+    if (p >= a.n_problems) return;  // warp-uniform; no block-wide barrier below
+    const int n_r = a.n_r;
+    float* Hs = smem + warp * build_smem_floats<NT>(n_r);
+    float* Gc = Hs + 2 * n_r * NT;
+    float* Lc = Gc + 2 * NT * NT;
+    float* yv = Lc + 2 * NT * NT;
+    float* zv = yv + 2 * n_r;
+    float* mv = zv + 2 * n_r;  // matched filter [NT] c
+    float* gv = mv + 2 * NT;   // g as floats [2NT]
+    int* flag = reinterpret_cast<int*>(gv + 2 * NT);
+
+    const int c = a.chan_index ? a.chan_index[p] : p;
+    if (c < 0 || c >= a.n_chan) {  // bad channel index: flag it, emit an all-zero problem
+        if (lane == 0) atomicOr(a.err, kErrChanIndex);
+        for (int e = lane; e < n * n; e += 32) a.Aq[(size_t)p * n * n + e] = 0;
+        for (int e = lane; e < n; e += 32) {
+            a.hq[(size_t)p * n + e] = 0;
+            a.g[(size_t)p * n + e] = 0;
+        }
+        return;
+    }
+    const float* Hg = a.H + (size_t)c * 2 * n_r * NT;
+    const float* yg = a.y + (size_t)p * 2 * n_r;
+    for (int e = lane; e < 2 * n_r * NT; e += 32) Hs[e] = mulrn(a.kappa, Hg[e]);
+    for (int e = lane; e < 2 * n_r; e += 32) yv[e] = yg[e];
+    if (lane == 0) flag[0] = 0;
+    __syncwarp();
+
+    // Gram G_c = Hs^H Hs (upper triangle + Hermitian mirror) and m = Hs^H y.
+    for (int t = lane; t < NT * NT + NT; t += 32) {
+        if (t < NT * NT) {
+            const int i = t / NT, j = t % NT;
+            if (i > j) continue;
+            if (i == j) {
+                float acc = 0.0f;
+                for (int k = 0; k < n_r; ++k) {
+                    const float ar = Hs[2 * (k * NT + i)], ai = Hs[2 * (k * NT + i) + 1];
+                    acc = fmarn(ar, ar, acc);
+                    acc = fmarn(ai, ai, acc);
+                }
+                Gc[2 * (i * NT + i)] = acc;
+                Gc[2 * (i * NT + i) + 1] = 0.0f;
+            } else {
+                float re = 0.0f, im = 0.0f;
+                for (int k = 0; k < n_r; ++k) {
+                    const float ar = Hs[2 * (k * NT + i)], ai = Hs[2 * (k * NT + i) + 1];
+                    const float br = Hs[2 * (k * NT + j)], bi = Hs[2 * (k * NT + j) + 1];
+                    re = fmarn(ar, br, re);
+                    re = fmarn(ai, bi, re);
+                    im = fmarn(ar, bi, im);
+                    im = fmarn(-ai, br, im);
+                }
+                Gc[2 * (i * NT + j)] = re;
+                Gc[2 * (i * NT + j) + 1] = im;
+                Gc[2 * (j * NT + i)] = re;
+                Gc[2 * (j * NT + i) + 1] = -im;
+            }
+        } else {
+            const int i = t - NT * NT;
+            float re = 0.0f, im = 0.0f;
+            for (int k = 0; k < n_r; ++k) {
+                const float ar = Hs[2 * (k * NT + i)], ai = Hs[2 * (k * NT + i) + 1];
+                const float br = yv[2 * k], bi = yv[2 * k + 1];
+                re = fmarn(ar, br, re);
+                re = fmarn(ai, bi, re);
+                im = fmarn(ar, bi, im);
+                im = fmarn(-ai, br, im);
+            }
+            mv[2 * i] = re;
+            mv[2 * i + 1] = im;
+        }
+    }
+    __syncwarp();
+
+    // MMSE (Eq. 3): Cholesky of G_c + rho I (rho = noise_var kappa^2),
+    // left-looking, one column per step; lane j the pivot, lanes i > j the rest.
+    const float rho = mulrn(a.noise_var[p], a.kappa2);
+    for (int j = 0; j < NT; ++j) {
+        if (lane == j) {
+            float d = addrn(Gc[2 * (j * NT + j)], rho);
+            for (int k = 0; k < j; ++k) {
+                const float lr = Lc[2 * (j * NT + k)], li = Lc[2 * (j * NT + k) + 1];
+                d = fmarn(-lr, lr, d);
+                d = fmarn(-li, li, d);
+            }
+            const bool ok = (d > 0.0f) && !isinf(d);
+            if (!ok) flag[0] = 1;
+            Lc[2 * (j * NT + j)] = ok ? __fsqrt_rn(d) : 1.0f;
+            Lc[2 * (j * NT + j) + 1] = 0.0f;
+        }
+        __syncwarp();
+        const float ljj = Lc[2 * (j * NT + j)];
+        if (lane > j && lane < NT) {
+            const int i = lane;
+            float re = Gc[2 * (i * NT + j)], im = Gc[2 * (i * NT + j) + 1];
+            for (int k = 0; k < j; ++k) {
+                const float ar = Lc[2 * (i * NT + k)], ai = Lc[2 * (i * NT + k) + 1];
+                const float br = Lc[2 * (j * NT + k)], bi = Lc[2 * (j * NT + k) + 1];
+                re = fmarn(-ar, br, re);
+                re = fmarn(-ai, bi, re);
+                im = fmarn(-ai, br, im);
+                im = fmarn(ar, bi, im);
+            }
+            Lc[2 * (i * NT + j)] = __fdiv_rn(re, ljj);
+            Lc[2 * (i * NT + j) + 1] = __fdiv_rn(im, ljj);
+        }
+        __syncwarp();
+    }
+    const bool chol_failed = flag[0] != 0;
+
+    // forward solve L w = m (right-looking; per row the updates arrive in
+    // ascending k, the same sequence as the left-looking sum)
+    float accr = 0.0f, acci = 0.0f;
+    if (lane < NT) { accr = mv[2 * lane]; acci = mv[2 * lane + 1]; }
+    float wr = 0.0f, wi = 0.0f;
+    for (int k = 0; k < NT; ++k) {
+        if (lane == k) {
+            const float lkk = Lc[2 * (k * NT + k)];
+            wr = __fdiv_rn(accr, lkk);
+            wi = __fdiv_rn(acci, lkk);
+        }
+        const float br = __shfl_sync(0xffffffffu, wr, k), bi = __shfl_sync(0xffffffffu, wi, k);
+        if (lane > k && lane < NT) {
+            const float ar = Lc[2 * (lane * NT + k)], ai = Lc[2 * (lane * NT + k) + 1];
+            accr = fmarn(-ar, br, accr);
+            accr = fmarn(ai, bi, accr);
+            acci = fmarn(-ar, bi, acci);
+            acci = fmarn(-ai, br, acci);
+        }
+    }
+    // backward solve L^H x = w, k descending
+    accr = wr;
+    acci = wi;
+    float xr = 0.0f, xi = 0.0f;
+    for (int k = NT - 1; k >= 0; --k) {
+        if (lane == k) {
+            const float lkk = Lc[2 * (k * NT + k)];
+            xr = __fdiv_rn(accr, lkk);
+            xi = __fdiv_rn(acci, lkk);
+        }
+        const float br = __shfl_sync(0xffffffffu, xr, k), bi = __shfl_sync(0xffffffffu, xi, k);
+        if (lane < k) {
+            const float ar = Lc[2 * (k * NT + lane)], ai = Lc[2 * (k * NT + lane) + 1];
+            accr = fmarn(-ar, br, accr);
+            accr = fmarn(-ai, bi, accr);
+            acci = fmarn(-ar, bi, acci);
+            acci = fmarn(ai, br, acci);
+        }
+    }
+    // hard decision to the nearest alphabet point (ties upward)
+    const int side = 1 << (a.mod_bits >> 1);
+    const float Lm = (float)(side - 1);
+    if (lane < NT) {
+        float v[2] = {chol_failed ? 0.0f : xr, chol_failed ? 0.0f : xi};
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            float xc = fmaxf(v[cc], -Lm);
+            xc = fminf(xc, Lm);
+            const int gi = 2 * (int)floorf(mulrn(xc, 0.5f)) + 1;
+            gv[cc * NT + lane] = (float)gi;
+        }
+    }
+    __syncwarp();
+
+    // residual z = y - Hs g, field h_c = Hs^H z
+    for (int k = lane; k < n_r; k += 32) {
+        float re = yv[2 * k], im = yv[2 * k + 1];
+        for (int j = 0; j < NT; ++j) {
+            const float ar = Hs[2 * (k * NT + j)], ai = Hs[2 * (k * NT + j) + 1];
+            const float br = gv[j], bi = gv[NT + j];
+            re = fmarn(-ar, br, re);
+            re = fmarn(ai, bi, re);
+            im = fmarn(-ar, bi, im);
+            im = fmarn(-ai, br, im);
+        }
+        zv[2 * k] = re;
+        zv[2 * k + 1] = im;
+    }
+    __syncwarp();
+    float hre = 0.0f, him = 0.0f;
+    if (lane < NT) {
+        for (int k = 0; k < n_r; ++k) {
+            const float ar = Hs[2 * (k * NT + lane)], ai = Hs[2 * (k * NT + lane) + 1];
+            const float br = zv[2 * k], bi = zv[2 * k + 1];
+            hre = fmarn(ar, br, hre);
+            hre = fmarn(ai, bi, hre);
+            him = fmarn(ar, bi, him);
+            him = fmarn(-ai, br, him);
+        }
+    }
+
+    // power-of-two normaliser over the real-form couplings and field
+    float mx = 0.0f;
+    for (int e = lane; e < NT * NT; e += 32) mx = fmaxf(mx, fmaxf(fabsf(Gc[2 * e]), fabsf(Gc[2 * e + 1])));
+    if (lane < NT) mx = fmaxf(mx, fmaxf(fabsf(hre), fabsf(him)));
+    mx = warp_max(mx);
+    const int se = sigma_exp_f(mx);
+    const bool finite = isfinite(mx);
+    const float s = ldexpf(1.0f, kQBits - se);
+
+    int16_t* Aq = a.Aq + (size_t)p * n * n;
+    float* G32 = a.G32 ? a.G32 + (size_t)p * n * n : nullptr;
+    for (int e = lane; e < n * n; e += 32) {
+        const int i = e / n, j = e % n;
+        const int ib = i % NT, jb = j % NT;
+        const float re = Gc[2 * (ib * NT + jb)], im = Gc[2 * (ib * NT + jb) + 1];
+        // G = [[Re G_c, -Im G_c], [Im G_c, Re G_c]]
+        const float G = (i < NT) == (j < NT) ? re : (i < NT ? -im : im);
+        Aq[e] = finite ? (int16_t)(int)rintf(mulrn(-G, s)) : (int16_t)0;
+        if (G32) G32[e] = G;
+    }
+    if (lane < NT) {
+        int16_t* hq = a.hq + (size_t)p * n;
+        hq[lane] = finite ? (int16_t)(int)rintf(mulrn(hre, s)) : (int16_t)0;
+        hq[NT + lane] = finite ? (int16_t)(int)rintf(mulrn(him, s)) : (int16_t)0;
+        int8_t* g = a.g + (size_t)p * n;
+        g[lane] = (int8_t)(int)gv[lane];
+        g[NT + lane] = (int8_t)(int)gv[NT + lane];
+        if (a.h32) {
+            a.h32[(size_t)p * n + lane] = hre;
+            a.h32[(size_t)p * n + NT + lane] = him;
+        }
+    }
+    if (lane == 0 && a.sigma_exp) a.sigma_exp[p] = se;
+}
+
+// =========================================================================
+// CIM-CAC solver: one CTA per problem, one thread per anneal (runs = CTA
+// size, a multiple of 32).  Each thread keeps its 2n+1 amplitudes x and
+// error variables e in registers; the couplings sit in shared memory and
+// are read as warp-uniform broadcasts.
+// =========================================================================
+
+// One forward-Euler step of Eqs. 10-11 for one spin with frozen field mu
+// (mu already carries the factor eps dt):
+//   x' = x (1 + dt (p-1) - dt x^2) + e mu,   e' = e (1 + dt zeta a - dt zeta x^2)
+__device__ __forceinline__ void euler_spin(float& x, float& e, float mu, const EulerConsts& k) {
+    const float q = mulrn(x, x);
+    const float t = fmarn(k.cdt, q, k.c1);
+    const float em = mulrn(e, mu);
+    const float xn = fmarn(x, t, em);
+    const float r = fmarn(k.cz, q, k.c2);
+    e = mulrn(e, r);
+    x = xn;
+}
+
+template <int NT>
+struct SolveSmem {
+    static constexpr int n = 2 * NT;
+    float A[n * n];       // eps dt * A_q 2^-14
+    float h[n];           // eps dt * h_q 2^-14
+    float nd[n];          // -diag(A)
+    int16_t Aq[n * n];    // integer copy for the exact energy
+    int16_t hq[n];
+    int8_t g[n];
+    long long key[4];
+    int ndiv[4];
+};
+
+// Coupling field refresh (Fig. 5): u = x1 + x2, m = A u, mu_a = b^T u.
+template <int n>
+__device__ __forceinline__ void coupling_mvm(const float* sA, const float* sh,
+                                             const float (&x)[2 * n + 1], float (&m)[n], float& mua) {
+    // The couplings are loop invariant; without this barrier (and without
+    // __restrict__ on the shared-memory pointers, which would let the compiler
+    // look through it) all n^2 loads are hoisted out of the time loop into
+    // registers and spill.  Re-reading them as warp-uniform broadcasts costs
+    // one LDS.128 per four FMAs.
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < n; ++i) m[i] = 0.0f;
+    mua = 0.0f;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+        const float u = addrn(x[j], x[n + j]);
+        mua = fmarn(sh[j], u, mua);
+        if constexpr (n % 4 == 0) {
+            const float4* row = reinterpret_cast<const float4*>(sA + j * n);
+#pragma unroll
+            for (int i4 = 0; i4 < n / 4; ++i4) {
+                const float4 a4 = row[i4];
+                m[4 * i4 + 0] = fmarn(a4.x, u, m[4 * i4 + 0]);
+                m[4 * i4 + 1] = fmarn(a4.y, u, m[4 * i4 + 1]);
+                m[4 * i4 + 2] = fmarn(a4.z, u, m[4 * i4 + 2]);
+                m[4 * i4 + 3] = fmarn(a4.w, u, m[4 * i4 + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < n; ++i) m[i] = fmarn(sA[j * n + i], u, m[i]);
+        }
+    }
+}
+
+// L Euler steps of every spin with the field frozen at the refresh:
+// c = m + b x_a, mu1 = c - diag(A) o x1, mu2 = c - diag(A) o x2.
+// Spins are independent while the field is frozen, so each spin's L steps
+// run back to back.
+template <int n, int L>
+__device__ __forceinline__ void frozen_steps(const float* sh, const float* snd,
+                                             float (&x)[2 * n + 1], float (&e)[2 * n + 1], const float (&m)[n],
+                                             float mua, const EulerConsts& k) {
+    const float xa = x[2 * n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const float c = fmarn(sh[i], xa, m[i]);
+        const float mu1 = fmarn(snd[i], x[i], c);
+        const float mu2 = fmarn(snd[i], x[n + i], c);
+#pragma unroll
+        for (int s = 0; s < L; ++s) {
+            euler_spin(x[i], e[i], mu1, k);
+            euler_spin(x[n + i], e[n + i], mu2, k);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < L; ++s) euler_spin(x[2 * n], e[2 * n], mua, k);
+}
+
+template <int n>
+__device__ __forceinline__ void frozen_steps_rt(const float* sh, const float* snd,
+                                                float (&x)[2 * n + 1], float (&e)[2 * n + 1], const float (&m)[n],
+                                                float mua, int L, const EulerConsts& k) {
+    const float xa = x[2 * n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const float c = fmarn(sh[i], xa, m[i]);
+        const float mu1 = fmarn(snd[i], x[i], c);
+        const float mu2 = fmarn(snd[i], x[n + i], c);
+#pragma unroll 1
+        for (int s = 0; s < L; ++s) {
+            euler_spin(x[i], e[i], mu1, k);
+            euler_spin(x[n + i], e[n + i], mu2, k);
+        }
+    }
+#pragma unroll 1
+    for (int s = 0; s < L; ++s) euler_spin(x[2 * n], e[2 * n], mua, k);
+}
+
+// F > 0: compile-time refresh period; F == 0: runtime period a.f_mvm.
+template <int NT, int F>
+__global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
+    constexpr int n = 2 * NT;
+    constexpr int N = 2 * n + 1;
+    __shared__ __align__(16) SolveSmem<NT> sm;
+    const int p = blockIdx.x;
+    const int run = threadIdx.x;
+    const int R = blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const EulerConsts k = a.k;
+
+    // stage the problem: Q14 codes -> exact floats -> one rounding by eps dt
+    {
+        const int16_t* Aq = a.Aq + (size_t)p * n * n;
+        for (int e = run; e < n * n; e += R) {
+            const int16_t v = Aq[e];
+            sm.Aq[e] = v;
+            sm.A[e] = mulrn(mulrn((float)v, 0x1p-14f), k.ce);
+        }
+        const int16_t* hq = a.hq + (size_t)p * n;
+        for (int i = run; i < n; i += R) {
+            const int16_t v = hq[i];
+            sm.hq[i] = v;
+            sm.h[i] = mulrn(mulrn((float)v, 0x1p-14f), k.ce);
+            sm.g[i] = a.g ? a.g[(size_t)p * n + i] : (int8_t)0;
+        }
+    }
+    __syncthreads();
+    for (int i = run; i < n; i += R) sm.nd[i] = -sm.A[i * n + i];
+    __syncthreads();
+
+    // initial amplitudes from Philox: spin k uses word k%4 of counter
+    // (k/4, run, problem_lo, problem_hi)
+    float x[N], e[N];
+    {
+        const uint64_t pg = a.problem_offset + (uint64_t)p;
+#pragma unroll
+        for (int q4 = 0; q4 < (N + 3) / 4; ++q4) {
+            const U4 w = philox4x32_10(U4{(uint32_t)q4, (uint32_t)run, (uint32_t)pg, (uint32_t)(pg >> 32)}, a.key0,
+                                       a.key1);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (4 * q4 + t < N) {
+                    const int v = (int)(ws[t] >> 8) - 8388608;
+                    x[4 * q4 + t] = mulrn((float)v, k.xs);
+                    e[4 * q4 + t] = 1.0f;
+                }
+            }
+        }
+    }
+
+    // anneal
+    float m[n];
+    float mua;
+    const int S = a.steps;
+    int t = 0;
+    if constexpr (F > 0) {
+#pragma unroll 1
+        for (; t + F <= S; t += F) {
+            coupling_mvm<n>(sm.A, sm.h, x, m, mua);
+            frozen_steps<n, F>(sm.h, sm.nd, x, e, m, mua, k);
+        }
+    } else {
+        const int f = a.f_mvm;
+#pragma unroll 1
+        for (; t + f <= S; t += f) {
+            coupling_mvm<n>(sm.A, sm.h, x, m, mua);
+            frozen_steps_rt<n>(sm.h, sm.nd, x, e, m, mua, f, k);
+        }
+    }
+    if (t < S) {
+        coupling_mvm<n>(sm.A, sm.h, x, m, mua);
+        frozen_steps_rt<n>(sm.h, sm.nd, x, e, m, mua, S - t, k);
+    }
+
+    // spins -> offset d = s_a (s1 + s2) / 2, clipped to the alphabet
+    bool valid = true;
+#pragma unroll
+    for (int q = 0; q < N; ++q) valid = valid && (fabsf(x[q]) <= k.x_max) && (e[q] > 0.0f);
+    const int sa = x[2 * n] >= 0.0f ? 1 : -1;
+    int d[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int s1 = x[i] >= 0.0f ? 1 : -1, s2 = x[n + i] >= 0.0f ? 1 : -1;
+        int di = sa * (s1 + s2) / 2;
+        if (a.level_max > 0) {
+            const int xv = (int)sm.g[i] + 2 * di;
+            if (xv > a.level_max || xv < -a.level_max) di = 0;
+        }
+        d[i] = di;
+    }
+    // exact quantised energy E = -d^T A_q d - h_q^T d
+    int E = 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) r += (int)sm.Aq[i * n + j] * d[j];
+        E -= d[i] * r;
+        E -= (int)sm.hq[i] * d[i];
+    }
+    // MMSE fallback: a diverged anneal or one worse than the guess returns the guess
+    const bool keep = valid && E <= 0;
+    const int Ec = keep ? E : 0;
+    long long key = (long long)Ec * 4294967296LL + (long long)run;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long other = __shfl_xor_sync(0xffffffffu, key, o);
+        key = other < key ? other : key;
+    }
+    const unsigned divmask = __ballot_sync(0xffffffffu, !valid);
+    if (lane == 0) {
+        sm.key[warp] = key;
+        sm.ndiv[warp] = __popc(divmask);
+    }
+    __syncthreads();
+    long long best = sm.key[0];
+    int ndiv = sm.ndiv[0];
+    for (int w = 1; w < R / 32; ++w) {
+        best = sm.key[w] < best ? sm.key[w] : best;
+        ndiv += sm.ndiv[w];
+    }
+    const int best_run = (int)(best & 0xffffffffLL);
+    if (run == best_run) {
+        const int bestE = (int)((best - (long long)best_run) / 4294967296LL);
+        if (a.d_out) {
+            int8_t* dout = a.d_out + (size_t)p * n;
+#pragma unroll
+            for (int i = 0; i < n; ++i) dout[i] = keep ? (int8_t)d[i] : (int8_t)0;
+        }
+        if (a.E_out) a.E_out[p] = bestE;
+        if (a.run_out) a.run_out[p] = best_run;
+        if (a.ndiv_out) a.ndiv_out[p] = ndiv;
+        if (a.sym_out) {
+            // fused decode: lattice x = g + 2d -> symbol index
+            const int side = 1 << (a.mod_bits >> 1), L = side - 1;
+            uint8_t* so = a.sym_out + (size_t)p * NT;
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                const int xr = (int)sm.g[i] + 2 * (keep ? d[i] : 0);
+                const int xi = (int)sm.g[NT + i] + 2 * (keep ? d[NT + i] : 0);
+                so[i] = (uint8_t)(((xr + L) / 2) * side + (xi + L) / 2);
+            }
+        }
+    }
+}
+
+// =========================================================================
+// Downlink VPP (Sec. 3.3) in FP64.
+// =========================================================================
+constexpr int kVppMaxNt = 64;
+
+// Q = (H H^H)^-1 per channel: one warp per channel.
+template <int NU>
+__global__ void __launch_bounds__(32) vpp_inverse_kernel(VppInvArgs a) {
+    extern __shared__ __align__(16) double dsm[];
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x;
+    const int n_t = a.n_t;
+    double* Hd = dsm;                    // [NU][n_t] c
+    double* K = Hd + 2 * NU * n_t;       // [NU][NU] c
+    double* Lc = K + 2 * NU * NU;        // [NU][NU] c
+    double* W = Lc + 2 * NU * NU;        // per column c: w [NU] c   ([NU][NU] c)
+    double* Cc = W + 2 * NU * NU;        // per column c: col [NU] c ([NU][NU] c)
+    __shared__ int fail;
+    const float* Hg = a.H + (size_t)c * 2 * NU * n_t;
+    for (int e = lane; e < 2 * NU * n_t; e += 32) Hd[e] = (double)Hg[e];
+    if (lane == 0) fail = 0;
+    __syncwarp();
+    for (int t = lane; t < NU * NU; t += 32) {
+        const int i = t / NU, j = t % NU;
+        if (i > j) continue;
+        if (i == j) {
+            double acc = 0.0;
+            for (int k = 0; k < n_t; ++k) {
+                const double ar = Hd[2 * (i * n_t + k)], ai = Hd[2 * (i * n_t + k) + 1];
+                acc = __fma_rn(ar, ar, acc);
+                acc = __fma_rn(ai, ai, acc);
+            }
+            K[2 * (i * NU + i)] = acc;
+            K[2 * (i * NU + i) + 1] = 0.0;
+        } else {
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < n_t; ++k) {
+                const double ar = Hd[2 * (i * n_t + k)], ai = Hd[2 * (i * n_t + k) + 1];
+                const double br = Hd[2 * (j * n_t + k)], bi = Hd[2 * (j * n_t + k) + 1];
+                re = __fma_rn(ar, br, re);
+                re = __fma_rn(ai, bi, re);
+                im = __fma_rn(ai, br, im);
+                im = __fma_rn(-ar, bi, im);
+            }
+            K[2 * (i * NU + j)] = re;
+            K[2 * (i * NU + j) + 1] = im;
+            K[2 * (j * NU + i)] = re;
+            K[2 * (j * NU + i) + 1] = -im;
+        }
+    }
+    __syncwarp();
+    for (int j = 0; j < NU; ++j) {
+        if (lane == j) {
+            double d = K[2 * (j * NU + j)];
+            for (int k = 0; k < j; ++k) {
+                const double lr = Lc[2 * (j * NU + k)], li = Lc[2 * (j * NU + k) + 1];
+                d = __fma_rn(-lr, lr, d);
+                d = __fma_rn(-li, li, d);
+            }
+            const bool ok = (d > 0.0) && !isinf(d);
+            if (!ok) fail = 1;
+            Lc[2 * (j * NU + j)] = ok ? __dsqrt_rn(d) : 1.0;
+            Lc[2 * (j * NU + j) + 1] = 0.0;
+        }
+        __syncwarp();
+        const double ljj = Lc[2 * (j * NU + j)];
+        if (lane > j && lane < NU) {
+            const int i = lane;
+            double re = K[2 * (i * NU + j)], im = K[2 * (i * NU + j) + 1];
+            for (int k = 0; k < j; ++k) {
+                const double ar = Lc[2 * (i * NU + k)], ai = Lc[2 * (i * NU + k) + 1];
+                const double br = Lc[2 * (j * NU + k)], bi = Lc[2 * (j * NU + k) + 1];
+                re = __fma_rn(-ar, br, re);
+                re = __fma_rn(-ai, bi, re);
+                im = __fma_rn(-ai, br, im);
+                im = __fma_rn(ar, bi, im);
+            }
+            Lc[2 * (i * NU + j)] = __ddiv_rn(re, ljj);
+            Lc[2 * (i * NU + j) + 1] = __ddiv_rn(im, ljj);
+        }
+        __syncwarp();
+    }
+    // lane cc solves K q = e_cc (forward ascending, backward descending)
+    if (lane < NU) {
+        const int cc = lane;
+        double* w = W + 2 * NU * cc;
+        double* col = Cc + 2 * NU * cc;
+        for (int i = 0; i < NU; ++i) {
+            double re = (i == cc) ? 1.0 : 0.0, im = 0.0;
+            for (int k = 0; k < i; ++k) {
+                const double ar = Lc[2 * (i * NU + k)], ai = Lc[2 * (i * NU + k) + 1];
+                const double br = w[2 * k], bi = w[2 * k + 1];
+                re = __fma_rn(-ar, br, re);
+                re = __fma_rn(ai, bi, re);
+                im = __fma_rn(-ar, bi, im);
+                im = __fma_rn(-ai, br, im);
+            }
+            const double lii = Lc[2 * (i * NU + i)];
+            w[2 * i] = __ddiv_rn(re, lii);
+            w[2 * i + 1] = __ddiv_rn(im, lii);
+        }
+        for (int i = NU - 1; i >= 0; --i) {
+            double re = w[2 * i], im = w[2 * i + 1];
+            for (int k = NU - 1; k > i; --k) {
+                const double ar = Lc[2 * (k * NU + i)], ai = Lc[2 * (k * NU + i) + 1];
+                const double br = col[2 * k], bi = col[2 * k + 1];
+                re = __fma_rn(-ar, br, re);
+                re = __fma_rn(-ai, bi, re);
+                im = __fma_rn(-ar, bi, im);
+                im = __fma_rn(ai, br, im);
+            }
+            const double lii = Lc[2 * (i * NU + i)];
+            col[2 * i] = __ddiv_rn(re, lii);
+            col[2 * i + 1] = __ddiv_rn(im, lii);
+        }
+    }
+    __syncwarp();
+    double* Q = a.Q + (size_t)c * 2 * NU * NU;
+    const bool failed = fail != 0;
+    for (int t = lane; t < NU * NU; t += 32) {
+        const int i = t / NU, j = t % NU;
+        double re, im;
+        if (i <= j) {
+            re = Cc[2 * (NU * j + i)];
+            im = (i == j) ? 0.0 : Cc[2 * (NU * j + i) + 1];
+        } else {
+            re = Cc[2 * (NU * i + j)];
+            im = -Cc[2 * (NU * i + j) + 1];
+        }
+        Q[2 * t] = failed ? 0.0 : re;
+        Q[2 * t + 1] = failed ? 0.0 : im;
+    }
+    if (lane == 0 && a.status) a.status[c] = failed ? 1 : 0;
+}
+
+// VPP delta-Ising build: G = (tau/2)^2 rr(Q), h = -(tau/2) rr(Q u), guess 0.
+template <int NU>
+__global__ void __launch_bounds__(128) vpp_build_kernel(VppBuildArgs a) {
+    constexpr int n = 2 * NU;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 4 + warp;
+    if (p >= a.n_problems) return;
+    const int c = a.chan_index ? a.chan_index[p] : p;
+    if (c < 0 || c >= a.n_chan) {
+        if (lane == 0) atomicOr(a.err, kErrChanIndex);
+        for (int e = lane; e < n * n; e += 32) a.Aq[(size_t)p * n * n + e] = 0;
+        for (int e = lane; e < n; e += 32) a.hq[(size_t)p * n + e] = 0;
+        return;
+    }
+    const double* Q = a.Q + (size_t)c * 2 * NU * NU;
+    const uint8_t* u = a.u_sym + (size_t)p * NU;
+    const int side = 1 << (a.mod_bits >> 1), L = side - 1;
+    const double half_tau = (double)side;  // tau / 2 = sqrt(M)
+    const double s2 = half_tau * half_tau;
+    double hre = 0.0, him = 0.0;
+    if (lane < NU) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < NU; ++j) {
+            const int sym = u[j];
+            const double ur = (double)(2 * (sym / side) - L), ui = (double)(2 * (sym % side) - L);
+            const double qr = Q[2 * (lane * NU + j)], qi = Q[2 * (lane * NU + j) + 1];
+            re = __fma_rn(qr, ur, re);
+            re = __fma_rn(-qi, ui, re);
+            im = __fma_rn(qr, ui, im);
+            im = __fma_rn(qi, ur, im);
+        }
+        hre = __dmul_rn(-half_tau, re);
+        him = __dmul_rn(-half_tau, im);
+    }
+    double mx = 0.0;
+    for (int e = lane; e < NU * NU; e += 32)
+        mx = fmax(mx, fmax(fabs(__dmul_rn(Q[2 * e], s2)), fabs(__dmul_rn(Q[2 * e + 1], s2))));
+    if (lane < NU) mx = fmax(mx, fmax(fabs(hre), fabs(him)));
+    mx = warp_max(mx);
+    const int se = sigma_exp_d(mx);
+    const double s = ldexp(1.0, kQBits - se);
+    int16_t* Aq = a.Aq + (size_t)p * n * n;
+    for (int e = lane; e < n * n; e += 32) {
+        const int i = e / n, j = e % n;
+        const int ib = i % NU, jb = j % NU;
+        const double re = __dmul_rn(Q[2 * (ib * NU + jb)], s2), im = __dmul_rn(Q[2 * (ib * NU + jb) + 1], s2);
+        const double G = (i < NU) == (j < NU) ? re : (i < NU ? -im : im);
+        Aq[e] = (int16_t)(int)rint(__dmul_rn(-G, s));
+    }
+    if (lane < NU) {
+        int16_t* hq = a.hq + (size_t)p * n;
+        hq[lane] = (int16_t)(int)rint(__dmul_rn(hre, s));
+        hq[NU + lane] = (int16_t)(int)rint(__dmul_rn(him, s));
+    }
+}
+
+// Precoder output: v = d, t = u + tau v, w = Q t, x = H^H w, power = t^H Q t.
+template <int NU>
+__global__ void __launch_bounds__(128) vpp_output_kernel(VppOutArgs a) {
+    constexpr int n = 2 * NU;
+    __shared__ double sw[4][2 * NU];
+    __shared__ double st[4][2 * NU];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 4 + warp;
+    if (p >= a.n_problems) return;
+    int c = a.chan_index ? a.chan_index[p] : p;
+    if (c < 0 || c >= a.n_chan) {  // flagged by the build stage; keep the reads in bounds
+        if (lane == 0) atomicOr(a.err, kErrChanIndex);
+        c = 0;
+    }
+    const double* Q = a.Q + (size_t)c * 2 * NU * NU;
+    const uint8_t* u = a.u_sym + (size_t)p * NU;
+    const int8_t* d = a.d + (size_t)p * n;
+    const int side = 1 << (a.mod_bits >> 1), L = side - 1, tau = 2 * side;
+    if (lane < NU) {
+        const int sym = u[lane];
+        st[warp][2 * lane] = (double)(2 * (sym / side) - L + tau * (int)d[lane]);
+        st[warp][2 * lane + 1] = (double)(2 * (sym % side) - L + tau * (int)d[NU + lane]);
+        if (a.v_out) {
+            a.v_out[(size_t)p * n + 2 * lane] = d[lane];
+            a.v_out[(size_t)p * n + 2 * lane + 1] = d[NU + lane];
+        }
+    }
+    __syncwarp();
+    if (lane < NU) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < NU; ++j) {
+            const double qr = Q[2 * (lane * NU + j)], qi = Q[2 * (lane * NU + j) + 1];
+            const double tr = st[warp][2 * j], ti = st[warp][2 * j + 1];
+            re = __fma_rn(qr, tr, re);
+            re = __fma_rn(-qi, ti, re);
+            im = __fma_rn(qr, ti, im);
+            im = __fma_rn(qi, tr, im);
+        }
+        sw[warp][2 * lane] = re;
+        sw[warp][2 * lane + 1] = im;
+    }
+    __syncwarp();
+    const int n_t = a.n_t;
+    if (a.x_out) {
+        const float* Hg = a.H + (size_t)c * 2 * NU * n_t;
+        for (int kk = lane; kk < n_t; kk += 32) {
+            double re = 0.0, im = 0.0;
+            for (int i = 0; i < NU; ++i) {
+                const double ar = (double)Hg[2 * (i * n_t + kk)], ai = (double)Hg[2 * (i * n_t + kk) + 1];
+                const double wr = sw[warp][2 * i], wi = sw[warp][2 * i + 1];
+                re = __fma_rn(ar, wr, re);
+                re = __fma_rn(ai, wi, re);
+                im = __fma_rn(ar, wi, im);
+                im = __fma_rn(-ai, wr, im);
+            }
+            a.x_out[(size_t)p * 2 * n_t + 2 * kk] = (float)re;
+            a.x_out[(size_t)p * 2 * n_t + 2 * kk + 1] = (float)im;
+        }
+    }
+    if (lane == 0 && a.power_out) {
+        double pw = 0.0;
+        for (int i = 0; i < NU; ++i) {
+            pw = __fma_rn(st[warp][2 * i], sw[warp][2 * i], pw);
+            pw = __fma_rn(st[warp][2 * i + 1], sw[warp][2 * i + 1], pw);
+        }
+        a.power_out[p] = (float)pw;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+template <int NT>
+cudaError_t launch_build_detect_impl(const BuildArgs& a, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    const size_t smem = (size_t)kBuildWarps * build_smem_floats<NT>(a.n_r) * sizeof(float);
+    cudaError_t err = cudaFuncSetAttribute(build_detect_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = (a.n_problems + kBuildWarps - 1) / kBuildWarps;
+    build_detect_kernel<NT><<<blocks, kBuildWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    if (a.f_mvm == 2) cac_solve_kernel<NT, 2><<<a.n_problems, runs, 0, s>>>(a);
+    else if (a.f_mvm == 1) cac_solve_kernel<NT, 1><<<a.n_problems, runs, 0, s>>>(a);
+    else cac_solve_kernel<NT, 0><<<a.n_problems, runs, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_vpp_inverse_impl(const VppInvArgs& a, cudaStream_t s) {
+    if (a.n_chan <= 0) return cudaSuccess;
+    const size_t smem = (size_t)(2 * NT * a.n_t + 8 * NT * NT) * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(vpp_inverse_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    vpp_inverse_kernel<NT><<<a.n_chan, 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_vpp_build_impl(const VppBuildArgs& a, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    vpp_build_kernel<NT><<<(a.n_problems + 3) / 4, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_vpp_output_impl(const VppOutArgs& a, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    vpp_output_kernel<NT><<<(a.n_problems + 3) / 4, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mmgap
+
+// Explicit instantiation of every launcher for one n_t.
+#define MMGAP_INSTANTIATE(NT)                                                                                  \
+    namespace mmgap {                                                                                          \
+    template <> cudaError_t launch_build_detect<NT>(const BuildArgs& a, cudaStream_t s) {                      \
+        return launch_build_detect_impl<NT>(a, s);                                                             \
+    }                                                                                                          \
+    template <> cudaError_t launch_solve<NT>(const SolveArgs& a, int runs, cudaStream_t s) {                   \
+        return launch_solve_impl<NT>(a, runs, s);                                                              \
+    }                                                                                                          \
+    template <> cudaError_t launch_vpp_inverse<NT>(const VppInvArgs& a, cudaStream_t s) {                      \
+        return launch_vpp_inverse_impl<NT>(a, s);                                                              \
+    }                                                                                                          \
+    template <> cudaError_t launch_vpp_build<NT>(const VppBuildArgs& a, cudaStream_t s) {                      \
+        return launch_vpp_build_impl<NT>(a, s);                                                                \
+    }                                                                                                          \
+    template <> cudaError_t launch_vpp_output<NT>(const VppOutArgs& a, cudaStream_t s) {                       \
+        return launch_vpp_output_impl<NT>(a, s);                                                               \
+    }                                                                                                          \
+    }
