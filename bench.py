@@ -65,7 +65,7 @@ class ClockSampler:
         self.proc = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -99,9 +99,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload(name: str, seed: int):
+def make_workload(name: str, seed: int, n_sub: int = synth.SUBCARRIERS_100MHZ_30KHZ):
     n_r, n_t, mb, model, hold, snr = WORKLOADS[name]
-    return synth.uplink(seed, n_r, n_t, mb, snr_db=snr, model=model, hold=hold)
+    return synth.uplink(seed, n_r, n_t, mb, n_sub=n_sub, snr_db=snr, model=model, hold=hold)
 
 
 def cpu_baseline(w, prm_fields: dict, seed: int, budget_s: float = 12.0, min_problems: int = 4):
@@ -158,7 +158,7 @@ def run_reference(args, rank: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mmgap", choices=["mmgap", "reference"])
     ap.add_argument("--workload", default="ul16x16_16qam_slot", choices=sorted(WORKLOADS))
@@ -168,6 +168,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=6.0)
+    ap.add_argument("--subcarriers", type=int, default=synth.SUBCARRIERS_100MHZ_30KHZ,
+                    help="subcarriers per slot (3276 = 100 MHz at 30 kHz; smaller only for profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -194,7 +196,7 @@ def main():
             dist.barrier()
 
     # each rank detects its own slot (different seed): weak scaling
-    w = make_workload(args.workload, 2025 + rank)
+    w = make_workload(args.workload, 2025 + rank, args.subcarriers)
     P = w["y"].shape[0]
     n_t, mb = w["n_t"], w["mod_bits"]
     prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
