@@ -216,6 +216,34 @@ mmgap_status mmgap_stage_times(mmgap_ctx* ctx, float ms_out[4], int* n_chunks_ou
  * Synchronises the device; clears the word if `clear` is non-zero. */
 mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
 
+/*
+ * Uplink detection that allocates nothing (no counterpart in the paper; this
+ * is a service to callers that cannot allocate device memory: a running
+ * real-time slot loop, where cudaMalloc may synchronise the device and miss
+ * the slot, a plug-in inside an application that owns all device memory, or
+ * code being recorded into a CUDA graph).
+ *
+ * Computes exactly what mmgap_detect computes for one job, without a
+ * context: the scratch between the build and solve kernels comes from an
+ * 8 MiB array compiled into the library (every GPU that loads the library
+ * holds it until the process exits).  Inputs and outputs are the caller's
+ * device memory, as for mmgap_detect; the call runs on the current device.
+ *
+ * Limit: the job must fit the array, i.e. align256(P n^2 2) + align256(P n 2)
+ * + align256(P n) <= 8 MiB with n = 2 n_t (about 3,900 problems of 16 users,
+ * 14,900 of 8 users); a larger job returns MMGAP_ENOMEM (with a message on
+ * stderr) and launches nothing.  Split it.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race: serialise them.  A channel index out of range gives an all-zero
+ * problem, as for mmgap_detect, but is not reported.
+ * Returns MMGAP_EINVAL / MMGAP_EUNSUPPORTED for bad arguments, MMGAP_ECUDA
+ * for a CUDA error.
+ */
+mmgap_status mmgap_detect_static(const mmgap_params* params, const mmgap_detect_job* job, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,14 +70,15 @@ _lib.mmgap_build_detect.argtypes = [_vp, C.POINTER(_DetectJob), _vp, _vp, _vp, _
 _lib.mmgap_set_timing.argtypes = [_vp, C.c_int]
 _lib.mmgap_stage_times.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)]
 _lib.mmgap_device_errors.argtypes = [_vp, C.POINTER(C.c_int), C.c_int]
+_lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), _vp]
 for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
            "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
-           "mmgap_device_errors"):
+           "mmgap_device_errors", "mmgap_detect_static"):
     getattr(_lib, _f).restype = C.c_int
 
 ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
                "mmgap_precode", "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing",
-               "mmgap_stage_times", "mmgap_device_errors")
+               "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static")
 
 
 @dataclasses.dataclass
@@ -265,6 +266,15 @@ class Context:
                                             _ptr(out["g"]), _ptr(out.get("G")), _ptr(out.get("h")),
                                             _ptr(out.get("sigma_exp")), self._stream()))
         return out
+
+    def detect_static(self, job: _DetectJob, params: Params):
+        """mmgap_detect_static on this context's device: the same detection
+        without any allocation (scratch in a fixed array inside the library),
+        for callers that must not allocate device memory."""
+        cp = params._c()
+        st = _lib.mmgap_detect_static(C.byref(cp), C.byref(job), self._stream())
+        if st != OK:
+            raise MMGaPError(st, "mmgap_detect_static failed (see stderr)")
 
     def set_timing(self, enable: bool):
         self._raise(_lib.mmgap_set_timing(self._h, 1 if enable else 0))

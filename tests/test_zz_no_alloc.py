@@ -1,0 +1,66 @@
+"""mmgap_detect_static against mmgap_detect.
+
+mmgap_detect_static is for callers that cannot allocate device memory: a
+real-time slot loop that must not call cudaMalloc once running (an
+allocation can synchronise the device and miss the slot), a plug-in inside an
+application that owns all device memory, or code being recorded into a CUDA
+graph.  It takes its scratch from a fixed array inside the library instead of
+a context workspace.  Its results must be the same bits as the context path's,
+call after call, although the array keeps the previous call's contents.
+
+This file sorts last so that a run stopping at the first failure has already
+run every other test.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+def _T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _outputs(P, n_t):
+    return {"sym": torch.full((P, n_t), 255, dtype=torch.uint8, device=DEV),
+            "energy": torch.full((P,), 7, dtype=torch.int32, device=DEV),
+            "guess": torch.zeros((P, 2 * n_t), dtype=torch.int8, device=DEV),
+            "offset": torch.zeros((P, 2 * n_t), dtype=torch.int8, device=DEV),
+            "ndiv": torch.full((P,), -1, dtype=torch.int32, device=DEV)}
+
+
+def test_static_scratch_matches_context_path_two_calls_in_a_row():
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=120)
+    cases = [synth.uplink(61, 16, 16, 4, n_sub=20, n_sym=10, snr_db=14.0),      # 200 problems, 16 users
+             synth.uplink(62, 8, 8, 2, n_sub=30, n_sym=10, snr_db=8.0, model="kron", hold="prb")]  # 300, 8 users
+    with pkg.Context(0) as ctx:
+        for i, w in enumerate(cases):
+            P, n_t = w["y"].shape[0], w["n_t"]
+            H, y, nv, ci = _T(w["H"]), _T(w["y"]), _T(w["noise_var"]), _T(w["chan_index"])
+            ref = _outputs(P, n_t)
+            ctx.detect_jobs([ctx.detect_job(H, y, nv, w["mod_bits"], 900 + i, ref, ci)], prm)
+            got = _outputs(P, n_t)
+            ctx.detect_static(ctx.detect_job(H, y, nv, w["mod_bits"], 900 + i, got, ci), prm)
+            torch.cuda.synchronize()
+            for k in ref:
+                assert torch.equal(got[k], ref[k]), (i, k)
+
+
+def test_static_scratch_rejects_a_job_larger_than_the_array():
+    import paper_2510_01579_gb300 as pkg
+    w = synth.uplink(63, 16, 16, 4, n_sub=300, n_sym=14)  # 4200 problems > 8 MiB of scratch
+    P = w["y"].shape[0]
+    with pkg.Context(0) as ctx:
+        got = _outputs(P, 16)
+        job = ctx.detect_job(_T(w["H"]), _T(w["y"]), _T(w["noise_var"]), 4, 1, got, _T(w["chan_index"]))
+        with pytest.raises(pkg.MMGaPError) as e:
+            ctx.detect_static(job, pkg.Params.default())
+        assert e.value.status == 2  # MMGAP_ENOMEM
+        torch.cuda.synchronize()
+        assert bool((got["sym"] == 255).all())  # nothing was launched
