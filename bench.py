@@ -167,6 +167,9 @@ def main():
     ap.add_argument("--f-mvm", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="solver launch shape (1 plain .. 4); default: autotuned at set-up")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-problem kernel")
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--subcarriers", type=int, default=synth.SUBCARRIERS_100MHZ_30KHZ,
                     help="subcarriers per slot (3276 = 100 MHz at 30 kHz; smaller only for profiling)")
@@ -184,6 +187,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2510_01579_gb300 import Context, Params
+    from paper_2510_01579_gb300.binding import VARIANT_NAMES
 
     if world > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
@@ -209,6 +213,12 @@ def main():
            "energy": torch.empty(P, dtype=torch.int32, device=dev),
            "guess": torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)}
     job = ctx.detect_job(H, y, nv, mb, 77, out, ci)
+    if args.variant >= 0:
+        ctx.set_solver_variant(n_t, args.variant)
+        tune_ms = None
+    else:  # autotune the launch shape on this size (results are identical across shapes)
+        _, tune_ms = ctx.autotune(prm, n_t, 8192)
+    variant = ctx.solver_variant(n_t, args.f_mvm)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
     ctx.set_timing(True)
     stream = torch.cuda.current_stream(dev)
@@ -304,14 +314,41 @@ def main():
         e2e = {"value": world * P * args.steps / (e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_total / args.steps}
 
+    # the paper's design point (one CTA per problem, one scalar thread per
+    # anneal) on the same inputs, for the speedup of the tuned launch shape
+    plain = None
+    if not args.no_plain:
+        from paper_2510_01579_gb300.binding import VARIANT_NAMES  # noqa: F401
+        ctx.set_solver_variant(n_t, 1)
+        for _ in range(2):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        pt = []
+        for i in range(min(args.steps, 5)):
+            flush.zero_()
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+            torch.cuda.synchronize()
+            pt.append(starts[i].elapsed_time(ends[i]))
+        if not torch.equal(out["sym"].cpu(), torch.from_numpy(sym)):
+            raise RuntimeError("plain and tuned solver shapes disagree")
+        ctx.set_solver_variant(n_t, variant)
+        plain = {"ms_per_step": statistics.mean(pt), "value": P / (statistics.mean(pt) / 1e3),
+                 "speedup_of_tuned": statistics.mean(pt) / ms_per_step}
+
     # roofline of the dominant kernel (the CIM-CAC solver), from the library's
     # own CUDA events on the launching stream
     flops = solver_flops(P, n_t, args.runs, args.solver_steps, args.f_mvm)
+    # DRAM bytes of the solver from ncu (profiles/cac_solve_16x16_slot_1024sc.md): 2,153 B per
+    # 16x16 problem, measured on 14,336 problems and scaled by problems; None for other shapes
+    traffic = 2153.0 * P if (n_t == 16 and variant == 3) else None
     solve_avg = statistics.mean(solve_ms)
     achieved = flops / (solve_avg / 1e3) / 1e12
     peak = alu_peak_tflops()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "cac_solve_kernel<16,2>",
+                "traffic": traffic, "kernel": f"cac_solve, launch shape {VARIANT_NAMES[variant]}",
                 "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts and max clock)",
                 "flops_per_launch": flops, "avg_launch_ms": solve_avg}
 
@@ -335,6 +372,8 @@ def main():
             "slot_latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "max": max(step_ms)},
             "stage_ms": {"build": statistics.mean(build_ms), "solve": solve_avg},
             "ber": {"mmgap": ber, "mmse": ber_mmse},
+            "solver_shape": {"chosen": VARIANT_NAMES[variant], "autotune_ms": tune_ms},
+            "plain_path": plain,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 2 * chunks, "clocks": clk, "wall_s": wall}
     if rank == 0:

@@ -217,6 +217,34 @@ mmgap_status mmgap_stage_times(mmgap_ctx* ctx, float ms_out[4], int* n_chunks_ou
 mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
 
 /*
+ * Launch shape of the CIM-CAC solver for n_t users (no counterpart in the
+ * paper, which runs one thread per anneal).  All shapes give bit-identical
+ * results; they differ only in speed:
+ *   0 default for the size (packed one-thread-per-anneal where compiled)
+ *   1 plain: one thread per anneal, scalar FP32 (the paper's design point)
+ *   2 tuned kernel, one thread per anneal, scalar FP32
+ *   3 tuned kernel, one thread per anneal, packed FP32 pairs
+ *   4 tuned kernel, two threads per anneal (shuffle-gathered field), packed
+ * Shapes 2-4 exist for n_t in {4, 8, 16} with f_mvm in {1, 2}; elsewhere 1
+ * runs.  The choice is per context and applies to detect, precode and
+ * solve_ising calls.
+ */
+mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant);
+
+/* The shape (1-4) a call with n_t users and refresh period f_mvm would run. */
+mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* variant_out);
+
+/*
+ * Autotuner: time every compiled solver shape for n_t users on n_problems
+ * random Q14 problems (0 = 8192; clamped to the workspace) with *params,
+ * keep the fastest for this context and return it in *variant_out.
+ * ms_out (may be NULL) receives [0] the best time and [v] the time of shape v
+ * (-1 if not compiled).  Synchronises the device; uses the workspace.
+ */
+mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
+                            float ms_out[5]);
+
+/*
  * Uplink detection that allocates nothing (no counterpart in the paper; this
  * is a service to callers that cannot allocate device memory: a running
  * real-time slot loop, where cudaMalloc may synchronise the device and miss

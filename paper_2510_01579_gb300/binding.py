@@ -71,14 +71,21 @@ _lib.mmgap_set_timing.argtypes = [_vp, C.c_int]
 _lib.mmgap_stage_times.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)]
 _lib.mmgap_device_errors.argtypes = [_vp, C.POINTER(C.c_int), C.c_int]
 _lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), _vp]
+_lib.mmgap_set_solver_variant.argtypes = [_vp, C.c_int, C.c_int]
+_lib.mmgap_get_solver_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
+_lib.mmgap_autotune.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
 for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
            "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
-           "mmgap_device_errors", "mmgap_detect_static"):
+           "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant", "mmgap_get_solver_variant",
+           "mmgap_autotune"):
     getattr(_lib, _f).restype = C.c_int
 
 ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
                "mmgap_precode", "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing",
-               "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static")
+               "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant",
+               "mmgap_get_solver_variant", "mmgap_autotune")
+
+VARIANT_NAMES = {0: "default", 1: "plain", 2: "tpa1", 3: "tpa1-packed", 4: "tpa2-packed"}
 
 
 @dataclasses.dataclass
@@ -275,6 +282,23 @@ class Context:
         st = _lib.mmgap_detect_static(C.byref(cp), C.byref(job), self._stream())
         if st != OK:
             raise MMGaPError(st, "mmgap_detect_static failed (see stderr)")
+
+    def set_solver_variant(self, n_t: int, variant: int):
+        """Force the solver's launch shape for n_t users (0 = size default)."""
+        self._raise(_lib.mmgap_set_solver_variant(self._h, n_t, variant))
+
+    def solver_variant(self, n_t: int, f_mvm: int = 2) -> int:
+        v = C.c_int()
+        self._raise(_lib.mmgap_get_solver_variant(self._h, n_t, f_mvm, C.byref(v)))
+        return v.value
+
+    def autotune(self, params: Params, n_t: int, n_problems: int = 0):
+        """Time every compiled launch shape, keep the fastest; returns (shape, {shape: ms})."""
+        v = C.c_int()
+        ms = (C.c_float * 5)()
+        cp = params._c()
+        self._raise(_lib.mmgap_autotune(self._h, C.byref(cp), n_t, n_problems, C.byref(v), ms))
+        return v.value, {i: ms[i] for i in range(1, 5) if ms[i] >= 0}
 
     def set_timing(self, enable: bool):
         self._raise(_lib.mmgap_set_timing(self._h, 1 if enable else 0))

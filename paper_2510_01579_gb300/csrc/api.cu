@@ -13,6 +13,7 @@
 
 #include "../../include/mmgap.h"
 #include "internal.h"
+#include "kernels.cuh"
 
 using namespace mmgap;
 
@@ -25,7 +26,41 @@ struct mmgap_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> events;  // 4 per chunk: start, built, solved, output
     int n_chunks = 0;
+    int variant[17] = {};             // solver launch shape per n_t (0 = default)
 };
+
+namespace mmgap {
+__global__ void random_ising_kernel(int16_t* Aq, int16_t* hq, int n, int n_problems, uint32_t k0, uint32_t k1) {
+    const long long total = (long long)n_problems * n * (n + 1);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(idx / (n * (n + 1)));
+        const int r = (int)(idx % (n * (n + 1)));
+        const U4 w = philox4x32_10(U4{(uint32_t)r, (uint32_t)p, 0x7u, 0u}, k0, k1);
+        const int16_t v = (int16_t)((int)(w.x % 32769u) - 16384);
+        if (r < n * n) {
+            const int i = r / n, j = r % n;
+            if (i <= j) {
+                Aq[(size_t)p * n * n + i * n + j] = v;
+                Aq[(size_t)p * n * n + j * n + i] = v;
+            }
+        } else {
+            hq[(size_t)p * n + (r - n * n)] = v;
+        }
+    }
+}
+cudaError_t launch_random_ising(int16_t* Aq, int16_t* hq, int n, int n_problems, uint64_t seed, cudaStream_t s) {
+    random_ising_kernel<<<1024, 256, 0, s>>>(Aq, hq, n, n_problems, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return cudaGetLastError();
+}
+}  // namespace mmgap
+
+int mmgap::resolve_variant(int n_t, int f_mvm, int requested) {
+    const bool tuned = (n_t == 4 || n_t == 8 || n_t == 16) && (f_mvm == 1 || f_mvm == 2);
+    if (!tuned) return kVariantPlain;
+    if (requested <= kVariantAuto || requested >= kVariantCount) return kVariantTpa1Packed;
+    return requested;
+}
 
 namespace {
 
@@ -328,6 +363,7 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     a.E_out = E_out;
     a.run_out = run_out;
     a.ndiv_out = ndiv_out;
+    a.variant = ctx->variant[n / 2];
     cudaError_t e = dispatch_nt<OpSolve>(n / 2, a, params->runs, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
     return MMGAP_OK;
@@ -395,6 +431,7 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
             a.ndiv_out = J.ndiv_out ? J.ndiv_out + p0 : nullptr;
             a.sym_out = J.sym_out + (size_t)p0 * J.n_t;
             a.mod_bits = J.mod_bits;
+            a.variant = ctx->variant[J.n_t];
             e = dispatch_nt<OpSolve>(J.n_t, a, params->runs, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
             if (J.guess_out) {
@@ -479,6 +516,7 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
             a.d_out = d;
             a.E_out = J.energy_out ? J.energy_out + p0 : nullptr;
             a.ndiv_out = J.ndiv_out ? J.ndiv_out + p0 : nullptr;
+            a.variant = ctx->variant[J.n_u];
             e = dispatch_nt<OpSolve>(J.n_u, a, params->runs, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
             if ((st = timing_mark(ctx, 2, s)) != MMGAP_OK) return st;
@@ -501,6 +539,87 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
             if ((st = timing_mark(ctx, 3, s)) != MMGAP_OK) return st;
         }
     }
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant) {
+    if (!ctx) return MMGAP_EINVAL;
+    if (!nt_supported(n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d", n_t);
+    if (variant < 0 || variant >= kVariantCount) return fail(ctx, MMGAP_EINVAL, "variant=%d", variant);
+    ctx->variant[n_t] = variant;
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* variant_out) {
+    if (!ctx || !variant_out) return MMGAP_EINVAL;
+    if (!nt_supported(n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d", n_t);
+    *variant_out = resolve_variant(n_t, f_mvm, ctx->variant[n_t]);
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
+                            float ms_out[5]) {
+    if (!ctx) return MMGAP_EINVAL;
+    mmgap_status st = check_params(ctx, params);
+    if (st != MMGAP_OK) return st;
+    if (!nt_supported(n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d", n_t);
+    const int n = 2 * n_t;
+    if (n_problems <= 0) n_problems = 8192;
+    const size_t per = (size_t)n * n * 2 + (size_t)n * 2 + (size_t)n + 32;
+    const size_t cap = (ctx->ws_bytes - 4 * kAlign) / per;
+    if (cap < 1) return fail(ctx, MMGAP_ENOMEM, "workspace too small for autotuning");
+    if ((size_t)n_problems > cap) n_problems = (int)cap;
+    CurrentDevice cd(ctx->device);
+    int16_t* Aq = (int16_t*)ctx->ws;
+    int16_t* hq = (int16_t*)(ctx->ws + align_up((size_t)n_problems * n * n * 2));
+    int8_t* d = (int8_t*)((char*)hq + align_up((size_t)n_problems * n * 2));
+    int32_t* E = (int32_t*)((char*)d + align_up((size_t)n_problems * n));
+    cudaStream_t s = nullptr;
+    cudaError_t e = launch_random_ising(Aq, hq, n, n_problems, 0x5eedULL, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "random problems");
+    SolveArgs a{};
+    a.Aq = Aq;
+    a.hq = hq;
+    a.n_problems = n_problems;
+    a.steps = params->steps;
+    a.f_mvm = params->f_mvm;
+    a.key0 = 1;
+    a.k = euler_consts(*params);
+    a.d_out = d;
+    a.E_out = E;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    float best = 1e30f;
+    int best_v = kVariantPlain;
+    for (int v = kVariantPlain; v < kVariantCount; ++v) {
+        if (ms_out) ms_out[v] = -1.0f;
+        if (resolve_variant(n_t, params->f_mvm, v) != v) continue;  // not compiled for this size
+        a.variant = v;
+        e = dispatch_nt<OpSolve>(n_t, a, params->runs, s);  // warm up
+        float ms = 0.0f;
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+            cudaEventRecord(t0, s);
+            e = dispatch_nt<OpSolve>(n_t, a, params->runs, s);
+            cudaEventRecord(t1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float m = 0.0f;
+            cudaEventElapsedTime(&m, t0, t1);
+            ms = r == 0 ? m : std::min(ms, m);
+        }
+        if (e != cudaSuccess) break;
+        if (ms_out) ms_out[v] = ms;
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+    ctx->variant[n_t] = best_v;
+    if (variant_out) *variant_out = best_v;
+    if (ms_out) ms_out[0] = best;
     return MMGAP_OK;
 }
 

@@ -39,7 +39,22 @@ struct SolveArgs {
     // fused uplink decode (detect): symbols of g + 2 d
     uint8_t* sym_out;          // [P][n_t] or nullptr
     int mod_bits;
+    int variant;               // SolverVariant; 0 = the size's default
 };
+
+// Launch shapes of the solver.  All produce bit-identical results.
+enum SolverVariant : int {
+    kVariantAuto = 0,
+    kVariantPlain = 1,       // one thread per anneal, scalar FP32 (the paper's design point)
+    kVariantTpa1 = 2,        // tuned kernel, one thread per anneal
+    kVariantTpa1Packed = 3,  // tuned kernel, one thread per anneal, packed FP32 pairs
+    kVariantTpa2Packed = 4,  // tuned kernel, two threads per anneal, packed FP32 pairs
+    kVariantCount = 5
+};
+
+// Variant used for n_t users and refresh period f_mvm when `requested` is
+// kVariantAuto or not compiled for that size.
+int resolve_variant(int n_t, int f_mvm, int requested);
 
 struct BuildArgs {
     const float* H;            // complex [n_chan][n_r][n_t]
@@ -104,6 +119,10 @@ template <int NT> cudaError_t launch_solve(const SolveArgs& a, int runs, cudaStr
 template <int NT> cudaError_t launch_vpp_inverse(const VppInvArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_build(const VppBuildArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_output(const VppOutArgs& a, cudaStream_t s);
+
+// Random symmetric Q14 problems (uniform codes in [-2^14, 2^14]) for the
+// autotuner, drawn from Philox on the device (defined in api.cu).
+cudaError_t launch_random_ising(int16_t* Aq, int16_t* hq, int n, int n_problems, uint64_t seed, cudaStream_t s);
 
 constexpr int kMaxNr = 64;
 

@@ -578,6 +578,312 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
 }
 
 // =========================================================================
+// Tuned CIM-CAC solver: TPA threads per anneal.  Thread q of an anneal owns
+// rows [q NS, (q+1) NS) of both half-size blocks (NS = n / TPA) and keeps the
+// auxiliary spin redundantly; at each field refresh the anneal's u = x1 + x2 is
+// gathered with warp shuffles, then every thread forms its NS rows of m = A u
+// in the same ascending-j FMA order as the one-thread form.  PACKED runs
+// pairs of rows with the packed FP32 instructions (__ffma2_rn, __fmul2_rn,
+// __fadd2_rn: two IEEE round-to-nearest operations each).  All variants
+// produce bit-identical results; they differ in registers per thread
+// (hence warps in flight to hide shared-memory latency) and instruction count.
+// =========================================================================
+
+__device__ __forceinline__ void euler_pair(float2& x, float2& e, float2 mu, float2 cdt, float2 c1, float2 cz,
+                                           float2 c2) {
+    const float2 q = __fmul2_rn(x, x);
+    const float2 t = __ffma2_rn(cdt, q, c1);
+    const float2 em = __fmul2_rn(e, mu);
+    const float2 xn = __ffma2_rn(x, t, em);
+    const float2 r = __ffma2_rn(cz, q, c2);
+    e = __fmul2_rn(e, r);
+    x = xn;
+}
+
+// Field refresh + L frozen Euler steps of one thread's rows (L == 0: runtime Lrt).
+template <int n, int NS, int TPA, bool PACKED, int L>
+__device__ __forceinline__ void tuned_block(const float* sA, const float* sh, const float* snd, float (&x1)[NS],
+                                            float (&x2)[NS], float (&e1)[NS], float (&e2)[NS], float& xa, float& ea,
+                                            int q, int lane, int Lrt, const EulerConsts& k) {
+    asm volatile("" ::: "memory");  // keep the coupling loads inside the time loop
+    const int row0 = q * NS;
+    // u = x1 + x2 of this thread's rows, then of the whole anneal
+    float uo[NS];
+    if constexpr (PACKED) {
+#pragma unroll
+        for (int i = 0; i < NS; i += 2) {
+            const float2 s2 = __fadd2_rn(make_float2(x1[i], x1[i + 1]), make_float2(x2[i], x2[i + 1]));
+            uo[i] = s2.x;
+            uo[i + 1] = s2.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) uo[i] = addrn(x1[i], x2[i]);
+    }
+    float u[TPA == 1 ? 1 : n];
+    if constexpr (TPA == 1) {
+        // uo is the whole anneal's u; used directly below
+    } else if constexpr (TPA == 2) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const float other = __shfl_xor_sync(0xffffffffu, uo[i], 1);
+            u[i] = q == 0 ? uo[i] : other;
+            u[NS + i] = q == 0 ? other : uo[i];
+        }
+    } else {
+        const int base = lane & ~(TPA - 1);
+#pragma unroll
+        for (int qq = 0; qq < TPA; ++qq)
+#pragma unroll
+            for (int i = 0; i < NS; ++i) u[qq * NS + i] = __shfl_sync(0xffffffffu, uo[i], base | qq);
+    }
+    // m = A u for this thread's rows (ascending j), mu_a = b^T u
+    float m[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) m[i] = 0.0f;
+    float mua = 0.0f;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+        float uj;
+        if constexpr (TPA == 1) uj = uo[j];
+        else uj = u[j];
+        mua = fmarn(sh[j], uj, mua);
+        const float4* row = reinterpret_cast<const float4*>(sA + j * n + row0);
+#pragma unroll
+        for (int i4 = 0; i4 < NS / 4; ++i4) {
+            const float4 a4 = row[i4];
+            if constexpr (PACKED) {
+                const float2 uu = make_float2(uj, uj);
+                const float2 lo = __ffma2_rn(make_float2(a4.x, a4.y), uu, make_float2(m[4 * i4], m[4 * i4 + 1]));
+                const float2 hi = __ffma2_rn(make_float2(a4.z, a4.w), uu, make_float2(m[4 * i4 + 2], m[4 * i4 + 3]));
+                m[4 * i4] = lo.x;
+                m[4 * i4 + 1] = lo.y;
+                m[4 * i4 + 2] = hi.x;
+                m[4 * i4 + 3] = hi.y;
+            } else {
+                m[4 * i4 + 0] = fmarn(a4.x, uj, m[4 * i4 + 0]);
+                m[4 * i4 + 1] = fmarn(a4.y, uj, m[4 * i4 + 1]);
+                m[4 * i4 + 2] = fmarn(a4.z, uj, m[4 * i4 + 2]);
+                m[4 * i4 + 3] = fmarn(a4.w, uj, m[4 * i4 + 3]);
+            }
+        }
+    }
+    // frozen field: c = m + b x_a, mu1 = c - diag(A) x1, mu2 = c - diag(A) x2
+    if constexpr (PACKED) {
+        const float2 xa2 = make_float2(xa, xa);
+        const float2 cdt = make_float2(k.cdt, k.cdt), c1 = make_float2(k.c1, k.c1);
+        const float2 cz = make_float2(k.cz, k.cz), c2 = make_float2(k.c2, k.c2);
+#pragma unroll
+        for (int i = 0; i < NS; i += 2) {
+            const float2 hh = *reinterpret_cast<const float2*>(sh + row0 + i);
+            const float2 nd = *reinterpret_cast<const float2*>(snd + row0 + i);
+            const float2 c = __ffma2_rn(hh, xa2, make_float2(m[i], m[i + 1]));
+            float2 X1 = make_float2(x1[i], x1[i + 1]), X2 = make_float2(x2[i], x2[i + 1]);
+            float2 E1 = make_float2(e1[i], e1[i + 1]), E2 = make_float2(e2[i], e2[i + 1]);
+            const float2 mu1 = __ffma2_rn(nd, X1, c);
+            const float2 mu2 = __ffma2_rn(nd, X2, c);
+            if constexpr (L > 0) {
+#pragma unroll
+                for (int s = 0; s < L; ++s) {
+                    euler_pair(X1, E1, mu1, cdt, c1, cz, c2);
+                    euler_pair(X2, E2, mu2, cdt, c1, cz, c2);
+                }
+            } else {
+#pragma unroll 1
+                for (int s = 0; s < Lrt; ++s) {
+                    euler_pair(X1, E1, mu1, cdt, c1, cz, c2);
+                    euler_pair(X2, E2, mu2, cdt, c1, cz, c2);
+                }
+            }
+            x1[i] = X1.x; x1[i + 1] = X1.y; x2[i] = X2.x; x2[i + 1] = X2.y;
+            e1[i] = E1.x; e1[i + 1] = E1.y; e2[i] = E2.x; e2[i + 1] = E2.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const float c = fmarn(sh[row0 + i], xa, m[i]);
+            const float mu1 = fmarn(snd[row0 + i], x1[i], c);
+            const float mu2 = fmarn(snd[row0 + i], x2[i], c);
+            if constexpr (L > 0) {
+#pragma unroll
+                for (int s = 0; s < L; ++s) {
+                    euler_spin(x1[i], e1[i], mu1, k);
+                    euler_spin(x2[i], e2[i], mu2, k);
+                }
+            } else {
+#pragma unroll 1
+                for (int s = 0; s < Lrt; ++s) {
+                    euler_spin(x1[i], e1[i], mu1, k);
+                    euler_spin(x2[i], e2[i], mu2, k);
+                }
+            }
+        }
+    }
+    if constexpr (L > 0) {
+#pragma unroll
+        for (int s = 0; s < L; ++s) euler_spin(xa, ea, mua, k);
+    } else {
+#pragma unroll 1
+        for (int s = 0; s < Lrt; ++s) euler_spin(xa, ea, mua, k);
+    }
+}
+
+template <int NT, int F, int TPA, bool PACKED>
+__global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a) {
+    constexpr int n = 2 * NT;
+    constexpr int NS = n / TPA;
+    static_assert(n % TPA == 0 && NS % 4 == 0, "rows per thread must be a multiple of 4");
+    static_assert(F > 0, "compile-time refresh period");
+    __shared__ __align__(16) SolveSmem<NT> sm;
+    __shared__ long long skey[4 * TPA];
+    __shared__ int sdiv[4 * TPA];
+    const int p = blockIdx.x;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int q = tid % TPA, run = tid / TPA;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int row0 = q * NS;
+    const EulerConsts k = a.k;
+    {
+        const int16_t* Aq = a.Aq + (size_t)p * n * n;
+        for (int e = tid; e < n * n; e += T) {
+            const int16_t v = Aq[e];
+            sm.Aq[e] = v;
+            sm.A[e] = mulrn(mulrn((float)v, 0x1p-14f), k.ce);
+        }
+        const int16_t* hq = a.hq + (size_t)p * n;
+        for (int i = tid; i < n; i += T) {
+            const int16_t v = hq[i];
+            sm.hq[i] = v;
+            sm.h[i] = mulrn(mulrn((float)v, 0x1p-14f), k.ce);
+            sm.g[i] = a.g ? a.g[(size_t)p * n + i] : (int8_t)0;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += T) sm.nd[i] = -sm.A[i * n + i];
+    __syncthreads();
+
+    // Philox initial amplitudes of this thread's spins (k = row, n + row, 2n)
+    float x1[NS], x2[NS], e1[NS], e2[NS], xa, ea = 1.0f;
+    {
+        const uint64_t pg = a.problem_offset + (uint64_t)p;
+        const uint32_t c2 = (uint32_t)pg, c3 = (uint32_t)(pg >> 32);
+#pragma unroll
+        for (int b = 0; b < NS / 4; ++b) {
+            const U4 w1 = philox4x32_10(U4{(uint32_t)((row0 >> 2) + b), (uint32_t)run, c2, c3}, a.key0, a.key1);
+            const U4 w2 = philox4x32_10(U4{(uint32_t)(((n + row0) >> 2) + b), (uint32_t)run, c2, c3}, a.key0, a.key1);
+            const uint32_t v1[4] = {w1.x, w1.y, w1.z, w1.w}, v2[4] = {w2.x, w2.y, w2.z, w2.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                x1[4 * b + t] = mulrn((float)((int)(v1[t] >> 8) - 8388608), k.xs);
+                x2[4 * b + t] = mulrn((float)((int)(v2[t] >> 8) - 8388608), k.xs);
+                e1[4 * b + t] = 1.0f;
+                e2[4 * b + t] = 1.0f;
+            }
+        }
+        const U4 wa = philox4x32_10(U4{(uint32_t)((2 * n) >> 2), (uint32_t)run, c2, c3}, a.key0, a.key1);
+        xa = mulrn((float)((int)(wa.x >> 8) - 8388608), k.xs);  // 2n is a multiple of 4: word 0
+    }
+
+    const int S = a.steps;
+    int t = 0;
+#pragma unroll 1
+    for (; t + F <= S; t += F)
+        tuned_block<n, NS, TPA, PACKED, F>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
+    if (t < S) tuned_block<n, NS, TPA, PACKED, 0>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
+
+    // validity over the whole anneal
+    bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+        valid = valid && (fabsf(x1[i]) <= k.x_max) && (e1[i] > 0.0f) && (fabsf(x2[i]) <= k.x_max) && (e2[i] > 0.0f);
+#pragma unroll
+    for (int o = 1; o < TPA; o <<= 1) valid = __shfl_xor_sync(0xffffffffu, (int)valid, o) && valid;
+    // offsets of this thread's rows, then the whole anneal's (2-bit codes)
+    const int sa = xa >= 0.0f ? 1 : -1;
+    int dmine[NS];
+    uint64_t code = 0;  // 2-bit two's-complement offset per row
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const int s1 = x1[i] >= 0.0f ? 1 : -1, s2 = x2[i] >= 0.0f ? 1 : -1;
+        int di = sa * (s1 + s2) / 2;
+        if (a.level_max > 0) {
+            const int xv = (int)sm.g[row0 + i] + 2 * di;
+            if (xv > a.level_max || xv < -a.level_max) di = 0;
+        }
+        dmine[i] = di;
+        code |= (uint64_t)(di & 3) << (2 * i);
+    }
+    int d[n];
+    {
+        const int base = lane & ~(TPA - 1);
+#pragma unroll
+        for (int qq = 0; qq < TPA; ++qq) {
+            const uint64_t c = TPA == 1 ? code : __shfl_sync(0xffffffffu, code, base | qq);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                const int v = (int)((c >> (2 * i)) & 3u);
+                d[qq * NS + i] = v == 3 ? -1 : v;
+            }
+        }
+    }
+    // exact quantised energy: this thread's rows, then summed over the anneal
+    int E = 0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) r += (int)sm.Aq[(row0 + i) * n + j] * d[j];
+        E -= dmine[i] * r;
+        E -= (int)sm.hq[row0 + i] * dmine[i];
+    }
+#pragma unroll
+    for (int o = 1; o < TPA; o <<= 1) E += __shfl_xor_sync(0xffffffffu, E, o);
+    const bool keep = valid && E <= 0;
+    const int Ec = keep ? E : 0;
+    long long key = (long long)Ec * 4294967296LL + (long long)run;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long other = __shfl_xor_sync(0xffffffffu, key, o);
+        key = other < key ? other : key;
+    }
+    const unsigned divmask = __ballot_sync(0xffffffffu, !valid && q == 0);
+    if (lane == 0) {
+        skey[warp] = key;
+        sdiv[warp] = __popc(divmask);
+    }
+    __syncthreads();
+    long long best = skey[0];
+    int ndiv = sdiv[0];
+    for (int w = 1; w < T / 32; ++w) {
+        best = skey[w] < best ? skey[w] : best;
+        ndiv += sdiv[w];
+    }
+    const int best_run = (int)(best & 0xffffffffLL);
+    if (run == best_run) {
+        if (a.d_out) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) a.d_out[(size_t)p * n + row0 + i] = keep ? (int8_t)dmine[i] : (int8_t)0;
+        }
+        if (q == 0) {
+            const int bestE = (int)((best - (long long)best_run) / 4294967296LL);
+            if (a.E_out) a.E_out[p] = bestE;
+            if (a.run_out) a.run_out[p] = best_run;
+            if (a.ndiv_out) a.ndiv_out[p] = ndiv;
+            if (a.sym_out) {
+                const int side = 1 << (a.mod_bits >> 1), L = side - 1;
+                uint8_t* so = a.sym_out + (size_t)p * NT;
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    const int xr = (int)sm.g[i] + 2 * (keep ? d[i] : 0);
+                    const int xi = (int)sm.g[NT + i] + 2 * (keep ? d[NT + i] : 0);
+                    so[i] = (uint8_t)(((xr + L) / 2) * side + (xi + L) / 2);
+                }
+            }
+        }
+    }
+}
+
+// =========================================================================
 // Downlink VPP (Sec. 3.3) in FP64.
 // =========================================================================
 constexpr int kVppMaxNt = 64;
@@ -850,12 +1156,31 @@ cudaError_t launch_build_detect_impl(const BuildArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Tuned kernels exist for n_t in {4, 8, 16} and f_mvm in {1, 2}.
+__host__ __device__ constexpr bool tuned_size(int NT) { return NT == 4 || NT == 8 || NT == 16; }
+
+template <int NT, int F>
+cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t s) {
+    if constexpr (tuned_size(NT)) {
+        switch (variant) {
+        case kVariantTpa1: cac_solve_tuned_kernel<NT, F, 1, false><<<a.n_problems, runs, 0, s>>>(a); break;
+        case kVariantTpa1Packed: cac_solve_tuned_kernel<NT, F, 1, true><<<a.n_problems, runs, 0, s>>>(a); break;
+        case kVariantTpa2Packed: cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a); break;
+        default: cac_solve_kernel<NT, F><<<a.n_problems, runs, 0, s>>>(a); break;
+        }
+    } else {
+        cac_solve_kernel<NT, F><<<a.n_problems, runs, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 template <int NT>
 cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
-    if (a.f_mvm == 2) cac_solve_kernel<NT, 2><<<a.n_problems, runs, 0, s>>>(a);
-    else if (a.f_mvm == 1) cac_solve_kernel<NT, 1><<<a.n_problems, runs, 0, s>>>(a);
-    else cac_solve_kernel<NT, 0><<<a.n_problems, runs, 0, s>>>(a);
+    const int v = resolve_variant(NT, a.f_mvm, a.variant);
+    if (a.f_mvm == 2) return launch_tuned<NT, 2>(a, runs, v, s);
+    if (a.f_mvm == 1) return launch_tuned<NT, 1>(a, runs, v, s);
+    cac_solve_kernel<NT, 0><<<a.n_problems, runs, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -336,3 +336,45 @@ def test_bad_channel_index_is_flagged(mm):
     assert ctx.device_errors(clear=True) & 1
     assert ctx.device_errors(clear=True) == 0
     assert out["sym"].shape == (3, 4)
+
+
+# ---------------------------------------------------------- solver shapes
+@pytest.mark.parametrize("nt", [4, 8, 16])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("f_mvm,steps,runs", [(2, 200, 32), (1, 41, 64), (2, 77, 96)])
+def test_solver_shapes_bit_exact(mm, nt, variant, f_mvm, steps, runs):
+    """Every launch shape gives the oracle's bits (ragged step counts too)."""
+    pkg, ctx = mm
+    w = synth.uplink(600 + nt, nt, nt, 4, n_sub=7, n_sym=1, snr_db=13.0, hold="problem")
+    bs = [oracle.build_detect32(w["H"][p], w["y"][p], w["noise_var"][p], 4) for p in range(7)]
+    Aq = np.stack([b["Aq"] for b in bs])
+    hq = np.stack([b["hq"] for b in bs])
+    g = np.stack([b["g"] for b in bs]).astype(np.int8)
+    prm = pkg.Params.default(runs=runs, f_mvm=f_mvm, steps=steps)
+    ctx.set_solver_variant(nt, variant)
+    try:
+        assert ctx.solver_variant(nt, f_mvm) == variant
+        got = ctx.solve_ising(T(Aq), T(hq), prm, seed=4242, g=T(g), level_max=3)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_solver_variant(nt, 0)
+    ref = oracle.solve_batch(Aq, hq, g, 3, oparams(prm), 4242)
+    assert np.array_equal(got["d"].cpu().numpy(), ref["d"])
+    assert np.array_equal(got["E"].cpu().numpy(), ref["E"])
+    assert np.array_equal(got["run"].cpu().numpy(), ref["run"])
+    assert np.array_equal(got["ndiv"].cpu().numpy(), ref["n_div"])
+
+
+def test_autotuner_picks_a_compiled_shape(mm):
+    pkg, _ = mm
+    with pkg.Context(0) as ctx:
+        v, ms = ctx.autotune(pkg.Params.default(steps=40), 16, 2048)
+        assert v in ms and all(t > 0 for t in ms.values()) and set(ms) == {1, 2, 3, 4}
+        assert ms[v] == min(ms.values())
+        v4, ms4 = ctx.autotune(pkg.Params.default(steps=40), 3, 512)
+        assert v4 == 1 and set(ms4) == {1}
+        w = synth.uplink(9, 16, 16, 4, n_sub=4, n_sym=2)
+        prm = pkg.Params.default(steps=50)
+        got = _detect(ctx, w, prm, 3)
+    ref = oracle.detect_batch(w["H"], w["y"], w["noise_var"], 4, oparams(prm), 3, w["chan_index"])
+    assert np.array_equal(got["sym"], ref["sym"]) and np.array_equal(got["energy"], ref["E"])
