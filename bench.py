@@ -39,6 +39,9 @@ WORKLOADS = {
     "ul16x16_16qam_slot": (16, 16, 4, "iid", "subcarrier", 16.0),
     "ul8x8_16qam_slot_kron_prb": (8, 8, 4, "kron", "prb", 15.0),
 }
+# one slot each of 16x16 16-QAM, 16x16 64-QAM and 8x8 QPSK (i.i.d. Rayleigh), detected together
+MIXED = [(16, 16, 4, "iid", "subcarrier", 16.0), (16, 16, 6, "iid", "subcarrier", 24.0),
+         (8, 8, 2, "iid", "subcarrier", 10.0)]
 
 
 def solver_flops(P: int, n_t: int, runs: int, steps: int, f_mvm: int) -> float:
@@ -99,6 +102,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank value over all ranks (the step time of a weak-scaling
+    run is the slowest rank's); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank detects its own slot (own channels, symbols and noise)."""
+    return 2025 + rank
+
+
 def make_workload(name: str, seed: int, n_sub: int = synth.SUBCARRIERS_100MHZ_30KHZ):
     n_r, n_t, mb, model, hold, snr = WORKLOADS[name]
     return synth.uplink(seed, n_r, n_t, mb, n_sub=n_sub, snr_db=snr, model=model, hold=hold)
@@ -155,13 +175,170 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed(args):
+    """Three slots of different sizes (16x16 16-QAM, 16x16 64-QAM, 8x8 QPSK):
+    per-job path (one build + one solve launch per job) against one batched
+    persistent launch replayed from a CUDA graph."""
+    import torch
+
+    from paper_2510_01579_gb300 import Batch, Context, Params
+    dev = torch.device("cuda", 0)
+    prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
+    ctx = Context(0, workspace_bytes=512 << 20)
+    keep, jobs, outs, total = [], [], [], 0
+    for i, (n_r, n_t, mb, model, hold, snr) in enumerate(MIXED):
+        w = synth.uplink(3000 + i, n_r, n_t, mb, n_sub=args.subcarriers, snr_db=snr, model=model, hold=hold)
+        t = [torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index")]
+        P = w["y"].shape[0]
+        o = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev)}
+        keep += t + [o["sym"]]
+        outs.append(o)
+        jobs.append(ctx.detect_job(t[0], t[1], t[2], mb, 10 + i, o, t[3]))
+        total += P
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    per_job = timed(lambda: ctx.detect_jobs(jobs, prm))
+    ref = [o["sym"].clone() for o in outs]
+    clocks = ClockSampler(0)
+    with Batch(0, prm, jobs, keepalive=keep) as batch:
+        bt = timed(lambda: batch.run(use_graph=True))
+    clk = clocks.stop()
+    for o, r in zip(outs, ref):
+        if not torch.equal(o["sym"], r):
+            raise RuntimeError("batched and per-job paths disagree")
+    ms = statistics.mean(bt)
+    line = {"metric": "detections/s (mixed 16x16 16-QAM + 16x16 64-QAM + 8x8 QPSK slots, one launch)",
+            "value": total / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "mixed", "problems_per_step": total, "subcarriers": args.subcarriers,
+                       "runs": args.runs, "solver_steps": args.solver_steps,
+                       "l2": "flushed between steps (256 MiB write)"},
+            "per_job_path": {"ms_per_step": statistics.mean(per_job), "launches_per_step": 2 * len(jobs)},
+            "speedup_batched_vs_per_job": statistics.mean(per_job) / ms, "gpu_launches": args.steps,
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serve(args):
+    """Serving: Poisson arrivals of uplink jobs (one OFDM symbol each: 100-3276
+    subcarriers, 4x4 to 16x16, QPSK to 64-QAM, channel state resident on the
+    device) at `load` x measured capacity.  The continuous-batching server
+    (2 lanes, graph replay, memory admission) against the plain per-job path
+    (one mmgap_detect per job in arrival order on one stream)."""
+    import torch
+
+    from paper_2510_01579_gb300 import Context, Params, Server
+    dev = torch.device("cuda", 0)
+    prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
+    rng = np.random.default_rng(7)
+    ctx = Context(0, workspace_bytes=512 << 20)
+    pool, keep = [], []
+    for i in range(48):
+        n_t = int(rng.choice([4, 8, 16]))
+        mb = int(rng.choice([2, 4, 6]))
+        n_sub = int(rng.integers(100, 3277))
+        w = synth.uplink(5000 + i, n_t, n_t, mb, n_sub=n_sub, n_sym=1, snr_db=float(rng.uniform(5, 30)),
+                         model=str(rng.choice(["iid", "kron"])), hold="prb")
+        t = [torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index")]
+        o = {"sym": torch.empty((n_sub, n_t), dtype=torch.uint8, device=dev)}
+        keep += t + [o["sym"]]
+        pool.append((ctx.detect_job(t[0], t[1], t[2], mb, 60 + i, o, t[3]), n_sub))
+    # capacity: the whole pool through the per-job path, back to back
+    for _ in range(2):
+        ctx.detect_jobs([j for j, _ in pool], prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.detect_jobs([j for j, _ in pool], prm)
+    torch.cuda.synchronize()
+    pool_s = time.perf_counter() - t0
+    rate = args.load * len(pool) / pool_s  # jobs per second offered
+    n_jobs = max(len(pool), int(rate * args.serve_seconds))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
+    which = [i % len(pool) for i in range(n_jobs)]
+    total_problems = sum(pool[k][1] for k in which)
+    deadline = 500.0
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+
+    # continuous-batching server
+    clocks = ClockSampler(0)
+    with Server(0, prm, scratch_bytes=2 << 30, n_lanes=2, max_jobs_per_group=32, deadline_us=deadline) as srv:
+        srv.submit(pool[0][0])  # warm up (graph capture on both lanes)
+        srv.submit(pool[1][0])
+        time.sleep(0.2)
+        srv.stats(reset=True)
+        tks = []
+        start = time.perf_counter()
+        for a, k in zip(arrivals, which):
+            while time.perf_counter() - start < a:
+                pass
+            tks.append(srv.submit(pool[k][0]))
+        lat = [srv.wait(tk)["latency_us"] for tk in tks]
+        st = srv.stats()
+    clk = clocks.stop()
+    span = st["span_us"] / 1e6
+    served = {"value": total_problems / span, "jobs": n_jobs, "p50_us": pct(lat, 0.5), "p99_us": pct(lat, 0.99),
+              "deadline_misses": st["deadline_misses"], "groups": st["groups"], "max_group_jobs": st["max_group_jobs"]}
+
+    # plain per-job path: one launch pair per job, in arrival order, one stream
+    stream = torch.cuda.current_stream(dev)
+    ref_ev = torch.cuda.Event(enable_timing=True)
+    done = [torch.cuda.Event(enable_timing=True) for _ in range(n_jobs)]
+    torch.cuda.synchronize()
+    start = time.perf_counter()
+    ref_ev.record(stream)
+    for i, (a, k) in enumerate(zip(arrivals, which)):
+        while time.perf_counter() - start < a:
+            pass
+        ctx.detect_jobs([pool[k][0]], prm)
+        done[i].record(stream)
+    torch.cuda.synchronize()
+    plain_lat = [ref_ev.elapsed_time(done[i]) * 1e3 - arrivals[i] * 1e6 for i in range(n_jobs)]
+    plain_span = ref_ev.elapsed_time(done[-1]) / 1e3
+    plain = {"value": total_problems / plain_span, "p50_us": pct(plain_lat, 0.5), "p99_us": pct(plain_lat, 0.99),
+             "deadline_misses": int(sum(x > deadline for x in plain_lat))}
+    line = {"metric": "detections/s served (Poisson mixed-size uplink jobs); p50/p99 job latency",
+            "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": n_jobs, "warmup": 2,
+            "ms_per_step": span * 1e3 / n_jobs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve", "offered_load": args.load, "jobs": n_jobs,
+                       "job_sizes": "n_t in {4,8,16}, QPSK..64-QAM, 100-3276 subcarriers x 1 symbol",
+                       "arrival_rate_jobs_per_s": rate, "deadline_us": deadline, "lanes": 2,
+                       "runs": args.runs, "solver_steps": args.solver_steps},
+            "server": served, "plain_per_job_path": plain,
+            "p99_speedup_vs_plain": plain["p99_us"] / served["p99_us"], "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mmgap", choices=["mmgap", "reference"])
-    ap.add_argument("--workload", default="ul16x16_16qam_slot", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ul16x16_16qam_slot", choices=sorted(WORKLOADS) + ["mixed", "serve"])
+    ap.add_argument("--load", type=float, default=0.7, help="serve: offered load as a fraction of capacity")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: length of the arrival trace")
     ap.add_argument("--runs", type=int, default=32)
     ap.add_argument("--solver-steps", type=int, default=200)
     ap.add_argument("--f-mvm", type=int, default=2)
@@ -170,6 +347,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="solver launch shape (1 plain .. 4); default: autotuned at set-up")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-problem kernel")
+    ap.add_argument("--no-batch", action="store_true", help="skip timing the batched persistent launch")
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--subcarriers", type=int, default=synth.SUBCARRIERS_100MHZ_30KHZ,
                     help="subcarriers per slot (3276 = 100 MHz at 30 kHz; smaller only for profiling)")
@@ -181,6 +359,12 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "mixed":
+        run_mixed(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
 
     import torch
@@ -200,7 +384,7 @@ def main():
             dist.barrier()
 
     # each rank detects its own slot (different seed): weak scaling
-    w = make_workload(args.workload, 2025 + rank, args.subcarriers)
+    w = make_workload(args.workload, rank_seed(rank), args.subcarriers)
     P = w["y"].shape[0]
     n_t, mb = w["n_t"], w["mod_bits"]
     prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
@@ -253,11 +437,7 @@ def main():
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
     value = world * P * args.steps / (total_ms / 1e3)
 
@@ -304,11 +484,7 @@ def main():
             ee[i].record(stream)
         torch.cuda.synchronize()
         barrier()
-        e_total = sum(es[i].elapsed_time(ee[i]) for i in range(args.steps))
-        if world > 1:
-            t = torch.tensor([e_total], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_total = float(t.item())
+        e_total = max_over_ranks(sum(es[i].elapsed_time(ee[i]) for i in range(args.steps)), dev)
         if not torch.equal(hsym, out["sym"].cpu()):
             raise RuntimeError("host-buffer path disagrees with the device-resident path")
         e2e = {"value": world * P * args.steps / (e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -337,6 +513,34 @@ def main():
         ctx.set_solver_variant(n_t, variant)
         plain = {"ms_per_step": statistics.mean(pt), "value": P / (statistics.mean(pt) / 1e3),
                  "speedup_of_tuned": statistics.mean(pt) / ms_per_step}
+
+    # the batched persistent launch (fused build + anneal per warp, replayed
+    # from a CUDA graph) on the same slot
+    batched = None
+    if not args.no_batch:
+        from paper_2510_01579_gb300 import Batch
+        bout = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
+                "energy": torch.empty(P, dtype=torch.int32, device=dev)}
+        bjob = ctx.detect_job(H, y, nv, mb, 77, bout, ci)
+        with Batch(local, prm, [bjob], keepalive=(H, y, nv, ci, bout)) as batch:
+            for _ in range(args.warmup):
+                flush.zero_()
+                batch.run(use_graph=True)
+            torch.cuda.synchronize()
+            bt = []
+            for i in range(args.steps):
+                flush.zero_()
+                starts[i].record(stream)
+                batch.run(use_graph=True)
+                ends[i].record(stream)
+            torch.cuda.synchronize()
+            bt = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+        if not torch.equal(bout["sym"].cpu(), torch.from_numpy(sym)):
+            raise RuntimeError("batched and per-job paths disagree")
+        bsrt = sorted(bt)
+        batched = {"ms_per_step": statistics.mean(bt), "value": world * P / (statistics.mean(bt) / 1e3),
+                   "p99_ms": bsrt[min(len(bsrt) - 1, int(math.ceil(0.99 * len(bsrt))) - 1)],
+                   "launches_per_step": 1, "graph": True}
 
     # roofline of the dominant kernel (the CIM-CAC solver), from the library's
     # own CUDA events on the launching stream
@@ -374,6 +578,7 @@ def main():
             "ber": {"mmgap": ber, "mmse": ber_mmse},
             "solver_shape": {"chosen": VARIANT_NAMES[variant], "autotune_ms": tune_ms},
             "plain_path": plain,
+            "batched_path": batched,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 2 * chunks, "clocks": clk, "wall_s": wall}
     if rank == 0:

@@ -245,6 +245,85 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
                             float ms_out[5]);
 
 /*
+ * Batched persistent launch of mixed-size uplink jobs (no counterpart in the
+ * paper, which launches one fixed-size grid per kernel).
+ *
+ * mmgap_batch_create validates the jobs (n_t in {4, 8, 16}, n_r <= 64,
+ * runs = 32, f_mvm in {1, 2}), uploads a job table (largest users first) and
+ * sizes a persistent grid from the occupancy of the kernel.  Each warp then
+ * pulls problems from one atomic counter across all jobs, builds the
+ * delta-Ising problem of the resource element in shared memory (the Sec. 3.2
+ * pre-processing) and anneals it with 32 anneals on its 32 lanes (solver and
+ * post-processing), writing the same outputs as mmgap_detect, bit for bit.
+ * Job arrays are the caller's device memory and must stay valid for the life
+ * of the batch; their contents may change between runs.  The batch owns a
+ * small device table (allocated at create).
+ * mmgap_batch_run enqueues the whole batch on `stream` as one kernel launch;
+ * with use_graph != 0 the first run captures the launch into a CUDA graph (on
+ * a private stream) and this and later runs launch the graph on `stream`.
+ */
+typedef struct mmgap_batch mmgap_batch;
+mmgap_status mmgap_batch_create(mmgap_batch** batch, int device, const mmgap_params* params,
+                                const mmgap_detect_job* jobs, int n_jobs);
+mmgap_status mmgap_batch_run(mmgap_batch* batch, int use_graph, void* stream);
+mmgap_status mmgap_batch_destroy(mmgap_batch* batch);
+
+/*
+ * Serving loop with continuous batching (no counterpart in the paper, which
+ * times one batch; this is the slot-driven request path of a 5G receiver).
+ *
+ * Jobs are uplink detection jobs whose inputs are already on the device
+ * (channel state can stay resident across slots) and whose outputs are the
+ * caller's device memory; they must stay valid until the job completes.  A
+ * dispatcher thread admits queued jobs in arrival order into launch groups:
+ * a group goes to a free lane (a CUDA stream with its own job table and
+ * coupling scratch of scratch_bytes / n_lanes) and takes jobs while they fit
+ * that lane's scratch and limits (admission by memory).  Each group is one
+ * batched launch (as mmgap_batch_run, replayed from a CUDA graph when
+ * use_graph != 0); groups on different lanes overlap on the device, and jobs
+ * that arrive while others run are admitted as soon as a lane frees up.
+ * Results equal mmgap_detect's bit for bit, whatever the grouping.
+ * Latency = completion (host callback at the end of the group) - submission,
+ * on the host's steady clock.  deadline_us > 0 counts jobs over it;
+ * inject_delay_us > 0 delays every launch on the host (fault injection for
+ * tests: a stalled dispatcher).  Limits as mmgap_batch_create (n_t in
+ * {4, 8, 16} up to max_n_t, n_r <= max_n_r, runs = 32, f_mvm in {1, 2}).
+ */
+typedef struct mmgap_server mmgap_server;
+typedef struct {
+    int32_t n_lanes;                /* concurrent groups (streams), 1..16 */
+    int32_t max_jobs_per_group;
+    int64_t max_problems_per_group;
+    size_t scratch_bytes;           /* device memory budget for coupling scratch, split across lanes */
+    int32_t max_n_t, max_n_r;
+    double deadline_us;
+    double inject_delay_us;
+    int32_t use_graph;
+} mmgap_server_config;
+typedef struct {
+    uint64_t ticket;
+    int32_t status;                 /* MMGAP_OK when done */
+    double submit_us, start_us, done_us;
+} mmgap_job_info;
+typedef struct {
+    int64_t completed, problems, deadline_misses, groups, max_group_jobs, queued;
+    double p50_us, p99_us, max_us, mean_us, span_us;  /* latency percentiles; span = first submit .. last done */
+} mmgap_serve_stats;
+
+mmgap_status mmgap_server_create(mmgap_server** server, int device, const mmgap_params* params,
+                                 const mmgap_server_config* config);
+/* Queue a job (non-blocking).  MMGAP_ENOMEM if it could never fit a lane. */
+mmgap_status mmgap_server_submit(mmgap_server* server, const mmgap_detect_job* job, uint64_t* ticket);
+/* Wait for a job (timeout_us < 0: forever).  MMGAP_ETIMEOUT if not done in
+ * time (the job stays queued or running; wait again).  On completion the
+ * ticket is released and *info (may be NULL) gets its timestamps. */
+mmgap_status mmgap_server_wait(mmgap_server* server, uint64_t ticket, int64_t timeout_us, mmgap_job_info* info);
+/* Statistics of completed jobs since creation or the last reset. */
+mmgap_status mmgap_server_stats(mmgap_server* server, mmgap_serve_stats* out, int reset);
+/* Finish queued and running jobs, then stop and free the server. */
+mmgap_status mmgap_server_destroy(mmgap_server* server);
+
+/*
  * Uplink detection that allocates nothing (no counterpart in the paper; this
  * is a service to callers that cannot allocate device memory: a running
  * real-time slot loop, where cudaMalloc may synchronise the device and miss

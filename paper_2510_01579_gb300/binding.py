@@ -74,16 +74,46 @@ _lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), 
 _lib.mmgap_set_solver_variant.argtypes = [_vp, C.c_int, C.c_int]
 _lib.mmgap_get_solver_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
 _lib.mmgap_autotune.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+_lib.mmgap_batch_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int]
+_lib.mmgap_batch_run.argtypes = [_vp, C.c_int, _vp]
+_lib.mmgap_batch_destroy.argtypes = [_vp]
+
+
+class _ServerConfig(C.Structure):
+    _fields_ = [("n_lanes", C.c_int32), ("max_jobs_per_group", C.c_int32), ("max_problems_per_group", C.c_int64),
+                ("scratch_bytes", C.c_size_t), ("max_n_t", C.c_int32), ("max_n_r", C.c_int32),
+                ("deadline_us", C.c_double), ("inject_delay_us", C.c_double), ("use_graph", C.c_int32)]
+
+
+class _JobInfo(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("status", C.c_int32), ("submit_us", C.c_double), ("start_us", C.c_double),
+                ("done_us", C.c_double)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("problems", C.c_int64), ("deadline_misses", C.c_int64),
+                ("groups", C.c_int64), ("max_group_jobs", C.c_int64), ("queued", C.c_int64), ("p50_us", C.c_double),
+                ("p99_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double), ("span_us", C.c_double)]
+
+
+_lib.mmgap_server_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(_Params), C.POINTER(_ServerConfig)]
+_lib.mmgap_server_submit.argtypes = [_vp, C.POINTER(_DetectJob), C.POINTER(C.c_uint64)]
+_lib.mmgap_server_wait.argtypes = [_vp, C.c_uint64, C.c_int64, C.POINTER(_JobInfo)]
+_lib.mmgap_server_stats.argtypes = [_vp, C.POINTER(_ServerStats), C.c_int]
+_lib.mmgap_server_destroy.argtypes = [_vp]
 for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
            "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
            "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant", "mmgap_get_solver_variant",
-           "mmgap_autotune"):
+           "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run", "mmgap_batch_destroy", "mmgap_server_create",
+           "mmgap_server_submit", "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy"):
     getattr(_lib, _f).restype = C.c_int
 
 ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
                "mmgap_precode", "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing",
                "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant",
-               "mmgap_get_solver_variant", "mmgap_autotune")
+               "mmgap_get_solver_variant", "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run",
+               "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_wait",
+               "mmgap_server_stats", "mmgap_server_destroy")
 
 VARIANT_NAMES = {0: "default", 1: "plain", 2: "tpa1", 3: "tpa1-packed", 4: "tpa2-packed"}
 
@@ -314,3 +344,109 @@ class Context:
         f = C.c_int()
         self._raise(_lib.mmgap_device_errors(self._h, C.byref(f), 1 if clear else 0))
         return f.value
+
+
+class Batch:
+    """mmgap_batch: a fixed set of uplink jobs of mixed sizes run by one
+    persistent kernel launch (optionally replayed from a CUDA graph).  The
+    jobs' tensors must stay alive (and at the same addresses) for the life of
+    the batch; their contents may change between runs."""
+
+    def __init__(self, device: int, params: Params, jobs, keepalive=()):
+        self._keep = list(keepalive)
+        arr = (_DetectJob * len(jobs))(*jobs)
+        cp = params._c()
+        h = C.c_void_p()
+        st = _lib.mmgap_batch_create(C.byref(h), device, C.byref(cp), arr, len(jobs))
+        if st != OK:
+            raise MMGaPError(st, "mmgap_batch_create failed (see stderr)")
+        self._h = h
+        self.device = torch.device("cuda", device)
+
+    def run(self, use_graph: bool = False, stream=None):
+        s = torch.cuda.current_stream(self.device) if stream is None else stream
+        st = _lib.mmgap_batch_run(self._h, 1 if use_graph else 0, C.c_void_p(s.cuda_stream))
+        if st != OK:
+            raise MMGaPError(st, "mmgap_batch_run failed (see stderr)")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mmgap_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """mmgap_server: continuous-batching serving loop on one device.
+
+    submit() queues a detection job (device tensors, kept alive by the
+    caller or via `keepalive`) and returns a ticket; wait() blocks until it is
+    done (or raises MMGaPError with ETIMEOUT); stats() gives latency
+    percentiles of completed jobs."""
+
+    def __init__(self, device: int, params: Params, scratch_bytes: int = 1 << 30, n_lanes: int = 2,
+                 max_jobs_per_group: int = 64, max_problems_per_group: int = 1 << 20, max_n_t: int = 16,
+                 max_n_r: int = 16, deadline_us: float = 0.0, inject_delay_us: float = 0.0, use_graph: bool = True):
+        cfg = _ServerConfig(n_lanes, max_jobs_per_group, max_problems_per_group, scratch_bytes, max_n_t, max_n_r,
+                            deadline_us, inject_delay_us, 1 if use_graph else 0)
+        cp = params._c()
+        h = C.c_void_p()
+        st = _lib.mmgap_server_create(C.byref(h), device, C.byref(cp), C.byref(cfg))
+        if st != OK:
+            raise MMGaPError(st, "mmgap_server_create failed (see stderr)")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, job: _DetectJob, keepalive=None) -> int:
+        t = C.c_uint64()
+        st = _lib.mmgap_server_submit(self._h, C.byref(job), C.byref(t))
+        if st != OK:
+            raise MMGaPError(st, "mmgap_server_submit failed")
+        if keepalive is not None:
+            self._keep[t.value] = keepalive
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> dict:
+        info = _JobInfo()
+        st = _lib.mmgap_server_wait(self._h, ticket, timeout_us, C.byref(info))
+        if st != OK:
+            raise MMGaPError(st, f"ticket {ticket}")
+        self._keep.pop(ticket, None)
+        return {"submit_us": info.submit_us, "start_us": info.start_us, "done_us": info.done_us,
+                "latency_us": info.done_us - info.submit_us}
+
+    def stats(self, reset: bool = False) -> dict:
+        s = _ServerStats()
+        st = _lib.mmgap_server_stats(self._h, C.byref(s), 1 if reset else 0)
+        if st != OK:
+            raise MMGaPError(st, "server fault")
+        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mmgap_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

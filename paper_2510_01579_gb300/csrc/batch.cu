@@ -1,0 +1,328 @@
+// Batched launch of mixed-size uplink jobs (mmgap_batch_*).
+//
+// A batch is a fixed set of detection jobs (device inputs and outputs).  One
+// run = job-table upload, one builder kernel over every problem of every job
+// and one persistent solver kernel whose warps pull problems across all jobs
+// from one atomic counter, largest problems first, so jobs of different sizes
+// share the GPU instead of one pair of grids per job.  The run can be captured
+// once into a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mmgap.h"
+#include "batch.h"
+#include "kernels.cuh"
+
+using namespace mmgap;
+
+namespace mmgap {
+
+namespace {
+
+bool batch_nt(int nt) { return nt == 4 || nt == 8 || nt == 16; }
+
+int build_floats_for(int nt, int n_r) {
+    switch (nt) {
+    case 16: return build_smem_floats<16>(n_r);
+    case 8: return build_smem_floats<8>(n_r);
+    default: return build_smem_floats<4>(n_r);
+    }
+}
+
+template <int NTMAX>
+const void* solve_ptr(int f) {
+    return f == 1 ? (const void*)batch_solve_kernel<NTMAX, 1> : (const void*)batch_solve_kernel<NTMAX, 2>;
+}
+
+const void* pick_solve(int ntmax, int f) {
+    switch (ntmax) {
+    case 16: return solve_ptr<16>(f);
+    case 8: return solve_ptr<8>(f);
+    default: return solve_ptr<4>(f);
+    }
+}
+
+const void* pick_build(int ntmax) {
+    switch (ntmax) {
+    case 16: return (const void*)batch_build_kernel<16>;
+    case 8: return (const void*)batch_build_kernel<8>;
+    default: return (const void*)batch_build_kernel<4>;
+    }
+}
+
+constexpr int kBatchWarps = 4;
+constexpr size_t kScratchAlign = 256;
+size_t salign(size_t v) { return (v + kScratchAlign - 1) / kScratchAlign * kScratchAlign; }
+
+}  // namespace
+
+const char* BatchRunner::check_params(const mmgap_params& P) {
+    if (P.runs != 32) return "batched launch runs 32 anneals per problem (one warp)";
+    if (P.f_mvm != 1 && P.f_mvm != 2) return "batched launch supports f_mvm 1 or 2";
+    if (P.steps < 0 || P.steps > (1 << 20) || !(P.dt > 0.0f) || !(P.x_max > 0.0f)) return "bad solver parameters";
+    return nullptr;
+}
+
+const char* BatchRunner::check_job(const mmgap_detect_job& J) {
+    if (!batch_nt(J.n_t)) return "batched launch supports n_t 4, 8, 16";
+    if (J.n_r < 1 || J.n_r > kMaxNr) return "n_r out of [1, 64]";
+    if (!(J.mod_bits == 2 || J.mod_bits == 4 || J.mod_bits == 6)) return "mod_bits must be 2, 4 or 6";
+    if (J.n_problems < 0) return "n_problems < 0";
+    if (J.n_problems > 0 && (!J.H || !J.y || !J.noise_var || !J.sym_out || J.n_chan < 1)) return "NULL input/output";
+    if (J.n_problems > 0 && !J.chan_index && J.n_chan < J.n_problems) return "chan_index NULL needs n_chan >= n";
+    return nullptr;
+}
+
+size_t BatchRunner::scratch_bytes(int n_t, int n_problems) {
+    const size_t n = 2 * (size_t)n_t, P = (size_t)n_problems;
+    return salign(P * n * n * 2) + salign(P * n * 2) + salign(P * n);
+}
+
+cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r,
+                              int ntmax, int* err_word) {
+    device_ = device;
+    capacity_ = capacity_jobs;
+    capacity_problems_ = capacity_problems;
+    ntmax_ = ntmax;
+    err_word_ = err_word;
+    build_floats_ = 0;
+    for (int nt : {4, 8, 16})
+        if (nt <= ntmax) build_floats_ = std::max(build_floats_, build_floats_for(nt, max_n_r));
+    build_floats_ = (build_floats_ + 3) / 4 * 4;
+    build_smem_ = (size_t)kBuildWarps * build_floats_ * 4;
+    scratch_bytes_ = scratch;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_jobs_, sizeof(BatchJob) * (size_t)std::max(1, capacity_jobs))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d_head_, sizeof(BatchHeader))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&scratch_, std::max<size_t>(scratch, 256))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&h_jobs_, sizeof(BatchJob) * (size_t)std::max(1, capacity_jobs))) != cudaSuccess)
+        return e;
+    if ((e = cudaMallocHost(&h_head_, sizeof(BatchHeader))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(pick_build(ntmax), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem_)) !=
+        cudaSuccess)
+        return e;
+    int per_sm = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_solve(ntmax, 2), kBatchWarps * 32, 0)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+    grid_ = std::max(1, per_sm) * sms;
+    return cudaSuccess;
+}
+
+void BatchRunner::release() {
+    if (cap_stream_) cudaStreamDestroy(cap_stream_);
+    cap_stream_ = nullptr;
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    if (d_jobs_) cudaFree(d_jobs_);
+    if (d_head_) cudaFree(d_head_);
+    if (scratch_) cudaFree(scratch_);
+    scratch_ = nullptr;
+    if (h_jobs_) cudaFreeHost(h_jobs_);
+    if (h_head_) cudaFreeHost(h_head_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+    d_jobs_ = h_jobs_ = nullptr;
+    d_head_ = h_head_ = nullptr;
+}
+
+int BatchRunner::stage(const mmgap_detect_job* jobs, const int* order, int n_jobs) {
+    if (n_jobs > capacity_) return -1;
+    long long first = 0;
+    size_t off = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        const mmgap_detect_job& J = jobs[order ? order[i] : i];
+        BatchJob& B = h_jobs_[i];
+        B = BatchJob{};
+        B.b.H = J.H;
+        B.b.chan_index = J.chan_index;
+        B.b.y = J.y;
+        B.b.noise_var = J.noise_var;
+        B.b.n_r = J.n_r;
+        B.b.mod_bits = J.mod_bits;
+        B.b.n_problems = J.n_problems;
+        B.b.n_chan = J.chan_index ? J.n_chan : J.n_problems;
+        const double M = (double)(1 << J.mod_bits);
+        B.b.kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
+        B.b.kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
+        B.b.err = err_word_;
+        B.nt = J.n_t;
+        B.key0 = (uint32_t)J.seed;
+        B.key1 = (uint32_t)(J.seed >> 32);
+        B.first = first;
+        const size_t n = 2 * (size_t)J.n_t, P = (size_t)J.n_problems;
+        if (off + scratch_bytes(J.n_t, J.n_problems) > scratch_bytes_) return -2;
+        B.Aq = (int16_t*)(scratch_ + off);
+        B.hq = (int16_t*)(scratch_ + off + salign(P * n * n * 2));
+        B.g = (int8_t*)(scratch_ + off + salign(P * n * n * 2) + salign(P * n * 2));
+        off += scratch_bytes(J.n_t, J.n_problems);
+        B.sym_out = J.sym_out;
+        B.energy_out = J.energy_out;
+        B.guess_out = J.guess_out;
+        B.offset_out = J.offset_out;
+        B.ndiv_out = J.ndiv_out;
+        first += J.n_problems;
+    }
+    if (first > capacity_problems_) return -3;
+    h_head_->n_jobs = n_jobs;
+    h_head_->pad = 0;
+    h_head_->total = first;
+    h_head_->counter = 0;
+    return 0;
+}
+
+cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_jobs_, h_jobs_, sizeof(BatchJob) * (size_t)std::max(1, capacity_),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(d_head_, h_head_, sizeof(BatchHeader), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    BatchArgs a{};
+    a.jobs = d_jobs_;
+    a.head = d_head_;
+    a.steps = P.steps;
+    const double dt = P.dt, p = P.p, aa = P.a, zeta = P.zeta, eps = P.eps;
+    a.k.c1 = (float)(1.0 + dt * (p - 1.0));
+    a.k.cdt = (float)(-dt);
+    a.k.cz = (float)(-(dt * zeta));
+    a.k.c2 = (float)(1.0 + (dt * zeta) * aa);
+    a.k.ce = (float)(eps * dt);
+    a.k.xs = (float)((double)P.sigma0 * 0x1p-23);
+    a.k.x_max = P.x_max;
+    a.build_floats = build_floats_;
+    void* args[] = {&a};
+    // builder grid covers the batch's capacity; warps past the staged total exit at once
+    const long long bblocks = std::max(1LL, (capacity_problems_ + kBuildWarps - 1) / kBuildWarps);
+    if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3((unsigned)bblocks), dim3(kBuildWarps * 32), args, build_smem_,
+                              s)) != cudaSuccess)
+        return e;
+    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm), dim3(grid_), dim3(kBatchWarps * 32), args, 0, s);
+}
+
+cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_graph) {
+    if (!use_graph) return enqueue(P, s);
+    cudaError_t e;
+    if (exec_ && std::memcmp(&graph_params_, &P, sizeof P) != 0) {  // parameters are baked into the graph
+        cudaGraphExecDestroy(exec_);
+        cudaGraphDestroy(graph_);
+        exec_ = nullptr;
+        graph_ = nullptr;
+    }
+    if (!exec_) {
+        // capture on the runner's own stream (the caller's may be the legacy
+        // default stream, which cannot be captured); replay on the caller's
+        if (!cap_stream_ && (e = cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        cudaError_t le = enqueue(P, cap_stream_);
+        e = cudaStreamEndCapture(cap_stream_, &graph_);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        if ((e = cudaGraphInstantiate(&exec_, graph_, 0)) != cudaSuccess) return e;
+        graph_params_ = P;
+    }
+    return cudaGraphLaunch(exec_, s);
+}
+
+}  // namespace mmgap
+
+struct mmgap_batch {
+    mmgap::BatchRunner runner;
+    mmgap_params params{};
+    std::vector<mmgap_detect_job> jobs;
+    int* err_word = nullptr;
+    int device = 0;
+};
+
+extern "C" {
+
+mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_params* params,
+                                const mmgap_detect_job* jobs, int n_jobs) {
+    if (!out) return MMGAP_EINVAL;
+    *out = nullptr;
+    if (!params || n_jobs < 1 || !jobs) return MMGAP_EINVAL;
+    if (BatchRunner::check_params(*params)) {
+        fprintf(stderr, "mmgap_batch_create: %s\n", BatchRunner::check_params(*params));
+        return MMGAP_EUNSUPPORTED;
+    }
+    int ntmax = 4, max_n_r = 1;
+    long long total = 0;
+    size_t scratch = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        if (const char* why = BatchRunner::check_job(jobs[i])) {
+            fprintf(stderr, "mmgap_batch_create: job %d: %s\n", i, why);
+            return MMGAP_EUNSUPPORTED;
+        }
+        ntmax = std::max(ntmax, jobs[i].n_t);
+        max_n_r = std::max(max_n_r, jobs[i].n_r);
+        total += jobs[i].n_problems;
+        scratch += BatchRunner::scratch_bytes(jobs[i].n_t, jobs[i].n_problems);
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) return MMGAP_EINVAL;
+    auto* b = new (std::nothrow) mmgap_batch();
+    if (!b) return MMGAP_ENOMEM;
+    b->device = device;
+    b->params = *params;
+    b->jobs.assign(jobs, jobs + n_jobs);
+    mmgap_status st = MMGAP_OK;
+    if (cudaMalloc(&b->err_word, sizeof(int)) != cudaSuccess || cudaMemset(b->err_word, 0, sizeof(int)) != cudaSuccess)
+        st = MMGAP_ENOMEM;
+    if (st == MMGAP_OK && b->runner.init(device, n_jobs, total, scratch, max_n_r, ntmax, b->err_word) != cudaSuccess)
+        st = MMGAP_ENOMEM;
+    if (st == MMGAP_OK) {
+        // largest problems first, so the tail of the launch is made of small ones
+        std::vector<int> order(n_jobs);
+        for (int i = 0; i < n_jobs; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return jobs[x].n_t > jobs[y].n_t; });
+        if (b->runner.stage(jobs, order.data(), n_jobs) != 0) st = MMGAP_EINVAL;
+    }
+    if (st != MMGAP_OK) {
+        cudaGetLastError();
+        b->runner.release();
+        if (b->err_word) cudaFree(b->err_word);
+        delete b;
+        if (prev >= 0) cudaSetDevice(prev);
+        return st;
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    *out = b;
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_batch_run(mmgap_batch* b, int use_graph, void* stream) {
+    if (!b) return MMGAP_EINVAL;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    cudaError_t e = b->runner.run(b->params, (cudaStream_t)stream, use_graph != 0);
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mmgap_batch_run: %s\n", cudaGetErrorString(e));
+        return MMGAP_ECUDA;
+    }
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_batch_destroy(mmgap_batch* b) {
+    if (!b) return MMGAP_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    b->runner.release();
+    cudaFree(b->err_word);
+    delete b;
+    if (prev >= 0) cudaSetDevice(prev);
+    return MMGAP_OK;
+}
+
+}  // extern "C"

@@ -85,15 +85,23 @@ __host__ __device__ constexpr int build_smem_floats(int n_r) {
     return 2 * n_r * NT + 4 * NT * NT + 4 * n_r + 4 * NT + 4;
 }
 
+// Where one problem's build writes its results (global or shared memory).
+struct BuildOut {
+    int16_t* Aq;        // [n][n]
+    int16_t* hq;        // [n]
+    int8_t* g;          // [n]
+    float* G32;         // [n][n] or nullptr
+    float* h32;         // [n] or nullptr
+    int32_t* sigma_exp; // or nullptr
+};
+
+// Build problem p of `a` with one warp; ws = build_smem_floats<NT>(n_r)
+// floats of this warp's shared memory.
 template <int NT>
-__global__ void __launch_bounds__(kBuildWarps * 32) build_detect_kernel(BuildArgs a) {
-    extern __shared__ __align__(16) float smem[];
+__device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, int lane, float* ws, const BuildOut& o) {
     constexpr int n = 2 * NT;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * kBuildWarps + warp;
-    if (p >= a.n_problems) return;  // warp-uniform; no block-wide barrier below
     const int n_r = a.n_r;
-    float* Hs = smem + warp * build_smem_floats<NT>(n_r);
+    float* Hs = ws;
     float* Gc = Hs + 2 * n_r * NT;
     float* Lc = Gc + 2 * NT * NT;
     float* yv = Lc + 2 * NT * NT;
@@ -105,11 +113,12 @@ __global__ void __launch_bounds__(kBuildWarps * 32) build_detect_kernel(BuildArg
     const int c = a.chan_index ? a.chan_index[p] : p;
     if (c < 0 || c >= a.n_chan) {  // bad channel index: flag it, emit an all-zero problem
         if (lane == 0) atomicOr(a.err, kErrChanIndex);
-        for (int e = lane; e < n * n; e += 32) a.Aq[(size_t)p * n * n + e] = 0;
+        for (int e = lane; e < n * n; e += 32) o.Aq[e] = 0;
         for (int e = lane; e < n; e += 32) {
-            a.hq[(size_t)p * n + e] = 0;
-            a.g[(size_t)p * n + e] = 0;
+            o.hq[e] = 0;
+            o.g[e] = 0;
         }
+        __syncwarp();
         return;
     }
     const float* Hg = a.H + (size_t)c * 2 * n_r * NT;
@@ -291,30 +300,44 @@ __global__ void __launch_bounds__(kBuildWarps * 32) build_detect_kernel(BuildArg
     const bool finite = isfinite(mx);
     const float s = ldexpf(1.0f, kQBits - se);
 
-    int16_t* Aq = a.Aq + (size_t)p * n * n;
-    float* G32 = a.G32 ? a.G32 + (size_t)p * n * n : nullptr;
     for (int e = lane; e < n * n; e += 32) {
         const int i = e / n, j = e % n;
         const int ib = i % NT, jb = j % NT;
         const float re = Gc[2 * (ib * NT + jb)], im = Gc[2 * (ib * NT + jb) + 1];
         // G = [[Re G_c, -Im G_c], [Im G_c, Re G_c]]
         const float G = (i < NT) == (j < NT) ? re : (i < NT ? -im : im);
-        Aq[e] = finite ? (int16_t)(int)rintf(mulrn(-G, s)) : (int16_t)0;
-        if (G32) G32[e] = G;
+        o.Aq[e] = finite ? (int16_t)(int)rintf(mulrn(-G, s)) : (int16_t)0;
+        if (o.G32) o.G32[e] = G;
     }
     if (lane < NT) {
-        int16_t* hq = a.hq + (size_t)p * n;
-        hq[lane] = finite ? (int16_t)(int)rintf(mulrn(hre, s)) : (int16_t)0;
-        hq[NT + lane] = finite ? (int16_t)(int)rintf(mulrn(him, s)) : (int16_t)0;
-        int8_t* g = a.g + (size_t)p * n;
-        g[lane] = (int8_t)(int)gv[lane];
-        g[NT + lane] = (int8_t)(int)gv[NT + lane];
-        if (a.h32) {
-            a.h32[(size_t)p * n + lane] = hre;
-            a.h32[(size_t)p * n + NT + lane] = him;
+        o.hq[lane] = finite ? (int16_t)(int)rintf(mulrn(hre, s)) : (int16_t)0;
+        o.hq[NT + lane] = finite ? (int16_t)(int)rintf(mulrn(him, s)) : (int16_t)0;
+        o.g[lane] = (int8_t)(int)gv[lane];
+        o.g[NT + lane] = (int8_t)(int)gv[NT + lane];
+        if (o.h32) {
+            o.h32[lane] = hre;
+            o.h32[NT + lane] = him;
         }
     }
-    if (lane == 0 && a.sigma_exp) a.sigma_exp[p] = se;
+    if (lane == 0 && o.sigma_exp) *o.sigma_exp = se;
+    __syncwarp();
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kBuildWarps * 32) build_detect_kernel(BuildArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    constexpr int n = 2 * NT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * kBuildWarps + warp;
+    if (p >= a.n_problems) return;  // warp-uniform; no block-wide barrier below
+    BuildOut o;
+    o.Aq = a.Aq + (size_t)p * n * n;
+    o.hq = a.hq + (size_t)p * n;
+    o.g = a.g + (size_t)p * n;
+    o.G32 = a.G32 ? a.G32 + (size_t)p * n * n : nullptr;
+    o.h32 = a.h32 ? a.h32 + (size_t)p * n : nullptr;
+    o.sigma_exp = a.sigma_exp ? a.sigma_exp + p : nullptr;
+    build_problem_warp<NT>(a, p, lane, smem + warp * build_smem_floats<NT>(a.n_r), o);
 }
 
 // =========================================================================
@@ -879,6 +902,218 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
                     so[i] = (uint8_t)(((xr + L) / 2) * side + (xi + L) / 2);
                 }
             }
+        }
+    }
+}
+
+// =========================================================================
+// Batched launch of mixed-size uplink jobs, in two kernels replayed as one
+// graph.  The builder runs one warp per problem over the whole batch (all
+// jobs, all sizes) into batch scratch; the solver is persistent: warps pull
+// problems from one atomic counter over a device job table (largest users
+// first), stage the problem's Q14 couplings in shared memory and anneal it
+// with 32 anneals on the warp's 32 lanes (one thread per anneal, packed
+// FP32).  Results equal the per-job path bit for bit: the Philox counters use
+// each problem's index within its own job.
+// =========================================================================
+struct BatchJob {
+    BuildArgs b;            // inputs, n_r, mod_bits, n_problems, n_chan, kappa, err
+    int nt;
+    uint32_t key0, key1;
+    long long first;        // batch index of the job's problem 0
+    int16_t* Aq;            // scratch [P][n][n]
+    int16_t* hq;            // scratch [P][n]
+    int8_t* g;              // scratch [P][n]
+    uint8_t* sym_out;
+    int32_t* energy_out;
+    int8_t* guess_out;
+    int8_t* offset_out;
+    int32_t* ndiv_out;
+};
+
+struct BatchHeader {
+    int n_jobs;
+    int pad;
+    long long total;             // problems in the batch
+    unsigned long long counter;  // next problem to hand out (reset before each run)
+};
+
+struct BatchArgs {
+    const BatchJob* jobs;
+    BatchHeader* head;
+    int steps;
+    EulerConsts k;
+    int build_floats;       // builder shared memory per warp (floats)
+};
+
+template <int NTMAX>
+__host__ __device__ constexpr size_t batch_solve_bytes() {
+    return (sizeof(SolveSmem<NTMAX>) + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ int batch_find_job(const BatchJob* jobs, int n_jobs, long long w) {
+    int lo = 0, hi = n_jobs - 1;  // last job with first <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].first <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Builder over the whole batch: warp w of the grid builds problem w.
+template <int NTMAX>
+__global__ void __launch_bounds__(kBuildWarps * 32) batch_build_kernel(BatchArgs A) {
+    extern __shared__ __align__(16) float bws[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long w = (long long)blockIdx.x * kBuildWarps + warp;
+    if (w >= A.head->total) return;
+    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
+    const int p = (int)(w - J.first);
+    float* ws = bws + warp * A.build_floats;
+    const int n = 2 * J.nt;
+    BuildOut o{J.Aq + (size_t)p * n * n, J.hq + (size_t)p * n, J.g + (size_t)p * n, nullptr, nullptr, nullptr};
+    if (J.nt == 16) {
+        if constexpr (NTMAX >= 16) build_problem_warp<16>(J.b, p, lane, ws, o);
+    } else if (J.nt == 8) {
+        if constexpr (NTMAX >= 8) build_problem_warp<8>(J.b, p, lane, ws, o);
+    } else {
+        build_problem_warp<4>(J.b, p, lane, ws, o);
+    }
+}
+
+// Anneal one problem already built into sm (Aq, hq, g) with one warp.
+template <int NT, int F>
+__device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const BatchJob& J, int p, int lane,
+                                                 SolveSmem<NT>& sm) {
+    constexpr int n = 2 * NT;
+    const EulerConsts k = A.k;
+    for (int e = lane; e < n * n; e += 32) sm.A[e] = mulrn(mulrn((float)sm.Aq[e], 0x1p-14f), k.ce);
+    for (int i = lane; i < n; i += 32) sm.h[i] = mulrn(mulrn((float)sm.hq[i], 0x1p-14f), k.ce);
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) sm.nd[i] = -sm.A[i * n + i];
+    __syncwarp();
+    const int run = lane;
+    float x1[n], x2[n], e1[n], e2[n], xa, ea = 1.0f;
+    {
+        const uint32_t c2 = (uint32_t)p, c3 = 0u;
+#pragma unroll
+        for (int b = 0; b < n / 4; ++b) {
+            const U4 w1 = philox4x32_10(U4{(uint32_t)b, (uint32_t)run, c2, c3}, J.key0, J.key1);
+            const U4 w2 = philox4x32_10(U4{(uint32_t)((n >> 2) + b), (uint32_t)run, c2, c3}, J.key0, J.key1);
+            const uint32_t v1[4] = {w1.x, w1.y, w1.z, w1.w}, v2[4] = {w2.x, w2.y, w2.z, w2.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                x1[4 * b + t] = mulrn((float)((int)(v1[t] >> 8) - 8388608), k.xs);
+                x2[4 * b + t] = mulrn((float)((int)(v2[t] >> 8) - 8388608), k.xs);
+                e1[4 * b + t] = 1.0f;
+                e2[4 * b + t] = 1.0f;
+            }
+        }
+        const U4 wa = philox4x32_10(U4{(uint32_t)((2 * n) >> 2), (uint32_t)run, c2, c3}, J.key0, J.key1);
+        xa = mulrn((float)((int)(wa.x >> 8) - 8388608), k.xs);
+    }
+    const int S = A.steps;
+    int t = 0;
+#pragma unroll 1
+    for (; t + F <= S; t += F) tuned_block<n, n, 1, true, F>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, F, k);
+    if (t < S) tuned_block<n, n, 1, true, 0>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, S - t, k);
+
+    bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+        valid = valid && (fabsf(x1[i]) <= k.x_max) && (e1[i] > 0.0f) && (fabsf(x2[i]) <= k.x_max) && (e2[i] > 0.0f);
+    const int level_max = (1 << (J.b.mod_bits >> 1)) - 1;
+    const int sa = xa >= 0.0f ? 1 : -1;
+    int d[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int s1 = x1[i] >= 0.0f ? 1 : -1, s2 = x2[i] >= 0.0f ? 1 : -1;
+        int di = sa * (s1 + s2) / 2;
+        const int xv = (int)sm.g[i] + 2 * di;
+        if (xv > level_max || xv < -level_max) di = 0;
+        d[i] = di;
+    }
+    int E = 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) r += (int)sm.Aq[i * n + j] * d[j];
+        E -= d[i] * r;
+        E -= (int)sm.hq[i] * d[i];
+    }
+    const bool keep = valid && E <= 0;
+    const int Ec = keep ? E : 0;
+    long long key = (long long)Ec * 4294967296LL + (long long)run;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long other = __shfl_xor_sync(0xffffffffu, key, o);
+        key = other < key ? other : key;
+    }
+    const int ndiv = __popc(__ballot_sync(0xffffffffu, !valid));
+    const int best_run = (int)(key & 0xffffffffLL);
+    if (run == best_run) {
+        const int bestE = (int)((key - (long long)best_run) / 4294967296LL);
+        if (J.energy_out) J.energy_out[p] = bestE;
+        if (J.ndiv_out) J.ndiv_out[p] = ndiv;
+        if (J.offset_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) J.offset_out[(size_t)p * n + i] = keep ? (int8_t)d[i] : (int8_t)0;
+        }
+        if (J.guess_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) J.guess_out[(size_t)p * n + i] = sm.g[i];
+        }
+        const int side = 1 << (J.b.mod_bits >> 1), L = side - 1;
+        uint8_t* so = J.sym_out + (size_t)p * NT;
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+            const int xr = (int)sm.g[i] + 2 * (keep ? d[i] : 0);
+            const int xi = (int)sm.g[NT + i] + 2 * (keep ? d[NT + i] : 0);
+            so[i] = (uint8_t)(((xr + L) / 2) * side + (xi + L) / 2);
+        }
+    }
+    __syncwarp();  // the warp's shared memory is reused by its next problem
+}
+
+template <int NT, int F>
+__device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const BatchJob& J, int p, int lane,
+                                                    unsigned char* solve_mem) {
+    constexpr int n = 2 * NT;
+    SolveSmem<NT>& sm = *reinterpret_cast<SolveSmem<NT>*>(solve_mem);
+    const int16_t* Aq = J.Aq + (size_t)p * n * n;
+    for (int e = lane; e < n * n; e += 32) sm.Aq[e] = Aq[e];
+    for (int i = lane; i < n; i += 32) {
+        sm.hq[i] = J.hq[(size_t)p * n + i];
+        sm.g[i] = J.g[(size_t)p * n + i];
+    }
+    __syncwarp();
+    batch_solve_warp<NT, F>(A, J, p, lane, sm);
+}
+
+// Persistent solver over the batch: one warp per problem, problems handed
+// out by an atomic counter.
+template <int NTMAX, int F>
+__global__ void __launch_bounds__(128) batch_solve_kernel(BatchArgs A) {
+    __shared__ __align__(16) unsigned char ssm[4 * batch_solve_bytes<NTMAX>()];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* mine = ssm + (size_t)warp * batch_solve_bytes<NTMAX>();
+    const int n_jobs = A.head->n_jobs;
+    const long long total = A.head->total;
+    for (;;) {
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(&A.head->counter, 1ULL);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if ((long long)w >= total) break;
+        const BatchJob& J = A.jobs[batch_find_job(A.jobs, n_jobs, (long long)w)];
+        const int p = (int)((long long)w - J.first);
+        if (J.nt == 16) {
+            if constexpr (NTMAX >= 16) batch_solve_problem<16, F>(A, J, p, lane, mine);
+        } else if (J.nt == 8) {
+            if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, mine);
+        } else {
+            batch_solve_problem<4, F>(A, J, p, lane, mine);
         }
     }
 }

@@ -1,0 +1,99 @@
+"""Batched persistent launch (mixed sizes in one kernel, CUDA-graph replay)
+against the per-job path, bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _outs(P, n_t):
+    return {"sym": torch.full((P, n_t), 255, dtype=torch.uint8, device=DEV),
+            "energy": torch.full((P,), 9, dtype=torch.int32, device=DEV),
+            "guess": torch.zeros((P, 2 * n_t), dtype=torch.int8, device=DEV),
+            "offset": torch.zeros((P, 2 * n_t), dtype=torch.int8, device=DEV),
+            "ndiv": torch.full((P,), -1, dtype=torch.int32, device=DEV)}
+
+
+def _workloads():
+    return [synth.uplink(71, 16, 16, 4, n_sub=24, n_sym=14, snr_db=16.0),                 # 16x16 16-QAM
+            synth.uplink(72, 16, 16, 6, n_sub=12, n_sym=14, snr_db=24.0),                 # 16x16 64-QAM
+            synth.uplink(73, 8, 8, 2, n_sub=36, n_sym=14, snr_db=8.0, model="kron", hold="prb"),  # 8x8 QPSK
+            synth.uplink(74, 12, 8, 4, n_sub=5, n_sym=7, snr_db=12.0, hold="problem"),     # 12x8, H per problem
+            synth.uplink(75, 4, 4, 4, n_sub=9, n_sym=14, snr_db=14.0)]                    # 4x4 16-QAM
+
+
+def test_mixed_batch_equals_per_job_path():
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=90)
+    ws = _workloads()
+    with pkg.Context(0) as ctx:
+        tens, outs, jobs, refs = [], [], [], []
+        for i, w in enumerate(ws):
+            t = (T(w["H"]), T(w["y"]), T(w["noise_var"]), T(w["chan_index"]))
+            P = w["y"].shape[0]
+            o = _outs(P, w["n_t"])
+            tens.append(t)
+            outs.append(o)
+            jobs.append(ctx.detect_job(*t[:3], w["mod_bits"], 500 + i, o, t[3]))
+            r = _outs(P, w["n_t"])
+            ctx.detect_jobs([ctx.detect_job(*t[:3], w["mod_bits"], 500 + i, r, t[3])], prm)
+            refs.append(r)
+        with pkg.Batch(0, prm, jobs, keepalive=(tens, outs)) as b:
+            b.run()
+            torch.cuda.synchronize()
+        for i in range(len(ws)):
+            for k in refs[i]:
+                assert torch.equal(outs[i][k], refs[i][k]), (i, k)
+    # and against the oracle for a few problems of the 12x8 job
+    w = ws[3]
+    for p in (0, 17, 34):
+        b = oracle.build_detect32(w["H"][p], w["y"][p], w["noise_var"][p], 4)
+        r = oracle.cac_solve(b["Aq"], b["hq"], b["g"], 3, oracle.Params(steps=90), 503, p)
+        assert np.array_equal(outs[3]["sym"][p].cpu().numpy(), oracle.decode_detect(8, 4, b["g"], r["d"]))
+
+
+def test_graph_replay_sees_new_inputs():
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=60)
+    w1 = synth.uplink(81, 16, 16, 4, n_sub=10, n_sym=14)
+    w2 = synth.uplink(82, 16, 16, 4, n_sub=10, n_sym=14)
+    H, y, nv, ci = T(w1["H"]), T(w1["y"]), T(w1["noise_var"]), T(w1["chan_index"])
+    P = y.shape[0]
+    with pkg.Context(0) as ctx:
+        o = _outs(P, 16)
+        job = ctx.detect_job(H, y, nv, 4, 9, o, ci)
+        with pkg.Batch(0, prm, [job], keepalive=(H, y, nv, ci, o)) as b:
+            for w in (w1, w2, w1):
+                H.copy_(T(w["H"]))
+                y.copy_(T(w["y"]))
+                nv.copy_(T(w["noise_var"]))
+                b.run(use_graph=True)
+                torch.cuda.synchronize()
+                ref = ctx.detect(T(w["H"]), T(w["y"]), T(w["noise_var"]), 4, prm, 9, chan_index=ci)
+                torch.cuda.synchronize()
+                assert torch.equal(o["sym"], ref["sym"])
+
+
+def test_batch_rejects_unsupported_shapes():
+    import paper_2510_01579_gb300 as pkg
+    w = synth.uplink(83, 3, 3, 2, n_sub=2, n_sym=1)
+    with pkg.Context(0) as ctx:
+        o = _outs(2, 3)
+        job = ctx.detect_job(T(w["H"]), T(w["y"]), T(w["noise_var"]), 2, 1, o, T(w["chan_index"]))
+        with pytest.raises(pkg.MMGaPError):
+            pkg.Batch(0, pkg.Params.default(), [job])
+        w8 = synth.uplink(84, 8, 8, 2, n_sub=2, n_sym=1)
+        o8 = _outs(2, 8)
+        job8 = ctx.detect_job(T(w8["H"]), T(w8["y"]), T(w8["noise_var"]), 2, 1, o8, T(w8["chan_index"]))
+        with pytest.raises(pkg.MMGaPError):
+            pkg.Batch(0, pkg.Params.default(runs=64), [job8])

@@ -1,0 +1,93 @@
+"""Serving loop (continuous batching): every job's result is the same alone
+and in the mix; admission by memory; bounded waits and deadline accounting
+under a host-injected stall (no GPU fault involved)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _jobs(ctx, specs):
+    out = []
+    for i, (n_t, mb, n_sub, model, hold) in enumerate(specs):
+        w = synth.uplink(900 + i, n_t, n_t, mb, n_sub=n_sub, n_sym=1, snr_db=14.0, model=model, hold=hold)
+        t = [T(w[k]) for k in ("H", "y", "noise_var", "chan_index")]
+        P = w["y"].shape[0]
+        o = {"sym": torch.full((P, n_t), 255, dtype=torch.uint8, device=DEV),
+             "energy": torch.full((P,), 5, dtype=torch.int32, device=DEV),
+             "ndiv": torch.full((P,), -1, dtype=torch.int32, device=DEV)}
+        out.append((w, t, o, ctx.detect_job(t[0], t[1], t[2], mb, 40 + i, o, t[3])))
+    return out
+
+
+SPECS = [(16, 4, 300, "iid", "subcarrier"), (8, 2, 1200, "kron", "prb"), (4, 6, 500, "iid", "problem"),
+         (16, 6, 150, "iid", "problem"), (8, 4, 800, "iid", "subcarrier"), (4, 2, 2000, "iid", "subcarrier"),
+         (16, 4, 64, "kron", "prb"), (8, 6, 333, "iid", "problem")]
+
+
+def test_each_job_same_alone_and_in_the_mix():
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=80)
+    with pkg.Context(0) as ctx:
+        jobs = _jobs(ctx, SPECS)
+        refs = []
+        for w, t, o, job in jobs:  # alone, through mmgap_detect
+            r = {k: torch.empty_like(v) for k, v in o.items()}
+            ctx.detect_jobs([ctx.detect_job(t[0], t[1], t[2], w["mod_bits"], job.seed, r, t[3])], prm)
+            refs.append(r)
+        torch.cuda.synchronize()
+        # in the mix: all submitted at once; a budget that forces several groups per lane
+        with pkg.Server(0, prm, scratch_bytes=8 << 20, n_lanes=2, max_jobs_per_group=3) as srv:
+            tickets = [srv.submit(job) for _, _, _, job in jobs]
+            infos = [srv.wait(tk, timeout_us=60_000_000) for tk in tickets]
+            st = srv.stats()
+        for (w, t, o, job), r in zip(jobs, refs):
+            for k in o:
+                assert torch.equal(o[k], r[k]), k
+        assert st["completed"] == len(jobs) and st["groups"] >= 3 and st["max_group_jobs"] <= 3
+        assert st["problems"] == sum(w["y"].shape[0] for w, _, _, _ in jobs)
+        assert st["p50_us"] <= st["p99_us"] <= st["max_us"]
+        assert all(i["submit_us"] <= i["start_us"] <= i["done_us"] for i in infos)
+
+
+def test_admission_by_memory():
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=20)
+    with pkg.Context(0) as ctx:
+        jobs = _jobs(ctx, [(16, 4, 400, "iid", "problem")] * 4)
+        # one lane with room for exactly one of these jobs at a time
+        need = 400 * (32 * 32 * 2) + 3 * 256 + 400 * 96
+        with pkg.Server(0, prm, scratch_bytes=need + 1024, n_lanes=1) as srv:
+            tks = [srv.submit(j) for _, _, _, j in jobs]
+            for tk in tks:
+                srv.wait(tk)
+            st = srv.stats()
+            assert st["groups"] == 4 and st["max_group_jobs"] == 1
+            big = _jobs(ctx, [(16, 4, 2000, "iid", "problem")])[0][3]
+            with pytest.raises(pkg.MMGaPError) as e:
+                srv.submit(big)
+            assert e.value.status == 2  # MMGAP_ENOMEM: can never be admitted
+
+
+def test_stalled_dispatcher_times_out_and_misses_deadlines():
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=10)
+    with pkg.Context(0) as ctx:
+        jobs = _jobs(ctx, [(4, 2, 100, "iid", "problem")] * 2)
+        with pkg.Server(0, prm, n_lanes=1, deadline_us=1000.0, inject_delay_us=300_000.0) as srv:
+            tk = srv.submit(jobs[0][3])
+            with pytest.raises(pkg.MMGaPError) as e:
+                srv.wait(tk, timeout_us=1000)
+            assert e.value.status == 4  # MMGAP_ETIMEOUT, job still pending
+            info = srv.wait(tk, timeout_us=30_000_000)
+            assert info["latency_us"] >= 300_000.0
+            assert srv.stats()["deadline_misses"] == 1
