@@ -215,13 +215,16 @@ def run_mixed(args):
     per_job = timed(lambda: ctx.detect_jobs(jobs, prm))
     ref = [o["sym"].clone() for o in outs]
     clocks = ClockSampler(0)
-    with Batch(0, prm, jobs, keepalive=keep) as batch:
-        bt = timed(lambda: batch.run(use_graph=True))
+    modes = {}
+    for mode, persistent in (("grid", False), ("persistent", True)):
+        with Batch(0, prm, jobs, keepalive=keep, persistent=persistent) as batch:
+            modes[mode] = statistics.mean(timed(lambda: batch.run(use_graph=True)))
+        for o, r in zip(outs, ref):
+            if not torch.equal(o["sym"], r):
+                raise RuntimeError("batched and per-job paths disagree")
     clk = clocks.stop()
-    for o, r in zip(outs, ref):
-        if not torch.equal(o["sym"], r):
-            raise RuntimeError("batched and per-job paths disagree")
-    ms = statistics.mean(bt)
+    best = min(modes, key=modes.get)
+    ms = modes[best]
     line = {"metric": "detections/s (mixed 16x16 16-QAM + 16x16 64-QAM + 8x8 QPSK slots, one launch)",
             "value": total / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -229,8 +232,9 @@ def run_mixed(args):
             "config": {"workload": "mixed", "problems_per_step": total, "subcarriers": args.subcarriers,
                        "runs": args.runs, "solver_steps": args.solver_steps,
                        "l2": "flushed between steps (256 MiB write)"},
+            "batched_modes_ms": modes, "batched_mode": best,
             "per_job_path": {"ms_per_step": statistics.mean(per_job), "launches_per_step": 2 * len(jobs)},
-            "speedup_batched_vs_per_job": statistics.mean(per_job) / ms, "gpu_launches": args.steps,
+            "speedup_batched_vs_per_job": statistics.mean(per_job) / ms, "gpu_launches": 2 * args.steps,
             "clocks": clk}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -281,9 +285,12 @@ def run_serve(args):
 
     # continuous-batching server
     clocks = ClockSampler(0)
-    with Server(0, prm, scratch_bytes=2 << 30, n_lanes=2, max_jobs_per_group=32, deadline_us=deadline) as srv:
+    with Server(0, prm, scratch_bytes=2 << 30, n_lanes=args.lanes, max_jobs_per_group=32,
+                max_problems_per_group=1 << 16, deadline_us=deadline) as srv:
         srv.submit(pool[0][0])  # warm up (graph capture on both lanes)
         srv.submit(pool[1][0])
+        srv.submit(pool[2][0])
+        srv.submit(pool[3][0])
         time.sleep(0.2)
         srv.stats(reset=True)
         tks = []
@@ -322,7 +329,7 @@ def run_serve(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve", "offered_load": args.load, "jobs": n_jobs,
                        "job_sizes": "n_t in {4,8,16}, QPSK..64-QAM, 100-3276 subcarriers x 1 symbol",
-                       "arrival_rate_jobs_per_s": rate, "deadline_us": deadline, "lanes": 2,
+                       "arrival_rate_jobs_per_s": rate, "deadline_us": deadline, "lanes": args.lanes,
                        "runs": args.runs, "solver_steps": args.solver_steps},
             "server": served, "plain_per_job_path": plain,
             "p99_speedup_vs_plain": plain["p99_us"] / served["p99_us"], "clocks": clk}
@@ -339,6 +346,7 @@ def main():
     ap.add_argument("--workload", default="ul16x16_16qam_slot", choices=sorted(WORKLOADS) + ["mixed", "serve"])
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load as a fraction of capacity")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: length of the arrival trace")
+    ap.add_argument("--lanes", type=int, default=4, help="serve: concurrent launch groups (streams)")
     ap.add_argument("--runs", type=int, default=32)
     ap.add_argument("--solver-steps", type=int, default=200)
     ap.add_argument("--f-mvm", type=int, default=2)
@@ -519,28 +527,29 @@ def main():
     batched = None
     if not args.no_batch:
         from paper_2510_01579_gb300 import Batch
-        bout = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
-                "energy": torch.empty(P, dtype=torch.int32, device=dev)}
-        bjob = ctx.detect_job(H, y, nv, mb, 77, bout, ci)
-        with Batch(local, prm, [bjob], keepalive=(H, y, nv, ci, bout)) as batch:
-            for _ in range(args.warmup):
-                flush.zero_()
-                batch.run(use_graph=True)
-            torch.cuda.synchronize()
-            bt = []
-            for i in range(args.steps):
-                flush.zero_()
-                starts[i].record(stream)
-                batch.run(use_graph=True)
-                ends[i].record(stream)
-            torch.cuda.synchronize()
-            bt = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
-        if not torch.equal(bout["sym"].cpu(), torch.from_numpy(sym)):
-            raise RuntimeError("batched and per-job paths disagree")
-        bsrt = sorted(bt)
-        batched = {"ms_per_step": statistics.mean(bt), "value": world * P / (statistics.mean(bt) / 1e3),
-                   "p99_ms": bsrt[min(len(bsrt) - 1, int(math.ceil(0.99 * len(bsrt))) - 1)],
-                   "launches_per_step": 1, "graph": True}
+        batched = {}
+        for mode, persistent in (("grid", False), ("persistent", True)):
+            bout = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
+                    "energy": torch.empty(P, dtype=torch.int32, device=dev)}
+            bjob = ctx.detect_job(H, y, nv, mb, 77, bout, ci)
+            with Batch(local, prm, [bjob], keepalive=(H, y, nv, ci, bout), persistent=persistent) as batch:
+                for _ in range(args.warmup):
+                    flush.zero_()
+                    batch.run(use_graph=True)
+                torch.cuda.synchronize()
+                for i in range(args.steps):
+                    flush.zero_()
+                    starts[i].record(stream)
+                    batch.run(use_graph=True)
+                    ends[i].record(stream)
+                torch.cuda.synchronize()
+                bt = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+            if not torch.equal(bout["sym"].cpu(), torch.from_numpy(sym)):
+                raise RuntimeError("batched and per-job paths disagree")
+            bsrt = sorted(bt)
+            batched[mode] = {"ms_per_step": statistics.mean(bt), "value": world * P / (statistics.mean(bt) / 1e3),
+                             "p99_ms": bsrt[min(len(bsrt) - 1, int(math.ceil(0.99 * len(bsrt))) - 1)],
+                             "graph": True}
 
     # roofline of the dominant kernel (the CIM-CAC solver), from the library's
     # own CUDA events on the launching stream

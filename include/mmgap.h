@@ -249,12 +249,14 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
  * paper, which launches one fixed-size grid per kernel).
  *
  * mmgap_batch_create validates the jobs (n_t in {4, 8, 16}, n_r <= 64,
- * runs = 32, f_mvm in {1, 2}), uploads a job table (largest users first) and
- * sizes a persistent grid from the occupancy of the kernel.  Each warp then
- * pulls problems from one atomic counter across all jobs, builds the
- * delta-Ising problem of the resource element in shared memory (the Sec. 3.2
- * pre-processing) and anneals it with 32 anneals on its 32 lanes (solver and
- * post-processing), writing the same outputs as mmgap_detect, bit for bit.
+ * runs = 32, f_mvm in {1, 2}) and uploads a job table (largest users first).
+ * A run is one builder kernel over every problem of every job (the Sec. 3.2
+ * pre-processing, one warp per resource element) into batch-owned scratch,
+ * then one solver kernel that anneals each problem with 32 anneals on the 32
+ * lanes of a warp (solver and post-processing): either one CTA per problem
+ * (flags 0) or, with MMGAP_BATCH_PERSISTENT, a grid sized from the kernel's
+ * occupancy whose warps pull problems from one atomic counter across all
+ * jobs.  Outputs equal mmgap_detect's bit for bit.
  * Job arrays are the caller's device memory and must stay valid for the life
  * of the batch; their contents may change between runs.  The batch owns a
  * small device table (allocated at create).
@@ -263,8 +265,9 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
  * a private stream) and this and later runs launch the graph on `stream`.
  */
 typedef struct mmgap_batch mmgap_batch;
+#define MMGAP_BATCH_PERSISTENT 1 /* flags: persistent solver warps on an atomic counter (else one CTA per problem) */
 mmgap_status mmgap_batch_create(mmgap_batch** batch, int device, const mmgap_params* params,
-                                const mmgap_detect_job* jobs, int n_jobs);
+                                const mmgap_detect_job* jobs, int n_jobs, int flags);
 mmgap_status mmgap_batch_run(mmgap_batch* batch, int use_graph, void* stream);
 mmgap_status mmgap_batch_destroy(mmgap_batch* batch);
 
@@ -299,6 +302,7 @@ typedef struct {
     double deadline_us;
     double inject_delay_us;
     int32_t use_graph;
+    int32_t persistent;             /* solver mode of each group, as MMGAP_BATCH_PERSISTENT */
 } mmgap_server_config;
 typedef struct {
     uint64_t ticket;

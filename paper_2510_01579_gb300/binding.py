@@ -74,7 +74,8 @@ _lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), 
 _lib.mmgap_set_solver_variant.argtypes = [_vp, C.c_int, C.c_int]
 _lib.mmgap_get_solver_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
 _lib.mmgap_autotune.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
-_lib.mmgap_batch_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int]
+_lib.mmgap_batch_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int,
+                                    C.c_int]
 _lib.mmgap_batch_run.argtypes = [_vp, C.c_int, _vp]
 _lib.mmgap_batch_destroy.argtypes = [_vp]
 
@@ -82,7 +83,8 @@ _lib.mmgap_batch_destroy.argtypes = [_vp]
 class _ServerConfig(C.Structure):
     _fields_ = [("n_lanes", C.c_int32), ("max_jobs_per_group", C.c_int32), ("max_problems_per_group", C.c_int64),
                 ("scratch_bytes", C.c_size_t), ("max_n_t", C.c_int32), ("max_n_r", C.c_int32),
-                ("deadline_us", C.c_double), ("inject_delay_us", C.c_double), ("use_graph", C.c_int32)]
+                ("deadline_us", C.c_double), ("inject_delay_us", C.c_double), ("use_graph", C.c_int32),
+                ("persistent", C.c_int32)]
 
 
 class _JobInfo(C.Structure):
@@ -352,12 +354,12 @@ class Batch:
     jobs' tensors must stay alive (and at the same addresses) for the life of
     the batch; their contents may change between runs."""
 
-    def __init__(self, device: int, params: Params, jobs, keepalive=()):
+    def __init__(self, device: int, params: Params, jobs, keepalive=(), persistent: bool = False):
         self._keep = list(keepalive)
         arr = (_DetectJob * len(jobs))(*jobs)
         cp = params._c()
         h = C.c_void_p()
-        st = _lib.mmgap_batch_create(C.byref(h), device, C.byref(cp), arr, len(jobs))
+        st = _lib.mmgap_batch_create(C.byref(h), device, C.byref(cp), arr, len(jobs), 1 if persistent else 0)
         if st != OK:
             raise MMGaPError(st, "mmgap_batch_create failed (see stderr)")
         self._h = h
@@ -397,9 +399,10 @@ class Server:
 
     def __init__(self, device: int, params: Params, scratch_bytes: int = 1 << 30, n_lanes: int = 2,
                  max_jobs_per_group: int = 64, max_problems_per_group: int = 1 << 20, max_n_t: int = 16,
-                 max_n_r: int = 16, deadline_us: float = 0.0, inject_delay_us: float = 0.0, use_graph: bool = True):
+                 max_n_r: int = 16, deadline_us: float = 0.0, inject_delay_us: float = 0.0, use_graph: bool = True,
+                 persistent: bool = False):
         cfg = _ServerConfig(n_lanes, max_jobs_per_group, max_problems_per_group, scratch_bytes, max_n_t, max_n_r,
-                            deadline_us, inject_delay_us, 1 if use_graph else 0)
+                            deadline_us, inject_delay_us, 1 if use_graph else 0, 1 if persistent else 0)
         cp = params._c()
         h = C.c_void_p()
         st = _lib.mmgap_server_create(C.byref(h), device, C.byref(cp), C.byref(cfg))

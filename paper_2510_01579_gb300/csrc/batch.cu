@@ -35,15 +35,17 @@ int build_floats_for(int nt, int n_r) {
 }
 
 template <int NTMAX>
-const void* solve_ptr(int f) {
-    return f == 1 ? (const void*)batch_solve_kernel<NTMAX, 1> : (const void*)batch_solve_kernel<NTMAX, 2>;
+const void* solve_ptr(int f, bool persistent) {
+    if (persistent)
+        return f == 1 ? (const void*)batch_solve_kernel<NTMAX, 1> : (const void*)batch_solve_kernel<NTMAX, 2>;
+    return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1> : (const void*)batch_solve_grid_kernel<NTMAX, 2>;
 }
 
-const void* pick_solve(int ntmax, int f) {
+const void* pick_solve(int ntmax, int f, bool persistent) {
     switch (ntmax) {
-    case 16: return solve_ptr<16>(f);
-    case 8: return solve_ptr<8>(f);
-    default: return solve_ptr<4>(f);
+    case 16: return solve_ptr<16>(f, persistent);
+    case 8: return solve_ptr<8>(f, persistent);
+    default: return solve_ptr<4>(f, persistent);
     }
 }
 
@@ -84,8 +86,9 @@ size_t BatchRunner::scratch_bytes(int n_t, int n_problems) {
 }
 
 cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r,
-                              int ntmax, int* err_word) {
+                              int ntmax, int* err_word, bool persistent) {
     device_ = device;
+    persistent_ = persistent;
     capacity_ = capacity_jobs;
     capacity_problems_ = capacity_problems;
     ntmax_ = ntmax;
@@ -106,12 +109,16 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
     if ((e = cudaFuncSetAttribute(pick_build(ntmax), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem_)) !=
         cudaSuccess)
         return e;
-    int per_sm = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_solve(ntmax, 2), kBatchWarps * 32, 0)) !=
+    int per_sm = 0, sms = 0, bper_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_solve(ntmax, 2, true), kBatchWarps * 32, 0)) !=
         cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bper_sm, pick_build(ntmax), kBuildWarps * 32,
+                                                           build_smem_)) != cudaSuccess)
         return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
     grid_ = std::max(1, per_sm) * sms;
+    build_grid_max_ = std::max(1, bper_sm) * sms;
     return cudaSuccess;
 }
 
@@ -177,6 +184,13 @@ int BatchRunner::stage(const mmgap_detect_job* jobs, const int* order, int n_job
     return 0;
 }
 
+void BatchRunner::grids(unsigned* build_grid, unsigned* solve_grid) const {
+    const long long total = h_head_ ? h_head_->total : capacity_problems_;
+    const long long bb = (std::max(1LL, total) + kBuildWarps - 1) / kBuildWarps;
+    *build_grid = (unsigned)std::min<long long>(bb, build_grid_max_);
+    *solve_grid = persistent_ ? (unsigned)grid_ : (unsigned)std::max(1LL, total);
+}
+
 cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaMemcpyAsync(d_jobs_, h_jobs_, sizeof(BatchJob) * (size_t)std::max(1, capacity_),
@@ -184,7 +198,8 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
         return e;
     if ((e = cudaMemcpyAsync(d_head_, h_head_, sizeof(BatchHeader), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;
-    BatchArgs a{};
+    BatchArgs& a = args_;
+    a = BatchArgs{};
     a.jobs = d_jobs_;
     a.head = d_head_;
     a.steps = P.steps;
@@ -198,12 +213,13 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     a.k.x_max = P.x_max;
     a.build_floats = build_floats_;
     void* args[] = {&a};
-    // builder grid covers the batch's capacity; warps past the staged total exit at once
-    const long long bblocks = std::max(1LL, (capacity_problems_ + kBuildWarps - 1) / kBuildWarps);
-    if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3((unsigned)bblocks), dim3(kBuildWarps * 32), args, build_smem_,
-                              s)) != cudaSuccess)
+    unsigned bg, sg;
+    grids(&bg, &sg);
+    if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3(bg), dim3(kBuildWarps * 32), args, build_smem_, s)) !=
+        cudaSuccess)
         return e;
-    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm), dim3(grid_), dim3(kBatchWarps * 32), args, 0, s);
+    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, persistent_), dim3(sg),
+                            dim3(persistent_ ? kBatchWarps * 32 : 32), args, 0, s);
 }
 
 cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_graph) {
@@ -227,6 +243,40 @@ cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_gra
         if (e != cudaSuccess) return e;
         if ((e = cudaGraphInstantiate(&exec_, graph_, 0)) != cudaSuccess) return e;
         graph_params_ = P;
+        // remember the two kernel nodes so each replay can size their grids
+        build_node_ = solve_node_ = nullptr;
+        size_t count = 0;
+        if ((e = cudaGraphGetNodes(graph_, nullptr, &count)) != cudaSuccess) return e;
+        std::vector<cudaGraphNode_t> nodes(count);
+        if ((e = cudaGraphGetNodes(graph_, nodes.data(), &count)) != cudaSuccess) return e;
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+            if (kp.func == pick_build(ntmax_)) build_node_ = nd;
+            else solve_node_ = nd;
+        }
+        if (!build_node_ || !solve_node_) return cudaErrorInvalidValue;
+    } else {
+        // grids follow the staged total; the kernel arguments are unchanged
+        unsigned bg, sg;
+        grids(&bg, &sg);
+        void* args[] = {&args_};
+        cudaKernelNodeParams kb{};
+        kb.func = (void*)pick_build(ntmax_);
+        kb.gridDim = dim3(bg);
+        kb.blockDim = dim3(kBuildWarps * 32);
+        kb.sharedMemBytes = (unsigned)build_smem_;
+        kb.kernelParams = args;
+        if ((e = cudaGraphExecKernelNodeSetParams(exec_, build_node_, &kb)) != cudaSuccess) return e;
+        cudaKernelNodeParams ks{};
+        ks.func = (void*)pick_solve(ntmax_, P.f_mvm, persistent_);
+        ks.gridDim = dim3(sg);
+        ks.blockDim = dim3(persistent_ ? kBatchWarps * 32 : 32);
+        ks.sharedMemBytes = 0;
+        ks.kernelParams = args;
+        if ((e = cudaGraphExecKernelNodeSetParams(exec_, solve_node_, &ks)) != cudaSuccess) return e;
     }
     return cudaGraphLaunch(exec_, s);
 }
@@ -244,7 +294,7 @@ struct mmgap_batch {
 extern "C" {
 
 mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_params* params,
-                                const mmgap_detect_job* jobs, int n_jobs) {
+                                const mmgap_detect_job* jobs, int n_jobs, int flags) {
     if (!out) return MMGAP_EINVAL;
     *out = nullptr;
     if (!params || n_jobs < 1 || !jobs) return MMGAP_EINVAL;
@@ -276,7 +326,8 @@ mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_param
     mmgap_status st = MMGAP_OK;
     if (cudaMalloc(&b->err_word, sizeof(int)) != cudaSuccess || cudaMemset(b->err_word, 0, sizeof(int)) != cudaSuccess)
         st = MMGAP_ENOMEM;
-    if (st == MMGAP_OK && b->runner.init(device, n_jobs, total, scratch, max_n_r, ntmax, b->err_word) != cudaSuccess)
+    if (st == MMGAP_OK && b->runner.init(device, n_jobs, total, scratch, max_n_r, ntmax, b->err_word,
+                                         (flags & MMGAP_BATCH_PERSISTENT) != 0) != cudaSuccess)
         st = MMGAP_ENOMEM;
     if (st == MMGAP_OK) {
         // largest problems first, so the tail of the launch is made of small ones

@@ -966,19 +966,22 @@ template <int NTMAX>
 __global__ void __launch_bounds__(kBuildWarps * 32) batch_build_kernel(BatchArgs A) {
     extern __shared__ __align__(16) float bws[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long w = (long long)blockIdx.x * kBuildWarps + warp;
-    if (w >= A.head->total) return;
-    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
-    const int p = (int)(w - J.first);
+    const long long total = A.head->total;
+    const int n_jobs = A.head->n_jobs;
     float* ws = bws + warp * A.build_floats;
-    const int n = 2 * J.nt;
-    BuildOut o{J.Aq + (size_t)p * n * n, J.hq + (size_t)p * n, J.g + (size_t)p * n, nullptr, nullptr, nullptr};
-    if (J.nt == 16) {
-        if constexpr (NTMAX >= 16) build_problem_warp<16>(J.b, p, lane, ws, o);
-    } else if (J.nt == 8) {
-        if constexpr (NTMAX >= 8) build_problem_warp<8>(J.b, p, lane, ws, o);
-    } else {
-        build_problem_warp<4>(J.b, p, lane, ws, o);
+    for (long long w = (long long)blockIdx.x * kBuildWarps + warp; w < total;
+         w += (long long)gridDim.x * kBuildWarps) {
+        const BatchJob& J = A.jobs[batch_find_job(A.jobs, n_jobs, w)];
+        const int p = (int)(w - J.first);
+        const int n = 2 * J.nt;
+        BuildOut o{J.Aq + (size_t)p * n * n, J.hq + (size_t)p * n, J.g + (size_t)p * n, nullptr, nullptr, nullptr};
+        if (J.nt == 16) {
+            if constexpr (NTMAX >= 16) build_problem_warp<16>(J.b, p, lane, ws, o);
+        } else if (J.nt == 8) {
+            if constexpr (NTMAX >= 8) build_problem_warp<8>(J.b, p, lane, ws, o);
+        } else {
+            build_problem_warp<4>(J.b, p, lane, ws, o);
+        }
     }
 }
 
@@ -1090,6 +1093,25 @@ __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const Ba
     }
     __syncwarp();
     batch_solve_warp<NT, F>(A, J, p, lane, sm);
+}
+
+// Grid solver over the batch: one 32-thread CTA per problem (the hardware
+// CTA scheduler balances sizes); CTAs past the staged total exit.
+template <int NTMAX, int F>
+__global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
+    __shared__ __align__(16) unsigned char ssm[batch_solve_bytes<NTMAX>()];
+    const long long w = blockIdx.x;
+    if (w >= A.head->total) return;
+    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
+    const int p = (int)(w - J.first);
+    const int lane = threadIdx.x;
+    if (J.nt == 16) {
+        if constexpr (NTMAX >= 16) batch_solve_problem<16, F>(A, J, p, lane, ssm);
+    } else if (J.nt == 8) {
+        if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, ssm);
+    } else {
+        batch_solve_problem<4, F>(A, J, p, lane, ssm);
+    }
 }
 
 // Persistent solver over the batch: one warp per problem, problems handed

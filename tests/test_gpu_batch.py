@@ -32,7 +32,8 @@ def _workloads():
             synth.uplink(75, 4, 4, 4, n_sub=9, n_sym=14, snr_db=14.0)]                    # 4x4 16-QAM
 
 
-def test_mixed_batch_equals_per_job_path():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_mixed_batch_equals_per_job_path(persistent):
     import paper_2510_01579_gb300 as pkg
     prm = pkg.Params.default(steps=90)
     ws = _workloads()
@@ -48,7 +49,7 @@ def test_mixed_batch_equals_per_job_path():
             r = _outs(P, w["n_t"])
             ctx.detect_jobs([ctx.detect_job(*t[:3], w["mod_bits"], 500 + i, r, t[3])], prm)
             refs.append(r)
-        with pkg.Batch(0, prm, jobs, keepalive=(tens, outs)) as b:
+        with pkg.Batch(0, prm, jobs, keepalive=(tens, outs), persistent=persistent) as b:
             b.run()
             torch.cuda.synchronize()
         for i in range(len(ws)):
@@ -62,7 +63,8 @@ def test_mixed_batch_equals_per_job_path():
         assert np.array_equal(outs[3]["sym"][p].cpu().numpy(), oracle.decode_detect(8, 4, b["g"], r["d"]))
 
 
-def test_graph_replay_sees_new_inputs():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_graph_replay_sees_new_inputs(persistent):
     import paper_2510_01579_gb300 as pkg
     prm = pkg.Params.default(steps=60)
     w1 = synth.uplink(81, 16, 16, 4, n_sub=10, n_sym=14)
@@ -72,7 +74,7 @@ def test_graph_replay_sees_new_inputs():
     with pkg.Context(0) as ctx:
         o = _outs(P, 16)
         job = ctx.detect_job(H, y, nv, 4, 9, o, ci)
-        with pkg.Batch(0, prm, [job], keepalive=(H, y, nv, ci, o)) as b:
+        with pkg.Batch(0, prm, [job], keepalive=(H, y, nv, ci, o), persistent=persistent) as b:
             for w in (w1, w2, w1):
                 H.copy_(T(w["H"]))
                 y.copy_(T(w["y"]))

@@ -34,7 +34,8 @@ SPECS = [(16, 4, 300, "iid", "subcarrier"), (8, 2, 1200, "kron", "prb"), (4, 6, 
          (16, 4, 64, "kron", "prb"), (8, 6, 333, "iid", "problem")]
 
 
-def test_each_job_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_each_job_same_alone_and_in_the_mix(persistent):
     import paper_2510_01579_gb300 as pkg
     prm = pkg.Params.default(steps=80)
     with pkg.Context(0) as ctx:
@@ -46,7 +47,7 @@ def test_each_job_same_alone_and_in_the_mix():
             refs.append(r)
         torch.cuda.synchronize()
         # in the mix: all submitted at once; a budget that forces several groups per lane
-        with pkg.Server(0, prm, scratch_bytes=8 << 20, n_lanes=2, max_jobs_per_group=3) as srv:
+        with pkg.Server(0, prm, scratch_bytes=8 << 20, n_lanes=2, max_jobs_per_group=3, persistent=persistent) as srv:
             tickets = [srv.submit(job) for _, _, _, job in jobs]
             infos = [srv.wait(tk, timeout_us=60_000_000) for tk in tickets]
             st = srv.stats()
