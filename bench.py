@@ -337,13 +337,113 @@ def run_serve(args):
     ctx.close()
 
 
+def run_precode(args):
+    """Downlink VPP: 3276 subcarriers of 16x16 16-QAM (one problem each), i.i.d.
+    Rayleigh; transmit power against zero forcing (v = 0)."""
+    import torch
+
+    from paper_2510_01579_gb300 import Context, Params
+    dev = torch.device("cuda", 0)
+    prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
+    d = synth.downlink(4000, 16, 16, 4, n_sub=args.subcarriers)
+    H, u, ci = (torch.from_numpy(d[k]).to(dev) for k in ("H", "u_sym", "chan_index"))
+    P = u.shape[0]
+    ctx = Context(0, workspace_bytes=512 << 20)
+    ctx.set_timing(True)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        flush.zero_()
+        out = ctx.precode(H, u, 4, prm, 5, chan_index=ci)
+    torch.cuda.synchronize()
+    stages = []
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        out = ctx.precode(H, u, 4, prm, 5, chan_index=ci)
+        b.record(stream)
+        stages.append(ctx.stage_times())
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    # zero-forcing power of the same u (the v = 0 fallback), in FP64 on the host
+    side = 4
+    ul = (2 * (d["u_sym"].astype(int) // side) - 3) + 1j * (2 * (d["u_sym"].astype(int) % side) - 3)
+    Hh = d["H"].astype(np.complex128)
+    zf = np.array([np.linalg.norm(Hh[c].conj().T @ np.linalg.solve(Hh[c] @ Hh[c].conj().T, ul[p])) ** 2
+                   for p, c in enumerate(d["chan_index"])])
+    pw = out["power"].cpu().numpy().astype(np.float64)
+    line = {"metric": "precodings/s (16x16 16-QAM vector perturbation)", "value": P / (ms / 1e3), "unit": "problems/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 inverse, f32 solve", "data": "synthetic",
+            "config": {"workload": "precode", "problems_per_step": P, "runs": args.runs,
+                       "solver_steps": args.solver_steps},
+            "stage_ms": {"inverse+build": statistics.mean(s[0] for s in stages),
+                         "solve": statistics.mean(s[1] for s in stages),
+                         "output": statistics.mean(s[2] for s in stages)},
+            "power": {"mean_vpp_over_zf": float(np.mean(pw / zf)), "median_vpp_over_zf": float(np.median(pw / zf)),
+                      "frac_perturbed": float(np.mean(np.any(out["v"].cpu().numpy() != 0, axis=(1, 2))))}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_precision(args):
+    """Gram in FP32 (fixed order) vs BF16 / FP16 tensor cores with FP32
+    accumulation, against FP64 on sampled channels; BER of each on the slot."""
+    import torch
+
+    import oracle
+    from paper_2510_01579_gb300 import Context, Params
+    dev = torch.device("cuda", 0)
+    prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
+    w = make_workload("ul16x16_16qam_slot", rank_seed(0), args.subcarriers)
+    H, y, nv, ci = (torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index"))
+    ctx = Context(0, workspace_bytes=512 << 20)
+    ctx.set_timing(True)
+    k = oracle.qam_kappa(4)
+    res = {}
+    samples = list(range(0, w["y"].shape[0], max(1, w["y"].shape[0] // 64)))
+    for name, prec in (("fp32", 0), ("bf16_tc", 1), ("fp16_tc", 2), ("bf16x3_tc", 3)):
+        b = ctx.build_detect(H, y, nv, 4, chan_index=ci, gram_precision=prec)
+        G = b["G"].cpu().numpy()
+        worst = 0.0
+        for p in samples:
+            c = int(w["chan_index"][p])
+            t = oracle.build_detect64(w["H"][c].astype(np.complex128), w["y"][p].astype(np.complex128),
+                                      float(w["noise_var"][p]), 4)
+            Hs = np.abs(k * w["H"][c].astype(np.complex128))
+            scale = np.block([[Hs.T @ Hs] * 2] * 2)
+            worst = max(worst, float(np.max(np.abs(G[p] - t["G"]) / scale)))
+        for _ in range(args.warmup):
+            out = ctx.detect(H, y, nv, 4, prm, 7, chan_index=ci, gram_precision=prec)
+        torch.cuda.synchronize()
+        bms = []
+        for _ in range(args.steps):
+            out = ctx.detect(H, y, nv, 4, prm, 7, chan_index=ci, gram_precision=prec)
+            bms.append(ctx.stage_times()[0])
+        sym = out["sym"].cpu().numpy()
+        res[name] = {"max_normwise_gram_err": worst, "ber": synth.bit_errors(sym, w["sym"], 4) / sym.size / 4,
+                     "build_ms": statistics.mean(bms)}
+    ref = res["fp32"]["ber"]
+    line = {"metric": "BER at 16 dB (16x16 16-QAM slot) by Gram precision", "value": res["bf16x3_tc"]["ber"],
+            "unit": "bit error rate", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["bf16x3_tc"]["build_ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "split bf16 Gram (tensor cores), f32 accumulate", "data": "synthetic",
+            "config": {"workload": "precision", "problems": int(w["y"].shape[0]), "sampled_channels": len(samples)},
+            "precision": res,
+            "ber_ratio_over_fp32": {k: v["ber"] / ref for k, v in res.items()} if ref else None}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mmgap", choices=["mmgap", "reference"])
-    ap.add_argument("--workload", default="ul16x16_16qam_slot", choices=sorted(WORKLOADS) + ["mixed", "serve"])
+    ap.add_argument("--workload", default="ul16x16_16qam_slot",
+                    choices=sorted(WORKLOADS) + ["mixed", "serve", "precode", "precision"])
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load as a fraction of capacity")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: length of the arrival trace")
     ap.add_argument("--lanes", type=int, default=4, help="serve: concurrent launch groups (streams)")
@@ -373,6 +473,12 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "precode":
+        run_precode(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
         return
 
     import torch

@@ -94,6 +94,14 @@ typedef struct {
  *   guess_out:  int8 [n_problems][2 n_t] MMSE lattice guess (re block, im block)
  *   offset_out: int8 [n_problems][2 n_t] selected offset d in {-1, 0, 1}
  *   ndiv_out:   int32 [n_problems] diverged anneals
+ * gram_precision: 0 = FP32 Gram in the fixed operation order (bit-exact
+ *   against the CPU oracle); 1 = BF16, 2 = FP16 and 3 = split BF16 (each
+ *   operand as bf16 hi + bf16 lo, products hi*hi + hi*lo + lo*hi) on tensor
+ *   cores with FP32 accumulation (a precision variant of the Sec. 3.2
+ *   pre-processing: per element |dG_ij| <= (2u + u^2 + 2 n_r 2^-24)
+ *   sum_k |Hs_ki| |Hs_kj|, u = 2^-8 for BF16, 2^-11 for FP16, 2^-15 for the
+ *   split form; the matched filter, MMSE, field and quantisation stay FP32).
+ *   Only mmgap_detect and mmgap_build_detect accept 1-3.
  */
 typedef struct {
     int32_t n_r, n_t, mod_bits;
@@ -108,6 +116,7 @@ typedef struct {
     int8_t* guess_out;
     int8_t* offset_out;
     int32_t* ndiv_out;
+    int32_t gram_precision;
 } mmgap_detect_job;
 
 /*

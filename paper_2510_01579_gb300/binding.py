@@ -46,7 +46,7 @@ class _DetectJob(C.Structure):
                 ("n_chan", C.c_int32), ("chan_index", C.c_void_p), ("H", C.c_void_p), ("y", C.c_void_p),
                 ("noise_var", C.c_void_p), ("seed", C.c_uint64), ("sym_out", C.c_void_p),
                 ("energy_out", C.c_void_p), ("guess_out", C.c_void_p), ("offset_out", C.c_void_p),
-                ("ndiv_out", C.c_void_p)]
+                ("ndiv_out", C.c_void_p), ("gram_precision", C.c_int32)]
 
 
 class _PrecodeJob(C.Structure):
@@ -203,7 +203,7 @@ class Context:
 
     # ------------------------------------------------------------------ API
     def detect(self, H, y, noise_var, mod_bits: int, params: Params, seed: int, chan_index=None,
-               want_energy=False, want_guess=False, want_offset=False, want_ndiv=False):
+               want_energy=False, want_guess=False, want_offset=False, want_ndiv=False, gram_precision: int = 0):
         """Uplink detection of P problems.  H: complex64 (n_chan, n_r, n_t),
         y: complex64 (P, n_r), noise_var: float32 (P,), chan_index: int32 (P,)
         or None.  Returns a dict of CUDA tensors (sym uint8 (P, n_t), ...)."""
@@ -223,15 +223,15 @@ class Context:
             out["offset"] = torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)
         if want_ndiv:
             out["ndiv"] = torch.empty(P, dtype=torch.int32, device=dev)
-        job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index)
+        job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index, gram_precision)
         self.detect_jobs([job], params)
         return out
 
-    def detect_job(self, H, y, noise_var, mod_bits, seed, out, chan_index=None) -> _DetectJob:
+    def detect_job(self, H, y, noise_var, mod_bits, seed, out, chan_index=None, gram_precision=0) -> _DetectJob:
         n_chan, n_r, n_t = H.shape
         return _DetectJob(n_r, n_t, mod_bits, y.shape[0], n_chan, _ptr(chan_index), _ptr(H), _ptr(y),
                           _ptr(noise_var), seed, _ptr(out["sym"]), _ptr(out.get("energy")), _ptr(out.get("guess")),
-                          _ptr(out.get("offset")), _ptr(out.get("ndiv")))
+                          _ptr(out.get("offset")), _ptr(out.get("ndiv")), gram_precision)
 
     def detect_jobs(self, jobs, params: Params, stream=None):
         arr = (_DetectJob * len(jobs))(*jobs)
@@ -282,7 +282,7 @@ class Context:
                                            seed, _ptr(d), _ptr(E), _ptr(run), _ptr(nd), self._stream()))
         return dict(d=d, E=E, run=run, ndiv=nd)
 
-    def build_detect(self, H, y, noise_var, mod_bits: int, chan_index=None, want_float=True):
+    def build_detect(self, H, y, noise_var, mod_bits: int, chan_index=None, want_float=True, gram_precision=0):
         """Builder only: quantised delta-Ising coefficients of P detection problems."""
         n_chan, n_r, n_t = H.shape
         P = y.shape[0]
@@ -300,7 +300,7 @@ class Context:
             out["h"] = torch.empty((P, n), dtype=torch.float32, device=dev)
             out["sigma_exp"] = torch.empty(P, dtype=torch.int32, device=dev)
         job = _DetectJob(n_r, n_t, mod_bits, P, n_chan, _ptr(chan_index), _ptr(H), _ptr(y), _ptr(noise_var), 0,
-                         None, None, None, None, None)
+                         None, None, None, None, None, gram_precision)
         self._raise(_lib.mmgap_build_detect(self._h, C.byref(job), _ptr(out["A_q"]), _ptr(out["h_q"]),
                                             _ptr(out["g"]), _ptr(out.get("G")), _ptr(out.get("h")),
                                             _ptr(out.get("sigma_exp")), self._stream()))

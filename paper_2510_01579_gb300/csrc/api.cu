@@ -132,6 +132,7 @@ template <int NT> struct OpSolve { static cudaError_t run(const SolveArgs& a, in
 template <int NT> struct OpVppInv { static cudaError_t run(const VppInvArgs& a, cudaStream_t s) { return launch_vpp_inverse<NT>(a, s); } };
 template <int NT> struct OpVppBuild { static cudaError_t run(const VppBuildArgs& a, cudaStream_t s) { return launch_vpp_build<NT>(a, s); } };
 template <int NT> struct OpVppOut { static cudaError_t run(const VppOutArgs& a, cudaStream_t s) { return launch_vpp_output<NT>(a, s); } };
+template <int NT> struct OpGram { static cudaError_t run(const GramArgs& a, cudaStream_t s) { return launch_gram_tc<NT>(a, s); } };
 
 // QAM normalisation kappa = 1/sqrt(2 (M-1)/3) and kappa^2, rounded once to float.
 void qam_kappa(int mod_bits, float* kappa, float* kappa2) {
@@ -186,6 +187,32 @@ mmgap_status check_detect_job(mmgap_ctx* ctx, const mmgap_detect_job& j, bool ne
     if (j.n_chan < 1) return fail(ctx, MMGAP_EINVAL, "n_chan < 1");
     if (!j.chan_index && j.n_chan < j.n_problems)
         return fail(ctx, MMGAP_EINVAL, "chan_index NULL needs n_chan >= n_problems");
+    if (j.gram_precision < 0 || j.gram_precision > 3)
+        return fail(ctx, MMGAP_EINVAL, "gram_precision=%d: 0 FP32, 1 BF16, 2 FP16, 3 BF16x3", j.gram_precision);
+    return MMGAP_OK;
+}
+
+// Tensor-core Gram of every channel of a job into the workspace head (for
+// gram_precision 1/2); *gc_out = nullptr for the FP32 path.
+mmgap_status job_gram(mmgap_ctx* ctx, const mmgap_detect_job& J, cudaStream_t s, float** gc_out, size_t* used) {
+    *gc_out = nullptr;
+    *used = 0;
+    if (J.gram_precision == 0 || J.n_problems == 0) return MMGAP_OK;
+    const int n_chan = J.chan_index ? J.n_chan : J.n_problems;
+    const size_t bytes = align_up((size_t)n_chan * J.n_t * J.n_t * 8);
+    if (bytes + 4 * kAlign >= ctx->ws_bytes) return fail(ctx, MMGAP_ENOMEM, "workspace too small for the Gram");
+    GramArgs g{};
+    g.H = J.H;
+    g.n_r = J.n_r;
+    g.n_chan = n_chan;
+    float k2;
+    qam_kappa(J.mod_bits, &g.kappa, &k2);
+    g.fp16 = J.gram_precision == 2 ? 1 : (J.gram_precision == 3 ? 2 : 0);
+    g.Gc = (float*)ctx->ws;
+    cudaError_t e = dispatch_nt<OpGram>(J.n_t, g, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gram_tc launch");
+    *gc_out = g.Gc;
+    *used = bytes;
     return MMGAP_OK;
 }
 
@@ -329,6 +356,10 @@ mmgap_status mmgap_build_detect(mmgap_ctx* ctx, const mmgap_detect_job* job, int
     a.G32 = G_out;
     a.h32 = h_out;
     a.sigma_exp = sigma_exp_out;
+    float* gc = nullptr;
+    size_t used = 0;
+    if ((st = job_gram(ctx, *job, (cudaStream_t)stream, &gc, &used)) != MMGAP_OK) return st;
+    a.Gc_pre = gc;
     cudaError_t e = dispatch_nt<OpBuild>(job->n_t, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "build_detect launch");
     return MMGAP_OK;
@@ -386,17 +417,24 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
         if (J.n_problems == 0) continue;
         const int n = 2 * J.n_t;
         const size_t per = align_up((size_t)n * n * 2) + align_up((size_t)n * 2) + align_up((size_t)n);
+        if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
+        float* gc = nullptr;
+        size_t gc_bytes = 0;
+        if ((st = job_gram(ctx, J, s, &gc, &gc_bytes)) != MMGAP_OK) return st;
+        char* base = ctx->ws + gc_bytes;
+        const size_t avail = ctx->ws_bytes - gc_bytes;
         // chunk so that three aligned regions of chunk size fit the workspace
-        long long chunk = (long long)(ctx->ws_bytes / (per + 3 * kAlign));
+        long long chunk = (long long)(avail / (per + 3 * kAlign));
         if (chunk < 1) return fail(ctx, MMGAP_ENOMEM, "workspace of %zu bytes holds no problem", ctx->ws_bytes);
         if (chunk > J.n_problems) chunk = J.n_problems;
         for (long long p0 = 0; p0 < J.n_problems; p0 += chunk) {
             const int P = (int)std::min<long long>(chunk, J.n_problems - p0);
-            int16_t* Aq = (int16_t*)ctx->ws;
-            int16_t* hq = (int16_t*)(ctx->ws + align_up((size_t)P * n * n * 2));
+            int16_t* Aq = (int16_t*)base;
+            int16_t* hq = (int16_t*)(base + align_up((size_t)P * n * n * 2));
             int8_t* g = (int8_t*)((char*)hq + align_up((size_t)P * n * 2));
-            if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
+            if (p0 > 0 && (st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
             BuildArgs b{};
+            b.Gc_pre = gc ? (J.chan_index ? gc : gc + (size_t)p0 * 2 * J.n_t * J.n_t) : nullptr;
             b.H = J.chan_index ? J.H : J.H + (size_t)p0 * 2 * J.n_r * J.n_t;
             b.chan_index = J.chan_index ? J.chan_index + p0 : nullptr;
             b.y = J.y + (size_t)p0 * 2 * J.n_r;

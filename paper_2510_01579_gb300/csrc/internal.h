@@ -67,6 +67,7 @@ struct BuildArgs {
     int n_chan;                // channels addressable through chan_index
     float kappa, kappa2;
     int* err;                  // device error word (bit 0: channel index out of range)
+    const float* Gc_pre;       // optional precomputed Gram of kappa H per channel, complex [n_chan][n_t][n_t]
     // outputs
     int16_t* Aq;               // [P][n][n]
     int16_t* hq;               // [P][n]
@@ -74,6 +75,17 @@ struct BuildArgs {
     float* G32;                // [P][n][n] or nullptr
     float* h32;                // [P][n] or nullptr
     int32_t* sigma_exp;        // [P] or nullptr
+};
+
+// Gram of kappa H per channel on tensor cores (BF16 or FP16 operands, FP32
+// accumulation); Hermitian by construction (upper triangle mirrored).
+struct GramArgs {
+    const float* H;   // complex [n_chan][n_r][n_t]
+    int n_r;
+    int n_chan;
+    float kappa;
+    int fp16;         // 0: BF16 operands, 1: FP16 operands, 2: split BF16 (hi + lo, three products)
+    float* Gc;        // complex [n_chan][n_t][n_t]
 };
 
 struct VppInvArgs {
@@ -117,6 +129,7 @@ struct VppOutArgs {
 template <int NT> cudaError_t launch_build_detect(const BuildArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_solve(const SolveArgs& a, int runs, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_inverse(const VppInvArgs& a, cudaStream_t s);
+template <int NT> cudaError_t launch_gram_tc(const GramArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_build(const VppBuildArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_output(const VppOutArgs& a, cudaStream_t s);
 

@@ -17,6 +17,7 @@
 #pragma once
 #include <cstdint>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -129,7 +130,11 @@ __device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, in
     __syncwarp();
 
     // Gram G_c = Hs^H Hs (upper triangle + Hermitian mirror) and m = Hs^H y.
-    for (int t = lane; t < NT * NT + NT; t += 32) {
+    // With a precomputed (tensor-core) Gram only the matched filter is formed here.
+    const float* Gpre = a.Gc_pre ? a.Gc_pre + (size_t)c * 2 * NT * NT : nullptr;
+    if (Gpre)
+        for (int e = lane; e < 2 * NT * NT; e += 32) Gc[e] = Gpre[e];
+    for (int t = lane + (Gpre ? NT * NT : 0); t < NT * NT + NT; t += 32) {
         if (t < NT * NT) {
             const int i = t / NT, j = t % NT;
             if (i > j) continue;
@@ -1141,6 +1146,147 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchArgs A) {
 }
 
 // =========================================================================
+// Precision variant of the Gram (pre-processing, Sec. 3.2): G_c = Hs^H Hs per
+// channel with mma.sync m16n8k16 (BF16, FP16 or split BF16x3 operands, FP32
+// accumulation).
+// With A = [Re Hs^T | Im Hs^T] (n_t x 2 n_r):
+//   Re G_c = A [Re Hs; Im Hs],   Im G_c = A [Im Hs; -Re Hs].
+// One warp per channel; n_t <= 16 (rows padded to 16), 2 n_r padded to a
+// multiple of 16.  Each element of Hs = kappa H is rounded once to FP32 and
+// once to the 16-bit type.
+// =========================================================================
+__device__ __forceinline__ uint32_t pack16(float lo, float hi, int fp16) {
+    uint32_t r;
+    if (fp16) {
+        asm("{ .reg .f16 l, h;\n cvt.rn.f16.f32 l, %1;\n cvt.rn.f16.f32 h, %2;\n mov.b32 %0, {l, h}; }"
+            : "=r"(r) : "f"(lo), "f"(hi));
+    } else {
+        asm("cvt.rn.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(lo), "f"(hi));
+    }
+    return r;
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2], int fp16) {
+    if (fp16) {
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                     "{%0,%1,%2,%3};"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    } else {
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                     "{%0,%1,%2,%3};"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128) gram_tc_kernel(GramArgs a) {
+    static_assert(NT <= 16, "one 16-row tile");
+    extern __shared__ __align__(16) float gsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 4 + warp;
+    if (c >= a.n_chan) return;
+    const int n_r = a.n_r;
+    const int K = (2 * n_r + 15) / 16 * 16;
+    float* Hs = gsm + (size_t)warp * 2 * kMaxNr * NT;  // [n_r][NT] complex
+    const float* Hg = a.H + (size_t)c * 2 * n_r * NT;
+    for (int e = lane; e < 2 * n_r * NT; e += 32) Hs[e] = mulrn(a.kappa, Hg[e]);
+    __syncwarp();
+    // element (k', col) of the stacked operands, zero outside the matrix
+    auto At = [&](int row, int kk) -> float {  // A[row][kk] = [Re Hs^T | Im Hs^T]
+        if (row >= NT || kk >= 2 * n_r) return 0.0f;
+        return kk < n_r ? Hs[2 * (kk * NT + row)] : Hs[2 * ((kk - n_r) * NT + row) + 1];
+    };
+    auto Bre = [&](int kk, int col) -> float {  // [Re Hs; Im Hs]
+        if (col >= NT || kk >= 2 * n_r) return 0.0f;
+        return kk < n_r ? Hs[2 * (kk * NT + col)] : Hs[2 * ((kk - n_r) * NT + col) + 1];
+    };
+    auto Bim = [&](int kk, int col) -> float {  // [Im Hs; -Re Hs]
+        if (col >= NT || kk >= 2 * n_r) return 0.0f;
+        return kk < n_r ? Hs[2 * (kk * NT + col) + 1] : -Hs[2 * ((kk - n_r) * NT + col)];
+    };
+    const int gid = lane >> 2, tig = lane & 3;
+    constexpr int NTILES = (NT + 7) / 8;
+    float re[NTILES][4], im[NTILES][4];
+#pragma unroll
+    for (int t = 0; t < NTILES; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) re[t][q] = im[t][q] = 0.0f;
+    // split operands (BF16x3): v = hi + lo with hi = bf16(v), lo = bf16(v - hi);
+    // products hi*hi + hi*lo + lo*hi
+    const int fp16 = a.fp16 == 1;
+    const bool split = a.fp16 == 2;
+    auto hi = [&](float v) -> float { return split ? __bfloat162float(__float2bfloat16_rn(v)) : v; };
+    auto lo = [&](float v) -> float { return __fsub_rn(v, hi(v)); };
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const float av[8] = {At(gid, k0 + 2 * tig), At(gid, k0 + 2 * tig + 1), At(gid + 8, k0 + 2 * tig),
+                             At(gid + 8, k0 + 2 * tig + 1), At(gid, k0 + 2 * tig + 8), At(gid, k0 + 2 * tig + 9),
+                             At(gid + 8, k0 + 2 * tig + 8), At(gid + 8, k0 + 2 * tig + 9)};
+        uint32_t fa[4], fal[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            fa[r] = pack16(hi(av[2 * r]), hi(av[2 * r + 1]), fp16);
+            fal[r] = pack16(lo(av[2 * r]), lo(av[2 * r + 1]), fp16);
+        }
+#pragma unroll
+        for (int t = 0; t < NTILES; ++t) {
+            const int col = 8 * t + gid;
+            const float rv[4] = {Bre(k0 + 2 * tig, col), Bre(k0 + 2 * tig + 1, col), Bre(k0 + 2 * tig + 8, col),
+                                 Bre(k0 + 2 * tig + 9, col)};
+            const float iv[4] = {Bim(k0 + 2 * tig, col), Bim(k0 + 2 * tig + 1, col), Bim(k0 + 2 * tig + 8, col),
+                                 Bim(k0 + 2 * tig + 9, col)};
+            uint32_t br[2], bi[2], brl[2], bil[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                br[r] = pack16(hi(rv[2 * r]), hi(rv[2 * r + 1]), fp16);
+                bi[r] = pack16(hi(iv[2 * r]), hi(iv[2 * r + 1]), fp16);
+                brl[r] = pack16(lo(rv[2 * r]), lo(rv[2 * r + 1]), fp16);
+                bil[r] = pack16(lo(iv[2 * r]), lo(iv[2 * r + 1]), fp16);
+            }
+            if (split) {  // small terms first
+                mma16816(re[t], fal, br, 0);
+                mma16816(re[t], fa, brl, 0);
+                mma16816(im[t], fal, bi, 0);
+                mma16816(im[t], fa, bil, 0);
+            }
+            mma16816(re[t], fa, br, fp16);
+            mma16816(im[t], fa, bi, fp16);
+        }
+    }
+    // accumulator (row, col): [0] (gid, 2tig) [1] (gid, 2tig+1) [2] (gid+8, 2tig) [3] (gid+8, 2tig+1);
+    // write the upper triangle and its Hermitian mirror
+    float* G = a.Gc + (size_t)c * 2 * NT * NT;
+#pragma unroll
+    for (int t = 0; t < NTILES; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int row = gid + (q >= 2 ? 8 : 0), col = 8 * t + 2 * tig + (q & 1);
+            if (row >= NT || col >= NT || row > col) continue;
+            const float r = re[t][q], m = row == col ? 0.0f : im[t][q];
+            G[2 * (row * NT + col)] = r;
+            G[2 * (row * NT + col) + 1] = m;
+            G[2 * (col * NT + row)] = r;
+            G[2 * (col * NT + row) + 1] = -m;
+        }
+}
+
+template <int NT>
+cudaError_t launch_gram_tc_impl(const GramArgs& a, cudaStream_t s) {
+    if (a.n_chan <= 0) return cudaSuccess;
+    if constexpr (NT > 16) {
+        return cudaErrorInvalidValue;
+    } else {
+        const size_t smem = (size_t)4 * 2 * kMaxNr * NT * sizeof(float);
+        cudaError_t err =
+            cudaFuncSetAttribute(gram_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        gram_tc_kernel<NT><<<(a.n_chan + 3) / 4, 128, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+}
+
+// =========================================================================
 // Downlink VPP (Sec. 3.3) in FP64.
 // =========================================================================
 constexpr int kVppMaxNt = 64;
@@ -1485,5 +1631,8 @@ cudaError_t launch_vpp_output_impl(const VppOutArgs& a, cudaStream_t s) {
     }                                                                                                          \
     template <> cudaError_t launch_vpp_output<NT>(const VppOutArgs& a, cudaStream_t s) {                       \
         return launch_vpp_output_impl<NT>(a, s);                                                               \
+    }                                                                                                          \
+    template <> cudaError_t launch_gram_tc<NT>(const GramArgs& a, cudaStream_t s) {                            \
+        return launch_gram_tc_impl<NT>(a, s);                                                                  \
     }                                                                                                          \
     }
