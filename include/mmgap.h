@@ -175,6 +175,26 @@ const char* mmgap_last_error(const mmgap_ctx* ctx);
 mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job* jobs, int n_jobs,
                           void* stream);
 
+/*
+ * MMGaP-E (Sec. 3.2.2): multi-stage, multi-seed uplink detection.  For each
+ * problem two delta-Ising instances are solved per stage: instance 0 around
+ * the MMSE guess, instance 1 around an MMSE-SIC guess (the Cholesky of
+ * H^H H + rho I pivoted on the smallest current Schur diagonal, back
+ * substitution with each symbol sliced before it is cancelled); in each later
+ * stage an instance is rebuilt around its own previous solution.  Stage s,
+ * instance i anneals with Philox key seed + (2 (s - 1) + i) 0x9E3779B97F4A7C15.
+ * The output is the candidate with the lowest FP32 ML objective ||y - Hs x||^2
+ * (ties: first) among [MMSE guess, SIC guess, stage-1 solutions (instance 0,
+ * 1), stage-2 solutions, ...].
+ *   stages in [1, 8]; job outputs used: sym_out (required); other job
+ *   outputs are ignored.
+ *   best_out: int32 [P] index of the chosen candidate (may be NULL)
+ *   obj_out:  float [P] its objective (may be NULL)
+ *   cand_out: int8 [2 + 2 stages][P][2 n_t] every candidate (may be NULL)
+ */
+mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job* job, int stages,
+                            int32_t* best_out, float* obj_out, int8_t* cand_out, void* stream);
+
 /* Downlink vector-perturbation precoding (Sec. 3.3): the same solver on the
  * detection form y~ = W u, H_p = -tau W / 2, guess 0. */
 mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_precode_job* jobs, int n_jobs,

@@ -121,6 +121,15 @@ _lib.orc_detect_batch.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _nullable(
                                   C.POINTER(CParams), C.c_uint64, _u8p, _i32p, _i32p, _i32p, _nullable(_i32p),
                                   _nullable(_i8p)]
 
+_lib.orc_sic_guess32.argtypes = [C.c_int, C.c_int, C.c_int, _f32p, _f32p, C.c_float, _i32p, _nullable(_i32p)]
+_lib.orc_ml_objective32.restype = C.c_float
+_lib.orc_ml_objective32.argtypes = [C.c_int, C.c_int, C.c_int, _f32p, _f32p, _i32p]
+_lib.orc_stage_seed.restype = C.c_uint64
+_lib.orc_stage_seed.argtypes = [C.c_uint64, C.c_int, C.c_int]
+_lib.orc_detect_e.argtypes = [C.c_int, C.c_int, C.c_int, _f32p, _f32p, C.c_float, C.c_int, C.POINTER(CParams),
+                              C.c_uint64, C.c_uint64, _u8p, C.POINTER(C.c_int), C.POINTER(C.c_float),
+                              _nullable(_i32p)]
+
 QBITS = 14
 
 
@@ -395,3 +404,38 @@ def precode_batch(H, u_sym, mod_bits, params: Params, seed, chan_index=None):
         out["E"][p], out["run"][p], out["n_div"][p] = r["E"], r["run"], r["n_div"]
         out["Aq"][p], out["hq"][p] = b["Aq"], b["hq"]
     return out
+
+
+# -------------------------------------------------------------- MMGaP-E
+def sic_guess32(H, y, noise_var, mod_bits):
+    """MMSE-SIC guess (sorted-Cholesky order), FP32 mirror; returns (g, perm, status)."""
+    H = np.asarray(H)
+    n_r, n_t = H.shape
+    g = np.zeros(2 * n_t, np.int32)
+    perm = np.zeros(n_t, np.int32)
+    st = _lib.orc_sic_guess32(n_r, n_t, mod_bits, _c64(H), _c64(y), np.float32(noise_var), g, perm)
+    return g, perm, st
+
+
+def ml_objective32(H, y, x, mod_bits) -> np.float32:
+    n_r, n_t = np.asarray(H).shape
+    return np.float32(_lib.orc_ml_objective32(n_r, n_t, mod_bits, _c64(H), _c64(y),
+                                              np.ascontiguousarray(x, np.int32)))
+
+
+def stage_seed(seed, stage, inst) -> int:
+    return int(_lib.orc_stage_seed(seed, stage, inst))
+
+
+def detect_e(H, y, noise_var, mod_bits, stages, params: Params, seed, problem):
+    """MMGaP-E of one problem: dict(sym, best, obj, candidates)."""
+    H = np.asarray(H)
+    n_r, n_t = H.shape
+    nc = 2 + 2 * stages
+    sym = np.zeros(n_t, np.uint8)
+    best, obj = C.c_int(), C.c_float()
+    X = np.zeros(nc * 2 * n_t, np.int32)
+    cp = params.c()
+    _lib.orc_detect_e(n_r, n_t, mod_bits, _c64(H), _c64(y), np.float32(noise_var), stages, C.byref(cp), int(seed),
+                      int(problem), sym, C.byref(best), C.byref(obj), X)
+    return dict(sym=sym, best=best.value, obj=obj.value, candidates=X.reshape(nc, 2 * n_t))

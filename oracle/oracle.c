@@ -1115,3 +1115,251 @@ int orc_detect_batch(int n_r, int n_t, int mod_bits, int P, const int32_t* chan_
     free(g); free(Aq); free(hq); free(d);
     return status;
 }
+
+/* ========================================================================= */
+/* MMGaP-E (Sec. 3.2.2): a second guess from MMSE-SIC and multi-stage        */
+/* re-centring, FP32 mirror.                                                  */
+/* ========================================================================= */
+
+/* Nearest alphabet point of one real dimension (ties upward), as the guess. */
+static int slice_f(float x, int Lmax)
+{
+    float xc = fmaxf(x, (float)-Lmax);
+    xc = fminf(xc, (float)Lmax);
+    return 2 * (int)floorf(f_mul(xc, 0.5f)) + 1;
+}
+
+/*
+ * MMSE-SIC guess (the paper's second initial guess, Sec. 3.2.2), FP32.
+ * Cholesky of B = G_c + rho I with sorted pivoting: at step j the remaining
+ * user with the smallest current Schur diagonal d (ties: first position) is
+ * factored next, so the users with the largest d are detected first.  The
+ * forward solve gives w = L^-1 P m; successive interference cancellation is
+ * then the back substitution x_j = (w_j - sum_{k>j} conj(L_kj) xhat_k) / L_jj
+ * (k descending) with each x_j sliced to the alphabet before it is
+ * substituted.  Same operation patterns as orc_build_detect32.
+ * Outputs g [2 n_t] (re block, im block) and, optionally, perm [n_t]
+ * (position -> user).  Returns ORC_ENUM if a pivot is not positive
+ * (then the guess is the slice of 0 for every user).
+ */
+int orc_sic_guess32(int n_r, int n_t, int mod_bits, const float* H, const float* y, float noise_var, int* g_out,
+                    int* perm_out)
+{
+    if (n_r < 1 || n_t < 1 || mod_bits < 2 || (mod_bits & 1)) return ORC_EINVAL;
+    const int Lmax = orc_qam_level_max(mod_bits);
+    const float kappa = qam_kappa_f(mod_bits);
+    const float rho = f_mul(noise_var, qam_kappa2_f(mod_bits));
+    float* Hs = (float*)malloc(sizeof(float) * 2 * (size_t)(n_r * n_t));
+    float* Gc = (float*)malloc(sizeof(float) * 2 * (size_t)(n_t * n_t));
+    float* Lc = (float*)calloc(2 * (size_t)(n_t * n_t), sizeof(float));
+    float* m = (float*)malloc(sizeof(float) * 2 * (size_t)n_t);
+    float* w = (float*)malloc(sizeof(float) * 2 * (size_t)n_t);
+    float* xh = (float*)malloc(sizeof(float) * 2 * (size_t)n_t);
+    float* d = (float*)malloc(sizeof(float) * (size_t)n_t);
+    int* perm = (int*)malloc(sizeof(int) * (size_t)n_t);
+    int status = ORC_OK;
+    for (int e = 0; e < 2 * n_r * n_t; ++e) Hs[e] = f_mul(kappa, H[e]);
+    for (int i = 0; i < n_t; ++i) {
+        float acc = 0.0f;
+        for (int k = 0; k < n_r; ++k) {
+            const float* a = Hs + 2 * (k * n_t + i);
+            acc = fmaf(a[0], a[0], acc);
+            acc = fmaf(a[1], a[1], acc);
+        }
+        Gc[2 * (i * n_t + i)] = acc;
+        Gc[2 * (i * n_t + i) + 1] = 0.0f;
+        for (int j = i + 1; j < n_t; ++j) {
+            float re = 0.0f, im = 0.0f;
+            for (int k = 0; k < n_r; ++k) {
+                const float* a = Hs + 2 * (k * n_t + i);
+                const float* b = Hs + 2 * (k * n_t + j);
+                re = fmaf(a[0], b[0], re);
+                re = fmaf(a[1], b[1], re);
+                im = fmaf(a[0], b[1], im);
+                im = fmaf(-a[1], b[0], im);
+            }
+            Gc[2 * (i * n_t + j)] = re;
+            Gc[2 * (i * n_t + j) + 1] = im;
+            Gc[2 * (j * n_t + i)] = re;
+            Gc[2 * (j * n_t + i) + 1] = -im;
+        }
+    }
+    for (int i = 0; i < n_t; ++i) {
+        float re = 0.0f, im = 0.0f;
+        for (int k = 0; k < n_r; ++k) {
+            const float* a = Hs + 2 * (k * n_t + i);
+            const float* b = y + 2 * k;
+            re = fmaf(a[0], b[0], re);
+            re = fmaf(a[1], b[1], re);
+            im = fmaf(a[0], b[1], im);
+            im = fmaf(-a[1], b[0], im);
+        }
+        m[2 * i] = re;
+        m[2 * i + 1] = im;
+    }
+    for (int i = 0; i < n_t; ++i) {
+        perm[i] = i;
+        d[i] = f_add(Gc[2 * (i * n_t + i)], rho);
+    }
+    int ok = 1;
+    for (int j = 0; j < n_t && ok; ++j) {
+        int best = j; /* position of the smallest current diagonal among j..n_t-1 */
+        for (int i = j + 1; i < n_t; ++i)
+            if (d[perm[i]] < d[perm[best]]) best = i;
+        int t = perm[j];
+        perm[j] = perm[best];
+        perm[best] = t;
+        /* rows of L are positions; swap the already computed columns k < j of rows j and best */
+        for (int k = 0; k < j; ++k) {
+            float r0 = Lc[2 * (j * n_t + k)], r1 = Lc[2 * (j * n_t + k) + 1];
+            Lc[2 * (j * n_t + k)] = Lc[2 * (best * n_t + k)];
+            Lc[2 * (j * n_t + k) + 1] = Lc[2 * (best * n_t + k) + 1];
+            Lc[2 * (best * n_t + k)] = r0;
+            Lc[2 * (best * n_t + k) + 1] = r1;
+        }
+        const int u = perm[j];
+        float dj = d[u];
+        if (!(dj > 0.0f) || isinf(dj)) { ok = 0; break; }
+        float ljj = sqrtf(dj);
+        Lc[2 * (j * n_t + j)] = ljj;
+        Lc[2 * (j * n_t + j) + 1] = 0.0f;
+        for (int i = j + 1; i < n_t; ++i) {
+            const int v = perm[i];
+            float re = Gc[2 * (v * n_t + u)], im = Gc[2 * (v * n_t + u) + 1];
+            for (int k = 0; k < j; ++k) {
+                const float* a = Lc + 2 * (i * n_t + k);
+                const float* b = Lc + 2 * (j * n_t + k);
+                re = fmaf(-a[0], b[0], re);
+                re = fmaf(-a[1], b[1], re);
+                im = fmaf(-a[1], b[0], im);
+                im = fmaf(a[0], b[1], im);
+            }
+            float lr = re / ljj, li = im / ljj;
+            Lc[2 * (i * n_t + j)] = lr;
+            Lc[2 * (i * n_t + j) + 1] = li;
+            d[v] = fmaf(-lr, lr, d[v]);
+            d[v] = fmaf(-li, li, d[v]);
+        }
+    }
+    if (ok) {
+        for (int i = 0; i < n_t; ++i) {
+            float re = m[2 * perm[i]], im = m[2 * perm[i] + 1];
+            for (int k = 0; k < i; ++k) {
+                const float* a = Lc + 2 * (i * n_t + k);
+                const float* b = w + 2 * k;
+                re = fmaf(-a[0], b[0], re);
+                re = fmaf(a[1], b[1], re);
+                im = fmaf(-a[0], b[1], im);
+                im = fmaf(-a[1], b[0], im);
+            }
+            float lii = Lc[2 * (i * n_t + i)];
+            w[2 * i] = re / lii;
+            w[2 * i + 1] = im / lii;
+        }
+        for (int i = n_t - 1; i >= 0; --i) {
+            float re = w[2 * i], im = w[2 * i + 1];
+            for (int k = n_t - 1; k > i; --k) {
+                const float* a = Lc + 2 * (k * n_t + i);
+                const float* b = xh + 2 * k;
+                re = fmaf(-a[0], b[0], re);
+                re = fmaf(-a[1], b[1], re);
+                im = fmaf(-a[0], b[1], im);
+                im = fmaf(a[1], b[0], im);
+            }
+            float lii = Lc[2 * (i * n_t + i)];
+            xh[2 * i] = (float)slice_f(re / lii, Lmax);
+            xh[2 * i + 1] = (float)slice_f(im / lii, Lmax);
+        }
+        for (int i = 0; i < n_t; ++i) {
+            g_out[perm[i]] = (int)xh[2 * i];
+            g_out[n_t + perm[i]] = (int)xh[2 * i + 1];
+        }
+    } else {
+        for (int i = 0; i < n_t; ++i) {
+            g_out[i] = slice_f(0.0f, Lmax);
+            g_out[n_t + i] = slice_f(0.0f, Lmax);
+        }
+        status = ORC_ENUM;
+    }
+    if (perm_out) memcpy(perm_out, perm, sizeof(int) * (size_t)n_t);
+    free(Hs); free(Gc); free(Lc); free(m); free(w); free(xh); free(d); free(perm);
+    return status;
+}
+
+/* ML objective ||y - Hs x||^2 of a lattice vector in FP32, pinned order:
+ * r_k = y_k - sum_j Hs_kj x_j (j ascending, as the residual of the build),
+ * then sum_k fma(r.re, r.re), fma(r.im, r.im) from 0, k ascending. */
+float orc_ml_objective32(int n_r, int n_t, int mod_bits, const float* H, const float* y, const int* x)
+{
+    const float kappa = qam_kappa_f(mod_bits);
+    float obj = 0.0f;
+    for (int k = 0; k < n_r; ++k) {
+        float re = y[2 * k], im = y[2 * k + 1];
+        for (int j = 0; j < n_t; ++j) {
+            float ar = f_mul(kappa, H[2 * (k * n_t + j)]), ai = f_mul(kappa, H[2 * (k * n_t + j) + 1]);
+            float br = (float)x[j], bi = (float)x[n_t + j];
+            re = fmaf(-ar, br, re);
+            re = fmaf(ai, bi, re);
+            im = fmaf(-ar, bi, im);
+            im = fmaf(-ai, br, im);
+        }
+        obj = fmaf(re, re, obj);
+        obj = fmaf(im, im, obj);
+    }
+    return obj;
+}
+
+/* Seed of instance `inst` (0: from the MMSE guess, 1: from the SIC guess) of
+ * stage `stage` (1-based): seed + (2 (stage - 1) + inst) * 0x9E3779B97F4A7C15. */
+uint64_t orc_stage_seed(uint64_t seed, int stage, int inst)
+{
+    return seed + (uint64_t)(2 * (stage - 1) + inst) * 0x9E3779B97F4A7C15ULL;
+}
+
+/*
+ * MMGaP-E for one problem (Sec. 3.2.2): candidates in this order --
+ * the MMSE guess, the SIC guess, then for each stage s = 1..stages the
+ * solutions of instance 0 and instance 1; instance i of stage s is the
+ * delta-Ising problem around instance i's previous candidate (stage 1: the
+ * MMSE / SIC guess), annealed with orc_stage_seed(seed, s, i).  The output is
+ * the candidate with the lowest FP32 ML objective (ties: first).
+ * Outputs sym [n_t], best (candidate index), obj (its objective), and
+ * optionally all candidates x_all [(2 + 2 stages)][2 n_t].
+ */
+int orc_detect_e(int n_r, int n_t, int mod_bits, const float* H, const float* y, float noise_var, int stages,
+                 const orc_params* P, uint64_t seed, uint64_t problem, uint8_t* sym, int* best_out, float* obj_out,
+                 int* x_all)
+{
+    const int n = 2 * n_t, nc = 2 + 2 * stages;
+    const int Lm = orc_qam_level_max(mod_bits);
+    int* X = (int*)malloc(sizeof(int) * (size_t)(nc * n));
+    int16_t* Aq = (int16_t*)malloc(sizeof(int16_t) * (size_t)(n * n));
+    int16_t* hq = (int16_t*)malloc(sizeof(int16_t) * (size_t)n);
+    int* g = (int*)malloc(sizeof(int) * (size_t)n);
+    int8_t* d = (int8_t*)malloc((size_t)n);
+    int se;
+    orc_build_detect32(n_r, n_t, mod_bits, H, y, noise_var, NULL, X, NULL, NULL, &se, Aq, hq);
+    orc_sic_guess32(n_r, n_t, mod_bits, H, y, noise_var, X + n, NULL);
+    for (int s = 1; s <= stages; ++s)
+        for (int inst = 0; inst < 2; ++inst) {
+            const int* prev = X + (size_t)(s == 1 ? inst : 2 + 2 * (s - 2) + inst) * n;
+            orc_build_detect32(n_r, n_t, mod_bits, H, y, noise_var, prev, g, NULL, NULL, &se, Aq, hq);
+            int32_t E, run, nd;
+            orc_cac_solve(n, Aq, hq, g, Lm, P, orc_stage_seed(seed, s, inst), problem, d, &E, &run, &nd, NULL, NULL);
+            int* out = X + (size_t)(2 + 2 * (s - 1) + inst) * n;
+            for (int i = 0; i < n; ++i) out[i] = g[i] + 2 * d[i];
+        }
+    int best = 0;
+    float bo = orc_ml_objective32(n_r, n_t, mod_bits, H, y, X);
+    for (int c = 1; c < nc; ++c) {
+        float o = orc_ml_objective32(n_r, n_t, mod_bits, H, y, X + (size_t)c * n);
+        if (o < bo) { bo = o; best = c; }
+    }
+    int8_t* zero = (int8_t*)calloc((size_t)n, 1);
+    orc_decode_detect(n_t, mod_bits, X + (size_t)best * n, zero, sym);
+    if (best_out) *best_out = best;
+    if (obj_out) *obj_out = bo;
+    if (x_all) memcpy(x_all, X, sizeof(int) * (size_t)(nc * n));
+    free(zero); free(X); free(Aq); free(hq); free(g); free(d);
+    return ORC_OK;
+}

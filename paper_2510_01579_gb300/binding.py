@@ -72,6 +72,7 @@ _lib.mmgap_stage_times.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)
 _lib.mmgap_device_errors.argtypes = [_vp, C.POINTER(C.c_int), C.c_int]
 _lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), _vp]
 _lib.mmgap_set_solver_variant.argtypes = [_vp, C.c_int, C.c_int]
+_lib.mmgap_detect_e.argtypes = [_vp, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int, _vp, _vp, _vp, _vp]
 _lib.mmgap_get_solver_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
 _lib.mmgap_autotune.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
 _lib.mmgap_batch_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int,
@@ -106,6 +107,7 @@ _lib.mmgap_server_destroy.argtypes = [_vp]
 for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
            "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
            "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant", "mmgap_get_solver_variant",
+           "mmgap_detect_e",
            "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run", "mmgap_batch_destroy", "mmgap_server_create",
            "mmgap_server_submit", "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy"):
     getattr(_lib, _f).restype = C.c_int
@@ -113,6 +115,7 @@ for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detec
 ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
                "mmgap_precode", "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing",
                "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant",
+               "mmgap_detect_e",
                "mmgap_get_solver_variant", "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run",
                "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_wait",
                "mmgap_server_stats", "mmgap_server_destroy")
@@ -225,6 +228,28 @@ class Context:
             out["ndiv"] = torch.empty(P, dtype=torch.int32, device=dev)
         job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index, gram_precision)
         self.detect_jobs([job], params)
+        return out
+
+    def detect_e(self, H, y, noise_var, mod_bits: int, params: Params, seed: int, stages: int = 1, chan_index=None,
+                 want_candidates=False, gram_precision: int = 0):
+        """MMGaP-E (multi-stage, MMSE and MMSE-SIC guesses).  Returns dict(sym,
+        best, obj[, candidates (2 + 2 stages, P, 2 n_t)])."""
+        n_chan, n_r, n_t = H.shape
+        P = y.shape[0]
+        dev = self.device
+        _check(H, "H", torch.complex64, (n_chan, n_r, n_t), dev)
+        _check(y, "y", torch.complex64, (P, n_r), dev)
+        _check(noise_var, "noise_var", torch.float32, (P,), dev)
+        _check(chan_index, "chan_index", torch.int32, (P,), dev)
+        out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
+               "best": torch.empty(P, dtype=torch.int32, device=dev),
+               "obj": torch.empty(P, dtype=torch.float32, device=dev)}
+        if want_candidates:
+            out["candidates"] = torch.empty((2 + 2 * stages, P, 2 * n_t), dtype=torch.int8, device=dev)
+        job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index, gram_precision)
+        cp = params._c()
+        self._raise(_lib.mmgap_detect_e(self._h, C.byref(cp), C.byref(job), stages, _ptr(out["best"]),
+                                        _ptr(out["obj"]), _ptr(out.get("candidates")), self._stream()))
         return out
 
     def detect_job(self, H, y, noise_var, mod_bits, seed, out, chan_index=None, gram_precision=0) -> _DetectJob:

@@ -133,6 +133,7 @@ template <int NT> struct OpVppInv { static cudaError_t run(const VppInvArgs& a, 
 template <int NT> struct OpVppBuild { static cudaError_t run(const VppBuildArgs& a, cudaStream_t s) { return launch_vpp_build<NT>(a, s); } };
 template <int NT> struct OpVppOut { static cudaError_t run(const VppOutArgs& a, cudaStream_t s) { return launch_vpp_output<NT>(a, s); } };
 template <int NT> struct OpGram { static cudaError_t run(const GramArgs& a, cudaStream_t s) { return launch_gram_tc<NT>(a, s); } };
+template <int NT> struct OpSelect { static cudaError_t run(const SelectArgs& a, cudaStream_t s) { return launch_select<NT>(a, s); } };
 
 // QAM normalisation kappa = 1/sqrt(2 (M-1)/3) and kappa^2, rounded once to float.
 void qam_kappa(int mod_bits, float* kappa, float* kappa2) {
@@ -576,6 +577,120 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
             if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_output launch");
             if ((st = timing_mark(ctx, 3, s)) != MMGAP_OK) return st;
         }
+    }
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job* job, int stages,
+                            int32_t* best_out, float* obj_out, int8_t* cand_out, void* stream) {
+    if (!ctx) return MMGAP_EINVAL;
+    mmgap_status st = check_params(ctx, params);
+    if (st != MMGAP_OK) return st;
+    if (!job) return fail(ctx, MMGAP_EINVAL, "job is NULL");
+    if ((st = check_detect_job(ctx, *job, true)) != MMGAP_OK) return st;
+    if (stages < 1 || stages > 8) return fail(ctx, MMGAP_EINVAL, "stages=%d out of [1, 8]", stages);
+    const mmgap_detect_job& J = *job;
+    if (J.n_problems == 0) return MMGAP_OK;
+    CurrentDevice cd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = 2 * J.n_t, nc = 2 + 2 * stages;
+    const EulerConsts k = euler_consts(*params);
+    timing_begin(ctx);
+    if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
+    float* gc = nullptr;
+    size_t gc_bytes = 0;
+    if ((st = job_gram(ctx, J, s, &gc, &gc_bytes)) != MMGAP_OK) return st;
+    char* base = ctx->ws + gc_bytes;
+    const size_t avail = ctx->ws_bytes - gc_bytes;
+    const size_t per = align_up((size_t)n * n * 2) + align_up((size_t)n * 2) + align_up((size_t)n) + (size_t)nc * n;
+    long long chunk = (long long)(avail / (per + 5 * kAlign));
+    if (chunk < 1) return fail(ctx, MMGAP_ENOMEM, "workspace of %zu bytes holds no problem", ctx->ws_bytes);
+    if (chunk > J.n_problems) chunk = J.n_problems;
+    float kappa, kappa2;
+    qam_kappa(J.mod_bits, &kappa, &kappa2);
+    for (long long p0 = 0; p0 < J.n_problems; p0 += chunk) {
+        const int P = (int)std::min<long long>(chunk, J.n_problems - p0);
+        int16_t* Aq = (int16_t*)base;
+        int16_t* hq = (int16_t*)(base + align_up((size_t)P * n * n * 2));
+        int8_t* gtmp = (int8_t*)((char*)hq + align_up((size_t)P * n * 2));
+        int8_t* cand = (int8_t*)((char*)gtmp + align_up((size_t)P * n));
+        auto C = [&](int c) { return cand + (size_t)c * P * n; };
+        if (p0 > 0 && (st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
+        BuildArgs b{};
+        b.H = J.chan_index ? J.H : J.H + (size_t)p0 * 2 * J.n_r * J.n_t;
+        b.chan_index = J.chan_index ? J.chan_index + p0 : nullptr;
+        b.y = J.y + (size_t)p0 * 2 * J.n_r;
+        b.noise_var = J.noise_var + p0;
+        b.n_r = J.n_r;
+        b.mod_bits = J.mod_bits;
+        b.n_problems = P;
+        b.n_chan = J.chan_index ? J.n_chan : P;
+        b.kappa = kappa;
+        b.kappa2 = kappa2;
+        b.err = ctx->dev_err;
+        b.Aq = Aq;
+        b.hq = hq;
+        b.Gc_pre = gc ? (J.chan_index ? gc : gc + (size_t)p0 * 2 * J.n_t * J.n_t) : nullptr;
+        SolveArgs a{};
+        a.Aq = Aq;
+        a.hq = hq;
+        a.level_max = (1 << (J.mod_bits >> 1)) - 1;
+        a.n_problems = P;
+        a.steps = params->steps;
+        a.f_mvm = params->f_mvm;
+        a.problem_offset = (uint64_t)p0;
+        a.k = k;
+        a.mod_bits = J.mod_bits;
+        a.variant = ctx->variant[J.n_t];
+        cudaError_t e = cudaSuccess;
+        for (int stg = 1; stg <= stages && e == cudaSuccess; ++stg)
+            for (int inst = 0; inst < 2 && e == cudaSuccess; ++inst) {
+                // instance inst of stage stg: around the MMSE / SIC guess (stage 1) or
+                // around its own previous solution
+                if (stg == 1) {
+                    b.guess_mode = inst;  // 0 MMSE, 1 MMSE-SIC
+                    b.g_in = nullptr;
+                    b.g = C(inst);
+                } else {
+                    b.guess_mode = 2;
+                    b.g_in = C(2 + 2 * (stg - 2) + inst);
+                    b.g = gtmp;
+                }
+                e = dispatch_nt<OpBuild>(J.n_t, b, s);
+                if (e != cudaSuccess) break;
+                const uint64_t seed = J.seed + (uint64_t)(2 * (stg - 1) + inst) * 0x9E3779B97F4A7C15ULL;
+                a.key0 = (uint32_t)seed;
+                a.key1 = (uint32_t)(seed >> 32);
+                a.g = stg == 1 ? C(inst) : C(2 + 2 * (stg - 2) + inst);
+                a.x_out = C(2 + 2 * (stg - 1) + inst);
+                e = dispatch_nt<OpSolve>(J.n_t, a, params->runs, s);
+            }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "MMGaP-E stage launch");
+        if ((st = timing_mark(ctx, 1, s)) != MMGAP_OK) return st;
+        if ((st = timing_mark(ctx, 2, s)) != MMGAP_OK) return st;
+        SelectArgs sa{};
+        sa.H = b.H;
+        sa.chan_index = b.chan_index;
+        sa.y = b.y;
+        sa.n_r = J.n_r;
+        sa.mod_bits = J.mod_bits;
+        sa.n_problems = P;
+        sa.n_chan = b.n_chan;
+        sa.kappa = kappa;
+        sa.cand = cand;
+        sa.n_cand = nc;
+        sa.sym_out = J.sym_out + (size_t)p0 * J.n_t;
+        sa.best_out = best_out ? best_out + p0 : nullptr;
+        sa.obj_out = obj_out ? obj_out + p0 : nullptr;
+        e = dispatch_nt<OpSelect>(J.n_t, sa, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "select launch");
+        if (cand_out)
+            for (int c = 0; c < nc; ++c) {
+                e = cudaMemcpyAsync(cand_out + ((size_t)c * J.n_problems + p0) * n, C(c), (size_t)P * n,
+                                    cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "candidate copy");
+            }
+        if ((st = timing_mark(ctx, 3, s)) != MMGAP_OK) return st;
     }
     return MMGAP_OK;
 }

@@ -40,6 +40,7 @@ struct SolveArgs {
     uint8_t* sym_out;          // [P][n_t] or nullptr
     int mod_bits;
     int variant;               // SolverVariant; 0 = the size's default
+    int8_t* x_out;             // [P][n] selected lattice point g + 2d, or nullptr
 };
 
 // Launch shapes of the solver.  All produce bit-identical results.
@@ -68,6 +69,8 @@ struct BuildArgs {
     float kappa, kappa2;
     int* err;                  // device error word (bit 0: channel index out of range)
     const float* Gc_pre;       // optional precomputed Gram of kappa H per channel, complex [n_chan][n_t][n_t]
+    int guess_mode;            // 0: MMSE, 1: MMSE-SIC (sorted Cholesky), 2: given g_in
+    const int8_t* g_in;        // [P][n] lattice guesses for guess_mode 2
     // outputs
     int16_t* Aq;               // [P][n][n]
     int16_t* hq;               // [P][n]
@@ -86,6 +89,20 @@ struct GramArgs {
     float kappa;
     int fp16;         // 0: BF16 operands, 1: FP16 operands, 2: split BF16 (hi + lo, three products)
     float* Gc;        // complex [n_chan][n_t][n_t]
+};
+
+// Best of several lattice candidates per problem by the FP32 ML objective.
+struct SelectArgs {
+    const float* H;            // complex [n_chan][n_r][n_t]
+    const int32_t* chan_index;
+    const float* y;            // complex [P][n_r]
+    int n_r, mod_bits, n_problems, n_chan;
+    float kappa;
+    const int8_t* cand;        // [n_cand][P][n]
+    int n_cand;
+    uint8_t* sym_out;          // [P][n_t]
+    int32_t* best_out;         // [P] or nullptr
+    float* obj_out;            // [P] or nullptr
 };
 
 struct VppInvArgs {
@@ -130,6 +147,7 @@ template <int NT> cudaError_t launch_build_detect(const BuildArgs& a, cudaStream
 template <int NT> cudaError_t launch_solve(const SolveArgs& a, int runs, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_inverse(const VppInvArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_gram_tc(const GramArgs& a, cudaStream_t s);
+template <int NT> cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_build(const VppBuildArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_output(const VppOutArgs& a, cudaStream_t s);
 

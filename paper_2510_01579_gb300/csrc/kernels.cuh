@@ -82,8 +82,9 @@ constexpr int kBuildWarps = 4;
 
 template <int NT>
 __host__ __device__ constexpr int build_smem_floats(int n_r) {
-    // Hs [n_r][NT] c, Gc [NT][NT] c, L [NT][NT] c, y [n_r] c, z [n_r] c, m [NT] c, g [2NT], flag
-    return 2 * n_r * NT + 4 * NT * NT + 4 * n_r + 4 * NT + 4;
+    // Hs [n_r][NT] c, Gc [NT][NT] c, L [NT][NT] c, y [n_r] c, z [n_r] c, m [NT] c, g [2NT],
+    // flag + pivot scratch (perm [NT], d [NT])
+    return 2 * n_r * NT + 4 * NT * NT + 4 * n_r + 4 * NT + 4 + 2 * NT;
 }
 
 // Where one problem's build writes its results (global or shared memory).
@@ -110,6 +111,8 @@ __device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, in
     float* mv = zv + 2 * n_r;  // matched filter [NT] c
     float* gv = mv + 2 * NT;   // g as floats [2NT]
     int* flag = reinterpret_cast<int*>(gv + 2 * NT);
+    int* perm = flag + 4;      // position -> user (SIC)
+    float* dg = reinterpret_cast<float*>(perm + NT);  // current Schur diagonal per user (SIC)
 
     const int c = a.chan_index ? a.chan_index[p] : p;
     if (c < 0 || c >= a.n_chan) {  // bad channel index: flag it, emit an all-zero problem
@@ -179,95 +182,156 @@ __device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, in
     }
     __syncwarp();
 
-    // MMSE (Eq. 3): Cholesky of G_c + rho I (rho = noise_var kappa^2),
-    // left-looking, one column per step; lane j the pivot, lanes i > j the rest.
-    const float rho = mulrn(a.noise_var[p], a.kappa2);
-    for (int j = 0; j < NT; ++j) {
-        if (lane == j) {
-            float d = addrn(Gc[2 * (j * NT + j)], rho);
-            for (int k = 0; k < j; ++k) {
-                const float lr = Lc[2 * (j * NT + k)], li = Lc[2 * (j * NT + k) + 1];
-                d = fmarn(-lr, lr, d);
-                d = fmarn(-li, li, d);
-            }
-            const bool ok = (d > 0.0f) && !isinf(d);
-            if (!ok) flag[0] = 1;
-            Lc[2 * (j * NT + j)] = ok ? __fsqrt_rn(d) : 1.0f;
-            Lc[2 * (j * NT + j) + 1] = 0.0f;
-        }
-        __syncwarp();
-        const float ljj = Lc[2 * (j * NT + j)];
-        if (lane > j && lane < NT) {
-            const int i = lane;
-            float re = Gc[2 * (i * NT + j)], im = Gc[2 * (i * NT + j) + 1];
-            for (int k = 0; k < j; ++k) {
-                const float ar = Lc[2 * (i * NT + k)], ai = Lc[2 * (i * NT + k) + 1];
-                const float br = Lc[2 * (j * NT + k)], bi = Lc[2 * (j * NT + k) + 1];
-                re = fmarn(-ar, br, re);
-                re = fmarn(-ai, bi, re);
-                im = fmarn(-ai, br, im);
-                im = fmarn(ar, bi, im);
-            }
-            Lc[2 * (i * NT + j)] = __fdiv_rn(re, ljj);
-            Lc[2 * (i * NT + j) + 1] = __fdiv_rn(im, ljj);
-        }
-        __syncwarp();
-    }
-    const bool chol_failed = flag[0] != 0;
-
-    // forward solve L w = m (right-looking; per row the updates arrive in
-    // ascending k, the same sequence as the left-looking sum)
-    float accr = 0.0f, acci = 0.0f;
-    if (lane < NT) { accr = mv[2 * lane]; acci = mv[2 * lane + 1]; }
-    float wr = 0.0f, wi = 0.0f;
-    for (int k = 0; k < NT; ++k) {
-        if (lane == k) {
-            const float lkk = Lc[2 * (k * NT + k)];
-            wr = __fdiv_rn(accr, lkk);
-            wi = __fdiv_rn(acci, lkk);
-        }
-        const float br = __shfl_sync(0xffffffffu, wr, k), bi = __shfl_sync(0xffffffffu, wi, k);
-        if (lane > k && lane < NT) {
-            const float ar = Lc[2 * (lane * NT + k)], ai = Lc[2 * (lane * NT + k) + 1];
-            accr = fmarn(-ar, br, accr);
-            accr = fmarn(ai, bi, accr);
-            acci = fmarn(-ar, bi, acci);
-            acci = fmarn(-ai, br, acci);
-        }
-    }
-    // backward solve L^H x = w, k descending
-    accr = wr;
-    acci = wi;
-    float xr = 0.0f, xi = 0.0f;
-    for (int k = NT - 1; k >= 0; --k) {
-        if (lane == k) {
-            const float lkk = Lc[2 * (k * NT + k)];
-            xr = __fdiv_rn(accr, lkk);
-            xi = __fdiv_rn(acci, lkk);
-        }
-        const float br = __shfl_sync(0xffffffffu, xr, k), bi = __shfl_sync(0xffffffffu, xi, k);
-        if (lane < k) {
-            const float ar = Lc[2 * (k * NT + lane)], ai = Lc[2 * (k * NT + lane) + 1];
-            accr = fmarn(-ar, br, accr);
-            accr = fmarn(-ai, bi, accr);
-            acci = fmarn(-ar, bi, acci);
-            acci = fmarn(ai, br, acci);
-        }
-    }
-    // hard decision to the nearest alphabet point (ties upward)
     const int side = 1 << (a.mod_bits >> 1);
     const float Lm = (float)(side - 1);
-    if (lane < NT) {
-        float v[2] = {chol_failed ? 0.0f : xr, chol_failed ? 0.0f : xi};
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            float xc = fmaxf(v[cc], -Lm);
-            xc = fminf(xc, Lm);
-            const int gi = 2 * (int)floorf(mulrn(xc, 0.5f)) + 1;
-            gv[cc * NT + lane] = (float)gi;
+    auto slice = [&](float v) -> float {  // nearest alphabet point (ties upward)
+        float xc = fmaxf(v, -Lm);
+        xc = fminf(xc, Lm);
+        return (float)(2 * (int)floorf(mulrn(xc, 0.5f)) + 1);
+    };
+    if (a.guess_mode == 2) {
+        // externally supplied guess (a previous stage's solution)
+        if (lane < NT) {
+            gv[lane] = (float)a.g_in[(size_t)p * n + lane];
+            gv[NT + lane] = (float)a.g_in[(size_t)p * n + NT + lane];
         }
+        __syncwarp();
+    } else {
+        // Cholesky of B = G_c + rho I (rho = noise_var kappa^2), left-looking, one
+        // column per step; lane j the pivot, lanes i > j the rest.  MMSE (Eq. 3)
+        // factors in natural order; MMSE-SIC (Sec. 3.2.2) pivots on the smallest
+        // current Schur diagonal (ties: first position), rows of L being positions.
+        const bool sic = a.guess_mode == 1;
+        const float rho = mulrn(a.noise_var[p], a.kappa2);
+        if (lane < NT) {
+            perm[lane] = lane;
+            dg[lane] = addrn(Gc[2 * (lane * NT + lane)], rho);
+        }
+        __syncwarp();
+        for (int j = 0; j < NT; ++j) {
+            if (sic) {
+                if (lane == 0) {
+                    int best = j;
+                    for (int i = j + 1; i < NT; ++i)
+                        if (dg[perm[i]] < dg[perm[best]]) best = i;
+                    flag[1] = best;
+                    const int t = perm[j];
+                    perm[j] = perm[best];
+                    perm[best] = t;
+                }
+                __syncwarp();
+                const int best = flag[1];
+                if (lane < j && best != j) {  // swap the computed part of rows j and best
+                    const float r0 = Lc[2 * (j * NT + lane)], r1 = Lc[2 * (j * NT + lane) + 1];
+                    Lc[2 * (j * NT + lane)] = Lc[2 * (best * NT + lane)];
+                    Lc[2 * (j * NT + lane) + 1] = Lc[2 * (best * NT + lane) + 1];
+                    Lc[2 * (best * NT + lane)] = r0;
+                    Lc[2 * (best * NT + lane) + 1] = r1;
+                }
+                __syncwarp();
+            }
+            const int u = sic ? perm[j] : j;
+            if (lane == j) {
+                float d;
+                if (sic) {
+                    d = dg[u];
+                } else {
+                    d = addrn(Gc[2 * (j * NT + j)], rho);
+                    for (int k = 0; k < j; ++k) {
+                        const float lr = Lc[2 * (j * NT + k)], li = Lc[2 * (j * NT + k) + 1];
+                        d = fmarn(-lr, lr, d);
+                        d = fmarn(-li, li, d);
+                    }
+                }
+                const bool ok = (d > 0.0f) && !isinf(d);
+                if (!ok) flag[0] = 1;
+                Lc[2 * (j * NT + j)] = ok ? __fsqrt_rn(d) : 1.0f;
+                Lc[2 * (j * NT + j) + 1] = 0.0f;
+            }
+            __syncwarp();
+            const float ljj = Lc[2 * (j * NT + j)];
+            if (lane > j && lane < NT) {
+                const int i = lane;
+                const int v = sic ? perm[i] : i;
+                float re = Gc[2 * (v * NT + u)], im = Gc[2 * (v * NT + u) + 1];
+                for (int k = 0; k < j; ++k) {
+                    const float ar = Lc[2 * (i * NT + k)], ai = Lc[2 * (i * NT + k) + 1];
+                    const float br = Lc[2 * (j * NT + k)], bi = Lc[2 * (j * NT + k) + 1];
+                    re = fmarn(-ar, br, re);
+                    re = fmarn(-ai, bi, re);
+                    im = fmarn(-ai, br, im);
+                    im = fmarn(ar, bi, im);
+                }
+                const float lr = __fdiv_rn(re, ljj), li = __fdiv_rn(im, ljj);
+                Lc[2 * (i * NT + j)] = lr;
+                Lc[2 * (i * NT + j) + 1] = li;
+                if (sic) {
+                    float dv = dg[v];
+                    dv = fmarn(-lr, lr, dv);
+                    dv = fmarn(-li, li, dv);
+                    dg[v] = dv;
+                }
+            }
+            __syncwarp();
+        }
+        const bool chol_failed = flag[0] != 0;
+
+        // forward solve L w = P m (right-looking; per row the updates arrive in
+        // ascending k, the same sequence as the left-looking sum)
+        float accr = 0.0f, acci = 0.0f;
+        if (lane < NT) {
+            const int src = sic ? perm[lane] : lane;
+            accr = mv[2 * src];
+            acci = mv[2 * src + 1];
+        }
+        float wr = 0.0f, wi = 0.0f;
+        for (int k = 0; k < NT; ++k) {
+            if (lane == k) {
+                const float lkk = Lc[2 * (k * NT + k)];
+                wr = __fdiv_rn(accr, lkk);
+                wi = __fdiv_rn(acci, lkk);
+            }
+            const float br = __shfl_sync(0xffffffffu, wr, k), bi = __shfl_sync(0xffffffffu, wi, k);
+            if (lane > k && lane < NT) {
+                const float ar = Lc[2 * (lane * NT + k)], ai = Lc[2 * (lane * NT + k) + 1];
+                accr = fmarn(-ar, br, accr);
+                accr = fmarn(ai, bi, accr);
+                acci = fmarn(-ar, bi, acci);
+                acci = fmarn(-ai, br, acci);
+            }
+        }
+        // backward solve L^H x = w, k descending; SIC slices each x_k before
+        // it is substituted (successive interference cancellation)
+        accr = wr;
+        acci = wi;
+        float xr = 0.0f, xi = 0.0f;
+        for (int k = NT - 1; k >= 0; --k) {
+            if (lane == k) {
+                const float lkk = Lc[2 * (k * NT + k)];
+                xr = __fdiv_rn(accr, lkk);
+                xi = __fdiv_rn(acci, lkk);
+                if (sic) {
+                    xr = slice(xr);
+                    xi = slice(xi);
+                }
+            }
+            const float br = __shfl_sync(0xffffffffu, xr, k), bi = __shfl_sync(0xffffffffu, xi, k);
+            if (lane < k) {
+                const float ar = Lc[2 * (k * NT + lane)], ai = Lc[2 * (k * NT + lane) + 1];
+                accr = fmarn(-ar, br, accr);
+                accr = fmarn(-ai, bi, accr);
+                acci = fmarn(-ar, bi, acci);
+                acci = fmarn(ai, br, acci);
+            }
+        }
+        // hard decision to the nearest alphabet point (ties upward)
+        if (lane < NT) {
+            const int dst = sic ? perm[lane] : lane;
+            gv[dst] = slice(chol_failed ? 0.0f : xr);
+            gv[NT + dst] = slice(chol_failed ? 0.0f : xi);
+        }
+        __syncwarp();
     }
-    __syncwarp();
 
     // residual z = y - Hs g, field h_c = Hs^H z
     for (int k = lane; k < n_r; k += 32) {
@@ -591,6 +655,10 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
         if (a.E_out) a.E_out[p] = bestE;
         if (a.run_out) a.run_out[p] = best_run;
         if (a.ndiv_out) a.ndiv_out[p] = ndiv;
+        if (a.x_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) a.x_out[(size_t)p * n + i] = (int8_t)((int)sm.g[i] + 2 * (keep ? d[i] : 0));
+        }
         if (a.sym_out) {
             // fused decode: lattice x = g + 2d -> symbol index
             const int side = 1 << (a.mod_bits >> 1), L = side - 1;
@@ -897,6 +965,11 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
             if (a.E_out) a.E_out[p] = bestE;
             if (a.run_out) a.run_out[p] = best_run;
             if (a.ndiv_out) a.ndiv_out[p] = ndiv;
+            if (a.x_out) {
+#pragma unroll
+                for (int i = 0; i < n; ++i)
+                    a.x_out[(size_t)p * n + i] = (int8_t)((int)sm.g[i] + 2 * (keep ? d[i] : 0));
+            }
             if (a.sym_out) {
                 const int side = 1 << (a.mod_bits >> 1), L = side - 1;
                 uint8_t* so = a.sym_out + (size_t)p * NT;
@@ -1287,6 +1360,83 @@ cudaError_t launch_gram_tc_impl(const GramArgs& a, cudaStream_t s) {
 }
 
 // =========================================================================
+// MMGaP-E selection (Sec. 3.2.2: the overall best solution is the output):
+// one warp per problem evaluates ||y - Hs x||^2 of every lattice candidate in
+// FP32 (residual r_k = y_k - sum_j Hs_kj x_j with j ascending, lanes over k;
+// then lane 0 sums k ascending) and keeps the first smallest.
+// =========================================================================
+template <int NT>
+__global__ void __launch_bounds__(128) select_kernel(SelectArgs a) {
+    extern __shared__ __align__(16) float ssel[];
+    constexpr int n = 2 * NT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 4 + warp;
+    if (p >= a.n_problems) return;
+    const int n_r = a.n_r;
+    float* Hs = ssel + (size_t)warp * (2 * kMaxNr * NT + 2 * kMaxNr + 2 * kMaxNr);
+    float* yv = Hs + 2 * kMaxNr * NT;
+    float* rr = yv + 2 * kMaxNr;
+    int c = a.chan_index ? a.chan_index[p] : p;
+    if (c < 0 || c >= a.n_chan) c = 0;  // flagged by the build stage
+    const float* Hg = a.H + (size_t)c * 2 * n_r * NT;
+    for (int e = lane; e < 2 * n_r * NT; e += 32) Hs[e] = mulrn(a.kappa, Hg[e]);
+    for (int e = lane; e < 2 * n_r; e += 32) yv[e] = a.y[(size_t)p * 2 * n_r + e];
+    __syncwarp();
+    float best_obj = 0.0f;
+    int best = 0;
+    for (int cand = 0; cand < a.n_cand; ++cand) {
+        const int8_t* x = a.cand + ((size_t)cand * a.n_problems + p) * n;
+        for (int k = lane; k < n_r; k += 32) {
+            float re = yv[2 * k], im = yv[2 * k + 1];
+            for (int j = 0; j < NT; ++j) {
+                const float ar = Hs[2 * (k * NT + j)], ai = Hs[2 * (k * NT + j) + 1];
+                const float br = (float)x[j], bi = (float)x[NT + j];
+                re = fmarn(-ar, br, re);
+                re = fmarn(ai, bi, re);
+                im = fmarn(-ar, bi, im);
+                im = fmarn(-ai, br, im);
+            }
+            rr[2 * k] = re;
+            rr[2 * k + 1] = im;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            float obj = 0.0f;
+            for (int k = 0; k < n_r; ++k) {
+                obj = fmarn(rr[2 * k], rr[2 * k], obj);
+                obj = fmarn(rr[2 * k + 1], rr[2 * k + 1], obj);
+            }
+            if (cand == 0 || obj < best_obj) {
+                best_obj = obj;
+                best = cand;
+            }
+        }
+        __syncwarp();
+    }
+    best = __shfl_sync(0xffffffffu, best, 0);
+    const int8_t* x = a.cand + ((size_t)best * a.n_problems + p) * n;
+    const int side = 1 << (a.mod_bits >> 1), L = side - 1;
+    if (lane < NT) {
+        const int xr = x[lane], xi = x[NT + lane];
+        a.sym_out[(size_t)p * NT + lane] = (uint8_t)(((xr + L) / 2) * side + (xi + L) / 2);
+    }
+    if (lane == 0) {
+        if (a.best_out) a.best_out[p] = best;
+        if (a.obj_out) a.obj_out[p] = best_obj;
+    }
+}
+
+template <int NT>
+cudaError_t launch_select_impl(const SelectArgs& a, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    const size_t smem = (size_t)4 * (2 * kMaxNr * NT + 4 * kMaxNr) * sizeof(float);
+    cudaError_t err = cudaFuncSetAttribute(select_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    select_kernel<NT><<<(a.n_problems + 3) / 4, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// =========================================================================
 // Downlink VPP (Sec. 3.3) in FP64.
 // =========================================================================
 constexpr int kVppMaxNt = 64;
@@ -1634,5 +1784,8 @@ cudaError_t launch_vpp_output_impl(const VppOutArgs& a, cudaStream_t s) {
     }                                                                                                          \
     template <> cudaError_t launch_gram_tc<NT>(const GramArgs& a, cudaStream_t s) {                            \
         return launch_gram_tc_impl<NT>(a, s);                                                                  \
+    }                                                                                                          \
+    template <> cudaError_t launch_select<NT>(const SelectArgs& a, cudaStream_t s) {                           \
+        return launch_select_impl<NT>(a, s);                                                                   \
     }                                                                                                          \
     }

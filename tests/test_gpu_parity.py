@@ -378,3 +378,24 @@ def test_autotuner_picks_a_compiled_shape(mm):
         got = _detect(ctx, w, prm, 3)
     ref = oracle.detect_batch(w["H"], w["y"], w["noise_var"], 4, oparams(prm), 3, w["chan_index"])
     assert np.array_equal(got["sym"], ref["sym"]) and np.array_equal(got["energy"], ref["E"])
+
+
+# ------------------------------------------------------------- MMGaP-E
+@pytest.mark.parametrize("n_r,nt,mb,stages,hold", [(8, 8, 6, 1, "problem"), (16, 16, 6, 2, "subcarrier"),
+                                                   (4, 4, 2, 2, "prb"), (12, 8, 4, 3, "problem"),
+                                                   (3, 3, 4, 1, "problem")])
+def test_detect_e_bit_exact(mm, n_r, nt, mb, stages, hold):
+    pkg, ctx = mm
+    w = synth.uplink(700 + nt + stages, n_r, nt, mb, n_sub=9, n_sym=2, snr_db=20.0, hold=hold)
+    prm = pkg.Params.default(steps=70)
+    out = ctx.detect_e(T(w["H"]), T(w["y"]), T(w["noise_var"]), mb, prm, 31, stages=stages,
+                       chan_index=T(w["chan_index"]), want_candidates=True)
+    torch.cuda.synchronize()
+    cands = out["candidates"].cpu().numpy()
+    for p in range(w["y"].shape[0]):
+        c = int(w["chan_index"][p])
+        r = oracle.detect_e(w["H"][c], w["y"][p], w["noise_var"][p], mb, stages, oparams(prm), 31, p)
+        assert np.array_equal(cands[:, p, :], r["candidates"].astype(np.int8)), p
+        assert int(out["best"][p]) == r["best"]
+        assert float(out["obj"][p]) == np.float32(r["obj"])
+        assert np.array_equal(out["sym"][p].cpu().numpy(), r["sym"])

@@ -407,3 +407,100 @@ def test_vpp_ground_state_is_best_perturbation():
                    for c in itertools.product([-1, 0, 1], repeat=4))
         got = np.linalg.norm(W @ (ul + 8 * (d[:2] + 1j * d[2:]))) ** 2
         assert math.isclose(got, best, rel_tol=1e-9)
+
+
+# ------------------------------------------------------------- MMGaP-E
+def _slice(v, L):
+    v = min(max(v, -L), L)
+    return 2 * math.floor(v / 2) + 1
+
+
+def test_sic_single_user_is_mmse():
+    """With one user there is nothing to cancel: SIC = MMSE hard decision."""
+    rng = np.random.default_rng(201)
+    for mb in (2, 4, 6):
+        H, y = _rand_problem(rng, 3, 1, mb, 0.3)
+        H32, y32 = H.astype(np.complex64), y.astype(np.complex64)
+        g, perm, st = o.sic_guess32(H32, y32, 0.3, mb)
+        b = o.build_detect32(H32, y32, np.float32(0.3), mb)
+        assert st == 0 and list(perm) == [0] and np.array_equal(g, b["g"])
+
+
+def test_sic_is_successive_mmse_on_reduced_systems():
+    """Sec. 3.2.2's MMSE-SIC guess: the user detected at each step is the slice of
+    the MMSE estimate of the system with the users detected so far cancelled
+    (explicit FP64 inverses here, a Cholesky back substitution in the oracle),
+    in the oracle's order; the first factored user has the smallest B_ii."""
+    rng = np.random.default_rng(202)
+    checked = 0
+    for _ in range(40):
+        n_t, mb, nv = 6, 4, 0.05
+        H, y = _rand_problem(rng, 6, n_t, mb, nv)
+        H32, y32 = H.astype(np.complex64), y.astype(np.complex64)
+        g, perm, st = o.sic_guess32(H32, y32, nv, mb)
+        k = o.qam_kappa(mb)
+        Hs = k * H32.astype(np.complex128)
+        yy = y32.astype(np.complex128)
+        rho = np.float32(nv) * k * k
+        B = Hs.conj().T @ Hs + rho * np.eye(n_t)
+        assert perm[0] == int(np.argmin(np.real(np.diag(B))))
+        L = (1 << (mb // 2)) - 1
+        remaining = list(range(n_t))
+        resid = yy.copy()
+        ok = True
+        for pos in range(n_t - 1, -1, -1):
+            u = int(perm[pos])
+            Hr = Hs[:, remaining]
+            est = np.linalg.solve(Hr.conj().T @ Hr + rho * np.eye(len(remaining)), Hr.conj().T @ resid)
+            xu = est[remaining.index(u)]
+            near = min(abs(xu.real - round(xu.real / 2) * 2), abs(xu.imag - round(xu.imag / 2) * 2))
+            if near < 1e-3:  # too close to a decision boundary for an FP32 / FP64 comparison
+                ok = False
+                break
+            dec = complex(_slice(xu.real, L), _slice(xu.imag, L))
+            assert (g[u], g[n_t + u]) == (int(dec.real), int(dec.imag))
+            resid = resid - Hs[:, u] * dec
+            remaining.remove(u)
+        checked += ok
+    assert checked >= 30
+
+
+def test_sic_recovers_noise_free_symbols():
+    rng = np.random.default_rng(203)
+    for _ in range(10):
+        n_t, mb = 8, 4
+        H = synth.channels(rng, 1, 8, n_t)[0].astype(np.complex64)
+        sym = rng.integers(0, 16, n_t)
+        y = (H.astype(np.complex128) @ synth.symbols_to_complex(sym, mb)).astype(np.complex64)
+        g, _, _ = o.sic_guess32(H, y, 1e-6, mb)
+        assert np.array_equal(o.decode_detect(n_t, mb, g, np.zeros(2 * n_t, np.int8)), sym)
+
+
+def test_detect_e_candidates_and_selection():
+    """MMGaP-E: candidates are [MMSE guess, SIC guess, stage solutions]; the
+    output is the candidate with the smallest ML objective (Eq. 2, checked in
+    FP64), and the FP32 objective matches FP64 to 1e-5."""
+    w = synth.uplink(204, 8, 8, 6, n_sub=12, n_sym=1, snr_db=22.0, hold="problem")
+    prm = o.Params(steps=80)
+    for p in range(12):
+        r = o.detect_e(w["H"][p], w["y"][p], w["noise_var"][p], 6, 2, prm, 9, p)
+        X = r["candidates"]
+        b = o.build_detect32(w["H"][p], w["y"][p], w["noise_var"][p], 6)
+        gs, _, _ = o.sic_guess32(w["H"][p], w["y"][p], w["noise_var"][p], 6)
+        assert np.array_equal(X[0], b["g"]) and np.array_equal(X[1], gs)
+        H64, y64 = w["H"][p].astype(np.complex128), w["y"][p].astype(np.complex128)
+        objs = [o.ml_objective(H64, y64, x, 6) for x in X]
+        assert abs(r["obj"] - objs[r["best"]]) <= 1e-5 * max(1.0, objs[r["best"]])
+        assert objs[r["best"]] <= min(objs) * (1 + 1e-5) + 1e-6
+        assert np.array_equal(r["sym"], o.decode_detect(8, 6, X[r["best"]], np.zeros(16, np.int8)))
+    assert o.stage_seed(9, 1, 0) == 9
+
+
+def test_mmgap_e_improves_on_mmgap_at_64qam():
+    """Behaviour (Sec. 5.2): at 64-QAM and high SNR the single MMSE guess limits
+    MMGaP; MMGaP-E with the SIC guess does better."""
+    w = synth.uplink(205, 8, 8, 6, n_sub=40, n_sym=1, snr_db=22.0, hold="problem")
+    prm = o.Params()
+    r0 = o.detect_batch(w["H"], w["y"], w["noise_var"], 6, prm, 5, w["chan_index"])
+    se = np.array([o.detect_e(w["H"][p], w["y"][p], w["noise_var"][p], 6, 1, prm, 5, p)["sym"] for p in range(40)])
+    assert synth.bit_errors(se, w["sym"], 6) < synth.bit_errors(r0["sym"], w["sym"], 6)
