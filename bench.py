@@ -436,6 +436,103 @@ def run_precision(args):
     ctx.close()
 
 
+def run_mmgap_e(args):
+    """16x16 64-QAM slot at 24 dB (i.i.d. Rayleigh): BER and time of MMSE,
+    MMSE-SIC, MMGaP and MMGaP-E (1 and 2 stages)."""
+    import torch
+
+    from paper_2510_01579_gb300 import Context, Params
+    dev = torch.device("cuda", 0)
+    prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
+    w = synth.uplink(rank_seed(0) + 100, 16, 16, 6, n_sub=args.subcarriers, snr_db=24.0)
+    H, y, nv, ci = (torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index"))
+    P = w["y"].shape[0]
+    ctx = Context(0, workspace_bytes=1 << 30)
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(1, args.steps // 4)):
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return r, statistics.mean(ts)
+
+    nbits = P * 16 * 6
+    res = {}
+    r, ms = timed(lambda: ctx.detect(H, y, nv, 6, prm, 3, chan_index=ci, want_guess=True))
+    g = r["guess"].cpu().numpy().astype(int)
+    mm = ((g[:, :16] + 7) // 2) * 8 + (g[:, 16:] + 7) // 2
+    res["mmse"] = {"ber": synth.bit_errors(mm, w["sym"], 6) / nbits}
+    res["mmgap"] = {"ber": synth.bit_errors(r["sym"].cpu().numpy(), w["sym"], 6) / nbits, "ms": ms}
+    for st in (1, 2):
+        r, ms = timed(lambda: ctx.detect_e(H, y, nv, 6, prm, 3, stages=st, chan_index=ci, want_candidates=(st == 1)))
+        if st == 1:
+            c = r["candidates"][1].cpu().numpy().astype(int)
+            sic = ((c[:, :16] + 7) // 2) * 8 + (c[:, 16:] + 7) // 2
+            res["mmse_sic"] = {"ber": synth.bit_errors(sic, w["sym"], 6) / nbits}
+        res[f"mmgap_e{st}"] = {"ber": synth.bit_errors(r["sym"].cpu().numpy(), w["sym"], 6) / nbits, "ms": ms}
+    line = {"metric": "BER of 16x16 64-QAM at 24 dB: MMSE / MMSE-SIC / MMGaP / MMGaP-E", "value": res["mmgap_e1"]["ber"],
+            "unit": "bit error rate", "n_gpus": 1, "steps": max(1, args.steps // 4), "warmup": 1,
+            "ms_per_step": res["mmgap_e1"]["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "mmgap_e", "problems": P, "runs": args.runs, "solver_steps": args.solver_steps},
+            "detectors": res}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_appendix(args):
+    """Appendix A on the GPU: 320 random Q14 instances x 32 anneals (33 spins),
+    initial amplitudes fixed by Philox across settings; for each (dt, f_mvm)
+    with N_I dt = 2.56, P_diverge and the fraction of final spin signs that
+    differ from the high-fidelity run (dt 0.01, f_mvm 1, N_I 256), after
+    aligning the global sign by the auxiliary spin."""
+    import torch
+
+    from paper_2510_01579_gb300 import Context, Params
+    dev = torch.device("cuda", 0)
+    A, h = synth.random_ising(2024, 320, 16)
+    A, h = torch.from_numpy(A).to(dev), torch.from_numpy(h).to(dev)
+    ctx = Context(0)
+    n_spins = 33
+
+    def run(dt, f):
+        prm = Params.default(dt=dt, f_mvm=f, steps=int(round(2.56 / dt)))
+        s = ctx.anneal_spins(A, h, prm, seed=11).cpu().numpy().view(np.uint64)
+        bits = np.stack([(s[..., 0] >> np.uint64(q)) & np.uint64(1) for q in range(n_spins - 1)] +
+                        [s[..., 1] & np.uint64(1)], axis=-1).astype(np.int8)
+        div = (s[..., 1] >> np.uint64(63)) & np.uint64(1)
+        return bits.reshape(-1, n_spins), div.reshape(-1).astype(bool)
+
+    t0 = time.perf_counter()
+    ref_bits, ref_div = run(0.01, 1)
+    ref_al = ref_bits ^ ref_bits[:, -1:]  # aligned by the auxiliary spin
+    grid = []
+    for dt in (0.005, 0.01, 0.02, 0.03, 0.04, 0.06, 0.08):
+        for f in (1, 2, 4, 8):
+            bits, div = run(dt, f)
+            ok = ~div & ~ref_div
+            al = bits ^ bits[:, -1:]
+            perr = float(np.mean(al[ok] != ref_al[ok])) if ok.any() else None
+            grid.append({"dt": dt, "f_mvm": f, "p_diverge": float(np.mean(div)), "p_error": perr})
+    line = {"metric": "P_diverge / P_error vs (dt, f_mvm) at N_I dt = 2.56 (Appendix A)",
+            "value": next(g["p_error"] for g in grid if g["dt"] == 0.02 and g["f_mvm"] == 2),
+            "unit": "fraction of spin signs", "n_gpus": 1, "steps": len(grid), "warmup": 0,
+            "ms_per_step": 1e3 * (time.perf_counter() - t0) / (len(grid) + 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "appendix", "instances": 320, "anneals_per_instance": 32, "spins": n_spins,
+                       "reference": "dt 0.01, f_mvm 1, N_I 256"},
+            "grid": grid}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,7 +540,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mmgap", choices=["mmgap", "reference"])
     ap.add_argument("--workload", default="ul16x16_16qam_slot",
-                    choices=sorted(WORKLOADS) + ["mixed", "serve", "precode", "precision"])
+                    choices=sorted(WORKLOADS) + ["mixed", "serve", "precode", "precision", "mmgap_e", "appendix"])
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load as a fraction of capacity")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: length of the arrival trace")
     ap.add_argument("--lanes", type=int, default=4, help="serve: concurrent launch groups (streams)")
@@ -479,6 +576,12 @@ def main():
         return
     if args.workload == "precision":
         run_precision(args)
+        return
+    if args.workload == "mmgap_e":
+        run_mmgap_e(args)
+        return
+    if args.workload == "appendix":
+        run_appendix(args)
         return
 
     import torch

@@ -220,6 +220,20 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
                                int8_t* d_out, int32_t* E_out, int32_t* run_out, int32_t* ndiv_out, void* stream);
 
 /*
+ * Integration study boundary (Appendix A): anneal n_problems quantised
+ * problems exactly as mmgap_solve_ising (no clipping, one-thread-per-anneal
+ * kernel) and return every anneal's final state instead of the selection:
+ * spins_out uint64 [n_problems][runs][2], word 0 bit q (q < 64) and word 1
+ * bit q - 64 set iff x_q >= 0 at the end (spin order x1, x2, x_a), word 1
+ * bit 63 set iff the anneal diverged.  P_diverge and P_error of the paper's
+ * (dt, f_mvm) study follow from comparing these words across parameter sets
+ * with equal N_I dt.  Uses the workspace for the discarded selection.
+ */
+mmgap_status mmgap_anneal_spins(mmgap_ctx* ctx, const mmgap_params* params, int n, int n_problems,
+                                const int16_t* A_q, const int16_t* h_q, uint64_t seed, uint64_t* spins_out,
+                                void* stream);
+
+/*
  * Builder boundary (Sec. 3.2 pre-processing, Eq. 3, Fig. 5): the delta-Ising
  * coefficients of one detection job, without solving.
  * Outputs (device): A_q int16 [P][n][n], h_q int16 [P][n], g int8 [P][n]

@@ -73,6 +73,7 @@ _lib.mmgap_device_errors.argtypes = [_vp, C.POINTER(C.c_int), C.c_int]
 _lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), _vp]
 _lib.mmgap_set_solver_variant.argtypes = [_vp, C.c_int, C.c_int]
 _lib.mmgap_detect_e.argtypes = [_vp, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int, _vp, _vp, _vp, _vp]
+_lib.mmgap_anneal_spins.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, _vp, _vp, C.c_uint64, _vp, _vp]
 _lib.mmgap_get_solver_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
 _lib.mmgap_autotune.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
 _lib.mmgap_batch_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int,
@@ -107,7 +108,7 @@ _lib.mmgap_server_destroy.argtypes = [_vp]
 for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
            "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
            "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant", "mmgap_get_solver_variant",
-           "mmgap_detect_e",
+           "mmgap_detect_e", "mmgap_anneal_spins",
            "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run", "mmgap_batch_destroy", "mmgap_server_create",
            "mmgap_server_submit", "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy"):
     getattr(_lib, _f).restype = C.c_int
@@ -115,7 +116,7 @@ for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detec
 ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
                "mmgap_precode", "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing",
                "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant",
-               "mmgap_detect_e",
+               "mmgap_detect_e", "mmgap_anneal_spins",
                "mmgap_get_solver_variant", "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run",
                "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_wait",
                "mmgap_server_stats", "mmgap_server_destroy")
@@ -306,6 +307,19 @@ class Context:
         self._raise(_lib.mmgap_solve_ising(self._h, C.byref(cp), n, P, _ptr(A_q), _ptr(h_q), _ptr(g), level_max,
                                            seed, _ptr(d), _ptr(E), _ptr(run), _ptr(nd), self._stream()))
         return dict(d=d, E=E, run=run, ndiv=nd)
+
+    def anneal_spins(self, A_q, h_q, params: Params, seed: int):
+        """Final sign bits of every anneal (Appendix A study): uint64 (P, runs, 2),
+        word 1 bit 63 = diverged."""
+        P, n, _ = A_q.shape
+        dev = self.device
+        _check(A_q, "A_q", torch.int16, (P, n, n), dev)
+        _check(h_q, "h_q", torch.int16, (P, n), dev)
+        out = torch.empty((P, params.runs, 2), dtype=torch.int64, device=dev)
+        cp = params._c()
+        self._raise(_lib.mmgap_anneal_spins(self._h, C.byref(cp), n, P, _ptr(A_q), _ptr(h_q), seed, _ptr(out),
+                                            self._stream()))
+        return out
 
     def build_detect(self, H, y, noise_var, mod_bits: int, chan_index=None, want_float=True, gram_precision=0):
         """Builder only: quantised delta-Ising coefficients of P detection problems."""

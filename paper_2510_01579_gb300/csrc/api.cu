@@ -695,6 +695,36 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
     return MMGAP_OK;
 }
 
+mmgap_status mmgap_anneal_spins(mmgap_ctx* ctx, const mmgap_params* params, int n, int n_problems, const int16_t* A_q,
+                                const int16_t* h_q, uint64_t seed, uint64_t* spins_out, void* stream) {
+    if (!ctx) return MMGAP_EINVAL;
+    mmgap_status st = check_params(ctx, params);
+    if (st != MMGAP_OK) return st;
+    if (n < 2 || (n & 1) || !nt_supported(n / 2))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "n=%d: supported 2, 4, 6, 8, 16, 32", n);
+    if (n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
+    if (n_problems == 0) return MMGAP_OK;
+    if (!A_q || !h_q || !spins_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q, h_q or spins_out");
+    CurrentDevice cd(ctx->device);
+    SolveArgs a{};
+    a.Aq = A_q;
+    a.hq = h_q;
+    a.n_problems = n_problems;
+    a.steps = params->steps;
+    a.f_mvm = params->f_mvm;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.k = euler_consts(*params);
+    a.spins_out = spins_out;
+    // the selection still runs; its outputs go to the workspace
+    if (ctx->ws_bytes < (size_t)n_problems * (n + 16) + 4 * kAlign)
+        return fail(ctx, MMGAP_ENOMEM, "workspace too small");
+    a.d_out = (int8_t*)ctx->ws;
+    cudaError_t e = dispatch_nt<OpSolve>(n / 2, a, params->runs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
+    return MMGAP_OK;
+}
+
 mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant) {
     if (!ctx) return MMGAP_EINVAL;
     if (!nt_supported(n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d", n_t);

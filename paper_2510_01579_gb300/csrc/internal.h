@@ -41,6 +41,7 @@ struct SolveArgs {
     int mod_bits;
     int variant;               // SolverVariant; 0 = the size's default
     int8_t* x_out;             // [P][n] selected lattice point g + 2d, or nullptr
+    uint64_t* spins_out;       // [P][runs][2] final sign bits per anneal (plain kernel), or nullptr
 };
 
 // Launch shapes of the solver.  All produce bit-identical results.

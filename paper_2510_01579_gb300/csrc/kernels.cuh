@@ -601,6 +601,18 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
     bool valid = true;
 #pragma unroll
     for (int q = 0; q < N; ++q) valid = valid && (fabsf(x[q]) <= k.x_max) && (e[q] > 0.0f);
+    if (a.spins_out) {  // final sign of every spin (bit q: x_q >= 0) and a divergence flag (word 1, bit 63)
+        uint64_t w0 = 0, w1 = 0;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const uint64_t bit = x[q] >= 0.0f ? 1ull : 0ull;
+            if (q < 64) w0 |= bit << q;
+            else w1 |= bit << (q - 64);
+        }
+        if (!valid) w1 |= 1ull << 63;
+        a.spins_out[((size_t)p * R + run) * 2] = w0;
+        a.spins_out[((size_t)p * R + run) * 2 + 1] = w1;
+    }
     const int sa = x[2 * n] >= 0.0f ? 1 : -1;
     int d[n];
 #pragma unroll
@@ -1730,7 +1742,7 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
 template <int NT>
 cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
-    const int v = resolve_variant(NT, a.f_mvm, a.variant);
+    const int v = a.spins_out ? (int)kVariantPlain : resolve_variant(NT, a.f_mvm, a.variant);
     if (a.f_mvm == 2) return launch_tuned<NT, 2>(a, runs, v, s);
     if (a.f_mvm == 1) return launch_tuned<NT, 1>(a, runs, v, s);
     cac_solve_kernel<NT, 0><<<a.n_problems, runs, 0, s>>>(a);

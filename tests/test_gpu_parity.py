@@ -399,3 +399,25 @@ def test_detect_e_bit_exact(mm, n_r, nt, mb, stages, hold):
         assert int(out["best"][p]) == r["best"]
         assert float(out["obj"][p]) == np.float32(r["obj"])
         assert np.array_equal(out["sym"][p].cpu().numpy(), r["sym"])
+
+
+# ------------------------------------------------------- Appendix A study
+def test_anneal_spins_bit_exact(mm):
+    """Every anneal's final sign pattern and divergence flag equal the oracle's
+    final states (random Appendix-style instances, a stable and a diverging dt)."""
+    pkg, ctx = mm
+    A, h = synth.random_ising(17, 6, 16)
+    for dt, steps in ((0.02, 128), (0.3, 60)):
+        prm = pkg.Params.default(dt=dt, steps=steps, f_mvm=2)
+        got = ctx.anneal_spins(T(A), T(h), prm, seed=77)
+        torch.cuda.synchronize()
+        got = got.cpu().numpy().view(np.uint64)
+        for p in range(6):
+            r = oracle.cac_solve(A[p], h[p], None, 0, oparams(prm), 77, p, want_states=True)
+            for run in range(prm.runs):
+                x = r["x_final"][run]
+                w0 = sum(1 << q for q in range(min(64, len(x))) if x[q] >= 0)
+                w1 = sum(1 << (q - 64) for q in range(64, len(x)) if x[q] >= 0)
+                if r["E_runs"][run] == 2 ** 31 - 1:
+                    w1 |= 1 << 63
+                assert int(got[p, run, 0]) == w0 and int(got[p, run, 1]) == w1, (dt, p, run)
