@@ -338,52 +338,71 @@ def run_serve(args):
 
 
 def run_precode(args):
-    """Downlink VPP: 3276 subcarriers of 16x16 16-QAM (one problem each), i.i.d.
-    Rayleigh; transmit power against zero forcing (v = 0)."""
+    """Downlink VPP on 3276 subcarriers (one problem each) of 8x8 and 16x16
+    16-QAM, i.i.d. Rayleigh, with the channel inverse in FP64 and in FP32 with
+    iterative refinement: slot time, inverse time, agreement of the two and
+    transmit power against zero forcing (v = 0)."""
     import torch
 
     from paper_2510_01579_gb300 import Context, Params
     dev = torch.device("cuda", 0)
     prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
-    d = synth.downlink(4000, 16, 16, 4, n_sub=args.subcarriers)
-    H, u, ci = (torch.from_numpy(d[k]).to(dev) for k in ("H", "u_sym", "chan_index"))
-    P = u.shape[0]
     ctx = Context(0, workspace_bytes=512 << 20)
-    ctx.set_timing(True)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for _ in range(args.warmup):
-        flush.zero_()
-        out = ctx.precode(H, u, 4, prm, 5, chan_index=ci)
-    torch.cuda.synchronize()
-    stages = []
-    for a, b in ev:
-        flush.zero_()
-        a.record(stream)
-        out = ctx.precode(H, u, 4, prm, 5, chan_index=ci)
-        b.record(stream)
-        stages.append(ctx.stage_times())
-    torch.cuda.synchronize()
-    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    # zero-forcing power of the same u (the v = 0 fallback), in FP64 on the host
-    side = 4
-    ul = (2 * (d["u_sym"].astype(int) // side) - 3) + 1j * (2 * (d["u_sym"].astype(int) % side) - 3)
-    Hh = d["H"].astype(np.complex128)
-    zf = np.array([np.linalg.norm(Hh[c].conj().T @ np.linalg.solve(Hh[c] @ Hh[c].conj().T, ul[p])) ** 2
-                   for p, c in enumerate(d["chan_index"])])
-    pw = out["power"].cpu().numpy().astype(np.float64)
-    line = {"metric": "precodings/s (16x16 16-QAM vector perturbation)", "value": P / (ms / 1e3), "unit": "problems/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 inverse, f32 solve", "data": "synthetic",
-            "config": {"workload": "precode", "problems_per_step": P, "runs": args.runs,
-                       "solver_steps": args.solver_steps},
-            "stage_ms": {"inverse+build": statistics.mean(s[0] for s in stages),
-                         "solve": statistics.mean(s[1] for s in stages),
-                         "output": statistics.mean(s[2] for s in stages)},
-            "power": {"mean_vpp_over_zf": float(np.mean(pw / zf)), "median_vpp_over_zf": float(np.median(pw / zf)),
-                      "frac_perturbed": float(np.mean(np.any(out["v"].cpu().numpy() != 0, axis=(1, 2))))}}
-    print(json.dumps(line), flush=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        out = None
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev), out
+
+    for n_u in (8, 16):
+        d = synth.downlink(4000 + n_u, n_u, n_u, 4, n_sub=args.subcarriers)
+        H, u, ci = (torch.from_numpy(d[k]).to(dev) for k in ("H", "u_sym", "chan_index"))
+        P = u.shape[0]
+        side = 4
+        ul = (2 * (d["u_sym"].astype(int) // side) - 3) + 1j * (2 * (d["u_sym"].astype(int) % side) - 3)
+        Hh = d["H"].astype(np.complex128)
+        zf = np.array([np.linalg.norm(Hh[c].conj().T @ np.linalg.solve(Hh[c] @ Hh[c].conj().T, ul[p])) ** 2
+                       for p, c in enumerate(d["chan_index"])])
+        res = {}
+        for name, ip in (("fp64", 0), ("fp32_ir", 1)):
+            ms_inv, (Q, st) = timed(lambda: ctx.vpp_inverse(H, ip))
+            ms, out = timed(lambda: ctx.precode(H, u, 4, prm, 5, chan_index=ci, inv_precision=ip))
+            pw = out["power"].cpu().numpy().astype(np.float64)
+            res[name] = {"ms_per_slot": ms, "problems_per_s": P / (ms / 1e3), "inverse_ms": ms_inv,
+                         "mean_power_over_zf": float(np.mean(pw / zf)),
+                         "frac_perturbed": float(np.mean(np.any(out["v"].cpu().numpy() != 0, axis=(1, 2)))),
+                         "_Q": Q, "_v": out["v"], "_pw": pw}
+        r64, rir = res["fp64"], res["fp32_ir"]
+        Q64, Qir = r64.pop("_Q"), rir.pop("_Q")
+        rel = ((Qir - Q64).abs().amax(dim=(1, 2)) / Q64.abs().amax(dim=(1, 2))).cpu().numpy()
+        # channels the FP32 kernel handed to the FP64 one are bit-identical to it
+        same = (Qir == Q64).all(dim=(1, 2)).cpu().numpy()
+        v_eq = (rir.pop("_v") == r64.pop("_v")).all(dim=(1, 2)).cpu().numpy()
+        p64, pir = r64.pop("_pw"), rir.pop("_pw")
+        line = {"metric": f"precodings/s ({n_u}x{n_u} 16-QAM vector perturbation)",
+                "value": rir["problems_per_s"], "unit": "problems/s", "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": rir["ms_per_slot"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+refinement inverse, f32 solve",
+                "data": "synthetic", "config": {"workload": f"precode_{n_u}x{n_u}_16qam_slot", "problems_per_step": P,
+                                                "runs": args.runs, "solver_steps": args.solver_steps,
+                                                "l2": "64 MiB flush between steps"},
+                "fp64": r64, "fp32_ir": rir,
+                "ir_vs_fp64": {"q_rel_err_median": float(np.median(rel)), "q_rel_err_max": float(rel.max()),
+                               "frac_channels_bit_identical": float(same.mean()),
+                               "frac_v_equal": float(v_eq.mean()),
+                               "power_ratio_sum": float(pir.sum() / p64.sum())}}
+        print(json.dumps(line), flush=True)
     ctx.close()
 
 

@@ -133,12 +133,15 @@ typedef struct {
  *               unnormalised (Eq. 6 scales it to power P); may be NULL
  *   power_out:  float [n_problems] ||W (u + tau v)||^2; may be NULL
  *   energy_out, ndiv_out: as for detection; may be NULL
+ *   inv_precision: how Q = (H H^H)^-1 is computed, see mmgap_vpp_inverse:
+ *               MMGAP_INV_FP64 (0) or MMGAP_INV_FP32_IR (1)
  * tau = 2 sqrt(M) in lattice units (2 (c_max + Delta / 2), Delta = 2).
- * W = H^H (H H^H)^-1 (Eq. 5) is formed through Q = (H H^H)^-1 in FP64.
+ * W = H^H (H H^H)^-1 (Eq. 5) is formed through Q = (H H^H)^-1.
  */
 typedef struct {
     int32_t n_u, n_t, mod_bits;
     int32_t n_problems, n_chan;
+    int32_t inv_precision;
     const int32_t* chan_index;
     const float* H;
     const uint8_t* u_sym;
@@ -232,6 +235,27 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
 mmgap_status mmgap_anneal_spins(mmgap_ctx* ctx, const mmgap_params* params, int n, int n_problems,
                                 const int16_t* A_q, const int16_t* h_q, uint64_t seed, uint64_t* spins_out,
                                 void* stream);
+
+/*
+ * Channel inverse of VPP (Sec. 2.2, Eq. 5): Q_c = (H_c H_c^H)^-1 for each of
+ * n_chan channels H_c, complex [n_chan][n_u][n_t] (device), written to Q_out,
+ * complex double [n_chan][n_u][n_u] (device, Hermitian).
+ *   MMGAP_INV_FP64 (0): Cholesky and column solves in FP64.
+ *   MMGAP_INV_FP32_IR (1): H H^H as an unevaluated double-FP32 sum, FP32
+ *     Cholesky and solves, then up to 10 refinement steps X <- X + K^-1 (I - K X)
+ *     with the residual as a compensated (double-FP32) sum, stopping when
+ *     the remaining error (last correction squared over the one before) is
+ *     predicted below 2^-40 max|X| or the corrections stall; a channel whose
+ *     remaining error is not below 2^-24 max|X| is recomputed in FP64.  Accuracy per channel: max|Q - Q_exact| <= about
+ *     (2^-44 kappa + 2^-28) max|Q| with kappa the condition number of H H^H.
+ * H must be 8-byte and Q_out 16-byte aligned.
+ * status_out (device int32 [n_chan]): 0, or 1 when H H^H is not positive
+ * definite in FP64 (Q_c is then all zero); when NULL the flags go to the
+ * context workspace.  n_u in {1, 2, 3, 4, 8, 16}, n_t in [n_u, 64].
+ */
+enum { MMGAP_INV_FP64 = 0, MMGAP_INV_FP32_IR = 1 };
+mmgap_status mmgap_vpp_inverse(mmgap_ctx* ctx, int n_u, int n_t, int n_chan, const float* H, int inv_precision,
+                               double* Q_out, int32_t* status_out, void* stream);
 
 /*
  * Builder boundary (Sec. 3.2 pre-processing, Eq. 3, Fig. 5): the delta-Ising

@@ -51,8 +51,8 @@ class _DetectJob(C.Structure):
 
 class _PrecodeJob(C.Structure):
     _fields_ = [("n_u", C.c_int32), ("n_t", C.c_int32), ("mod_bits", C.c_int32), ("n_problems", C.c_int32),
-                ("n_chan", C.c_int32), ("chan_index", C.c_void_p), ("H", C.c_void_p), ("u_sym", C.c_void_p),
-                ("seed", C.c_uint64), ("v_out", C.c_void_p), ("x_out", C.c_void_p), ("power_out", C.c_void_p),
+                ("n_chan", C.c_int32), ("inv_precision", C.c_int32), ("chan_index", C.c_void_p), ("H", C.c_void_p),
+                ("u_sym", C.c_void_p), ("seed", C.c_uint64), ("v_out", C.c_void_p), ("x_out", C.c_void_p), ("power_out", C.c_void_p),
                 ("energy_out", C.c_void_p), ("ndiv_out", C.c_void_p)]
 
 
@@ -73,6 +73,7 @@ _lib.mmgap_device_errors.argtypes = [_vp, C.POINTER(C.c_int), C.c_int]
 _lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), _vp]
 _lib.mmgap_set_solver_variant.argtypes = [_vp, C.c_int, C.c_int]
 _lib.mmgap_detect_e.argtypes = [_vp, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int, _vp, _vp, _vp, _vp]
+_lib.mmgap_vpp_inverse.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp]
 _lib.mmgap_anneal_spins.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, _vp, _vp, C.c_uint64, _vp, _vp]
 _lib.mmgap_get_solver_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
 _lib.mmgap_autotune.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
@@ -116,7 +117,7 @@ for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detec
 ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
                "mmgap_precode", "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing",
                "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant",
-               "mmgap_detect_e", "mmgap_anneal_spins",
+               "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse",
                "mmgap_get_solver_variant", "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run",
                "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_wait",
                "mmgap_server_stats", "mmgap_server_destroy")
@@ -266,8 +267,9 @@ class Context:
         self._raise(_lib.mmgap_detect(self._h, C.byref(cp), arr, len(jobs), s))
 
     def precode(self, H, u_sym, mod_bits: int, params: Params, seed: int, chan_index=None, want_x=True,
-                want_power=True, want_energy=False, want_ndiv=False):
-        """Downlink VPP of P problems.  H: complex64 (n_chan, n_u, n_t), u_sym: uint8 (P, n_u)."""
+                want_power=True, want_energy=False, want_ndiv=False, inv_precision=0):
+        """Downlink VPP of P problems.  H: complex64 (n_chan, n_u, n_t), u_sym: uint8 (P, n_u);
+        inv_precision 0 = FP64 channel inverse, 1 = FP32 with iterative refinement."""
         n_chan, n_u, n_t = H.shape
         P = u_sym.shape[0]
         dev = self.device
@@ -283,13 +285,24 @@ class Context:
             out["energy"] = torch.empty(P, dtype=torch.int32, device=dev)
         if want_ndiv:
             out["ndiv"] = torch.empty(P, dtype=torch.int32, device=dev)
-        job = _PrecodeJob(n_u, n_t, mod_bits, P, n_chan, _ptr(chan_index), _ptr(H), _ptr(u_sym), seed,
-                          _ptr(out["v"]), _ptr(out.get("x")), _ptr(out.get("power")), _ptr(out.get("energy")),
+        job = _PrecodeJob(n_u, n_t, mod_bits, P, n_chan, inv_precision, _ptr(chan_index), _ptr(H), _ptr(u_sym),
+                          seed, _ptr(out["v"]), _ptr(out.get("x")), _ptr(out.get("power")), _ptr(out.get("energy")),
                           _ptr(out.get("ndiv")))
         cp = params._c()
         arr = (_PrecodeJob * 1)(job)
         self._raise(_lib.mmgap_precode(self._h, C.byref(cp), arr, 1, self._stream()))
         return out
+
+    def vpp_inverse(self, H, inv_precision=0):
+        """Q = (H H^H)^-1 per channel.  H: complex64 (n_chan, n_u, n_t).  Returns Q complex128
+        (n_chan, n_u, n_u) and status int32 (n_chan,)."""
+        n_chan, n_u, n_t = H.shape
+        _check(H, "H", torch.complex64, (n_chan, n_u, n_t), self.device)
+        Q = torch.empty((n_chan, n_u, n_u), dtype=torch.complex128, device=self.device)
+        st = torch.empty(n_chan, dtype=torch.int32, device=self.device)
+        self._raise(_lib.mmgap_vpp_inverse(self._h, n_u, n_t, n_chan, _ptr(H), inv_precision, _ptr(Q), _ptr(st),
+                                           self._stream()))
+        return Q, st
 
     def solve_ising(self, A_q, h_q, params: Params, seed: int, g=None, level_max: int = 0):
         """Anneal P quantised delta-Ising problems: A_q int16 (P, n, n), h_q int16 (P, n),

@@ -130,6 +130,7 @@ cudaError_t dispatch_nt(int nt, Args&&... args) {
 template <int NT> struct OpBuild { static cudaError_t run(const BuildArgs& a, cudaStream_t s) { return launch_build_detect<NT>(a, s); } };
 template <int NT> struct OpSolve { static cudaError_t run(const SolveArgs& a, int r, cudaStream_t s) { return launch_solve<NT>(a, r, s); } };
 template <int NT> struct OpVppInv { static cudaError_t run(const VppInvArgs& a, cudaStream_t s) { return launch_vpp_inverse<NT>(a, s); } };
+template <int NT> struct OpVppInvIr { static cudaError_t run(const VppInvArgs& a, cudaStream_t s) { return launch_vpp_inverse_ir<NT>(a, s); } };
 template <int NT> struct OpVppBuild { static cudaError_t run(const VppBuildArgs& a, cudaStream_t s) { return launch_vpp_build<NT>(a, s); } };
 template <int NT> struct OpVppOut { static cudaError_t run(const VppOutArgs& a, cudaStream_t s) { return launch_vpp_output<NT>(a, s); } };
 template <int NT> struct OpGram { static cudaError_t run(const GramArgs& a, cudaStream_t s) { return launch_gram_tc<NT>(a, s); } };
@@ -229,7 +230,30 @@ mmgap_status check_precode_job(mmgap_ctx* ctx, const mmgap_precode_job& j) {
     if (j.n_chan < 1) return fail(ctx, MMGAP_EINVAL, "n_chan < 1");
     if (!j.chan_index && j.n_chan < j.n_problems)
         return fail(ctx, MMGAP_EINVAL, "chan_index NULL needs n_chan >= n_problems");
+    if ((uintptr_t)j.H % 8) return fail(ctx, MMGAP_EINVAL, "H must be 8-byte aligned");
+    if (j.inv_precision != MMGAP_INV_FP64 && j.inv_precision != MMGAP_INV_FP32_IR)
+        return fail(ctx, MMGAP_EINVAL, "inv_precision=%d: 0 (FP64) or 1 (FP32 + refinement)", j.inv_precision);
     return MMGAP_OK;
+}
+
+constexpr int kVppRefineSteps = 10;
+
+// Q = (H H^H)^-1 for n_chan channels; FP32 + refinement with FP64 for the
+// channels that do not converge, or FP64 alone.  status must be non-NULL.
+cudaError_t vpp_inverse(int n_u, int n_t, int n_chan, const float* H, int inv_precision, double* Q, int32_t* status,
+                        cudaStream_t s) {
+    VppInvArgs vi{};
+    vi.H = H;
+    vi.n_t = n_t;
+    vi.n_chan = n_chan;
+    vi.Q = Q;
+    vi.status = status;
+    vi.refine = kVppRefineSteps;
+    if (inv_precision == MMGAP_INV_FP64) return dispatch_nt<OpVppInv>(n_u, vi, s);
+    cudaError_t e = dispatch_nt<OpVppInvIr>(n_u, vi, s);
+    if (e != cudaSuccess) return e;
+    vi.only_failed = 1;
+    return dispatch_nt<OpVppInv>(n_u, vi, s);
 }
 
 }  // namespace
@@ -512,14 +536,8 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
         double* Q = (double*)ctx->ws;
         int32_t* qstat = (int32_t*)(ctx->ws + align_up((size_t)n_chan * J.n_u * J.n_u * 16));
         char* base = ctx->ws + qbytes;
-        VppInvArgs vi{};
-        vi.H = J.H;
-        vi.n_t = J.n_t;
-        vi.n_chan = n_chan;
-        vi.Q = Q;
-        vi.status = qstat;
         if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
-        cudaError_t e = dispatch_nt<OpVppInv>(J.n_u, vi, s);
+        cudaError_t e = vpp_inverse(J.n_u, J.n_t, n_chan, J.H, J.inv_precision, Q, qstat, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_inverse launch");
         for (long long p0 = 0; p0 < J.n_problems; p0 += chunk) {
             const int P = (int)std::min<long long>(chunk, J.n_problems - p0);
@@ -578,6 +596,30 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
             if ((st = timing_mark(ctx, 3, s)) != MMGAP_OK) return st;
         }
     }
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_vpp_inverse(mmgap_ctx* ctx, int n_u, int n_t, int n_chan, const float* H, int inv_precision,
+                               double* Q_out, int32_t* status_out, void* stream) {
+    if (!ctx) return MMGAP_EINVAL;
+    if (!nt_supported(n_u)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_u=%d: supported 1, 2, 3, 4, 8, 16", n_u);
+    if (n_t < n_u || n_t > kMaxNr) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d out of [n_u, %d]", n_t, kMaxNr);
+    if (n_chan < 0) return fail(ctx, MMGAP_EINVAL, "n_chan < 0");
+    if (inv_precision != MMGAP_INV_FP64 && inv_precision != MMGAP_INV_FP32_IR)
+        return fail(ctx, MMGAP_EINVAL, "inv_precision=%d: 0 (FP64) or 1 (FP32 + refinement)", inv_precision);
+    if (n_chan == 0) return MMGAP_OK;
+    if (!H || !Q_out) return fail(ctx, MMGAP_EINVAL, "NULL H or Q_out");
+    if ((uintptr_t)H % 8 || (uintptr_t)Q_out % 16)
+        return fail(ctx, MMGAP_EINVAL, "H must be 8-byte and Q_out 16-byte aligned");
+    int32_t* status = status_out;
+    if (!status) {
+        if ((size_t)n_chan * 4 > ctx->ws_bytes)
+            return fail(ctx, MMGAP_ENOMEM, "workspace too small for %d channel flags", n_chan);
+        status = (int32_t*)ctx->ws;
+    }
+    CurrentDevice cd(ctx->device);
+    cudaError_t e = vpp_inverse(n_u, n_t, n_chan, H, inv_precision, Q_out, status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_inverse launch");
     return MMGAP_OK;
 }
 

@@ -111,7 +111,9 @@ struct VppInvArgs {
     int n_t;
     int n_chan;
     double* Q;        // complex [n_chan][n_u][n_u]
-    int32_t* status;  // [n_chan] 0 ok, 1 not positive definite
+    int32_t* status;  // [n_chan] 0 ok, 1 not positive definite, 2 FP32 refinement did not converge
+    int refine;       // FP32 path: maximum refinement steps
+    int only_failed;  // FP64 path: recompute only channels whose status is non-zero
 };
 
 struct VppBuildArgs {
@@ -147,6 +149,7 @@ struct VppOutArgs {
 template <int NT> cudaError_t launch_build_detect(const BuildArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_solve(const SolveArgs& a, int runs, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_inverse(const VppInvArgs& a, cudaStream_t s);
+template <int NT> cudaError_t launch_vpp_inverse_ir(const VppInvArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_gram_tc(const GramArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_build(const VppBuildArgs& a, cudaStream_t s);
