@@ -241,11 +241,13 @@ def run_mixed(args):
 
 
 def run_serve(args):
-    """Serving: Poisson arrivals of uplink jobs (one OFDM symbol each: 100-3276
-    subcarriers, 4x4 to 16x16, QPSK to 64-QAM, channel state resident on the
-    device) at `load` x measured capacity.  The continuous-batching server
-    (2 lanes, graph replay, memory admission) against the plain per-job path
-    (one mmgap_detect per job in arrival order on one stream)."""
+    """Serving: Poisson arrivals of uplink detection jobs and downlink VPP
+    precoding jobs (one OFDM symbol each: 100-3276 subcarriers, 4x4 to 16x16,
+    QPSK to 64-QAM, channel state resident on the device; one job in three is
+    a precoding job, with the FP32 + refinement inverse) at `load` x measured
+    capacity.  The continuous-batching server (graph replay, memory
+    admission) against the plain per-job path (one mmgap_detect or
+    mmgap_precode per job in arrival order on one stream)."""
     import torch
 
     from paper_2510_01579_gb300 import Context, Params, Server
@@ -253,30 +255,49 @@ def run_serve(args):
     prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
     rng = np.random.default_rng(7)
     ctx = Context(0, workspace_bytes=512 << 20)
-    pool, keep = [], []
+    pool, keep = [], []  # (kind, job, problems): kind 0 detection, 1 precoding
     for i in range(48):
         n_t = int(rng.choice([4, 8, 16]))
         mb = int(rng.choice([2, 4, 6]))
         n_sub = int(rng.integers(100, 3277))
+        model = str(rng.choice(["iid", "kron"]))
+        if i % 3 == 2:
+            d = synth.downlink(5000 + i, n_t, n_t, mb, n_sub=n_sub, n_sym=1, model=model)
+            t = [torch.from_numpy(d[k]).to(dev) for k in ("H", "u_sym", "chan_index")]
+            o = {"v": torch.empty((n_sub, n_t, 2), dtype=torch.int8, device=dev),
+                 "x": torch.empty((n_sub, n_t), dtype=torch.complex64, device=dev),
+                 "power": torch.empty(n_sub, dtype=torch.float32, device=dev)}
+            keep += t + list(o.values())
+            pool.append((1, ctx.precode_job(t[0], t[1], mb, 60 + i, o, t[2], inv_precision=1), n_sub))
+            continue
         w = synth.uplink(5000 + i, n_t, n_t, mb, n_sub=n_sub, n_sym=1, snr_db=float(rng.uniform(5, 30)),
-                         model=str(rng.choice(["iid", "kron"])), hold="prb")
+                         model=model, hold="prb")
         t = [torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index")]
         o = {"sym": torch.empty((n_sub, n_t), dtype=torch.uint8, device=dev)}
         keep += t + [o["sym"]]
-        pool.append((ctx.detect_job(t[0], t[1], t[2], mb, 60 + i, o, t[3]), n_sub))
+        pool.append((0, ctx.detect_job(t[0], t[1], t[2], mb, 60 + i, o, t[3]), n_sub))
+
+    def per_job(kind, job):
+        if kind:
+            ctx.precode_jobs([job], prm)
+        else:
+            ctx.detect_jobs([job], prm)
+
     # capacity: the whole pool through the per-job path, back to back
     for _ in range(2):
-        ctx.detect_jobs([j for j, _ in pool], prm)
+        for kind, j, _ in pool:
+            per_job(kind, j)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx.detect_jobs([j for j, _ in pool], prm)
+    for kind, j, _ in pool:
+        per_job(kind, j)
     torch.cuda.synchronize()
     pool_s = time.perf_counter() - t0
     rate = args.load * len(pool) / pool_s  # jobs per second offered
     n_jobs = max(len(pool), int(rate * args.serve_seconds))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
     which = [i % len(pool) for i in range(n_jobs)]
-    total_problems = sum(pool[k][1] for k in which)
+    total_problems = sum(pool[k][2] for k in which)
     deadline = 500.0
 
     def pct(v, q):
@@ -287,18 +308,20 @@ def run_serve(args):
     clocks = ClockSampler(0)
     with Server(0, prm, scratch_bytes=2 << 30, n_lanes=args.lanes, max_jobs_per_group=32,
                 max_problems_per_group=1 << 16, deadline_us=deadline) as srv:
-        srv.submit(pool[0][0])  # warm up (graph capture on both lanes)
-        srv.submit(pool[1][0])
-        srv.submit(pool[2][0])
-        srv.submit(pool[3][0])
-        time.sleep(0.2)
+        def submit(k):
+            kind, job, _ = pool[k]
+            return srv.submit_precode(job) if kind else srv.submit(job)
+
+        for k in range(6):  # warm up (graph capture on every lane)
+            submit(k)
+        time.sleep(0.3)
         srv.stats(reset=True)
         tks = []
         start = time.perf_counter()
         for a, k in zip(arrivals, which):
             while time.perf_counter() - start < a:
                 pass
-            tks.append(srv.submit(pool[k][0]))
+            tks.append(submit(k))
         lat = [srv.wait(tk)["latency_us"] for tk in tks]
         st = srv.stats()
     clk = clocks.stop()
@@ -316,19 +339,20 @@ def run_serve(args):
     for i, (a, k) in enumerate(zip(arrivals, which)):
         while time.perf_counter() - start < a:
             pass
-        ctx.detect_jobs([pool[k][0]], prm)
+        per_job(pool[k][0], pool[k][1])
         done[i].record(stream)
     torch.cuda.synchronize()
     plain_lat = [ref_ev.elapsed_time(done[i]) * 1e3 - arrivals[i] * 1e6 for i in range(n_jobs)]
     plain_span = ref_ev.elapsed_time(done[-1]) / 1e3
     plain = {"value": total_problems / plain_span, "p50_us": pct(plain_lat, 0.5), "p99_us": pct(plain_lat, 0.99),
              "deadline_misses": int(sum(x > deadline for x in plain_lat))}
-    line = {"metric": "detections/s served (Poisson mixed-size uplink jobs); p50/p99 job latency",
+    line = {"metric": "problems/s served (Poisson mixed-size detection and precoding jobs); p50/p99 job latency",
             "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": n_jobs, "warmup": 2,
             "ms_per_step": span * 1e3 / n_jobs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve", "offered_load": args.load, "jobs": n_jobs,
                        "job_sizes": "n_t in {4,8,16}, QPSK..64-QAM, 100-3276 subcarriers x 1 symbol",
+                       "job_mix": "2/3 uplink detection, 1/3 downlink VPP (FP32 + refinement inverse)",
                        "arrival_rate_jobs_per_s": rate, "deadline_us": deadline, "lanes": args.lanes,
                        "runs": args.runs, "solver_steps": args.solver_steps},
             "server": served, "plain_per_job_path": plain,

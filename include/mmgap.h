@@ -352,7 +352,11 @@ mmgap_status mmgap_batch_destroy(mmgap_batch* batch);
  * batched launch (as mmgap_batch_run, replayed from a CUDA graph when
  * use_graph != 0); groups on different lanes overlap on the device, and jobs
  * that arrive while others run are admitted as soon as a lane frees up.
- * Results equal mmgap_detect's bit for bit, whatever the grouping.
+ * Precoding jobs (mmgap_server_submit_precode) share the groups: their
+ * channel inverses and VPP builds run just before the group's batched launch,
+ * their problems go through its solver, their outputs right after it.
+ * Results equal mmgap_detect's / mmgap_precode's bit for bit, whatever the
+ * grouping.
  * Latency = completion (host callback at the end of the group) - submission,
  * on the host's steady clock.  deadline_us > 0 counts jobs over it;
  * inject_delay_us > 0 delays every launch on the host (fault injection for
@@ -385,6 +389,11 @@ mmgap_status mmgap_server_create(mmgap_server** server, int device, const mmgap_
                                  const mmgap_server_config* config);
 /* Queue a job (non-blocking).  MMGAP_ENOMEM if it could never fit a lane. */
 mmgap_status mmgap_server_submit(mmgap_server* server, const mmgap_detect_job* job, uint64_t* ticket);
+/* Queue a downlink VPP precoding job (non-blocking): n_u in {4, 8, 16} up to
+ * max_n_t, n_t (antennas) up to 64, either inv_precision.  Its results equal
+ * mmgap_precode's for the same job.  MMGAP_ENOMEM if it could never fit a
+ * lane (its scratch adds n_chan n_u^2 16 bytes of channel inverses). */
+mmgap_status mmgap_server_submit_precode(mmgap_server* server, const mmgap_precode_job* job, uint64_t* ticket);
 /* Wait for a job (timeout_us < 0: forever).  MMGAP_ETIMEOUT if not done in
  * time (the job stays queued or running; wait again).  On completion the
  * ticket is released and *info (may be NULL) gets its timestamps. */

@@ -103,15 +103,17 @@ class _ServerStats(C.Structure):
 
 _lib.mmgap_server_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(_Params), C.POINTER(_ServerConfig)]
 _lib.mmgap_server_submit.argtypes = [_vp, C.POINTER(_DetectJob), C.POINTER(C.c_uint64)]
+_lib.mmgap_server_submit_precode.argtypes = [_vp, C.POINTER(_PrecodeJob), C.POINTER(C.c_uint64)]
 _lib.mmgap_server_wait.argtypes = [_vp, C.c_uint64, C.c_int64, C.POINTER(_JobInfo)]
 _lib.mmgap_server_stats.argtypes = [_vp, C.POINTER(_ServerStats), C.c_int]
 _lib.mmgap_server_destroy.argtypes = [_vp]
 for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
            "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
            "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant", "mmgap_get_solver_variant",
-           "mmgap_detect_e", "mmgap_anneal_spins",
+           "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse",
            "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run", "mmgap_batch_destroy", "mmgap_server_create",
-           "mmgap_server_submit", "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy"):
+           "mmgap_server_submit", "mmgap_server_submit_precode", "mmgap_server_wait", "mmgap_server_stats",
+           "mmgap_server_destroy"):
     getattr(_lib, _f).restype = C.c_int
 
 ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
@@ -119,8 +121,8 @@ ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_l
                "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant",
                "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse",
                "mmgap_get_solver_variant", "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run",
-               "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_wait",
-               "mmgap_server_stats", "mmgap_server_destroy")
+               "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_submit_precode",
+               "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy")
 
 VARIANT_NAMES = {0: "default", 1: "plain", 2: "tpa1", 3: "tpa1-packed", 4: "tpa2-packed"}
 
@@ -265,6 +267,21 @@ class Context:
         cp = params._c()
         s = self._stream() if stream is None else C.c_void_p(stream.cuda_stream)
         self._raise(_lib.mmgap_detect(self._h, C.byref(cp), arr, len(jobs), s))
+
+    def precode_job(self, H, u_sym, mod_bits, seed, out, chan_index=None, inv_precision=0) -> _PrecodeJob:
+        """A precoding job descriptor over device tensors (for Server.submit_precode).
+        out: dict with "v" int8 (P, n_u, 2) and optional "x" complex64 (P, n_t), "power" float32 (P,),
+        "energy" / "ndiv" int32 (P,)."""
+        n_chan, n_u, n_t = H.shape
+        return _PrecodeJob(n_u, n_t, mod_bits, u_sym.shape[0], n_chan, inv_precision, _ptr(chan_index), _ptr(H),
+                           _ptr(u_sym), seed, _ptr(out["v"]), _ptr(out.get("x")), _ptr(out.get("power")),
+                           _ptr(out.get("energy")), _ptr(out.get("ndiv")))
+
+    def precode_jobs(self, jobs, params: Params, stream=None):
+        arr = (_PrecodeJob * len(jobs))(*jobs)
+        cp = params._c()
+        s = self._stream() if stream is None else C.c_void_p(stream.cuda_stream)
+        self._raise(_lib.mmgap_precode(self._h, C.byref(cp), arr, len(jobs), s))
 
     def precode(self, H, u_sym, mod_bits: int, params: Params, seed: int, chan_index=None, want_x=True,
                 want_power=True, want_energy=False, want_ndiv=False, inv_precision=0):
@@ -444,8 +461,8 @@ class Batch:
 class Server:
     """mmgap_server: continuous-batching serving loop on one device.
 
-    submit() queues a detection job (device tensors, kept alive by the
-    caller or via `keepalive`) and returns a ticket; wait() blocks until it is
+    submit() queues a detection job and submit_precode() a VPP precoding job
+    (device tensors, kept alive by the caller or via `keepalive`); both return a ticket; wait() blocks until it is
     done (or raises MMGaPError with ETIMEOUT); stats() gives latency
     percentiles of completed jobs."""
 
@@ -468,6 +485,15 @@ class Server:
         st = _lib.mmgap_server_submit(self._h, C.byref(job), C.byref(t))
         if st != OK:
             raise MMGaPError(st, "mmgap_server_submit failed")
+        if keepalive is not None:
+            self._keep[t.value] = keepalive
+        return t.value
+
+    def submit_precode(self, job: _PrecodeJob, keepalive=None) -> int:
+        t = C.c_uint64()
+        st = _lib.mmgap_server_submit_precode(self._h, C.byref(job), C.byref(t))
+        if st != OK:
+            raise MMGaPError(st, "mmgap_server_submit_precode failed")
         if keepalive is not None:
             self._keep[t.value] = keepalive
         return t.value

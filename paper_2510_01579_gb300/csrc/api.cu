@@ -236,12 +236,12 @@ mmgap_status check_precode_job(mmgap_ctx* ctx, const mmgap_precode_job& j) {
     return MMGAP_OK;
 }
 
-constexpr int kVppRefineSteps = 10;
+}  // namespace
 
-// Q = (H H^H)^-1 for n_chan channels; FP32 + refinement with FP64 for the
-// channels that do not converge, or FP64 alone.  status must be non-NULL.
-cudaError_t vpp_inverse(int n_u, int n_t, int n_chan, const float* H, int inv_precision, double* Q, int32_t* status,
-                        cudaStream_t s) {
+namespace mmgap {
+
+cudaError_t vpp_inverse_any(int n_u, int n_t, int n_chan, const float* H, int inv_precision, double* Q,
+                            int32_t* status, cudaStream_t s) {
     VppInvArgs vi{};
     vi.H = H;
     vi.n_t = n_t;
@@ -256,7 +256,7 @@ cudaError_t vpp_inverse(int n_u, int n_t, int n_chan, const float* H, int inv_pr
     return dispatch_nt<OpVppInv>(n_u, vi, s);
 }
 
-}  // namespace
+}  // namespace mmgap
 
 extern "C" {
 
@@ -537,7 +537,7 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
         int32_t* qstat = (int32_t*)(ctx->ws + align_up((size_t)n_chan * J.n_u * J.n_u * 16));
         char* base = ctx->ws + qbytes;
         if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
-        cudaError_t e = vpp_inverse(J.n_u, J.n_t, n_chan, J.H, J.inv_precision, Q, qstat, s);
+        cudaError_t e = vpp_inverse_any(J.n_u, J.n_t, n_chan, J.H, J.inv_precision, Q, qstat, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_inverse launch");
         for (long long p0 = 0; p0 < J.n_problems; p0 += chunk) {
             const int P = (int)std::min<long long>(chunk, J.n_problems - p0);
@@ -618,7 +618,7 @@ mmgap_status mmgap_vpp_inverse(mmgap_ctx* ctx, int n_u, int n_t, int n_chan, con
         status = (int32_t*)ctx->ws;
     }
     CurrentDevice cd(ctx->device);
-    cudaError_t e = vpp_inverse(n_u, n_t, n_chan, H, inv_precision, Q_out, status, (cudaStream_t)stream);
+    cudaError_t e = vpp_inverse_any(n_u, n_t, n_chan, H, inv_precision, Q_out, status, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_inverse launch");
     return MMGAP_OK;
 }

@@ -81,6 +81,25 @@ const char* BatchRunner::check_job(const mmgap_detect_job& J) {
     return nullptr;
 }
 
+const char* BatchRunner::check_precode(const mmgap_precode_job& J) {
+    if (!batch_nt(J.n_u)) return "batched launch supports n_u 4, 8, 16";
+    if (J.n_t < J.n_u || J.n_t > kMaxNr) return "n_t out of [n_u, 64]";
+    if (!(J.mod_bits == 2 || J.mod_bits == 4 || J.mod_bits == 6)) return "mod_bits must be 2, 4 or 6";
+    if (J.n_problems < 0) return "n_problems < 0";
+    if (J.inv_precision != MMGAP_INV_FP64 && J.inv_precision != MMGAP_INV_FP32_IR) return "bad inv_precision";
+    if (J.n_problems > 0 && (!J.H || !J.u_sym || !J.v_out || J.n_chan < 1)) return "NULL input/output";
+    if (J.n_problems > 0 && (uintptr_t)J.H % 8) return "H must be 8-byte aligned";
+    if (J.n_problems > 0 && !J.chan_index && J.n_chan < J.n_problems) return "chan_index NULL needs n_chan >= n";
+    return nullptr;
+}
+
+size_t BatchRunner::precode_scratch_bytes(const mmgap_precode_job& J) {
+    const size_t n = 2 * (size_t)J.n_u, P = (size_t)J.n_problems;
+    const size_t n_chan = J.chan_index ? (size_t)J.n_chan : P;
+    return salign(P * n * n * 2) + salign(P * n * 2) + salign(P * n) +
+           salign(n_chan * J.n_u * J.n_u * 16) + salign(n_chan * 4);
+}
+
 size_t BatchRunner::scratch_bytes(int n_t, int n_problems) {
     const size_t n = 2 * (size_t)n_t, P = (size_t)n_problems;
     return salign(P * n * n * 2) + salign(P * n * 2) + salign(P * n);
@@ -142,40 +161,80 @@ void BatchRunner::release() {
 
 int BatchRunner::stage(const mmgap_detect_job* jobs, const int* order, int n_jobs) {
     if (n_jobs > capacity_) return -1;
+    std::vector<GroupJob> g((size_t)std::max(0, n_jobs));
+    for (int i = 0; i < n_jobs; ++i) g[i].det = &jobs[i];
+    return stage(g.data(), order, n_jobs);
+}
+
+int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
+    if (n_jobs > capacity_) return -1;
+    pre_.clear();
     long long first = 0;
     size_t off = 0;
     for (int i = 0; i < n_jobs; ++i) {
-        const mmgap_detect_job& J = jobs[order ? order[i] : i];
+        const GroupJob& G = jobs[order ? order[i] : i];
         BatchJob& B = h_jobs_[i];
         B = BatchJob{};
-        B.b.H = J.H;
-        B.b.chan_index = J.chan_index;
-        B.b.y = J.y;
-        B.b.noise_var = J.noise_var;
-        B.b.n_r = J.n_r;
-        B.b.mod_bits = J.mod_bits;
-        B.b.n_problems = J.n_problems;
-        B.b.n_chan = J.chan_index ? J.n_chan : J.n_problems;
-        const double M = (double)(1 << J.mod_bits);
-        B.b.kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
-        B.b.kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
-        B.b.err = err_word_;
-        B.nt = J.n_t;
-        B.key0 = (uint32_t)J.seed;
-        B.key1 = (uint32_t)(J.seed >> 32);
         B.first = first;
-        const size_t n = 2 * (size_t)J.n_t, P = (size_t)J.n_problems;
-        if (off + scratch_bytes(J.n_t, J.n_problems) > scratch_bytes_) return -2;
-        B.Aq = (int16_t*)(scratch_ + off);
-        B.hq = (int16_t*)(scratch_ + off + salign(P * n * n * 2));
-        B.g = (int8_t*)(scratch_ + off + salign(P * n * n * 2) + salign(P * n * 2));
-        off += scratch_bytes(J.n_t, J.n_problems);
-        B.sym_out = J.sym_out;
-        B.energy_out = J.energy_out;
-        B.guess_out = J.guess_out;
-        B.offset_out = J.offset_out;
-        B.ndiv_out = J.ndiv_out;
-        first += J.n_problems;
+        B.b.err = err_word_;
+        if (G.det) {
+            const mmgap_detect_job& J = *G.det;
+            B.b.H = J.H;
+            B.b.chan_index = J.chan_index;
+            B.b.y = J.y;
+            B.b.noise_var = J.noise_var;
+            B.b.n_r = J.n_r;
+            B.b.mod_bits = J.mod_bits;
+            B.b.n_problems = J.n_problems;
+            B.b.n_chan = J.chan_index ? J.n_chan : J.n_problems;
+            const double M = (double)(1 << J.mod_bits);
+            B.b.kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
+            B.b.kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
+            B.nt = J.n_t;
+            B.kind = 0;
+            B.key0 = (uint32_t)J.seed;
+            B.key1 = (uint32_t)(J.seed >> 32);
+            const size_t n = 2 * (size_t)J.n_t, P = (size_t)J.n_problems;
+            if (off + scratch_bytes(J.n_t, J.n_problems) > scratch_bytes_) return -2;
+            B.Aq = (int16_t*)(scratch_ + off);
+            B.hq = (int16_t*)(scratch_ + off + salign(P * n * n * 2));
+            B.g = (int8_t*)(scratch_ + off + salign(P * n * n * 2) + salign(P * n * 2));
+            off += scratch_bytes(J.n_t, J.n_problems);
+            B.sym_out = J.sym_out;
+            B.energy_out = J.energy_out;
+            B.guess_out = J.guess_out;
+            B.offset_out = J.offset_out;
+            B.ndiv_out = J.ndiv_out;
+            first += J.n_problems;
+        } else {
+            const mmgap_precode_job& J = *G.pre;
+            const size_t n = 2 * (size_t)J.n_u, P = (size_t)J.n_problems;
+            const size_t n_chan = J.chan_index ? (size_t)J.n_chan : P;
+            if (off + precode_scratch_bytes(J) > scratch_bytes_) return -2;
+            char* base = scratch_ + off;
+            Precode R{};
+            R.job = J;
+            R.Aq = (int16_t*)base;
+            R.hq = (int16_t*)(base + salign(P * n * n * 2));
+            R.d = (int8_t*)((char*)R.hq + salign(P * n * 2));
+            R.Q = (double*)((char*)R.d + salign(P * n));
+            R.status = (int32_t*)((char*)R.Q + salign(n_chan * J.n_u * J.n_u * 16));
+            off += precode_scratch_bytes(J);
+            B.b.mod_bits = J.mod_bits;
+            B.b.n_problems = J.n_problems;
+            B.nt = J.n_u;
+            B.kind = 1;
+            B.key0 = (uint32_t)J.seed;
+            B.key1 = (uint32_t)(J.seed >> 32);
+            B.Aq = R.Aq;
+            B.hq = R.hq;
+            B.g = nullptr;
+            B.offset_out = R.d;
+            B.energy_out = J.energy_out;
+            B.ndiv_out = J.ndiv_out;
+            first += J.n_problems;
+            if (J.n_problems > 0) pre_.push_back(R);
+        }
     }
     if (first > capacity_problems_) return -3;
     h_head_->n_jobs = n_jobs;
@@ -183,6 +242,70 @@ int BatchRunner::stage(const mmgap_detect_job* jobs, const int* order, int n_job
     h_head_->total = first;
     h_head_->counter = 0;
     return 0;
+}
+
+namespace {
+
+cudaError_t vpp_build_nu(int n_u, const VppBuildArgs& a, cudaStream_t s) {
+    switch (n_u) {
+    case 16: return launch_vpp_build<16>(a, s);
+    case 8: return launch_vpp_build<8>(a, s);
+    default: return launch_vpp_build<4>(a, s);
+    }
+}
+
+cudaError_t vpp_output_nu(int n_u, const VppOutArgs& a, cudaStream_t s) {
+    switch (n_u) {
+    case 16: return launch_vpp_output<16>(a, s);
+    case 8: return launch_vpp_output<8>(a, s);
+    default: return launch_vpp_output<4>(a, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t BatchRunner::precode_before(cudaStream_t s) {
+    for (const Precode& R : pre_) {
+        const mmgap_precode_job& J = R.job;
+        const int n_chan = J.chan_index ? J.n_chan : J.n_problems;
+        cudaError_t e = vpp_inverse_any(J.n_u, J.n_t, n_chan, J.H, J.inv_precision, R.Q, R.status, s);
+        if (e != cudaSuccess) return e;
+        VppBuildArgs b{};
+        b.Q = R.Q;
+        b.chan_index = J.chan_index;
+        b.u_sym = J.u_sym;
+        b.mod_bits = J.mod_bits;
+        b.n_problems = J.n_problems;
+        b.n_chan = n_chan;
+        b.err = err_word_;
+        b.Aq = R.Aq;
+        b.hq = R.hq;
+        if ((e = vpp_build_nu(J.n_u, b, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t BatchRunner::precode_after(cudaStream_t s) {
+    for (const Precode& R : pre_) {
+        const mmgap_precode_job& J = R.job;
+        VppOutArgs o{};
+        o.H = J.H;
+        o.Q = R.Q;
+        o.chan_index = J.chan_index;
+        o.u_sym = J.u_sym;
+        o.d = R.d;
+        o.n_t = J.n_t;
+        o.mod_bits = J.mod_bits;
+        o.n_problems = J.n_problems;
+        o.n_chan = J.chan_index ? J.n_chan : J.n_problems;
+        o.err = err_word_;
+        o.v_out = J.v_out;
+        o.x_out = J.x_out;
+        o.power_out = J.power_out;
+        cudaError_t e = vpp_output_nu(J.n_u, o, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 void BatchRunner::grids(unsigned* build_grid, unsigned* solve_grid) const {
@@ -224,6 +347,13 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
 }
 
 cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_graph) {
+    cudaError_t e = precode_before(s);
+    if (e != cudaSuccess) return e;
+    if ((e = run_batch(P, s, use_graph)) != cudaSuccess) return e;
+    return precode_after(s);
+}
+
+cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool use_graph) {
     if (!use_graph) return enqueue(P, s);
     cudaError_t e;
     if (exec_ && std::memcmp(&graph_params_, &P, sizeof P) != 0) {  // parameters are baked into the graph

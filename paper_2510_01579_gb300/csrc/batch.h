@@ -2,6 +2,7 @@
 // objects and the serving loop).  Not part of the ABI.
 #pragma once
 #include <cstring>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -10,14 +11,25 @@
 
 namespace mmgap {
 
+// One job of a group: a detection job or a VPP precoding job (exactly one set).
+struct GroupJob {
+    const mmgap_detect_job* det = nullptr;
+    const mmgap_precode_job* pre = nullptr;
+    int n_t() const { return det ? det->n_t : pre->n_u; }
+};
+
 class BatchRunner {
   public:
     // Reasons a parameter set / job cannot use the batched launch (nullptr = ok).
     static const char* check_params(const mmgap_params& P);
     static const char* check_job(const mmgap_detect_job& J);
+    static const char* check_precode(const mmgap_precode_job& J);
 
     // Scratch bytes (Q14 couplings, field, guess) of one job.
     static size_t scratch_bytes(int n_t, int n_problems);
+    // Scratch bytes of one precoding job: couplings, field, offsets, the
+    // channel inverses and their flags.
+    static size_t precode_scratch_bytes(const mmgap_precode_job& J);
     // Device job table for up to capacity_jobs jobs and capacity_problems
     // problems with n_r <= max_n_r and n_t <= ntmax, `scratch` bytes of
     // coupling scratch; err_word receives out-of-range channel indices.
@@ -29,13 +41,27 @@ class BatchRunner {
     // Fill the pinned host table with jobs[order[i]] (order may be NULL);
     // returns 0, or < 0 if the jobs exceed the table, scratch or problem capacity.
     int stage(const mmgap_detect_job* jobs, const int* order, int n_jobs);
-    // Copy the staged table to the device and launch (or replay the graph of)
-    // the persistent kernel on s.
+    int stage(const GroupJob* jobs, const int* order, int n_jobs);
+    // Launch on s: each precoding job's channel inverse and VPP build, then
+    // the batch (table upload, builder, solver; or the graph of them), then
+    // each precoding job's output kernel.
     cudaError_t run(const mmgap_params& P, cudaStream_t s, bool use_graph);
     int grid() const { return grid_; }
 
   private:
+    struct Precode {  // a staged precoding job and its scratch
+        mmgap_precode_job job;
+        int16_t* Aq;
+        int16_t* hq;
+        int8_t* d;
+        double* Q;
+        int32_t* status;
+    };
     cudaError_t enqueue(const mmgap_params& P, cudaStream_t s);
+    cudaError_t run_batch(const mmgap_params& P, cudaStream_t s, bool use_graph);
+    cudaError_t precode_before(cudaStream_t s);
+    cudaError_t precode_after(cudaStream_t s);
+    std::vector<Precode> pre_;
     void grids(unsigned* build_grid, unsigned* solve_grid) const;
     int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0, grid_ = 0, build_grid_max_ = 1;
     bool persistent_ = false;

@@ -155,6 +155,13 @@ template <int NT> cudaError_t launch_select(const SelectArgs& a, cudaStream_t s)
 template <int NT> cudaError_t launch_vpp_build(const VppBuildArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_output(const VppOutArgs& a, cudaStream_t s);
 
+// Q = (H H^H)^-1 for n_chan channels of n_u users (see mmgap_vpp_inverse):
+// FP64, or FP32 with iterative refinement and FP64 for the channels it does
+// not accept.  status: int32 [n_chan], required.  Defined in api.cu.
+constexpr int kVppRefineSteps = 10;
+cudaError_t vpp_inverse_any(int n_u, int n_t, int n_chan, const float* H, int inv_precision, double* Q,
+                            int32_t* status, cudaStream_t s);
+
 // Random symmetric Q14 problems (uniform codes in [-2^14, 2^14]) for the
 // autotuner, drawn from Philox on the device (defined in api.cu).
 cudaError_t launch_random_ising(int16_t* Aq, int16_t* hq, int n, int n_problems, uint64_t seed, cudaStream_t s);

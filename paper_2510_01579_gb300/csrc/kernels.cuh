@@ -1010,6 +1010,8 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
 struct BatchJob {
     BuildArgs b;            // inputs, n_r, mod_bits, n_problems, n_chan, kappa, err
     int nt;
+    int kind;               // 0 detection (built by the batch builder); 1 VPP, built before the
+                            // batch: no clipping (guess 0), offsets to offset_out, no symbols
     uint32_t key0, key1;
     long long first;        // batch index of the job's problem 0
     int16_t* Aq;            // scratch [P][n][n]
@@ -1054,7 +1056,7 @@ __device__ __forceinline__ int batch_find_job(const BatchJob* jobs, int n_jobs, 
 
 // Builder over the whole batch: warp w of the grid builds problem w.
 template <int NTMAX>
-__global__ void __launch_bounds__(kBuildWarps * 32) batch_build_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(kBuildWarps * 32, 8) batch_build_kernel(BatchArgs A) {
     extern __shared__ __align__(16) float bws[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long total = A.head->total;
@@ -1063,15 +1065,19 @@ __global__ void __launch_bounds__(kBuildWarps * 32) batch_build_kernel(BatchArgs
     for (long long w = (long long)blockIdx.x * kBuildWarps + warp; w < total;
          w += (long long)gridDim.x * kBuildWarps) {
         const BatchJob& J = A.jobs[batch_find_job(A.jobs, n_jobs, w)];
+        if (J.kind != 0) continue;  // built before the batch
         const int p = (int)(w - J.first);
         const int n = 2 * J.nt;
         BuildOut o{J.Aq + (size_t)p * n * n, J.hq + (size_t)p * n, J.g + (size_t)p * n, nullptr, nullptr, nullptr};
+        // a register copy of the job's arguments: read through the reference, every field would be
+        // reloaded from global memory after each of the builder's global stores
+        const BuildArgs b = J.b;
         if (J.nt == 16) {
-            if constexpr (NTMAX >= 16) build_problem_warp<16>(J.b, p, lane, ws, o);
+            if constexpr (NTMAX >= 16) build_problem_warp<16>(b, p, lane, ws, o);
         } else if (J.nt == 8) {
-            if constexpr (NTMAX >= 8) build_problem_warp<8>(J.b, p, lane, ws, o);
+            if constexpr (NTMAX >= 8) build_problem_warp<8>(b, p, lane, ws, o);
         } else {
-            build_problem_warp<4>(J.b, p, lane, ws, o);
+            build_problem_warp<4>(b, p, lane, ws, o);
         }
     }
 }
@@ -1117,7 +1123,7 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
 #pragma unroll
     for (int i = 0; i < n; ++i)
         valid = valid && (fabsf(x1[i]) <= k.x_max) && (e1[i] > 0.0f) && (fabsf(x2[i]) <= k.x_max) && (e2[i] > 0.0f);
-    const int level_max = (1 << (J.b.mod_bits >> 1)) - 1;
+    const int level_max = J.kind == 0 ? (1 << (J.b.mod_bits >> 1)) - 1 : 0;  // 0: no clipping
     const int sa = xa >= 0.0f ? 1 : -1;
     int d[n];
 #pragma unroll
@@ -1125,7 +1131,7 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
         const int s1 = x1[i] >= 0.0f ? 1 : -1, s2 = x2[i] >= 0.0f ? 1 : -1;
         int di = sa * (s1 + s2) / 2;
         const int xv = (int)sm.g[i] + 2 * di;
-        if (xv > level_max || xv < -level_max) di = 0;
+        if (level_max > 0 && (xv > level_max || xv < -level_max)) di = 0;
         d[i] = di;
     }
     int E = 0;
@@ -1159,13 +1165,15 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
 #pragma unroll
             for (int i = 0; i < n; ++i) J.guess_out[(size_t)p * n + i] = sm.g[i];
         }
-        const int side = 1 << (J.b.mod_bits >> 1), L = side - 1;
-        uint8_t* so = J.sym_out + (size_t)p * NT;
+        if (J.sym_out) {
+            const int side = 1 << (J.b.mod_bits >> 1), L = side - 1;
+            uint8_t* so = J.sym_out + (size_t)p * NT;
 #pragma unroll
-        for (int i = 0; i < NT; ++i) {
-            const int xr = (int)sm.g[i] + 2 * (keep ? d[i] : 0);
-            const int xi = (int)sm.g[NT + i] + 2 * (keep ? d[NT + i] : 0);
-            so[i] = (uint8_t)(((xr + L) / 2) * side + (xi + L) / 2);
+            for (int i = 0; i < NT; ++i) {
+                const int xr = (int)sm.g[i] + 2 * (keep ? d[i] : 0);
+                const int xi = (int)sm.g[NT + i] + 2 * (keep ? d[NT + i] : 0);
+                so[i] = (uint8_t)(((xr + L) / 2) * side + (xi + L) / 2);
+            }
         }
     }
     __syncwarp();  // the warp's shared memory is reused by its next problem
@@ -1180,7 +1188,7 @@ __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const Ba
     for (int e = lane; e < n * n; e += 32) sm.Aq[e] = Aq[e];
     for (int i = lane; i < n; i += 32) {
         sm.hq[i] = J.hq[(size_t)p * n + i];
-        sm.g[i] = J.g[(size_t)p * n + i];
+        sm.g[i] = J.g ? J.g[(size_t)p * n + i] : (int8_t)0;
     }
     __syncwarp();
     batch_solve_warp<NT, F>(A, J, p, lane, sm);

@@ -1,7 +1,8 @@
 // Slot-driven serving loop with continuous batching (mmgap_server_*).
 //
-// Callers submit uplink detection jobs (inputs already resident on the device,
-// e.g. channel state kept there across slots) from any host thread.  A
+// Callers submit uplink detection jobs and downlink VPP precoding jobs
+// (inputs already resident on the device, e.g. channel state kept there
+// across slots) from any host thread.  A
 // dispatcher thread admits queued jobs in arrival order into launch groups:
 // a group goes to a free lane (a CUDA stream with its own batch runner and
 // coupling scratch) and takes jobs while they fit that lane's scratch
@@ -10,7 +11,10 @@
 // jobs that arrive while others are running start as soon as a lane frees
 // up.  A host callback at the end of each group timestamps its jobs and frees
 // the lane.  Results do not depend on grouping: each job is computed exactly
-// as mmgap_detect computes it.
+// as mmgap_detect or mmgap_precode computes it.  A precoding job's channel
+// inverse and VPP build run just before its group's batched launch, its
+// problems go through the same batched solver, and its output kernel runs
+// right after.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -37,9 +41,21 @@ double now_us() {
 }
 
 struct JobRec {
-    mmgap_detect_job job;
+    bool precode = false;
+    mmgap_detect_job job{};
+    mmgap_precode_job pjob{};
     mmgap_job_info info;
     bool done = false;
+    int n_problems() const { return precode ? pjob.n_problems : job.n_problems; }
+    size_t scratch() const {
+        return precode ? BatchRunner::precode_scratch_bytes(pjob) : BatchRunner::scratch_bytes(job.n_t, job.n_problems);
+    }
+    GroupJob group_job() const {
+        GroupJob g;
+        if (precode) g.pre = &pjob;
+        else g.det = &job;
+        return g;
+    }
 };
 
 struct Lane {
@@ -57,6 +73,7 @@ struct mmgap_server {
     mmgap_params params{};
     size_t lane_scratch = 0;
     int lane_jobs = 0;
+    int max_n_t = 16, max_n_r = 16;
     long long lane_problems = 0;
     double deadline_us = 0.0;
     double inject_delay_us = 0.0;
@@ -101,7 +118,7 @@ void CUDART_CB on_group_done(void* p) {
             const double lat = t - r.info.submit_us;
             s->latencies_us.push_back(lat);
             s->completed++;
-            s->problems_done += r.job.n_problems;
+            s->problems_done += r.n_problems();
             if (s->deadline_us > 0.0 && lat > s->deadline_us) s->deadline_misses++;
         }
         s->last_done_us = t;
@@ -133,17 +150,18 @@ void dispatch_loop(mmgap_server* s) {
             }
         Lane& L = s->lanes[li];
         // admit queued jobs in arrival order while they fit this lane
-        std::vector<mmgap_detect_job> group;
+        // (records stay in the map, whose nodes do not move, until their tickets are waited for)
+        std::vector<GroupJob> group;
         size_t scratch = 0;
         long long probs = 0;
         while (!s->queue.empty() && (int)group.size() < s->lane_jobs) {
             const uint64_t tk = s->queue.front();
-            const mmgap_detect_job& J = s->jobs[tk].job;
-            const size_t need = BatchRunner::scratch_bytes(J.n_t, J.n_problems);
-            if (scratch + need > s->lane_scratch || probs + J.n_problems > s->lane_problems) break;
+            const JobRec& r = s->jobs[tk];
+            const size_t need = r.scratch();
+            if (scratch + need > s->lane_scratch || probs + r.n_problems() > s->lane_problems) break;
             scratch += need;
-            probs += J.n_problems;
-            group.push_back(J);
+            probs += r.n_problems();
+            group.push_back(r.group_job());
             L.tickets.push_back(tk);
             s->queue.pop_front();
         }
@@ -160,7 +178,7 @@ void dispatch_loop(mmgap_server* s) {
         // largest users first inside the group
         std::vector<int> order(group.size());
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return group[a].n_t > group[b].n_t; });
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return group[a].n_t() > group[b].n_t(); });
         cudaError_t e = cudaSuccess;
         if (L.runner.stage(group.data(), order.data(), (int)group.size()) != 0) e = cudaErrorInvalidValue;
         if (e == cudaSuccess) e = L.runner.run(s->params, L.stream, s->use_graph);
@@ -206,6 +224,8 @@ mmgap_status mmgap_server_create(mmgap_server** out, int device, const mmgap_par
     s->lane_scratch = cfg->scratch_bytes / (size_t)cfg->n_lanes;
     s->lane_jobs = cfg->max_jobs_per_group;
     s->lane_problems = cfg->max_problems_per_group;
+    s->max_n_t = cfg->max_n_t;
+    s->max_n_r = cfg->max_n_r;
     s->deadline_us = cfg->deadline_us;
     s->inject_delay_us = cfg->inject_delay_us;
     s->use_graph = cfg->use_graph != 0;
@@ -243,6 +263,7 @@ mmgap_status mmgap_server_submit(mmgap_server* s, const mmgap_detect_job* job, u
         fprintf(stderr, "mmgap_server_submit: %s\n", why);
         return MMGAP_EUNSUPPORTED;
     }
+    if (job->n_t > s->max_n_t || job->n_r > s->max_n_r) return MMGAP_EUNSUPPORTED;
     if (BatchRunner::scratch_bytes(job->n_t, job->n_problems) > s->lane_scratch ||
         job->n_problems > s->lane_problems)
         return MMGAP_ENOMEM;  // can never be admitted
@@ -252,6 +273,34 @@ mmgap_status mmgap_server_submit(mmgap_server* s, const mmgap_detect_job* job, u
         const uint64_t tk = s->next_ticket++;
         JobRec& r = s->jobs[tk];
         r.job = *job;
+        r.info = mmgap_job_info{};
+        r.info.ticket = tk;
+        r.info.status = -1;
+        r.info.submit_us = now_us();
+        if (s->first_submit_us < 0.0) s->first_submit_us = r.info.submit_us;
+        s->queue.push_back(tk);
+        *ticket = tk;
+    }
+    s->cv_dispatch.notify_one();
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_server_submit_precode(mmgap_server* s, const mmgap_precode_job* job, uint64_t* ticket) {
+    if (!s || !job || !ticket) return MMGAP_EINVAL;
+    if (const char* why = BatchRunner::check_precode(*job)) {
+        fprintf(stderr, "mmgap_server_submit_precode: %s\n", why);
+        return MMGAP_EUNSUPPORTED;
+    }
+    if (job->n_u > s->max_n_t) return MMGAP_EUNSUPPORTED;
+    if (BatchRunner::precode_scratch_bytes(*job) > s->lane_scratch || job->n_problems > s->lane_problems)
+        return MMGAP_ENOMEM;  // can never be admitted
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->stop) return MMGAP_EBUSY;
+        const uint64_t tk = s->next_ticket++;
+        JobRec& r = s->jobs[tk];
+        r.precode = true;
+        r.pjob = *job;
         r.info = mmgap_job_info{};
         r.info.ticket = tk;
         r.info.status = -1;

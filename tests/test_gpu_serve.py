@@ -92,3 +92,78 @@ def test_stalled_dispatcher_times_out_and_misses_deadlines():
             info = srv.wait(tk, timeout_us=30_000_000)
             assert info["latency_us"] >= 300_000.0
             assert srv.stats()["deadline_misses"] == 1
+
+
+PRE_SPECS = [(16, 16, 4, 200, 2, 0), (8, 8, 4, 300, 1, 1), (4, 6, 2, 250, 1, 0), (16, 24, 6, 64, 3, 1),
+             (8, 12, 4, 100, 2, 0)]  # (n_u, n_t, mod_bits, channels, symbols per channel, inv_precision)
+
+
+def _precode_jobs(ctx, specs):
+    out = []
+    for i, (n_u, n_t, mb, n_sub, n_sym, ip) in enumerate(specs):
+        d = synth.downlink(700 + i, n_u, n_t, mb, n_sub=n_sub, n_sym=n_sym)
+        t = [T(d[k]) for k in ("H", "u_sym", "chan_index")]
+        P = d["u_sym"].shape[0]
+        o = {"v": torch.full((P, n_u, 2), 9, dtype=torch.int8, device=DEV),
+             "x": torch.zeros((P, n_t), dtype=torch.complex64, device=DEV),
+             "power": torch.full((P,), -1.0, dtype=torch.float32, device=DEV),
+             "energy": torch.full((P,), 5, dtype=torch.int32, device=DEV),
+             "ndiv": torch.full((P,), -1, dtype=torch.int32, device=DEV)}
+        out.append((d, t, o, ip, ctx.precode_job(t[0], t[1], mb, 60 + i, o, t[2], inv_precision=ip)))
+    return out
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_precoding_jobs_in_the_mix_equal_mmgap_precode(persistent):
+    """Detection and VPP jobs of several sizes, both inverse precisions, submitted together: every
+    precoding output (v, x, power, energy, divergence count) equals mmgap_precode's alone, and every
+    detection output equals mmgap_detect's."""
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=80)
+    with pkg.Context(0) as ctx:
+        det = _jobs(ctx, SPECS[:4])
+        pre = _precode_jobs(ctx, PRE_SPECS)
+        det_ref, pre_ref = [], []
+        for w, t, o, job in det:
+            r = {k: torch.empty_like(v) for k, v in o.items()}
+            ctx.detect_jobs([ctx.detect_job(t[0], t[1], t[2], w["mod_bits"], job.seed, r, t[3])], prm)
+            det_ref.append(r)
+        for d, t, o, ip, job in pre:
+            pre_ref.append(ctx.precode(t[0], t[1], d["mod_bits"], prm, job.seed, chan_index=t[2], want_energy=True,
+                                       want_ndiv=True, inv_precision=ip))
+        torch.cuda.synchronize()
+        with pkg.Server(0, prm, scratch_bytes=16 << 20, n_lanes=2, max_jobs_per_group=3, max_n_r=16,
+                        persistent=persistent) as srv:
+            tickets = []
+            for i in range(max(len(det), len(pre))):  # interleaved arrivals
+                if i < len(det):
+                    tickets.append(srv.submit(det[i][3]))
+                if i < len(pre):
+                    tickets.append(srv.submit_precode(pre[i][4]))
+            for tk in tickets:
+                srv.wait(tk, timeout_us=60_000_000)
+            st = srv.stats()
+        for (w, t, o, job), r in zip(det, det_ref):
+            for k in o:
+                assert torch.equal(o[k], r[k]), k
+        for (d, t, o, ip, job), r in zip(pre, pre_ref):
+            for k in ("v", "x", "power", "energy", "ndiv"):
+                assert torch.equal(o[k], r[k]), (k, ip)
+        assert st["completed"] == len(tickets) and st["groups"] >= 3
+        assert st["problems"] == sum(w["y"].shape[0] for w, _, _, _ in det) + \
+            sum(d["u_sym"].shape[0] for d, _, _, _, _ in pre)
+
+
+def test_server_rejects_sizes_above_its_limits():
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=20)
+    with pkg.Context(0) as ctx:
+        det = _jobs(ctx, [(16, 4, 10, "iid", "subcarrier")])
+        pre = _precode_jobs(ctx, [(16, 16, 4, 10, 1, 0)])
+        with pkg.Server(0, prm, scratch_bytes=8 << 20, n_lanes=1, max_n_t=8) as srv:
+            with pytest.raises(pkg.MMGaPError) as e:
+                srv.submit(det[0][3])
+            assert e.value.status == 5
+            with pytest.raises(pkg.MMGaPError) as e:
+                srv.submit_precode(pre[0][4])
+            assert e.value.status == 5
