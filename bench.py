@@ -530,6 +530,60 @@ def run_mmgap_e(args):
     ctx.close()
 
 
+def run_critical(args):
+    """Critical-path latency (Sec. 5.3): one problem alone on the GPU, i.e.
+    the time a single problem takes with unlimited resources.  Per size, the
+    device time of one mmgap_detect call (build + solve) on one problem for
+    each solver launch shape, and of mmgap_detect_e (whose two instances of a
+    stage anneal in one launch, i.e. in parallel) with 1 and 2 stages."""
+    import torch
+
+    from paper_2510_01579_gb300 import VARIANT_NAMES, Context, Params
+    dev = torch.device("cuda", 0)
+    prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
+    ctx = Context(0)
+    stream = torch.cuda.current_stream(dev)
+    reps = max(20, args.steps * 5)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ts = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)
+        return {"median_us": ts[len(ts) // 2], "min_us": ts[0], "p99_us": ts[min(len(ts) - 1, int(0.99 * len(ts)))]}
+
+    sizes = {}
+    for n_t, mb in ((8, 4), (16, 4), (16, 6)):
+        w = synth.uplink(rank_seed(0) + 300 + n_t + mb, n_t, n_t, mb, n_sub=1, n_sym=1, snr_db=20.0)
+        H, y, nv, ci = (torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index"))
+        out = {"sym": torch.empty((1, n_t), dtype=torch.uint8, device=dev)}
+        job = ctx.detect_job(H, y, nv, mb, 11, out, ci)
+        r = {}
+        for v in (1, 2, 3, 4):
+            ctx.set_solver_variant(n_t, v)
+            r["mmgap_" + VARIANT_NAMES[v]] = timed(lambda: ctx.detect_jobs([job], prm))
+        ctx.set_solver_variant(n_t, 0)
+        for st in (1, 2):
+            r[f"mmgap_e{st}"] = timed(lambda: ctx.detect_e(H, y, nv, mb, prm, 11, stages=st, chan_index=ci))
+        sizes[f"{n_t}x{n_t}_{1 << mb}qam"] = r
+    best = min(v["median_us"] for k, v in sizes["16x16_16qam"].items() if not k.startswith("mmgap_e"))
+    line = {"metric": "critical-path latency of one problem (16x16 16-QAM, fastest launch shape)", "value": best,
+            "unit": "us", "n_gpus": 1, "steps": reps, "warmup": 3, "ms_per_step": best / 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "critical_path", "problems": 1, "runs": args.runs,
+                       "solver_steps": args.solver_steps, "f_mvm": args.f_mvm,
+                       "timing": "CUDA events around each call (device time incl. launch gaps)"},
+            "latency": sizes}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_appendix(args):
     """Appendix A on the GPU: 320 random Q14 instances x 32 anneals (33 spins),
     initial amplitudes fixed by Philox across settings; for each (dt, f_mvm)
@@ -583,7 +637,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mmgap", choices=["mmgap", "reference"])
     ap.add_argument("--workload", default="ul16x16_16qam_slot",
-                    choices=sorted(WORKLOADS) + ["mixed", "serve", "precode", "precision", "mmgap_e", "appendix"])
+                    choices=sorted(WORKLOADS) + ["mixed", "serve", "precode", "precision", "mmgap_e", "appendix",
+                                                  "critical"])
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load as a fraction of capacity")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: length of the arrival trace")
     ap.add_argument("--lanes", type=int, default=4, help="serve: concurrent launch groups (streams)")
@@ -595,6 +650,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="solver launch shape (1 plain .. 4); default: autotuned at set-up")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-problem kernel")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core field refresh variant")
     ap.add_argument("--no-batch", action="store_true", help="skip timing the batched persistent launch")
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--subcarriers", type=int, default=synth.SUBCARRIERS_100MHZ_30KHZ,
@@ -625,6 +681,9 @@ def main():
         return
     if args.workload == "appendix":
         run_appendix(args)
+        return
+    if args.workload == "critical":
+        run_critical(args)
         return
 
     import torch
@@ -774,6 +833,37 @@ def main():
         plain = {"ms_per_step": statistics.mean(pt), "value": P / (statistics.mean(pt) / 1e3),
                  "speedup_of_tuned": statistics.mean(pt) / ms_per_step}
 
+    # the tensor-core field refresh: a precision variant (FP16-split operands,
+    # FP32 accumulation; results not bit-identical), compared at equal BER
+    tc = None
+    if not args.no_tc and n_t in (8, 16) and args.f_mvm in (1, 2):
+        ctx.set_solver_variant(n_t, 5)
+        tout = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev)}
+        tjob = ctx.detect_job(H, y, nv, mb, 77, tout, ci)
+        for _ in range(2):
+            flush.zero_()
+            ctx.detect_jobs([tjob], prm)
+        torch.cuda.synchronize()
+        tt, ts = [], []
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            ctx.detect_jobs([tjob], prm)
+            ends[i].record(stream)
+            ts.append(ctx.stage_times()[1])
+        torch.cuda.synchronize()
+        tt = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+        ctx.set_solver_variant(n_t, variant)
+        tsym = tout["sym"].cpu().numpy()
+        ber_tc = synth.bit_errors(tsym, w["sym"], mb) / nbits
+        tc_solve = statistics.mean(ts)
+        tc = {"ms_per_step": statistics.mean(tt), "value": world * P / (statistics.mean(tt) / 1e3),
+              "solve_ms": tc_solve, "speedup_vs_exact": ms_per_step / statistics.mean(tt),
+              "ber": ber_tc, "ber_exact": ber, "ber_ratio": ber_tc / ber if ber > 0 else None,
+              "frac_problems_identical": float(np.mean(np.all(tsym == sym, axis=1))),
+              "algorithmic_tflops": solver_flops(P, n_t, args.runs, args.solver_steps, args.f_mvm) /
+              (tc_solve / 1e3) / 1e12}
+
     # the batched persistent launch (fused build + anneal per warp, replayed
     # from a CUDA graph) on the same slot
     batched = None
@@ -839,6 +929,7 @@ def main():
             "ber": {"mmgap": ber, "mmse": ber_mmse},
             "solver_shape": {"chosen": VARIANT_NAMES[variant], "autotune_ms": tune_ms},
             "plain_path": plain,
+            "tensor_core_refresh": tc,
             "batched_path": batched,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 2 * chunks, "clocks": clk, "wall_s": wall}

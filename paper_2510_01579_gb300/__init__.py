@@ -5,7 +5,7 @@ vector-perturbation precoding, behind the C ABI of include/mmgap.h.
 ``Context``, ``Params`` and ``MMGaPError`` come from the ctypes binding, which
 is imported on first use and raises if the CUDA library has not been built.
 """
-__all__ = ["Context", "Params", "MMGaPError", "SUPPORTED_NT", "Batch", "Server"]
+__all__ = ["Context", "Params", "MMGaPError", "SUPPORTED_NT", "Batch", "Server", "VARIANT_NAMES"]
 
 
 def __getattr__(name):

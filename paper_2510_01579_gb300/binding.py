@@ -124,7 +124,7 @@ ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_l
                "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_submit_precode",
                "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy")
 
-VARIANT_NAMES = {0: "default", 1: "plain", 2: "tpa1", 3: "tpa1-packed", 4: "tpa2-packed"}
+VARIANT_NAMES = {0: "default", 1: "plain", 2: "tpa1", 3: "tpa1-packed", 4: "tpa2-packed", 5: "tensor-core"}
 
 
 @dataclasses.dataclass

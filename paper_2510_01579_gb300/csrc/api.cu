@@ -59,6 +59,7 @@ int mmgap::resolve_variant(int n_t, int f_mvm, int requested) {
     const bool tuned = (n_t == 4 || n_t == 8 || n_t == 16) && (f_mvm == 1 || f_mvm == 2);
     if (!tuned) return kVariantPlain;
     if (requested <= kVariantAuto || requested >= kVariantCount) return kVariantTpa1Packed;
+    if (requested == kVariantTensorCore && n_t == 4) return kVariantTpa1Packed;
     return requested;
 }
 
@@ -771,6 +772,8 @@ mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant) {
     if (!ctx) return MMGAP_EINVAL;
     if (!nt_supported(n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d", n_t);
     if (variant < 0 || variant >= kVariantCount) return fail(ctx, MMGAP_EINVAL, "variant=%d", variant);
+    if (variant == kVariantTensorCore && n_t != 8 && n_t != 16)
+        return fail(ctx, MMGAP_EUNSUPPORTED, "tensor-core refresh needs n_t 8 or 16");
     ctx->variant[n_t] = variant;
     return MMGAP_OK;
 }
@@ -817,7 +820,7 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     cudaEventCreate(&t1);
     float best = 1e30f;
     int best_v = kVariantPlain;
-    for (int v = kVariantPlain; v < kVariantCount; ++v) {
+    for (int v = kVariantPlain; v < kVariantExactCount; ++v) {  // bit-identical shapes only
         if (ms_out) ms_out[v] = -1.0f;
         if (resolve_variant(n_t, params->f_mvm, v) != v) continue;  // not compiled for this size
         a.variant = v;

@@ -51,7 +51,9 @@ enum SolverVariant : int {
     kVariantTpa1 = 2,        // tuned kernel, one thread per anneal
     kVariantTpa1Packed = 3,  // tuned kernel, one thread per anneal, packed FP32 pairs
     kVariantTpa2Packed = 4,  // tuned kernel, two threads per anneal, packed FP32 pairs
-    kVariantCount = 5
+    kVariantExactCount = 5,  // variants below this one give bit-identical results
+    kVariantTensorCore = 5,  // field refresh on tensor cores (FP16 split, FP32 accumulation): not bit-identical
+    kVariantCount = 6
 };
 
 // Variant used for n_t users and refresh period f_mvm when `requested` is

@@ -837,15 +837,227 @@ __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, co
     }
 }
 
-template <int NT, int F, int TPA, bool PACKED>
+// FP16 / BF16 packing and the warp MMA used by the tensor-core refresh and Gram.
+__device__ __forceinline__ uint32_t pack16(float lo, float hi, int fp16) {
+    uint32_t r;
+    if (fp16) {
+        asm("{ .reg .f16 l, h;\n cvt.rn.f16.f32 l, %1;\n cvt.rn.f16.f32 h, %2;\n mov.b32 %0, {l, h}; }"
+            : "=r"(r) : "f"(lo), "f"(hi));
+    } else {
+        asm("cvt.rn.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(lo), "f"(hi));
+    }
+    return r;
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2], int fp16) {
+    if (fp16) {
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                     "{%0,%1,%2,%3};"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    } else {
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                     "{%0,%1,%2,%3};"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+}
+
+// -------------------------------------------------------------------------
+// Tensor-core field refresh (a precision variant of the refresh above; its
+// results are not bit-identical to the FP32 path's).  Per warp, the 32
+// anneals' fields are one product M = A U (n x n by n x 32) on mma.sync
+// m16n8k16 with FP16 operands and FP32 accumulation.  The Q14 couplings
+// c 2^-14 are exact as an FP16 pair (hi + lo); u 2^5 is split the same way
+// (22 bits), and M = Al Uh + Ah Ul + Ah Uh (the Al Ul term, ~2^-22, is
+// dropped), so m matches the FP32 refresh to about 2^-21 of sum |A||u|.
+// The scale 2^5 keeps |u| <= 2047 (every valid anneal: |x| <= x_max = 1000)
+// below the FP16 maximum; a larger u overflows to inf and its anneal ends
+// invalid.  U goes from registers to the MMA's B fragments through shared
+// memory (each lane writes its anneal's row of U^T), and M back to each
+// lane's registers the same way (rows of M^T; row strides padded so that
+// every access is free of bank conflicts).  mu_a = b^T u stays FP32.
+// -------------------------------------------------------------------------
+template <int NT>
+struct TcShape {
+    static constexpr int n = 2 * NT;
+    static constexpr int MT = n / 16;     // M tiles (rows i)
+    static constexpr int KT = n / 16;     // K steps (columns j)
+    static constexpr int UW = n / 2 + 4;  // 32-bit words per row of U^T (FP16 pairs), padded
+    static constexpr int MW = n + 4;      // floats per row of M^T, padded
+    static constexpr int WARP_WORDS = 2 * 32 * UW > 32 * MW ? 2 * 32 * UW : 32 * MW;
+    static constexpr int AF_WORDS = MT * KT * 2 * 4 * 32;  // A fragments, hi and lo
+};
+
+__device__ __forceinline__ uint32_t h2pack(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 h2unpack(uint32_t v) {
+    float2 f;
+    asm("{ .reg .f16 l, h;\n mov.b32 {l, h}, %2;\n cvt.f32.f16 %0, l;\n cvt.f32.f16 %1, h; }"
+        : "=f"(f.x), "=f"(f.y) : "r"(v));
+    return f;
+}
+
+// A fragments of every (M tile, K step) in lane order: word
+// ((mt KT + kk) 2 + hl) 4 + r) 32 + lane, hl = 0 hi, 1 lo.
+template <int NT>
+__device__ __forceinline__ void tc_stage_fragments(const int16_t* sAq, uint32_t* sAf, int tid, int T) {
+    using S = TcShape<NT>;
+    constexpr int n = S::n;
+    for (int idx = tid; idx < S::MT * S::KT * 4 * 32; idx += T) {
+        const int ln = idx & 31, r = (idx >> 5) & 3, tile = idx >> 7;
+        const int mt = tile / S::KT, kk = tile % S::KT;
+        const int g = ln >> 2, tg = ln & 3;
+        const int row = mt * 16 + g + ((r & 1) ? 8 : 0);
+        const int col = kk * 16 + 2 * tg + ((r & 2) ? 8 : 0);
+        const float a0 = (float)sAq[row * n + col] * 0x1p-14f, a1 = (float)sAq[row * n + col + 1] * 0x1p-14f;
+        const uint32_t hi = h2pack(a0, a1);
+        const float2 hf = h2unpack(hi);
+        const uint32_t lo = h2pack(a0 - hf.x, a1 - hf.y);  // exact: the codes have at most 15 bits
+        sAf[((tile * 2 + 0) * 4 + r) * 32 + ln] = hi;
+        sAf[((tile * 2 + 1) * 4 + r) * 32 + ln] = lo;
+    }
+}
+
+// Tensor-core refresh + L frozen Euler steps (packed FP32) of one anneal per lane.
+template <int NT, int L>
+__device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, const float* snd, uint32_t* wsm,
+                                         float (&x1)[2 * NT], float (&x2)[2 * NT], float (&e1)[2 * NT],
+                                         float (&e2)[2 * NT], float& xa, float& ea, int lane, int Lrt, float mscale,
+                                         const EulerConsts& k) {
+    using S = TcShape<NT>;
+    constexpr int n = S::n;
+    asm volatile("" ::: "memory");
+    uint32_t* sUh = wsm;
+    uint32_t* sUl = wsm + 32 * S::UW;
+    float* sM = reinterpret_cast<float*>(wsm);
+    // u = x1 + x2 and mu_a = b^T u (FP32, ascending j); FP16 split of 2^5 u into row `lane` of U^T
+    float mua = 0.0f;
+#pragma unroll
+    for (int w4 = 0; w4 < n / 8; ++w4) {
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = 8 * w4 + 2 * t;
+            const float2 u2 = __fadd2_rn(make_float2(x1[j], x1[j + 1]), make_float2(x2[j], x2[j + 1]));
+            mua = fmarn(sh[j], u2.x, mua);
+            mua = fmarn(sh[j + 1], u2.y, mua);
+            const float2 us = __fmul2_rn(u2, make_float2(32.0f, 32.0f));
+            hv[t] = h2pack(us.x, us.y);
+            const float2 hf = h2unpack(hv[t]);
+            lv[t] = h2pack(__fsub_rn(us.x, hf.x), __fsub_rn(us.y, hf.y));
+        }
+        *reinterpret_cast<uint4*>(sUh + lane * S::UW + 4 * w4) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(sUl + lane * S::UW + 4 * w4) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+    __syncwarp();
+    const int g = lane >> 2, tg = lane & 3;
+    float acc[S::MT][4][4];
+#pragma unroll
+    for (int mt = 0; mt < S::MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[mt][nt][c] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < S::KT; ++kk) {
+        uint32_t ah[S::MT][4], al[S::MT][4];
+#pragma unroll
+        for (int mt = 0; mt < S::MT; ++mt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                ah[mt][r] = sAf[(((mt * S::KT + kk) * 2 + 0) * 4 + r) * 32 + lane];
+                al[mt][r] = sAf[(((mt * S::KT + kk) * 2 + 1) * 4 + r) * 32 + lane];
+            }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int row = (nt * 8 + g) * S::UW + kk * 8 + tg;
+            const uint32_t bh[2] = {sUh[row], sUh[row + 4]};
+            const uint32_t bl[2] = {sUl[row], sUl[row + 4]};
+#pragma unroll
+            for (int mt = 0; mt < S::MT; ++mt) {  // small terms first
+                mma16816(acc[mt][nt], al[mt], bh, 1);
+                mma16816(acc[mt][nt], ah[mt], bl, 1);
+                mma16816(acc[mt][nt], ah[mt], bh, 1);
+            }
+        }
+    }
+    __syncwarp();  // every lane's B loads are done before M^T overwrites U^T
+#pragma unroll
+    for (int mt = 0; mt < S::MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int r0 = nt * 8 + 2 * tg, i0 = mt * 16 + g;
+            sM[r0 * S::MW + i0] = acc[mt][nt][0];
+            sM[(r0 + 1) * S::MW + i0] = acc[mt][nt][1];
+            sM[r0 * S::MW + i0 + 8] = acc[mt][nt][2];
+            sM[(r0 + 1) * S::MW + i0 + 8] = acc[mt][nt][3];
+        }
+    __syncwarp();
+    float m[n];
+#pragma unroll
+    for (int i4 = 0; i4 < n / 4; ++i4) {
+        const float4 v = *reinterpret_cast<const float4*>(sM + lane * S::MW + 4 * i4);
+        const float2 lo = __fmul2_rn(make_float2(v.x, v.y), make_float2(mscale, mscale));
+        const float2 hi = __fmul2_rn(make_float2(v.z, v.w), make_float2(mscale, mscale));
+        m[4 * i4] = lo.x;
+        m[4 * i4 + 1] = lo.y;
+        m[4 * i4 + 2] = hi.x;
+        m[4 * i4 + 3] = hi.y;
+    }
+    __syncwarp();  // the next refresh rewrites this warp's buffer
+    const float2 xa2 = make_float2(xa, xa);
+    const float2 cdt = make_float2(k.cdt, k.cdt), c1 = make_float2(k.c1, k.c1);
+    const float2 cz = make_float2(k.cz, k.cz), c2 = make_float2(k.c2, k.c2);
+#pragma unroll
+    for (int i = 0; i < n; i += 2) {
+        const float2 hh = *reinterpret_cast<const float2*>(sh + i);
+        const float2 nd = *reinterpret_cast<const float2*>(snd + i);
+        const float2 c = __ffma2_rn(hh, xa2, make_float2(m[i], m[i + 1]));
+        float2 X1 = make_float2(x1[i], x1[i + 1]), X2 = make_float2(x2[i], x2[i + 1]);
+        float2 E1 = make_float2(e1[i], e1[i + 1]), E2 = make_float2(e2[i], e2[i + 1]);
+        const float2 mu1 = __ffma2_rn(nd, X1, c);
+        const float2 mu2 = __ffma2_rn(nd, X2, c);
+        if constexpr (L > 0) {
+#pragma unroll
+            for (int s = 0; s < L; ++s) {
+                euler_pair(X1, E1, mu1, cdt, c1, cz, c2);
+                euler_pair(X2, E2, mu2, cdt, c1, cz, c2);
+            }
+        } else {
+#pragma unroll 1
+            for (int s = 0; s < Lrt; ++s) {
+                euler_pair(X1, E1, mu1, cdt, c1, cz, c2);
+                euler_pair(X2, E2, mu2, cdt, c1, cz, c2);
+            }
+        }
+        x1[i] = X1.x; x1[i + 1] = X1.y; x2[i] = X2.x; x2[i + 1] = X2.y;
+        e1[i] = E1.x; e1[i + 1] = E1.y; e2[i] = E2.x; e2[i + 1] = E2.y;
+    }
+    if constexpr (L > 0) {
+#pragma unroll
+        for (int s = 0; s < L; ++s) euler_spin(xa, ea, mua, k);
+    } else {
+#pragma unroll 1
+        for (int s = 0; s < Lrt; ++s) euler_spin(xa, ea, mua, k);
+    }
+}
+
+template <int NT, int F, int TPA, bool PACKED, bool TC = false>
 __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a) {
     constexpr int n = 2 * NT;
     constexpr int NS = n / TPA;
     static_assert(n % TPA == 0 && NS % 4 == 0, "rows per thread must be a multiple of 4");
     static_assert(F > 0, "compile-time refresh period");
+    static_assert(!TC || (TPA == 1 && PACKED && n % 16 == 0), "tensor-core refresh: one thread per anneal, n % 16 == 0");
     __shared__ __align__(16) SolveSmem<NT> sm;
     __shared__ long long skey[4 * TPA];
     __shared__ int sdiv[4 * TPA];
+    __shared__ __align__(16) uint32_t tc_af[TC ? TcShape<NT>::AF_WORDS : 1];
+    extern __shared__ __align__(16) uint32_t tc_ws[];  // TC: TcShape<NT>::WARP_WORDS per warp (dynamic)
     const int p = blockIdx.x;
     const int tid = threadIdx.x, T = blockDim.x;
     const int q = tid % TPA, run = tid / TPA;
@@ -869,6 +1081,7 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
     }
     __syncthreads();
     for (int i = tid; i < n; i += T) sm.nd[i] = -sm.A[i * n + i];
+    if constexpr (TC) tc_stage_fragments<NT>(sm.Aq, tc_af, tid, T);
     __syncthreads();
 
     // Philox initial amplitudes of this thread's spins (k = row, n + row, 2n)
@@ -895,10 +1108,18 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
 
     const int S = a.steps;
     int t = 0;
+    if constexpr (TC) {
+        uint32_t* wsm = tc_ws + warp * TcShape<NT>::WARP_WORDS;
+        const float mscale = mulrn(k.ce, 0x1p-5f);  // eps dt, and the 2^5 of u
 #pragma unroll 1
-    for (; t + F <= S; t += F)
-        tuned_block<n, NS, TPA, PACKED, F>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
-    if (t < S) tuned_block<n, NS, TPA, PACKED, 0>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
+        for (; t + F <= S; t += F) tc_block<NT, F>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, F, mscale, k);
+        if (t < S) tc_block<NT, 0>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, S - t, mscale, k);
+    } else {
+#pragma unroll 1
+        for (; t + F <= S; t += F)
+            tuned_block<n, NS, TPA, PACKED, F>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
+        if (t < S) tuned_block<n, NS, TPA, PACKED, 0>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
+    }
 
     // validity over the whole anneal
     bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
@@ -1249,31 +1470,6 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchArgs A) {
 // multiple of 16.  Each element of Hs = kappa H is rounded once to FP32 and
 // once to the 16-bit type.
 // =========================================================================
-__device__ __forceinline__ uint32_t pack16(float lo, float hi, int fp16) {
-    uint32_t r;
-    if (fp16) {
-        asm("{ .reg .f16 l, h;\n cvt.rn.f16.f32 l, %1;\n cvt.rn.f16.f32 h, %2;\n mov.b32 %0, {l, h}; }"
-            : "=r"(r) : "f"(lo), "f"(hi));
-    } else {
-        asm("cvt.rn.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(lo), "f"(hi));
-    }
-    return r;
-}
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2], int fp16) {
-    if (fp16) {
-        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                     "{%0,%1,%2,%3};"
-                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-    } else {
-        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                     "{%0,%1,%2,%3};"
-                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-    }
-}
-
 template <int NT>
 __global__ void __launch_bounds__(128) gram_tc_kernel(GramArgs a) {
     static_assert(NT <= 16, "one 16-row tile");
@@ -1963,6 +2159,13 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
         case kVariantTpa1: cac_solve_tuned_kernel<NT, F, 1, false><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa1Packed: cac_solve_tuned_kernel<NT, F, 1, true><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa2Packed: cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a); break;
+        case kVariantTensorCore:
+            if constexpr (NT % 8 == 0) {
+                cac_solve_tuned_kernel<NT, F, 1, true, true>
+                    <<<a.n_problems, runs, (size_t)(runs / 32) * TcShape<NT>::WARP_WORDS * 4, s>>>(a);
+                break;
+            }
+            [[fallthrough]];
         default: cac_solve_kernel<NT, F><<<a.n_problems, runs, 0, s>>>(a); break;
         }
     } else {

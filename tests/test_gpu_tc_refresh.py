@@ -1,0 +1,94 @@
+"""Tensor-core field refresh (solver launch shape 5).
+
+A precision variant of the CIM-CAC solver: the field m = A u of the 32
+anneals of a warp is one mma.sync product with FP16-split operands and FP32
+accumulation, so its results are not bit-identical to the FP32 path's.  What
+is required of it:
+  * the selection stays exact: every reported energy is the integer energy of
+    the reported offsets (checked with the oracle's energy);
+  * over a few steps, where the FP32 path's rounding has not yet been
+    amplified by the dynamics, it takes the same decisions;
+  * over full anneals it detects at the same bit error rate as the FP32 path
+    (within the binomial spread of the error counts) and better than MMSE;
+  * it is never chosen by the autotuner and is refused for sizes it lacks.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.fixture(scope="module")
+def mm():
+    import paper_2510_01579_gb300 as pkg
+    ctx = pkg.Context(0)
+    yield pkg, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("n_t,f,runs", [(8, 1, 32), (8, 2, 64), (16, 2, 32), (16, 1, 128)])
+def test_short_anneals_agree_and_energies_are_exact(mm, n_t, f, runs):
+    pkg, ctx = mm
+    n = 2 * n_t
+    Aq, hq = synth.random_ising(40 + n_t + f, 1500, n)
+    prm = pkg.Params.default(steps=7, f_mvm=f, runs=runs)
+    res = {}
+    for v in (3, 5):
+        ctx.set_solver_variant(n_t, v)
+        res[v] = ctx.solve_ising(T(Aq), T(hq), prm, 9)
+    ctx.set_solver_variant(n_t, 0)
+    torch.cuda.synchronize()
+    d3, d5 = res[3]["d"].cpu().numpy(), res[5]["d"].cpu().numpy()
+    same = np.all(d3 == d5, axis=1).mean()
+    assert same >= 0.99, same
+    E5 = res[5]["E"].cpu().numpy()
+    for p in range(0, 1500, 7):
+        assert E5[p] == oracle.energy_q(Aq[p], hq[p], d5[p]), p
+
+
+@pytest.mark.parametrize("n_t,mb,snr,model,hold", [(16, 4, 16.0, "iid", "subcarrier"), (8, 4, 15.0, "kron", "prb")])
+def test_detection_ber_equals_the_fp32_path(mm, n_t, mb, snr, model, hold):
+    """16x16 16-QAM i.i.d. and 8x8 16-QAM Kronecker, 32 anneals x 200 steps:
+    the bit-error counts of the two refreshes differ by less than four
+    standard deviations of a binomial count (and by less than 12 %)."""
+    pkg, ctx = mm
+    w = synth.uplink(77 + n_t, n_t, n_t, mb, n_sub=600, n_sym=14, snr_db=snr, model=model, hold=hold)
+    P = w["y"].shape[0]
+    prm = pkg.Params.default()
+    H, y, nv, ci = (T(w[k]) for k in ("H", "y", "noise_var", "chan_index"))
+    errs = {}
+    for v in (3, 5):
+        ctx.set_solver_variant(n_t, v)
+        out = ctx.detect(H, y, nv, mb, prm, 5, chan_index=ci, want_guess=(v == 3))
+        torch.cuda.synchronize()
+        errs[v] = synth.bit_errors(out["sym"].cpu().numpy(), w["sym"], mb)
+        if v == 3:
+            g = out["guess"].cpu().numpy().astype(int)
+            side = 1 << (mb // 2)
+            mmse = ((g[:, :n_t] + side - 1) // 2) * side + (g[:, n_t:] + side - 1) // 2
+            errs["mmse"] = synth.bit_errors(mmse, w["sym"], mb)
+    ctx.set_solver_variant(n_t, 0)
+    nbits = P * n_t * mb
+    e3, e5 = errs[3], errs[5]
+    sd = np.sqrt(e3 * (1 - e3 / nbits))
+    assert abs(e5 - e3) <= 4 * sd and abs(e5 - e3) <= 0.12 * e3, (e3, e5, sd)
+    assert e5 < errs["mmse"]
+
+
+def test_refused_where_not_built_and_never_autotuned(mm):
+    pkg, ctx = mm
+    with pytest.raises(pkg.MMGaPError) as e:
+        ctx.set_solver_variant(4, 5)
+    assert e.value.status == 5
+    v, ms = ctx.autotune(pkg.Params.default(steps=40), 16, 2048)
+    assert v in (1, 2, 3, 4) and 5 not in ms
