@@ -439,3 +439,113 @@ def detect_e(H, y, noise_var, mod_bits, stages, params: Params, seed, problem):
     _lib.orc_detect_e(n_r, n_t, mod_bits, _c64(H), _c64(y), np.float32(noise_var), stages, C.byref(cp), int(seed),
                       int(problem), sym, C.byref(best), C.byref(obj), X)
     return dict(sym=sym, best=best.value, obj=obj.value, candidates=X.reshape(nc, 2 * n_t))
+
+
+# ------------------------------------------------- direct (binary) mapping
+_lib.orc_build_direct64.argtypes = [C.c_int, C.c_int, C.c_int, _f64p, _f64p, _nullable(_f64p), _nullable(_f64p),
+                                    C.POINTER(C.c_double)]
+_lib.orc_direct_lattice.argtypes = [C.c_int, C.c_int, _i8p, _i32p]
+_lib.orc_direct_spins.argtypes = [C.c_int, C.c_int, _i32p, _i8p]
+_lib.orc_energy_direct.restype = C.c_int32
+_lib.orc_energy_direct.argtypes = [C.c_int, _i16p, _i16p, _i8p]
+_lib.orc_build_direct32.argtypes = [C.c_int, C.c_int, C.c_int, _f32p, _f32p, C.c_float, _i32p, _nullable(_f32p),
+                                    _nullable(_f32p), C.POINTER(C.c_int), _i16p, _i16p]
+_lib.orc_general_field.argtypes = [C.c_int, _f32p, _f32p, _f32p, _f32p]
+_lib.orc_cac_solve_general.argtypes = [C.c_int, _i16p, _i16p, _nullable(_i8p), C.POINTER(CParams), C.c_uint64,
+                                       C.c_uint64, _i8p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32), _nullable(_i32p)]
+_lib.orc_detect_direct.argtypes = [C.c_int, C.c_int, C.c_int, _f32p, _f32p, C.c_float, C.POINTER(CParams),
+                                   C.c_uint64, C.c_uint64, _u8p, _i32p, _i8p, C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+
+
+def direct_spins_count(n_t, mod_bits) -> int:
+    return 2 * n_t * (mod_bits // 2)
+
+
+def build_direct64(H, y, mod_bits):
+    """FP64 direct-mapping Ising form: dict(J (N, N), c (N,), const)."""
+    H = np.asarray(H)
+    n_r, n_t = H.shape
+    N = direct_spins_count(n_t, mod_bits)
+    J = np.zeros(N * N)
+    c = np.zeros(N)
+    k = C.c_double()
+    st = _lib.orc_build_direct64(n_r, n_t, mod_bits, _c128(H), _c128(y), J, c, C.byref(k))
+    if st:
+        raise ValueError("invalid arguments")
+    return dict(J=J.reshape(N, N), c=c, const=k.value)
+
+
+def direct_lattice(n_t, mod_bits, s) -> np.ndarray:
+    x = np.zeros(2 * n_t, np.int32)
+    _lib.orc_direct_lattice(n_t, mod_bits, np.ascontiguousarray(s, np.int8), x)
+    return x
+
+
+def direct_spins(n_t, mod_bits, x) -> np.ndarray:
+    s = np.zeros(direct_spins_count(n_t, mod_bits), np.int8)
+    _lib.orc_direct_spins(n_t, mod_bits, np.ascontiguousarray(x, np.int32), s)
+    return s
+
+
+def energy_direct(Jq, cq, s) -> int:
+    return int(_lib.orc_energy_direct(len(cq), np.ascontiguousarray(Jq, np.int16).ravel(),
+                                      np.ascontiguousarray(cq, np.int16), np.ascontiguousarray(s, np.int8)))
+
+
+def build_direct32(H, y, noise_var, mod_bits):
+    """FP32 direct build in the pinned order: dict(g, J32, c32, sigma_exp, Jq, cq, status)."""
+    H = np.asarray(H)
+    n_r, n_t = H.shape
+    N = direct_spins_count(n_t, mod_bits)
+    g = np.zeros(2 * n_t, np.int32)
+    J = np.zeros(N * N, np.float32)
+    c = np.zeros(N, np.float32)
+    se = C.c_int()
+    Jq = np.zeros(N * N, np.int16)
+    cq = np.zeros(N, np.int16)
+    st = _lib.orc_build_direct32(n_r, n_t, mod_bits, _c64(H), _c64(y), np.float32(noise_var), g, J, c, C.byref(se),
+                                 Jq, cq)
+    return dict(status=st, g=g, J32=J.reshape(N, N), c32=c, sigma_exp=se.value, Jq=Jq.reshape(N, N), cq=cq)
+
+
+def general_field(Jf, cf, x) -> np.ndarray:
+    N = len(cf)
+    mu = np.zeros(N + 1, np.float32)
+    _lib.orc_general_field(N, np.ascontiguousarray(Jf, np.float32).ravel(), np.ascontiguousarray(cf, np.float32),
+                           np.ascontiguousarray(x, np.float32), mu)
+    return mu
+
+
+def cac_solve_general(Jq, cq, s_ref, params: Params, seed, problem, want_energies=False):
+    N = len(cq)
+    s = np.zeros(N, np.int8)
+    E, run, nd = C.c_int32(), C.c_int32(), C.c_int32()
+    Er = np.zeros(params.runs, np.int32) if want_energies else None
+    sr = None if s_ref is None else np.ascontiguousarray(s_ref, np.int8)
+    cp = params.c()
+    st = _lib.orc_cac_solve_general(N, np.ascontiguousarray(Jq, np.int16).ravel(), np.ascontiguousarray(cq, np.int16),
+                                    sr, C.byref(cp), int(seed), int(problem), s, C.byref(E), C.byref(run),
+                                    C.byref(nd), Er)
+    if st:
+        raise ValueError("invalid solver arguments")
+    out = dict(s=s, E=E.value, run=run.value, n_div=nd.value)
+    if want_energies:
+        out["E_runs"] = Er
+    return out
+
+
+def detect_direct(H, y, noise_var, mod_bits, params: Params, seed, problem):
+    """Direct-mapping detection of one problem: dict(sym, g, s, E, run, n_div)."""
+    H = np.asarray(H)
+    n_r, n_t = H.shape
+    N = direct_spins_count(n_t, mod_bits)
+    sym = np.zeros(n_t, np.uint8)
+    g = np.zeros(2 * n_t, np.int32)
+    s = np.zeros(N, np.int8)
+    E, run, nd = C.c_int32(), C.c_int32(), C.c_int32()
+    cp = params.c()
+    _lib.orc_detect_direct(n_r, n_t, mod_bits, _c64(H), _c64(y), np.float32(noise_var), C.byref(cp), int(seed),
+                           int(problem), sym, g, s, C.byref(E), C.byref(run), C.byref(nd))
+    return dict(sym=sym, g=g, s=s, E=E.value, run=run.value, n_div=nd.value)

@@ -1363,3 +1363,278 @@ int orc_detect_e(int n_r, int n_t, int mod_bits, const float* H, const float* y,
     free(zero); free(X); free(Aq); free(hq); free(g); free(d);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Direct (binary-weighted) spin mapping.  The paper's method is the delta   */
+/* form above (Sec. 2.3, Sec. 3.2.1); the direct form is the mapping of the  */
+/* Ising-machine detectors it builds on, where each real dimension of the    */
+/* lattice symbol is a binary-weighted sum of spins.  The paper gives no     */
+/* formulas for it; the readings are:                                        */
+/*   B = mod_bits / 2 spins per real dimension, x_k = sum_b 2^b s_(kB+b),    */
+/*   i.e. x = T s with T = I_(2 n_t) (x) [1, 2, ..., 2^(B-1)]; real          */
+/*   dimensions k in the real-form order (Re of users, then Im of users).   */
+/*   ||y - Hs T s||^2 = s^T (T^T G T) s - 2 (T^T mf)^T s + ||y||^2 with     */
+/*   G = Hs_r^T Hs_r and mf = Hs_r^T y_r (real forms), so with an auxiliary  */
+/*   spin s_a the Ising form to maximise is s^T J s + 2 s_a c^T s with       */
+/*   J = -(T^T G T) (diagonal set to 0: s_i^2 = 1) and c = T^T mf, and       */
+/*   ||y - Hs T s||^2 = -s^T J s - 2 c^T s + ||y||^2 + tr(T^T G T).          */
+/* N = 2 n_t B spins (16 for 8x8 QPSK, 64 for 16x16 16-QAM, 96 for 16x16     */
+/* 64-QAM) plus the auxiliary one.                                          */
+/* ------------------------------------------------------------------------- */
+
+/* FP64 truth: J [N*N], c [N], and the constant ||y||^2 + tr(T^T G T). */
+int orc_build_direct64(int n_r, int n_t, int mod_bits, const double* H, const double* y, double* J_out,
+                       double* c_out, double* const_out)
+{
+    if (n_r < 1 || n_t < 1 || mod_bits < 2 || (mod_bits & 1)) return ORC_EINVAL;
+    const int n = 2 * n_t, B = mod_bits / 2, N = n * B;
+    const double kappa = orc_qam_kappa(mod_bits);
+    /* real forms Hr [2 n_r][n], yr [2 n_r] */
+    double* Hr = (double*)malloc(sizeof(double) * (size_t)(2 * n_r * n));
+    double* yr = (double*)malloc(sizeof(double) * (size_t)(2 * n_r));
+    for (int k = 0; k < n_r; ++k) {
+        yr[k] = y[2 * k];
+        yr[n_r + k] = y[2 * k + 1];
+        for (int i = 0; i < n_t; ++i) {
+            double re = kappa * H[2 * (k * n_t + i)], im = kappa * H[2 * (k * n_t + i) + 1];
+            Hr[k * n + i] = re;
+            Hr[k * n + n_t + i] = -im;
+            Hr[(n_r + k) * n + i] = im;
+            Hr[(n_r + k) * n + n_t + i] = re;
+        }
+    }
+    double* G = (double*)calloc((size_t)(n * n), sizeof(double));
+    double* mf = (double*)calloc((size_t)n, sizeof(double));
+    for (int a = 0; a < n; ++a) {
+        for (int b = 0; b < n; ++b)
+            for (int r = 0; r < 2 * n_r; ++r) G[a * n + b] += Hr[r * n + a] * Hr[r * n + b];
+        for (int r = 0; r < 2 * n_r; ++r) mf[a] += Hr[r * n + a] * yr[r];
+    }
+    double tr = 0.0, yy = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const int ki = i / B, bi = i % B;
+        for (int j = 0; j < N; ++j) {
+            const int kj = j / B, bj = j % B;
+            const double v = ldexp(G[ki * n + kj], bi + bj);
+            if (i == j) tr += v;
+            if (J_out) J_out[i * N + j] = i == j ? 0.0 : -v;
+        }
+        if (c_out) c_out[i] = ldexp(mf[ki], bi);
+    }
+    for (int r = 0; r < 2 * n_r; ++r) yy += yr[r] * yr[r];
+    if (const_out) *const_out = yy + tr;
+    free(Hr); free(yr); free(G); free(mf);
+    return ORC_OK;
+}
+
+/* Lattice symbol x [2 n_t] of spins s [N] (x = T s). */
+void orc_direct_lattice(int n_t, int mod_bits, const int8_t* s, int* x)
+{
+    const int B = mod_bits / 2;
+    for (int k = 0; k < 2 * n_t; ++k) {
+        int v = 0;
+        for (int b = 0; b < B; ++b) v += (1 << b) * (int)s[k * B + b];
+        x[k] = v;
+    }
+}
+
+/* Spins of an alphabet point: s_b = 2 bit_b((x + 2^B - 1) / 2) - 1. */
+void orc_direct_spins(int n_t, int mod_bits, const int* x, int8_t* s)
+{
+    const int B = mod_bits / 2;
+    for (int k = 0; k < 2 * n_t; ++k) {
+        const int u = (x[k] + (1 << B) - 1) / 2;
+        for (int b = 0; b < B; ++b) s[k * B + b] = (int8_t)(((u >> b) & 1) ? 1 : -1);
+    }
+}
+
+/* Exact quantised energy of spins s: E(s) = -s^T J_q s - 2 c_q^T s (int32),
+ * lower is better; equals (||y - Hs T s||^2 - const) 2^14 / sigma up to
+ * quantisation. */
+int32_t orc_energy_direct(int N, const int16_t* Jq, const int16_t* cq, const int8_t* s)
+{
+    int32_t e = 0;
+    for (int i = 0; i < N; ++i) {
+        int32_t r = 0;
+        for (int j = 0; j < N; ++j) r += (int32_t)Jq[i * N + j] * (int32_t)s[j];
+        e -= (int32_t)s[i] * r;
+        e -= 2 * (int32_t)cq[i] * (int32_t)s[i];
+    }
+    return e;
+}
+
+/*
+ * FP32 direct build in the pinned order: the FP32 real-form Gram G32 and the
+ * MMSE guess g are those of orc_build_detect32; the matched filter
+ * mf = Hs^H y follows its pattern (k ascending, from 0); then
+ *   J32_ij = -(2^(b_i + b_j) G32_(k_i k_j)) for i != j, 0 on the diagonal,
+ *   c32_i  = 2^(b_i) mf_(k_i)
+ * (exact scalings), sigma = 2^e the smallest power of two >= max(|J32|, |c32|),
+ * Jq = rint(J32 2^(14-e)), cq = rint(c32 2^(14-e)) as int16.
+ * Outputs: g [2 n_t], J32 [N*N], c32 [N] (may be NULL), sigma_exp, Jq, cq.
+ */
+int orc_build_direct32(int n_r, int n_t, int mod_bits, const float* H, const float* y, float noise_var, int* g_out,
+                       float* J32_out, float* c32_out, int* sigma_exp_out, int16_t* Jq_out, int16_t* cq_out)
+{
+    if (n_r < 1 || n_t < 1 || mod_bits < 2 || (mod_bits & 1)) return ORC_EINVAL;
+    const int n = 2 * n_t, B = mod_bits / 2, N = n * B;
+    float* G = (float*)malloc(sizeof(float) * (size_t)(n * n));
+    int16_t* Aq = (int16_t*)malloc(sizeof(int16_t) * (size_t)(n * n));
+    int16_t* hq = (int16_t*)malloc(sizeof(int16_t) * (size_t)n);
+    int se0;
+    int status = orc_build_detect32(n_r, n_t, mod_bits, H, y, noise_var, NULL, g_out, G, NULL, &se0, Aq, hq);
+    const float kappa = qam_kappa_f(mod_bits);
+    float* mf = (float*)malloc(sizeof(float) * (size_t)n);
+    for (int i = 0; i < n_t; ++i) {
+        float re = 0.0f, im = 0.0f;
+        for (int k = 0; k < n_r; ++k) {
+            const float ar = f_mul(kappa, H[2 * (k * n_t + i)]), ai = f_mul(kappa, H[2 * (k * n_t + i) + 1]);
+            const float br = y[2 * k], bi = y[2 * k + 1];
+            re = fmaf(ar, br, re);
+            re = fmaf(ai, bi, re);
+            im = fmaf(ar, bi, im);
+            im = fmaf(-ai, br, im);
+        }
+        mf[i] = re;
+        mf[n_t + i] = im;
+    }
+    float* J = (float*)malloc(sizeof(float) * (size_t)(N * N));
+    float* c = (float*)malloc(sizeof(float) * (size_t)N);
+    float mx = 0.0f;
+    for (int i = 0; i < N; ++i) {
+        const int ki = i / B, bi = i % B;
+        for (int j = 0; j < N; ++j) {
+            const int kj = j / B, bj = j % B;
+            J[i * N + j] = i == j ? 0.0f : -ldexpf(G[ki * n + kj], bi + bj);
+            mx = fmaxf(mx, fabsf(J[i * N + j]));
+        }
+        c[i] = ldexpf(mf[ki], bi);
+        mx = fmaxf(mx, fabsf(c[i]));
+    }
+    const int se = sigma_exp_f(mx);
+    const int finite = isfinite(mx);
+    const float s = pow2f(QBITS - se);
+    for (int e = 0; e < N * N; ++e) Jq_out[e] = finite ? (int16_t)rintf(f_mul(J[e], s)) : 0;
+    for (int i = 0; i < N; ++i) cq_out[i] = finite ? (int16_t)rintf(f_mul(c[i], s)) : 0;
+    if (!finite) status = ORC_ENUM;
+    if (J32_out) memcpy(J32_out, J, sizeof(float) * (size_t)(N * N));
+    if (c32_out) memcpy(c32_out, c, sizeof(float) * (size_t)N);
+    if (sigma_exp_out) *sigma_exp_out = se;
+    free(G); free(Aq); free(hq); free(mf); free(J); free(c);
+    return status;
+}
+
+/* Coupling field of a general Ising problem with an auxiliary spin:
+ * m_i = sum_j J_ji x_j (j ascending, FMA chain from 0; J symmetric with zero
+ * diagonal), mu_i = m_i + c_i x_a, mu_a = sum_j c_j x_j (j ascending).
+ * Jf, cf carry eps dt.  x, mu: [N + 1] (x_a last). */
+void orc_general_field(int N, const float* Jf, const float* cf, const float* x, float* mu)
+{
+    const float xa = x[N];
+    float mua = 0.0f;
+    for (int i = 0; i < N; ++i) {
+        float m = 0.0f;
+        for (int j = 0; j < N; ++j) m = fmaf(Jf[j * N + i], x[j], m);
+        mu[i] = fmaf(cf[i], xa, m);
+    }
+    for (int j = 0; j < N; ++j) mua = fmaf(cf[j], x[j], mua);
+    mu[N] = mua;
+}
+
+/*
+ * Anneal a general Ising problem (Jq [N*N] symmetric, zero diagonal; cq [N],
+ * coupled through the auxiliary spin) with R anneals of the same CIM-CAC
+ * dynamics as orc_cac_solve (initial amplitudes: spin k of run r is Philox
+ * word k mod 4 of counter (k/4, r, problem), k = N the auxiliary spin).
+ * Each anneal's spins s_i = sign(x_i) sign(x_a) (x >= 0 -> +1) are scored by
+ * the exact energy E(s); a diverged anneal is not a candidate.  The reference
+ * spins s_ref (may be NULL) are candidate -1 and win ties.  The output is the
+ * lowest (E, candidate index).
+ * Outputs: s_out [N], E_out, run_out (-1: s_ref, or no valid candidate when
+ * s_ref is NULL, then s = +1 and E = E(+1)), n_div_out; optional E_runs [R]
+ * (INT32_MAX for diverged anneals).
+ */
+int orc_cac_solve_general(int N, const int16_t* Jq, const int16_t* cq, const int8_t* s_ref, const orc_params* P,
+                          uint64_t seed, uint64_t problem, int8_t* s_out, int32_t* E_out, int32_t* run_out,
+                          int32_t* n_div_out, int32_t* E_runs)
+{
+    if (N < 1 || P->runs < 1 || P->steps < 0 || P->f_mvm < 1) return ORC_EINVAL;
+    orc_consts C;
+    orc_cac_consts(P, &C);
+    const float q = pow2f(-QBITS);
+    float* Jf = (float*)malloc(sizeof(float) * (size_t)(N * N));
+    float* cf = (float*)malloc(sizeof(float) * (size_t)N);
+    for (int e = 0; e < N * N; ++e) Jf[e] = f_mul(f_mul((float)Jq[e], q), C.ce);
+    for (int i = 0; i < N; ++i) cf[i] = f_mul(f_mul((float)cq[i], q), C.ce);
+    float* x = (float*)malloc(sizeof(float) * (size_t)(N + 1));
+    float* eh = (float*)malloc(sizeof(float) * (size_t)(N + 1));
+    float* mu = (float*)malloc(sizeof(float) * (size_t)(N + 1));
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    int32_t bestE;
+    int bestRun = -1, ndiv = 0;
+    if (s_ref) {
+        memcpy(s_out, s_ref, (size_t)N);
+    } else {
+        memset(s_out, 1, (size_t)N);
+    }
+    bestE = orc_energy_direct(N, Jq, cq, s_out);
+    int have = s_ref != NULL;
+    for (int r = 0; r < P->runs; ++r) {
+        for (int k = 0; k <= N; ++k) {
+            x[k] = orc_initial_x(seed, problem, r, k, C.xs);
+            eh[k] = 1.0f;
+        }
+        for (int t = 0; t < P->steps; ++t) {
+            if (t % P->f_mvm == 0) orc_general_field(N, Jf, cf, x, mu);
+            for (int k = 0; k <= N; ++k) euler_spin(&x[k], &eh[k], mu[k], &C);
+        }
+        int valid = 1;
+        for (int k = 0; k <= N; ++k)
+            if (!(fabsf(x[k]) <= P->x_max) || !(eh[k] > 0.0f)) valid = 0;
+        const int sa = x[N] >= 0.0f ? 1 : -1;
+        for (int i = 0; i < N; ++i) s[i] = (int8_t)((x[i] >= 0.0f ? 1 : -1) * sa);
+        const int32_t E = valid ? orc_energy_direct(N, Jq, cq, s) : INT32_MAX;
+        if (E_runs) E_runs[r] = E;
+        if (!valid) {
+            ndiv++;
+            continue;
+        }
+        if (!have || E < bestE) {
+            bestE = E;
+            bestRun = r;
+            memcpy(s_out, s, (size_t)N);
+            have = 1;
+        }
+    }
+    *E_out = bestE;
+    *run_out = bestRun;
+    *n_div_out = ndiv;
+    free(Jf); free(cf); free(x); free(eh); free(mu); free(s);
+    return ORC_OK;
+}
+
+/*
+ * Uplink detection of one problem with the direct mapping (FP32 mirror):
+ * build (orc_build_direct32), anneal with the MMSE guess's spins as the
+ * reference candidate, decode x = T s to symbol indices.
+ * Outputs: sym [n_t], g (MMSE guess, [2 n_t]), s [N], E, run, n_div.
+ */
+int orc_detect_direct(int n_r, int n_t, int mod_bits, const float* H, const float* y, float noise_var,
+                      const orc_params* P, uint64_t seed, uint64_t problem, uint8_t* sym, int* g, int8_t* s,
+                      int32_t* E, int32_t* run, int32_t* n_div)
+{
+    const int n = 2 * n_t, N = n * (mod_bits / 2);
+    int16_t* Jq = (int16_t*)malloc(sizeof(int16_t) * (size_t)(N * N));
+    int16_t* cq = (int16_t*)malloc(sizeof(int16_t) * (size_t)N);
+    int8_t* sref = (int8_t*)malloc((size_t)N);
+    int* x = (int*)malloc(sizeof(int) * (size_t)n);
+    int se;
+    orc_build_direct32(n_r, n_t, mod_bits, H, y, noise_var, g, NULL, NULL, &se, Jq, cq);
+    orc_direct_spins(n_t, mod_bits, g, sref);
+    orc_cac_solve_general(N, Jq, cq, sref, P, seed, problem, s, E, run, n_div, NULL);
+    orc_direct_lattice(n_t, mod_bits, s, x);
+    int8_t* zero = (int8_t*)calloc((size_t)n, 1);
+    orc_decode_detect(n_t, mod_bits, x, zero, sym);
+    free(Jq); free(cq); free(sref); free(x); free(zero);
+    return ORC_OK;
+}
