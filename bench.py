@@ -584,6 +584,64 @@ def run_critical(args):
     ctx.close()
 
 
+def run_direct(args):
+    """Direct (binary-weighted) spin mapping against the paper's delta mapping
+    on the same problems: one OFDM symbol of 3276 subcarriers for 8x8 QPSK
+    (16 spins), 8x8 16-QAM (32), 16x16 16-QAM (64) and 16x16 64-QAM (96),
+    i.i.d. Rayleigh; time per slot and BER of each, and of MMSE."""
+    import torch
+
+    from paper_2510_01579_gb300 import Context, Params
+    dev = torch.device("cuda", 0)
+    prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
+    ctx = Context(0, workspace_bytes=1 << 30)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    res = {}
+    for n_t, mb, snr in ((8, 2, 10.0), (8, 4, 16.0), (16, 4, 16.0), (16, 6, 24.0)):
+        w = synth.uplink(rank_seed(0) + 40 + n_t + mb, n_t, n_t, mb, n_sub=args.subcarriers, n_sym=1, snr_db=snr)
+        H, y, nv, ci = (torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index"))
+        P = w["y"].shape[0]
+        nbits = P * n_t * mb
+        r = {"spins_delta": 4 * n_t + 1, "spins_direct": 2 * n_t * (mb // 2) + 1, "problems": P, "snr_db": snr}
+        for name, mapping in (("delta", 0), ("direct", 1)):
+            out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
+                   "guess": torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)}
+            job = ctx.detect_job(H, y, nv, mb, 9, out, ci, mapping=mapping)
+            for _ in range(args.warmup):
+                flush.zero_()
+                ctx.detect_jobs([job], prm)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                ctx.detect_jobs([job], prm)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+            r[name] = {"ms_per_slot": ms, "problems_per_s": P / (ms / 1e3),
+                       "ber": synth.bit_errors(out["sym"].cpu().numpy(), w["sym"], mb) / nbits}
+            if name == "delta":
+                g = out["guess"].cpu().numpy().astype(int)
+                side = 1 << (mb // 2)
+                mm = ((g[:, :n_t] + side - 1) // 2) * side + (g[:, n_t:] + side - 1) // 2
+                r["mmse_ber"] = synth.bit_errors(mm, w["sym"], mb) / nbits
+        res[f"{n_t}x{n_t}_{1 << mb}qam"] = r
+    key = "16x16_16qam"
+    line = {"metric": "detections/s with the direct (binary) spin mapping, 16x16 16-QAM (64 spins)",
+            "value": res[key]["direct"]["problems_per_s"], "unit": "problems/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res[key]["direct"]["ms_per_slot"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "direct_vs_delta", "subcarriers": args.subcarriers, "symbols": 1,
+                       "runs": args.runs, "solver_steps": args.solver_steps, "f_mvm": args.f_mvm,
+                       "l2": "64 MiB flush between steps"},
+            "sizes": res}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_appendix(args):
     """Appendix A on the GPU: 320 random Q14 instances x 32 anneals (33 spins),
     initial amplitudes fixed by Philox across settings; for each (dt, f_mvm)
@@ -638,7 +696,7 @@ def main():
     ap.add_argument("--impl", default="mmgap", choices=["mmgap", "reference"])
     ap.add_argument("--workload", default="ul16x16_16qam_slot",
                     choices=sorted(WORKLOADS) + ["mixed", "serve", "precode", "precision", "mmgap_e", "appendix",
-                                                  "critical"])
+                                                  "critical", "direct"])
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load as a fraction of capacity")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: length of the arrival trace")
     ap.add_argument("--lanes", type=int, default=4, help="serve: concurrent launch groups (streams)")
@@ -684,6 +742,9 @@ def main():
         return
     if args.workload == "critical":
         run_critical(args)
+        return
+    if args.workload == "direct":
+        run_direct(args)
         return
 
     import torch

@@ -102,7 +102,24 @@ typedef struct {
  *   sum_k |Hs_ki| |Hs_kj|, u = 2^-8 for BF16, 2^-11 for FP16, 2^-15 for the
  *   split form; the matched filter, MMSE, field and quantisation stay FP32).
  *   Only mmgap_detect and mmgap_build_detect accept 1-3.
+ * mapping: how a problem becomes an Ising problem.
+ *   MMGAP_MAPPING_DELTA (0): the paper's delta form (Sec. 2.3, Sec. 3.2.1):
+ *     2 n_t spin pairs plus an auxiliary spin around the MMSE guess.
+ *   MMGAP_MAPPING_DIRECT (1): the binary-weighted form of earlier Ising
+ *     detectors (no counterpart formula in the paper): each real dimension
+ *     x = sum_b 2^b s_b over B = mod_bits / 2 spins, N = 2 n_t B spins plus an
+ *     auxiliary one; J = -(T^T G T) with zero diagonal, c = T^T Hs^T y
+ *     (G, Hs^T y: the FP32 Gram and matched filter of the delta build),
+ *     quantised like the delta form; annealed by the same CIM-CAC steps with
+ *     the full N x N field, scored by the exact energy -s^T Jq s - 2 cq^T s
+ *     with the MMSE guess as the reference candidate (it wins ties).
+ *     n_t in {4, 8, 16}, gram_precision 0, runs a multiple of 32 with
+ *     runs <= 256 / TPA (TPA = 1 for N <= 32, 2 for N <= 64, 4 for N = 96).
+ *     Outputs: sym_out; energy_out the selected candidate's energy;
+ *     guess_out the MMSE guess; offset_out (x - g) / 2 per real dimension;
+ *     ndiv_out.  Only mmgap_detect and mmgap_build_detect accept it.
  */
+enum { MMGAP_MAPPING_DELTA = 0, MMGAP_MAPPING_DIRECT = 1 };
 typedef struct {
     int32_t n_r, n_t, mod_bits;
     int32_t n_problems, n_chan;
@@ -117,6 +134,7 @@ typedef struct {
     int8_t* offset_out;
     int32_t* ndiv_out;
     int32_t gram_precision;
+    int32_t mapping;
 } mmgap_detect_job;
 
 /*
@@ -264,9 +282,32 @@ mmgap_status mmgap_vpp_inverse(mmgap_ctx* ctx, int n_u, int n_t, int n_chan, con
  * (required); optional G_out float [P][n][n] and h_out float [P][n] (real-form
  * Gram and field in lattice units before quantisation), sigma_exp_out int32
  * [P] (normaliser 2^sigma_exp).  job->sym_out etc. are ignored.
+ * With job->mapping == MMGAP_MAPPING_DIRECT the same pointers receive the
+ * direct form: A_q = J_q [P][N][N], h_q = c_q [P][N], g = the MMSE guess
+ * [P][2 n_t], G_out = J [P][N][N], h_out = c [P][N] (before quantisation).
  */
 mmgap_status mmgap_build_detect(mmgap_ctx* ctx, const mmgap_detect_job* job, int16_t* A_q_out, int16_t* h_q_out,
                                 int8_t* g_out, float* G_out, float* h_out, int32_t* sigma_exp_out, void* stream);
+
+/*
+ * General Ising boundary (the direct mapping's solver): P problems of N
+ * spins plus an auxiliary spin, J_q int16 [P][N][N] (symmetric, zero
+ * diagonal) and c_q int16 [P][N] (coupled through the auxiliary spin),
+ * annealed with params->runs CIM-CAC anneals (Eqs. 10-11, couplings
+ * J_q 2^-14, spin k of anneal r initialised from Philox word k mod 4 of
+ * counter (k/4, r, problem), k = N the auxiliary spin).  Each anneal's
+ * spins s_i = sign(x_i) sign(x_a) are scored by E(s) = -s^T J_q s - 2 c_q^T s
+ * (exact int32); a diverged anneal is not a candidate.  s_ref int8 [P][N]
+ * (may be NULL) is a reference candidate that wins ties; the result is the
+ * lowest (E, candidate) (run -1 = the reference, or all +1 when there is no
+ * reference and every anneal diverged).
+ * N in {8, 16, 24, 32, 48, 64, 96}; runs as for the direct mapping.
+ * Outputs (device): s_out int8 [P][N], E_out, run_out, ndiv_out int32 [P]
+ * (each may be NULL except s_out).  Uses no workspace.
+ */
+mmgap_status mmgap_solve_general(mmgap_ctx* ctx, const mmgap_params* params, int N, int n_problems,
+                                 const int16_t* J_q, const int16_t* c_q, const int8_t* s_ref, uint64_t seed,
+                                 int8_t* s_out, int32_t* E_out, int32_t* run_out, int32_t* ndiv_out, void* stream);
 
 /* Enable (1) or disable (0) per-stage CUDA-event timing of later detect /
  * precode calls on this context. */

@@ -46,7 +46,7 @@ class _DetectJob(C.Structure):
                 ("n_chan", C.c_int32), ("chan_index", C.c_void_p), ("H", C.c_void_p), ("y", C.c_void_p),
                 ("noise_var", C.c_void_p), ("seed", C.c_uint64), ("sym_out", C.c_void_p),
                 ("energy_out", C.c_void_p), ("guess_out", C.c_void_p), ("offset_out", C.c_void_p),
-                ("ndiv_out", C.c_void_p), ("gram_precision", C.c_int32)]
+                ("ndiv_out", C.c_void_p), ("gram_precision", C.c_int32), ("mapping", C.c_int32)]
 
 
 class _PrecodeJob(C.Structure):
@@ -74,6 +74,8 @@ _lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), 
 _lib.mmgap_set_solver_variant.argtypes = [_vp, C.c_int, C.c_int]
 _lib.mmgap_detect_e.argtypes = [_vp, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int, _vp, _vp, _vp, _vp]
 _lib.mmgap_vpp_inverse.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp]
+_lib.mmgap_solve_general.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, _vp, _vp, _vp, C.c_uint64, _vp, _vp,
+                                     _vp, _vp, _vp]
 _lib.mmgap_anneal_spins.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, _vp, _vp, C.c_uint64, _vp, _vp]
 _lib.mmgap_get_solver_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
 _lib.mmgap_autotune.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
@@ -110,7 +112,7 @@ _lib.mmgap_server_destroy.argtypes = [_vp]
 for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
            "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
            "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant", "mmgap_get_solver_variant",
-           "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse",
+           "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse", "mmgap_solve_general",
            "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run", "mmgap_batch_destroy", "mmgap_server_create",
            "mmgap_server_submit", "mmgap_server_submit_precode", "mmgap_server_wait", "mmgap_server_stats",
            "mmgap_server_destroy"):
@@ -119,7 +121,7 @@ for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detec
 ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_last_error", "mmgap_detect",
                "mmgap_precode", "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing",
                "mmgap_stage_times", "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant",
-               "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse",
+               "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse", "mmgap_solve_general",
                "mmgap_get_solver_variant", "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run",
                "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_submit_precode",
                "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy")
@@ -210,7 +212,8 @@ class Context:
 
     # ------------------------------------------------------------------ API
     def detect(self, H, y, noise_var, mod_bits: int, params: Params, seed: int, chan_index=None,
-               want_energy=False, want_guess=False, want_offset=False, want_ndiv=False, gram_precision: int = 0):
+               want_energy=False, want_guess=False, want_offset=False, want_ndiv=False, gram_precision: int = 0,
+               mapping: int = 0):
         """Uplink detection of P problems.  H: complex64 (n_chan, n_r, n_t),
         y: complex64 (P, n_r), noise_var: float32 (P,), chan_index: int32 (P,)
         or None.  Returns a dict of CUDA tensors (sym uint8 (P, n_t), ...)."""
@@ -230,7 +233,7 @@ class Context:
             out["offset"] = torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)
         if want_ndiv:
             out["ndiv"] = torch.empty(P, dtype=torch.int32, device=dev)
-        job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index, gram_precision)
+        job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index, gram_precision, mapping)
         self.detect_jobs([job], params)
         return out
 
@@ -256,11 +259,12 @@ class Context:
                                         _ptr(out["obj"]), _ptr(out.get("candidates")), self._stream()))
         return out
 
-    def detect_job(self, H, y, noise_var, mod_bits, seed, out, chan_index=None, gram_precision=0) -> _DetectJob:
+    def detect_job(self, H, y, noise_var, mod_bits, seed, out, chan_index=None, gram_precision=0,
+                   mapping=0) -> _DetectJob:
         n_chan, n_r, n_t = H.shape
         return _DetectJob(n_r, n_t, mod_bits, y.shape[0], n_chan, _ptr(chan_index), _ptr(H), _ptr(y),
                           _ptr(noise_var), seed, _ptr(out["sym"]), _ptr(out.get("energy")), _ptr(out.get("guess")),
-                          _ptr(out.get("offset")), _ptr(out.get("ndiv")), gram_precision)
+                          _ptr(out.get("offset")), _ptr(out.get("ndiv")), gram_precision, mapping)
 
     def detect_jobs(self, jobs, params: Params, stream=None):
         arr = (_DetectJob * len(jobs))(*jobs)
@@ -321,6 +325,24 @@ class Context:
                                            self._stream()))
         return Q, st
 
+    def solve_general(self, J_q, c_q, params: Params, seed: int, s_ref=None):
+        """Anneal P general Ising problems with an auxiliary spin: J_q int16 (P, N, N), c_q int16 (P, N),
+        s_ref int8 (P, N) or None.  Returns s int8 (P, N), E, run, ndiv int32 (P,)."""
+        P, N, _ = J_q.shape
+        dev = self.device
+        _check(J_q, "J_q", torch.int16, (P, N, N), dev)
+        _check(c_q, "c_q", torch.int16, (P, N), dev)
+        _check(s_ref, "s_ref", torch.int8, (P, N), dev)
+        out = dict(s=torch.empty((P, N), dtype=torch.int8, device=dev),
+                   E=torch.empty(P, dtype=torch.int32, device=dev),
+                   run=torch.empty(P, dtype=torch.int32, device=dev),
+                   ndiv=torch.empty(P, dtype=torch.int32, device=dev))
+        cp = params._c()
+        self._raise(_lib.mmgap_solve_general(self._h, C.byref(cp), N, P, _ptr(J_q), _ptr(c_q), _ptr(s_ref), seed,
+                                             _ptr(out["s"]), _ptr(out["E"]), _ptr(out["run"]), _ptr(out["ndiv"]),
+                                             self._stream()))
+        return out
+
     def solve_ising(self, A_q, h_q, params: Params, seed: int, g=None, level_max: int = 0):
         """Anneal P quantised delta-Ising problems: A_q int16 (P, n, n), h_q int16 (P, n),
         g int8 (P, n) or None.  Returns d int8 (P, n), E, run, ndiv int32 (P,)."""
@@ -351,11 +373,13 @@ class Context:
                                             self._stream()))
         return out
 
-    def build_detect(self, H, y, noise_var, mod_bits: int, chan_index=None, want_float=True, gram_precision=0):
-        """Builder only: quantised delta-Ising coefficients of P detection problems."""
+    def build_detect(self, H, y, noise_var, mod_bits: int, chan_index=None, want_float=True, gram_precision=0,
+                     mapping=0):
+        """Builder only: quantised Ising coefficients of P detection problems (delta form:
+        A_q (P, n, n), h_q (P, n); direct form, mapping=1: J_q (P, N, N), c_q (P, N) in the same keys)."""
         n_chan, n_r, n_t = H.shape
         P = y.shape[0]
-        n = 2 * n_t
+        n = 2 * n_t if mapping == 0 else 2 * n_t * (mod_bits // 2)
         dev = self.device
         _check(H, "H", torch.complex64, (n_chan, n_r, n_t), dev)
         _check(y, "y", torch.complex64, (P, n_r), dev)
@@ -363,13 +387,13 @@ class Context:
         _check(chan_index, "chan_index", torch.int32, (P,), dev)
         out = dict(A_q=torch.empty((P, n, n), dtype=torch.int16, device=dev),
                    h_q=torch.empty((P, n), dtype=torch.int16, device=dev),
-                   g=torch.empty((P, n), dtype=torch.int8, device=dev))
+                   g=torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev))
         if want_float:
             out["G"] = torch.empty((P, n, n), dtype=torch.float32, device=dev)
             out["h"] = torch.empty((P, n), dtype=torch.float32, device=dev)
             out["sigma_exp"] = torch.empty(P, dtype=torch.int32, device=dev)
         job = _DetectJob(n_r, n_t, mod_bits, P, n_chan, _ptr(chan_index), _ptr(H), _ptr(y), _ptr(noise_var), 0,
-                         None, None, None, None, None, gram_precision)
+                         None, None, None, None, None, gram_precision, mapping)
         self._raise(_lib.mmgap_build_detect(self._h, C.byref(job), _ptr(out["A_q"]), _ptr(out["h_q"]),
                                             _ptr(out["g"]), _ptr(out.get("G")), _ptr(out.get("h")),
                                             _ptr(out.get("sigma_exp")), self._stream()))

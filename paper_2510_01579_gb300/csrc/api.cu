@@ -192,6 +192,106 @@ mmgap_status check_detect_job(mmgap_ctx* ctx, const mmgap_detect_job& j, bool ne
         return fail(ctx, MMGAP_EINVAL, "chan_index NULL needs n_chan >= n_problems");
     if (j.gram_precision < 0 || j.gram_precision > 3)
         return fail(ctx, MMGAP_EINVAL, "gram_precision=%d: 0 FP32, 1 BF16, 2 FP16, 3 BF16x3", j.gram_precision);
+    if (j.mapping != MMGAP_MAPPING_DELTA && j.mapping != MMGAP_MAPPING_DIRECT)
+        return fail(ctx, MMGAP_EINVAL, "mapping=%d: 0 delta, 1 direct", j.mapping);
+    if (j.mapping == MMGAP_MAPPING_DIRECT) {
+        if (!(j.n_t == 4 || j.n_t == 8 || j.n_t == 16))
+            return fail(ctx, MMGAP_EUNSUPPORTED, "direct mapping: n_t=%d, supported 4, 8, 16", j.n_t);
+        if (j.gram_precision != 0) return fail(ctx, MMGAP_EUNSUPPORTED, "direct mapping builds the Gram in FP32");
+    }
+    return MMGAP_OK;
+}
+
+int direct_spins(const mmgap_detect_job& j) { return 2 * j.n_t * (j.mod_bits / 2); }
+
+// TPA of the general solver for N spins (as general_tpa<N>()).
+int general_threads_per_anneal(int N) { return N <= 32 ? 1 : (N <= 64 ? 2 : 4); }
+
+mmgap_status check_general_runs(mmgap_ctx* ctx, const mmgap_params* params, int N) {
+    if (params->runs % 32 || params->runs * general_threads_per_anneal(N) > 256)
+        return fail(ctx, MMGAP_EUNSUPPORTED, "general solver with N=%d: runs a multiple of 32, at most %d", N,
+                    256 / general_threads_per_anneal(N));
+    return MMGAP_OK;
+}
+
+cudaError_t dispatch_build_direct(int n_t, const DirectBuildArgs& a, cudaStream_t s) {
+    switch (n_t) {
+    case 16: return launch_build_direct<16>(a, s);
+    case 8: return launch_build_direct<8>(a, s);
+    case 4: return launch_build_direct<4>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// BuildArgs of problems [p0, p0 + P) of a detection job.
+BuildArgs job_build_args(mmgap_ctx* ctx, const mmgap_detect_job& J, long long p0, int P) {
+    BuildArgs b{};
+    b.H = J.chan_index ? J.H : J.H + (size_t)p0 * 2 * J.n_r * J.n_t;
+    b.chan_index = J.chan_index ? J.chan_index + p0 : nullptr;
+    b.y = J.y + (size_t)p0 * 2 * J.n_r;
+    b.noise_var = J.noise_var + p0;
+    b.n_r = J.n_r;
+    b.mod_bits = J.mod_bits;
+    b.n_problems = P;
+    b.n_chan = J.chan_index ? J.n_chan : P;
+    qam_kappa(J.mod_bits, &b.kappa, &b.kappa2);
+    b.err = ctx->dev_err;
+    return b;
+}
+
+// Direct-mapping detection of one job: per chunk, the direct build (J_q,
+// c_q, guess, reference spins) into the workspace, then the general solver
+// with the fused decode.
+mmgap_status detect_direct_job(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job& J,
+                               const EulerConsts& k, cudaStream_t s) {
+    const int N = direct_spins(J), n = 2 * J.n_t;
+    mmgap_status st = check_general_runs(ctx, params, N);
+    if (st != MMGAP_OK) return st;
+    const size_t per = align_up((size_t)N * N * 2) + align_up((size_t)N * 2) + align_up((size_t)n) +
+                       align_up((size_t)N);
+    long long chunk = (long long)(ctx->ws_bytes / (per + 4 * kAlign));
+    if (chunk < 1) return fail(ctx, MMGAP_ENOMEM, "workspace of %zu bytes holds no problem", ctx->ws_bytes);
+    if (chunk > J.n_problems) chunk = J.n_problems;
+    for (long long p0 = 0; p0 < J.n_problems; p0 += chunk) {
+        const int P = (int)std::min<long long>(chunk, J.n_problems - p0);
+        char* base = ctx->ws;
+        int16_t* Jq = (int16_t*)base;
+        int16_t* cq = (int16_t*)(base + align_up((size_t)P * N * N * 2));
+        int8_t* g = (int8_t*)((char*)cq + align_up((size_t)P * N * 2));
+        int8_t* sref = (int8_t*)((char*)g + align_up((size_t)P * n));
+        if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
+        DirectBuildArgs d{};
+        d.b = job_build_args(ctx, J, p0, P);
+        d.b.g = J.guess_out ? J.guess_out + (size_t)p0 * n : g;
+        d.B = J.mod_bits / 2;
+        d.Jq = Jq;
+        d.cq = cq;
+        d.s_ref = sref;
+        cudaError_t e = dispatch_build_direct(J.n_t, d, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "build_direct launch");
+        if ((st = timing_mark(ctx, 1, s)) != MMGAP_OK) return st;
+        GeneralArgs a{};
+        a.Jq = Jq;
+        a.cq = cq;
+        a.s_ref = sref;
+        a.n_problems = P;
+        a.steps = params->steps;
+        a.f_mvm = params->f_mvm;
+        a.key0 = (uint32_t)J.seed;
+        a.key1 = (uint32_t)(J.seed >> 32);
+        a.problem_offset = (uint64_t)p0;
+        a.k = k;
+        a.E_out = J.energy_out ? J.energy_out + p0 : nullptr;
+        a.ndiv_out = J.ndiv_out ? J.ndiv_out + p0 : nullptr;
+        a.mod_bits = J.mod_bits;
+        a.sym_out = J.sym_out + (size_t)p0 * J.n_t;
+        a.g = d.b.g;
+        a.offset_out = J.offset_out ? J.offset_out + (size_t)p0 * n : nullptr;
+        e = launch_solve_general(N, a, params->runs, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_general launch");
+        if ((st = timing_mark(ctx, 2, s)) != MMGAP_OK) return st;
+        if ((st = timing_mark(ctx, 3, s)) != MMGAP_OK) return st;
+    }
     return MMGAP_OK;
 }
 
@@ -365,6 +465,21 @@ mmgap_status mmgap_build_detect(mmgap_ctx* ctx, const mmgap_detect_job* job, int
     if (job->n_problems == 0) return MMGAP_OK;
     if (!A_q_out || !h_q_out || !g_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q_out, h_q_out or g_out");
     CurrentDevice cd(ctx->device);
+    if (job->mapping == MMGAP_MAPPING_DIRECT) {
+        DirectBuildArgs d{};
+        d.b = job_build_args(ctx, *job, 0, job->n_problems);
+        d.b.n_chan = job->n_chan;
+        d.b.g = g_out;
+        d.B = job->mod_bits / 2;
+        d.Jq = A_q_out;
+        d.cq = h_q_out;
+        d.J32 = G_out;
+        d.c32 = h_out;
+        d.sigma_exp = sigma_exp_out;
+        cudaError_t e = dispatch_build_direct(job->n_t, d, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "build_direct launch");
+        return MMGAP_OK;
+    }
     BuildArgs a{};
     a.H = job->H;
     a.chan_index = job->chan_index;
@@ -426,6 +541,37 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     return MMGAP_OK;
 }
 
+mmgap_status mmgap_solve_general(mmgap_ctx* ctx, const mmgap_params* params, int N, int n_problems,
+                                 const int16_t* J_q, const int16_t* c_q, const int8_t* s_ref, uint64_t seed,
+                                 int8_t* s_out, int32_t* E_out, int32_t* run_out, int32_t* ndiv_out, void* stream) {
+    if (!ctx) return MMGAP_EINVAL;
+    mmgap_status st = check_params(ctx, params);
+    if (st != MMGAP_OK) return st;
+    if (!general_supported(N)) return fail(ctx, MMGAP_EUNSUPPORTED, "N=%d: supported 8, 16, 24, 32, 48, 64, 96", N);
+    if ((st = check_general_runs(ctx, params, N)) != MMGAP_OK) return st;
+    if (n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
+    if (n_problems == 0) return MMGAP_OK;
+    if (!J_q || !c_q || !s_out) return fail(ctx, MMGAP_EINVAL, "NULL J_q, c_q or s_out");
+    CurrentDevice cd(ctx->device);
+    GeneralArgs a{};
+    a.Jq = J_q;
+    a.cq = c_q;
+    a.s_ref = s_ref;
+    a.n_problems = n_problems;
+    a.steps = params->steps;
+    a.f_mvm = params->f_mvm;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.k = euler_consts(*params);
+    a.s_out = s_out;
+    a.E_out = E_out;
+    a.run_out = run_out;
+    a.ndiv_out = ndiv_out;
+    cudaError_t e = launch_solve_general(N, a, params->runs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_general launch");
+    return MMGAP_OK;
+}
+
 mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job* jobs, int n_jobs,
                           void* stream) {
     if (!ctx) return MMGAP_EINVAL;
@@ -441,6 +587,10 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
     for (int j = 0; j < n_jobs; ++j) {
         const mmgap_detect_job& J = jobs[j];
         if (J.n_problems == 0) continue;
+        if (J.mapping == MMGAP_MAPPING_DIRECT) {
+            if ((st = detect_direct_job(ctx, params, J, k, s)) != MMGAP_OK) return st;
+            continue;
+        }
         const int n = 2 * J.n_t;
         const size_t per = align_up((size_t)n * n * 2) + align_up((size_t)n * 2) + align_up((size_t)n);
         if ((st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
@@ -631,6 +781,7 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
     if (st != MMGAP_OK) return st;
     if (!job) return fail(ctx, MMGAP_EINVAL, "job is NULL");
     if ((st = check_detect_job(ctx, *job, true)) != MMGAP_OK) return st;
+    if (job->mapping != MMGAP_MAPPING_DELTA) return fail(ctx, MMGAP_EUNSUPPORTED, "MMGaP-E uses the delta mapping");
     if (stages < 1 || stages > 8) return fail(ctx, MMGAP_EINVAL, "stages=%d out of [1, 8]", stages);
     const mmgap_detect_job& J = *job;
     if (J.n_problems == 0) return MMGAP_OK;

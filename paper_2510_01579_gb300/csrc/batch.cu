@@ -78,6 +78,7 @@ const char* BatchRunner::check_job(const mmgap_detect_job& J) {
     if (J.n_problems > 0 && (!J.H || !J.y || !J.noise_var || !J.sym_out || J.n_chan < 1)) return "NULL input/output";
     if (J.n_problems > 0 && !J.chan_index && J.n_chan < J.n_problems) return "chan_index NULL needs n_chan >= n";
     if (J.gram_precision != 0) return "batched launch builds the Gram in FP32 (gram_precision 0)";
+    if (J.mapping != MMGAP_MAPPING_DELTA) return "batched launch uses the delta mapping";
     return nullptr;
 }
 

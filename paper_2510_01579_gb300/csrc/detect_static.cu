@@ -98,6 +98,7 @@ mmgap_status mmgap_detect_static(const mmgap_params* params, const mmgap_detect_
     if (!J.H || !J.y || !J.noise_var || !J.sym_out || J.n_chan < 1) return MMGAP_EINVAL;
     if (!J.chan_index && J.n_chan < J.n_problems) return MMGAP_EINVAL;
     if (J.gram_precision != 0) return MMGAP_EUNSUPPORTED;  // the tensor-core Gram needs a workspace
+    if (J.mapping != MMGAP_MAPPING_DELTA) return MMGAP_EUNSUPPORTED;  // the direct mapping has its own scratch layout
 
     // scratch this job needs: A_q, h_q and g in three 256-B-aligned regions
     const int n = 2 * J.n_t;

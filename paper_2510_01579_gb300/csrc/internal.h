@@ -83,6 +83,44 @@ struct BuildArgs {
     int32_t* sigma_exp;        // [P] or nullptr
 };
 
+// Direct (binary-weighted) spin mapping: the delta build's MMSE guess, Gram
+// and matched filter (b.Aq / b.hq unused; b.g receives the guess), expanded by
+// powers of two into J = -(T^T G T) (zero diagonal) and c = T^T Hs^T y over
+// N = 2 n_t B spins, quantised like the delta form.
+struct DirectBuildArgs {
+    BuildArgs b;
+    int B;                     // spins per real dimension, mod_bits / 2
+    int16_t* Jq;               // [P][N][N]
+    int16_t* cq;               // [P][N]
+    int8_t* s_ref;             // [P][N] spins of the guess, or nullptr
+    float* J32;                // [P][N][N] or nullptr
+    float* c32;                // [P][N] or nullptr
+    int32_t* sigma_exp;        // [P] or nullptr
+};
+
+// General Ising problem with an auxiliary spin (J symmetric, zero diagonal;
+// c couples through the auxiliary spin), annealed by the same CIM-CAC steps.
+struct GeneralArgs {
+    const int16_t* Jq;         // [P][N][N]
+    const int16_t* cq;         // [P][N]
+    const int8_t* s_ref;       // [P][N] reference candidate (wins ties), or nullptr
+    int n_problems;
+    int steps;
+    int f_mvm;
+    uint32_t key0, key1;
+    uint64_t problem_offset;
+    EulerConsts k;
+    int8_t* s_out;             // [P][N] or nullptr
+    int32_t* E_out;            // [P] or nullptr
+    int32_t* run_out;          // [P] or nullptr (-1: the reference)
+    int32_t* ndiv_out;         // [P] or nullptr
+    // detection decode of x = T s (B = mod_bits / 2 spins per dimension)
+    int mod_bits;              // 0: no decode
+    uint8_t* sym_out;          // [P][n_t] or nullptr
+    const int8_t* g;           // [P][2 n_t] guess, for offset_out
+    int8_t* offset_out;        // [P][2 n_t] (x - g) / 2, or nullptr
+};
+
 // Gram of kappa H per channel on tensor cores (BF16 or FP16 operands, FP32
 // accumulation); Hermitian by construction (upper triangle mirrored).
 struct GramArgs {
@@ -152,6 +190,10 @@ template <int NT> cudaError_t launch_build_detect(const BuildArgs& a, cudaStream
 template <int NT> cudaError_t launch_solve(const SolveArgs& a, int runs, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_inverse(const VppInvArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_inverse_ir(const VppInvArgs& a, cudaStream_t s);
+template <int NT> cudaError_t launch_build_direct(const DirectBuildArgs& a, cudaStream_t s);
+// N in {8, 16, 24, 32, 48, 64, 96} (defined in general.cu); runs a multiple of 32.
+bool general_supported(int N);
+cudaError_t launch_solve_general(int N, const GeneralArgs& a, int runs, cudaStream_t s);
 template <int NT> cudaError_t launch_gram_tc(const GramArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_build(const VppBuildArgs& a, cudaStream_t s);
