@@ -326,15 +326,17 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
 
 /*
  * Launch shape of the CIM-CAC solver for n_t users (no counterpart in the
- * paper, which runs one thread per anneal).  Shapes 0-4 give bit-identical
- * results; they differ only in speed:
+ * paper, which runs one thread per anneal).  Shapes 0-4 and 6 give
+ * bit-identical results; they differ only in speed:
  *   0 default for the size (packed one-thread-per-anneal where compiled)
  *   1 plain: one thread per anneal, scalar FP32 (the paper's design point)
  *   2 tuned kernel, one thread per anneal, scalar FP32
  *   3 tuned kernel, one thread per anneal, packed FP32 pairs
  *   4 tuned kernel, two threads per anneal (shuffle-gathered field), packed
- * Shapes 2-4 exist for n_t in {4, 8, 16} with f_mvm in {1, 2}; elsewhere 1
- * runs.  Shape 5 is a precision variant, not bit-identical: shape 3 with
+ *   6 tuned kernel, one thread per anneal, packed, the field refresh shared
+ *     by lane pairs (each coupling read once for two anneals)
+ * Shapes 2-4 and 6 exist for n_t in {4, 8, 16} with f_mvm in {1, 2};
+ * elsewhere 1 runs.  Shape 5 is a precision variant, not bit-identical: shape 3 with
  * the coupling field of a warp's 32 anneals computed on the tensor cores
  * (mma.sync m16n8k16, couplings and u split into FP16 pairs, FP32
  * accumulation; about 2^-21 of sum |A||u| from the FP32 field), for n_t in
@@ -348,15 +350,15 @@ mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant);
 mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* variant_out);
 
 /*
- * Autotuner: time every compiled bit-identical solver shape (1-4) for n_t
- * users on n_problems random Q14 problems (0 = 8192; clamped to the
+ * Autotuner: time every compiled bit-identical solver shape (1-4, 6) for
+ * n_t users on n_problems random Q14 problems (0 = 8192; clamped to the
  * workspace) with *params, keep the fastest for this context and return it
  * in *variant_out.
- * ms_out (may be NULL) receives [0] the best time and [v] the time of shape v
- * (-1 if not compiled).  Synchronises the device; uses the workspace.
+ * ms_out (may be NULL, else 7 floats) receives [0] the best time and [v] the
+ * time of shape v (-1 if not compiled or not bit-identical).  Synchronises the device; uses the workspace.
  */
 mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
-                            float ms_out[5]);
+                            float ms_out[7]);
 
 /*
  * Batched persistent launch of mixed-size uplink jobs (no counterpart in the

@@ -937,7 +937,7 @@ mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* v
 }
 
 mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
-                            float ms_out[5]) {
+                            float ms_out[7]) {
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
@@ -971,8 +971,9 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     cudaEventCreate(&t1);
     float best = 1e30f;
     int best_v = kVariantPlain;
-    for (int v = kVariantPlain; v < kVariantExactCount; ++v) {  // bit-identical shapes only
+    for (int v = kVariantPlain; v < kVariantCount; ++v) {
         if (ms_out) ms_out[v] = -1.0f;
+        if (!variant_exact(v)) continue;                             // bit-identical shapes only
         if (resolve_variant(n_t, params->f_mvm, v) != v) continue;  // not compiled for this size
         a.variant = v;
         e = dispatch_nt<OpSolve>(n_t, a, params->runs, s);  // warm up

@@ -51,14 +51,16 @@ enum SolverVariant : int {
     kVariantTpa1 = 2,        // tuned kernel, one thread per anneal
     kVariantTpa1Packed = 3,  // tuned kernel, one thread per anneal, packed FP32 pairs
     kVariantTpa2Packed = 4,  // tuned kernel, two threads per anneal, packed FP32 pairs
-    kVariantExactCount = 5,  // variants below this one give bit-identical results
     kVariantTensorCore = 5,  // field refresh on tensor cores (FP16 split, FP32 accumulation): not bit-identical
-    kVariantCount = 6
+    kVariantPairPacked = 6,  // tuned kernel, one thread per anneal, refresh shared by lane pairs
+    kVariantCount = 7
 };
 
 // Variant used for n_t users and refresh period f_mvm when `requested` is
 // kVariantAuto or not compiled for that size.
 int resolve_variant(int n_t, int f_mvm, int requested);
+// Shapes whose results are bit-identical to the plain kernel's (the autotuner's candidates).
+constexpr bool variant_exact(int v) { return v != kVariantTensorCore; }
 
 struct BuildArgs {
     const float* H;            // complex [n_chan][n_r][n_t]

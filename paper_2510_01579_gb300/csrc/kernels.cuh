@@ -714,7 +714,12 @@ __device__ __forceinline__ void euler_pair(float2& x, float2& e, float2 mu, floa
 }
 
 // Field refresh + L frozen Euler steps of one thread's rows (L == 0: runtime Lrt).
-template <int n, int NS, int TPA, bool PACKED, int L>
+// PAIR (one thread per anneal, packed): lanes 2k and 2k+1 share the refresh
+// of their two anneals -- each forms half the rows of m for both anneals
+// (the partner's u_j arrives by shuffle), so each coupling loaded from shared
+// memory feeds two fused multiply-adds; the halves are then swapped.  Every
+// m_i is still the ascending-j FMA chain from 0, so results are unchanged.
+template <int n, int NS, int TPA, bool PACKED, int L, bool PAIR = false>
 __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, const float* snd, float (&x1)[NS],
                                             float (&x2)[NS], float (&e1)[NS], float (&e2)[NS], float& xa, float& ea,
                                             int q, int lane, int Lrt, const EulerConsts& k) {
@@ -755,6 +760,46 @@ __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, co
 #pragma unroll
     for (int i = 0; i < NS; ++i) m[i] = 0.0f;
     float mua = 0.0f;
+    if constexpr (PAIR) {
+        static_assert(TPA == 1 && PACKED && n % 8 == 0, "paired refresh: one thread per anneal, packed");
+        constexpr int H = n / 2;
+        const int half = lane & 1;
+        float mo[H], mp[H];  // this half's rows of m for this anneal and for the partner's
+#pragma unroll
+        for (int i = 0; i < H; ++i) mo[i] = mp[i] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+            const float uj = uo[j];
+            const float up = __shfl_xor_sync(0xffffffffu, uj, 1);
+            mua = fmarn(sh[j], uj, mua);
+            const float4* row = reinterpret_cast<const float4*>(sA + j * n + half * H);
+            const float2 uu = make_float2(uj, uj), pp = make_float2(up, up);
+#pragma unroll
+            for (int i4 = 0; i4 < H / 4; ++i4) {
+                const float4 a4 = row[i4];
+                const float2 al = make_float2(a4.x, a4.y), ah = make_float2(a4.z, a4.w);
+                float2 v = __ffma2_rn(al, uu, make_float2(mo[4 * i4], mo[4 * i4 + 1]));
+                mo[4 * i4] = v.x;
+                mo[4 * i4 + 1] = v.y;
+                v = __ffma2_rn(ah, uu, make_float2(mo[4 * i4 + 2], mo[4 * i4 + 3]));
+                mo[4 * i4 + 2] = v.x;
+                mo[4 * i4 + 3] = v.y;
+                v = __ffma2_rn(al, pp, make_float2(mp[4 * i4], mp[4 * i4 + 1]));
+                mp[4 * i4] = v.x;
+                mp[4 * i4 + 1] = v.y;
+                v = __ffma2_rn(ah, pp, make_float2(mp[4 * i4 + 2], mp[4 * i4 + 3]));
+                mp[4 * i4 + 2] = v.x;
+                mp[4 * i4 + 3] = v.y;
+            }
+        }
+        // swap: the partner formed this anneal's other half
+#pragma unroll
+        for (int i = 0; i < H; ++i) {  // (selects, not a runtime index: m stays in registers)
+            const float other = __shfl_xor_sync(0xffffffffu, mp[i], 1);
+            m[i] = half ? other : mo[i];
+            m[H + i] = half ? mo[i] : other;
+        }
+    } else {
 #pragma unroll
     for (int j = 0; j < n; ++j) {
         float uj;
@@ -780,6 +825,7 @@ __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, co
                 m[4 * i4 + 3] = fmarn(a4.w, uj, m[4 * i4 + 3]);
             }
         }
+    }
     }
     // frozen field: c = m + b x_a, mu1 = c - diag(A) x1, mu2 = c - diag(A) x2
     if constexpr (PACKED) {
@@ -1050,7 +1096,7 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
     }
 }
 
-template <int NT, int F, int TPA, bool PACKED, bool TC = false>
+template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false>
 __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a) {
     constexpr int n = 2 * NT;
     constexpr int NS = n / TPA;
@@ -1121,8 +1167,9 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
     } else {
 #pragma unroll 1
         for (; t + F <= S; t += F)
-            tuned_block<n, NS, TPA, PACKED, F>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
-        if (t < S) tuned_block<n, NS, TPA, PACKED, 0>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
+            tuned_block<n, NS, TPA, PACKED, F, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
+        if (t < S)
+            tuned_block<n, NS, TPA, PACKED, 0, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
     }
 
     // validity over the whole anneal
@@ -2499,6 +2546,9 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
         case kVariantTpa1: cac_solve_tuned_kernel<NT, F, 1, false><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa1Packed: cac_solve_tuned_kernel<NT, F, 1, true><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa2Packed: cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a); break;
+        case kVariantPairPacked:
+            cac_solve_tuned_kernel<NT, F, 1, true, false, true><<<a.n_problems, runs, 0, s>>>(a);
+            break;
         case kVariantTensorCore:
             if constexpr (NT % 8 == 0) {
                 cac_solve_tuned_kernel<NT, F, 1, true, true>

@@ -340,7 +340,7 @@ def test_bad_channel_index_is_flagged(mm):
 
 # ---------------------------------------------------------- solver shapes
 @pytest.mark.parametrize("nt", [4, 8, 16])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 6])
 @pytest.mark.parametrize("f_mvm,steps,runs", [(2, 200, 32), (1, 41, 64), (2, 77, 96)])
 def test_solver_shapes_bit_exact(mm, nt, variant, f_mvm, steps, runs):
     """Every launch shape gives the oracle's bits (ragged step counts too)."""
@@ -369,7 +369,7 @@ def test_autotuner_picks_a_compiled_shape(mm):
     pkg, _ = mm
     with pkg.Context(0) as ctx:
         v, ms = ctx.autotune(pkg.Params.default(steps=40), 16, 2048)
-        assert v in ms and all(t > 0 for t in ms.values()) and set(ms) == {1, 2, 3, 4}
+        assert v in ms and all(t > 0 for t in ms.values()) and set(ms) == {1, 2, 3, 4, 6}
         assert ms[v] == min(ms.values())
         v4, ms4 = ctx.autotune(pkg.Params.default(steps=40), 3, 512)
         assert v4 == 1 and set(ms4) == {1}
