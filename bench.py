@@ -30,6 +30,8 @@ import synth  # noqa: E402
 
 METRIC = "detections/s (subcarrier-problems, 16x16 16-QAM) at equal BER; p99 slot latency"
 UNIT = "problems/s"
+# solver launch shapes whose DRAM bytes per 16-user problem were taken with ncu (profiles/)
+TRAFFIC_MEASURED = (3, 6)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -959,7 +961,7 @@ def main():
     flops = solver_flops(P, n_t, args.runs, args.solver_steps, args.f_mvm)
     # DRAM bytes of the solver from ncu (profiles/cac_solve_16x16_slot_1024sc.md): 2,153 B per
     # 16x16 problem, measured on 14,336 problems and scaled by problems; None for other shapes
-    traffic = 2153.0 * P if (n_t == 16 and variant == 3) else None
+    traffic = 2153.0 * P if (n_t == 16 and variant in TRAFFIC_MEASURED) else None
     solve_avg = statistics.mean(solve_ms)
     achieved = flops / (solve_avg / 1e3) / 1e12
     peak = alu_peak_tflops()

@@ -1388,8 +1388,11 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
     const int S = A.steps;
     int t = 0;
 #pragma unroll 1
-    for (; t + F <= S; t += F) tuned_block<n, n, 1, true, F>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, F, k);
-    if (t < S) tuned_block<n, n, 1, true, 0>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, S - t, k);
+    // 16 users: the paired refresh (faster there, same bits); fewer users: one anneal per lane
+    constexpr bool kPair = NT == 16;
+    for (; t + F <= S; t += F)
+        tuned_block<n, n, 1, true, F, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, F, k);
+    if (t < S) tuned_block<n, n, 1, true, 0, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, S - t, k);
 
     bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
 #pragma unroll
