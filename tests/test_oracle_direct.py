@@ -157,3 +157,26 @@ def test_direct_detection_matches_ml_at_high_snr():
         side = 2
         ml_sym = ((xml[:8] + 1) // 2) * side + (xml[8:] + 1) // 2
         assert np.array_equal(r["sym"], ml_sym.astype(np.uint8)), p
+
+
+@pytest.mark.parametrize("n_t,mb", [(2, 2), (2, 4), (1, 6), (3, 4)])
+def test_integer_energy_tracks_the_ml_objective(n_t, mb):
+    """E(s) = -s^T Jq s - 2 cq^T s equals (||y - kappa H T s||^2 - const) 2^(14 - e)
+    up to the code roundings: |error| <= (N^2 - N) / 2 + N (each code off by <= 1/2)."""
+    w = synth.uplink(60 + n_t + mb, 3, n_t, mb, n_sub=2, n_sym=1, snr_db=10.0)
+    for p in range(2):
+        H, y = w["H"][w["chan_index"][p]], w["y"][p]
+        f32 = oracle.build_direct32(H, y, w["noise_var"][p], mb)
+        f64 = oracle.build_direct64(H.astype(np.complex128), y.astype(np.complex128), mb)
+        N = len(f32["cq"])
+        kap = oracle.qam_kappa(mb)
+        scale = 2.0 ** (14 - f32["sigma_exp"])
+        rng = np.random.default_rng(p)
+        for _ in range(64):
+            s = np.where(rng.random(N) < 0.5, 1, -1).astype(np.int8)
+            x = oracle.direct_lattice(n_t, mb, s)
+            obj = np.linalg.norm(y.astype(np.complex128) - kap * H.astype(np.complex128) @ (x[:n_t] + 1j * x[n_t:])) ** 2
+            e = oracle.energy_direct(f32["Jq"], f32["cq"], s)
+            # FP32 J, c differ from FP64 by <= 1e-5 normwise; allow that on top of the roundings
+            slack = (N * N - N) / 2 + N + 1e-4 * scale * (np.abs(f64["J"]).sum() + 2 * np.abs(f64["c"]).sum())
+            assert abs(e - (obj - f64["const"]) * scale) <= slack
