@@ -382,6 +382,9 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
  */
 typedef struct mmgap_batch mmgap_batch;
 #define MMGAP_BATCH_PERSISTENT 1 /* flags: persistent solver warps on an atomic counter (else one CTA per problem) */
+#define MMGAP_BATCH_TENSOR_CORE 2 /* flags: tensor-core field refresh for 8 and 16 users (solver shape 5: a
+                                     precision variant, results as mmgap_detect with that shape; implies
+                                     one CTA per problem) */
 mmgap_status mmgap_batch_create(mmgap_batch** batch, int device, const mmgap_params* params,
                                 const mmgap_detect_job* jobs, int n_jobs, int flags);
 mmgap_status mmgap_batch_run(mmgap_batch* batch, int use_graph, void* stream);
@@ -423,6 +426,7 @@ typedef struct {
     double inject_delay_us;
     int32_t use_graph;
     int32_t persistent;             /* solver mode of each group, as MMGAP_BATCH_PERSISTENT */
+    int32_t tensor_core;            /* as MMGAP_BATCH_TENSOR_CORE (precision variant) */
 } mmgap_server_config;
 typedef struct {
     uint64_t ticket;

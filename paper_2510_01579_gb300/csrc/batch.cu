@@ -35,17 +35,20 @@ int build_floats_for(int nt, int n_r) {
 }
 
 template <int NTMAX>
-const void* solve_ptr(int f, bool persistent) {
+const void* solve_ptr(int f, bool persistent, bool tc) {
+    if (tc)  // the tensor-core refresh runs in grid mode (its exchange buffer is per CTA)
+        return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1, true>
+                      : (const void*)batch_solve_grid_kernel<NTMAX, 2, true>;
     if (persistent)
         return f == 1 ? (const void*)batch_solve_kernel<NTMAX, 1> : (const void*)batch_solve_kernel<NTMAX, 2>;
     return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1> : (const void*)batch_solve_grid_kernel<NTMAX, 2>;
 }
 
-const void* pick_solve(int ntmax, int f, bool persistent) {
+const void* pick_solve(int ntmax, int f, bool persistent, bool tc) {
     switch (ntmax) {
-    case 16: return solve_ptr<16>(f, persistent);
-    case 8: return solve_ptr<8>(f, persistent);
-    default: return solve_ptr<4>(f, persistent);
+    case 16: return solve_ptr<16>(f, persistent, tc);
+    case 8: return solve_ptr<8>(f, persistent, tc);
+    default: return solve_ptr<4>(f, persistent, tc);
     }
 }
 
@@ -107,9 +110,10 @@ size_t BatchRunner::scratch_bytes(int n_t, int n_problems) {
 }
 
 cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r,
-                              int ntmax, int* err_word, bool persistent) {
+                              int ntmax, int* err_word, bool persistent, bool tensor_core) {
     device_ = device;
-    persistent_ = persistent;
+    tc_ = tensor_core && ntmax >= 8;
+    persistent_ = persistent && !tc_;
     capacity_ = capacity_jobs;
     capacity_problems_ = capacity_problems;
     ntmax_ = ntmax;
@@ -131,7 +135,7 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
         cudaSuccess)
         return e;
     int per_sm = 0, sms = 0, bper_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_solve(ntmax, 2, true), kBatchWarps * 32, 0)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_solve(ntmax, 2, true, false), kBatchWarps * 32, 0)) !=
         cudaSuccess)
         return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bper_sm, pick_build(ntmax), kBuildWarps * 32,
@@ -343,7 +347,7 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3(bg), dim3(kBuildWarps * 32), args, build_smem_, s)) !=
         cudaSuccess)
         return e;
-    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, persistent_), dim3(sg),
+    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, persistent_, tc_), dim3(sg),
                             dim3(persistent_ ? kBatchWarps * 32 : 32), args, 0, s);
 }
 
@@ -403,7 +407,7 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         kb.kernelParams = args;
         if ((e = cudaGraphExecKernelNodeSetParams(exec_, build_node_, &kb)) != cudaSuccess) return e;
         cudaKernelNodeParams ks{};
-        ks.func = (void*)pick_solve(ntmax_, P.f_mvm, persistent_);
+        ks.func = (void*)pick_solve(ntmax_, P.f_mvm, persistent_, tc_);
         ks.gridDim = dim3(sg);
         ks.blockDim = dim3(persistent_ ? kBatchWarps * 32 : 32);
         ks.sharedMemBytes = 0;
@@ -459,7 +463,8 @@ mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_param
     if (cudaMalloc(&b->err_word, sizeof(int)) != cudaSuccess || cudaMemset(b->err_word, 0, sizeof(int)) != cudaSuccess)
         st = MMGAP_ENOMEM;
     if (st == MMGAP_OK && b->runner.init(device, n_jobs, total, scratch, max_n_r, ntmax, b->err_word,
-                                         (flags & MMGAP_BATCH_PERSISTENT) != 0) != cudaSuccess)
+                                         (flags & MMGAP_BATCH_PERSISTENT) != 0,
+                                         (flags & MMGAP_BATCH_TENSOR_CORE) != 0) != cudaSuccess)
         st = MMGAP_ENOMEM;
     if (st == MMGAP_OK) {
         // largest problems first, so the tail of the launch is made of small ones

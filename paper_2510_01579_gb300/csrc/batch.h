@@ -34,9 +34,11 @@ class BatchRunner {
     // problems with n_r <= max_n_r and n_t <= ntmax, `scratch` bytes of
     // coupling scratch; err_word receives out-of-range channel indices.
     // persistent: the solver runs warps that pull problems from an atomic
-    // counter; otherwise one 32-thread CTA per problem.
+    // counter; otherwise one 32-thread CTA per problem.  tensor_core: the
+    // field refresh of 8- and 16-user problems on tensor cores (solver shape
+    // 5, a precision variant; grid mode).
     cudaError_t init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r, int ntmax,
-                     int* err_word, bool persistent);
+                     int* err_word, bool persistent, bool tensor_core = false);
     void release();
     // Fill the pinned host table with jobs[order[i]] (order may be NULL);
     // returns 0, or < 0 if the jobs exceed the table, scratch or problem capacity.
@@ -65,6 +67,7 @@ class BatchRunner {
     void grids(unsigned* build_grid, unsigned* solve_grid) const;
     int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0, grid_ = 0, build_grid_max_ = 1;
     bool persistent_ = false;
+    bool tc_ = false;  // tensor-core field refresh for 8 and 16 users (grid mode)
     long long capacity_problems_ = 0;
     size_t build_smem_ = 0, scratch_bytes_ = 0;
     char* scratch_ = nullptr;

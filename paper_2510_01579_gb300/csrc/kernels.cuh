@@ -1354,10 +1354,13 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 8) batch_build_kernel(BatchA
     }
 }
 
-// Anneal one problem already built into sm (Aq, hq, g) with one warp.
-template <int NT, int F>
+// Anneal one problem already built into sm (Aq, hq, g) with one warp.  TC:
+// the tensor-core field refresh (solver shape 5; tc_af / tc_ws hold the A
+// fragments and the warp's exchange buffer), for 8 and 16 users.
+template <int NT, int F, bool TC = false>
 __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const BatchJob& J, int p, int lane,
-                                                 SolveSmem<NT>& sm) {
+                                                 SolveSmem<NT>& sm, uint32_t* tc_af = nullptr,
+                                                 uint32_t* tc_ws = nullptr) {
     constexpr int n = 2 * NT;
     const EulerConsts k = A.k;
     for (int e = lane; e < n * n; e += 32) sm.A[e] = mulrn(mulrn((float)sm.Aq[e], 0x1p-14f), k.ce);
@@ -1387,12 +1390,22 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
     }
     const int S = A.steps;
     int t = 0;
+    if constexpr (TC && NT % 8 == 0) {
+        tc_stage_fragments<NT>(sm.Aq, tc_af, lane, 32);
+        __syncwarp();
+        const float mscale = mulrn(k.ce, 0x1p-5f);
 #pragma unroll 1
-    // 16 users: the paired refresh (faster there, same bits); fewer users: one anneal per lane
-    constexpr bool kPair = NT == 16;
-    for (; t + F <= S; t += F)
-        tuned_block<n, n, 1, true, F, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, F, k);
-    if (t < S) tuned_block<n, n, 1, true, 0, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, S - t, k);
+        for (; t + F <= S; t += F) tc_block<NT, F>(tc_af, sm.h, sm.nd, tc_ws, x1, x2, e1, e2, xa, ea, lane, F, mscale, k);
+        if (t < S) tc_block<NT, 0>(tc_af, sm.h, sm.nd, tc_ws, x1, x2, e1, e2, xa, ea, lane, S - t, mscale, k);
+    } else {
+        // 16 users: the paired refresh (faster there, same bits); fewer users: one anneal per lane
+        constexpr bool kPair = NT == 16;
+#pragma unroll 1
+        for (; t + F <= S; t += F)
+            tuned_block<n, n, 1, true, F, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, F, k);
+        if (t < S)
+            tuned_block<n, n, 1, true, 0, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, S - t, k);
+    }
 
     bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
 #pragma unroll
@@ -1454,9 +1467,10 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
     __syncwarp();  // the warp's shared memory is reused by its next problem
 }
 
-template <int NT, int F>
+template <int NT, int F, bool TC = false>
 __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const BatchJob& J, int p, int lane,
-                                                    unsigned char* solve_mem) {
+                                                    unsigned char* solve_mem, uint32_t* tc_af = nullptr,
+                                                    uint32_t* tc_ws = nullptr) {
     constexpr int n = 2 * NT;
     SolveSmem<NT>& sm = *reinterpret_cast<SolveSmem<NT>*>(solve_mem);
     const int16_t* Aq = J.Aq + (size_t)p * n * n;
@@ -1466,23 +1480,26 @@ __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const Ba
         sm.g[i] = J.g ? J.g[(size_t)p * n + i] : (int8_t)0;
     }
     __syncwarp();
-    batch_solve_warp<NT, F>(A, J, p, lane, sm);
+    batch_solve_warp<NT, F, TC>(A, J, p, lane, sm, tc_af, tc_ws);
 }
 
 // Grid solver over the batch: one 32-thread CTA per problem (the hardware
 // CTA scheduler balances sizes); CTAs past the staged total exit.
-template <int NTMAX, int F>
+template <int NTMAX, int F, bool TC = false>
 __global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
     __shared__ __align__(16) unsigned char ssm[batch_solve_bytes<NTMAX>()];
+    constexpr bool kTc = TC && NTMAX >= 8;
+    __shared__ __align__(16) uint32_t tc_af[kTc ? TcShape<NTMAX>::AF_WORDS : 1];
+    __shared__ __align__(16) uint32_t tc_ws[kTc ? TcShape<NTMAX>::WARP_WORDS : 1];
     const long long w = blockIdx.x;
     if (w >= A.head->total) return;
     const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
     const int p = (int)(w - J.first);
     const int lane = threadIdx.x;
     if (J.nt == 16) {
-        if constexpr (NTMAX >= 16) batch_solve_problem<16, F>(A, J, p, lane, ssm);
+        if constexpr (NTMAX >= 16) batch_solve_problem<16, F, kTc>(A, J, p, lane, ssm, tc_af, tc_ws);
     } else if (J.nt == 8) {
-        if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, ssm);
+        if constexpr (NTMAX >= 8) batch_solve_problem<8, F, kTc>(A, J, p, lane, ssm, tc_af, tc_ws);
     } else {
         batch_solve_problem<4, F>(A, J, p, lane, ssm);
     }

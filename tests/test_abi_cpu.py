@@ -54,4 +54,5 @@ def test_struct_layouts_match_header(lib_path):
     assert ctypes.sizeof(binding._DetectJob) == 5 * 4 + 4 + 4 * 8 + 8 + 5 * 8 + 8
     assert binding._DetectJob.mapping.offset == binding._DetectJob.gram_precision.offset + 4
     assert ctypes.sizeof(binding._PrecodeJob) == 6 * 4 + 3 * 8 + 8 + 5 * 8
+    assert ctypes.sizeof(binding._ServerConfig) == 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4
     assert binding._PrecodeJob.inv_precision.offset == 20 and binding._PrecodeJob.chan_index.offset == 24

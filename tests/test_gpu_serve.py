@@ -167,3 +167,39 @@ def test_server_rejects_sizes_above_its_limits():
             with pytest.raises(pkg.MMGaPError) as e:
                 srv.submit_precode(pre[0][4])
             assert e.value.status == 5
+
+
+def test_tensor_core_server_equals_per_job_tensor_core_shape():
+    """A server (and a batch) with the tensor-core refresh returns, for 8- and
+    16-user jobs, exactly what mmgap_detect returns with solver shape 5, and
+    for 4-user jobs what the exact shapes return."""
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=80)
+    with pkg.Context(0) as ctx:
+        jobs = _jobs(ctx, SPECS[:6])
+        refs = []
+        for w, t, o, job in jobs:
+            n_t = w["n_t"]
+            if n_t in (8, 16):
+                ctx.set_solver_variant(n_t, 5)
+            r = {k: torch.empty_like(v) for k, v in o.items()}
+            ctx.detect_jobs([ctx.detect_job(t[0], t[1], t[2], w["mod_bits"], job.seed, r, t[3])], prm)
+            ctx.set_solver_variant(n_t, 0)
+            refs.append(r)
+        torch.cuda.synchronize()
+        with pkg.Server(0, prm, scratch_bytes=16 << 20, n_lanes=2, max_jobs_per_group=3, tensor_core=True) as srv:
+            for tk in [srv.submit(job) for _, _, _, job in jobs]:
+                srv.wait(tk, timeout_us=60_000_000)
+        for (w, t, o, job), r in zip(jobs, refs):
+            for k in o:
+                assert torch.equal(o[k], r[k]), (w["n_t"], k)
+        # the batch object with the same flag
+        for (w, t, o, job), r in zip(jobs, refs):
+            for v in o.values():
+                v.fill_(0)
+        with pkg.Batch(0, prm, [j for _, _, _, j in jobs], keepalive=jobs, tensor_core=True) as b:
+            b.run(use_graph=True)
+            torch.cuda.synchronize()
+        for (w, t, o, job), r in zip(jobs, refs):
+            for k in o:
+                assert torch.equal(o[k], r[k]), (w["n_t"], k)
