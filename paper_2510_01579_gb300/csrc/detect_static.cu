@@ -30,7 +30,6 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)8 << 20;  // 8 MiB per device
 constexpr size_t kAlign = 256;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 static __device__ __align__(256) int g_scratch_err[1];

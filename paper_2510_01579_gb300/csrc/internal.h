@@ -213,6 +213,7 @@ cudaError_t vpp_inverse_any(int n_u, int n_t, int n_chan, const float* H, int in
 cudaError_t launch_random_ising(int16_t* Aq, int16_t* hq, int n, int n_problems, uint64_t seed, cudaStream_t s);
 
 constexpr int kMaxNr = 64;
+constexpr int kMaxDevices = 64;  // devices whose per-kernel launch attributes are cached
 
 // Bits of the device error word.
 constexpr int kErrChanIndex = 1;

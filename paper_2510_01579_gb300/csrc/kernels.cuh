@@ -16,6 +16,7 @@
 // translation units are compiled with -fmad=false as a second guard.
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -24,6 +25,26 @@
 #include "internal.h"
 
 namespace mmgap {
+
+// Raise a kernel's dynamic shared-memory limit once per device: the largest
+// size granted so far is remembered, so a launch that needs no more skips the
+// driver call (it sits on the host between dependent launches otherwise).
+template <auto Kernel>
+cudaError_t ensure_dynamic_smem(size_t bytes) {
+    static std::atomic<int> granted[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if ((int)bytes <= granted[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    int cur = granted[dev].load(std::memory_order_relaxed);
+    while ((int)bytes > cur && !granted[dev].compare_exchange_weak(cur, (int)bytes)) {
+    }
+    return cudaSuccess;
+}
 
 constexpr int kQBits = 14;
 
@@ -1617,7 +1638,7 @@ cudaError_t launch_build_direct_impl(const DirectBuildArgs& a, cudaStream_t s) {
     if (a.b.n_problems <= 0) return cudaSuccess;
     const size_t smem = (size_t)kBuildWarps * build_smem_floats<NT>(a.b.n_r) * sizeof(float);
     cudaError_t err =
-        cudaFuncSetAttribute(build_direct_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_dynamic_smem<build_direct_kernel<NT>>(smem);
     if (err != cudaSuccess) return err;
     const int blocks = (a.b.n_problems + kBuildWarps - 1) / kBuildWarps;
     build_direct_kernel<NT><<<blocks, kBuildWarps * 32, smem, s>>>(a);
@@ -1635,10 +1656,21 @@ cudaError_t launch_build_direct_impl(const DirectBuildArgs& a, cudaStream_t s) {
 // whole mu_a = c^T x.  Selection: exact int32 energy, arg-min of
 // (E, candidate) with the reference candidate first.
 // =========================================================================
+template <int N>
+__host__ __device__ constexpr int general_tpa() { return N <= 32 ? 1 : (N <= 64 ? 2 : 4); }
+
+// Row j of eps dt J is stored as TPA slices of NS columns, each followed by 4
+// floats of padding (row stride N + 4 TPA): the TPA threads of an anneal read
+// their slices of one row in the same instruction, and without the padding
+// those slices would start 128 bytes apart, in the same banks.
+template <int N>
+__host__ __device__ constexpr int general_row_stride() { return N + 4 * general_tpa<N>(); }
+
 template <int N, int NS, int L>
-__device__ __forceinline__ void general_block(const float* Jf, const float* cf, float* xrow, float (&x)[NS],
+__device__ __forceinline__ void general_block(const float* Jmine, const float* cf, float* xrow, float (&x)[NS],
                                               float (&e)[NS], float& xa, float& ea, int row0, int Lrt,
                                               const EulerConsts& k) {
+    constexpr int JS = general_row_stride<N>();
     asm volatile("" ::: "memory");
     __syncwarp();  // the anneal's threads finished reading the previous refresh's row
 #pragma unroll
@@ -1652,7 +1684,7 @@ __device__ __forceinline__ void general_block(const float* Jf, const float* cf, 
     for (int j = 0; j < N; ++j) {
         const float xj = xrow[j];
         mua = fmarn(cf[j], xj, mua);
-        const float4* row = reinterpret_cast<const float4*>(Jf + j * N + row0);
+        const float4* row = reinterpret_cast<const float4*>(Jmine + j * JS);
         const float2 xx = make_float2(xj, xj);
 #pragma unroll
         for (int i4 = 0; i4 < NS / 4; ++i4) {
@@ -1694,12 +1726,10 @@ __device__ __forceinline__ void general_block(const float* Jf, const float* cf, 
     }
 }
 
-template <int N>
-__host__ __device__ constexpr int general_tpa() { return N <= 32 ? 1 : (N <= 64 ? 2 : 4); }
 
 template <int N>
 __host__ __device__ constexpr size_t general_smem_bytes(int runs) {
-    return ((size_t)N * N + N + (size_t)runs * (N + 1)) * sizeof(float);
+    return ((size_t)N * general_row_stride<N>() + N + (size_t)runs * (N + 1)) * sizeof(float);
 }
 
 template <int N, int F>
@@ -1708,9 +1738,10 @@ __global__ void __launch_bounds__(256) cac_general_kernel(GeneralArgs a) {
     constexpr int NS = N / TPA;
     static_assert(N % TPA == 0 && NS % 4 == 0 && NS <= 32, "rows per thread: a multiple of 4, at most 32");
     extern __shared__ __align__(16) float gsm[];
-    float* Jf = gsm;        // [N][N] eps dt J
-    float* cf = Jf + N * N; // [N]   eps dt c
-    float* Xr = cf + N;     // [runs][N + 1]
+    constexpr int JS = general_row_stride<N>();
+    float* Jf = gsm;         // [N][JS] eps dt J, rows in TPA padded slices
+    float* cf = Jf + N * JS; // [N]   eps dt c
+    float* Xr = cf + N;      // [runs][N + 1]
     __shared__ long long skey[8];
     __shared__ int sdiv[8];
     __shared__ int sEref;
@@ -1723,7 +1754,10 @@ __global__ void __launch_bounds__(256) cac_general_kernel(GeneralArgs a) {
     const int16_t* Jq = a.Jq + (size_t)p * N * N;
     const int16_t* cq = a.cq + (size_t)p * N;
     const int8_t* sref = a.s_ref ? a.s_ref + (size_t)p * N : nullptr;
-    for (int e = tid; e < N * N; e += T) Jf[e] = mulrn(mulrn((float)Jq[e], 0x1p-14f), k.ce);
+    for (int e = tid; e < N * N; e += T) {
+        const int j = e / N, i = e % N;
+        Jf[j * JS + (i / NS) * (NS + 4) + i % NS] = mulrn(mulrn((float)Jq[e], 0x1p-14f), k.ce);
+    }
     for (int i = tid; i < N; i += T) cf[i] = mulrn(mulrn((float)cq[i], 0x1p-14f), k.ce);
     if (tid == 0) sEref = 0;
     __syncthreads();
@@ -1762,15 +1796,16 @@ __global__ void __launch_bounds__(256) cac_general_kernel(GeneralArgs a) {
     float* xrow = Xr + run * (N + 1);
     const int S = a.steps;
     int t = 0;
+    const float* Jmine = Jf + q * (NS + 4);  // this thread's slice of every row
     if constexpr (F > 0) {
 #pragma unroll 1
-        for (; t + F <= S; t += F) general_block<N, NS, F>(Jf, cf, xrow, x, e, xa, ea, row0, F, k);
+        for (; t + F <= S; t += F) general_block<N, NS, F>(Jmine, cf, xrow, x, e, xa, ea, row0, F, k);
     } else {
         const int f = a.f_mvm;
 #pragma unroll 1
-        for (; t + f <= S; t += f) general_block<N, NS, 0>(Jf, cf, xrow, x, e, xa, ea, row0, f, k);
+        for (; t + f <= S; t += f) general_block<N, NS, 0>(Jmine, cf, xrow, x, e, xa, ea, row0, f, k);
     }
-    if (t < S) general_block<N, NS, 0>(Jf, cf, xrow, x, e, xa, ea, row0, S - t, k);
+    if (t < S) general_block<N, NS, 0>(Jmine, cf, xrow, x, e, xa, ea, row0, S - t, k);
 
     bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
 #pragma unroll
@@ -1858,18 +1893,15 @@ cudaError_t launch_general_impl(const GeneralArgs& a, int runs, cudaStream_t s) 
     const size_t smem = general_smem_bytes<N>(runs);
     cudaError_t err;
     if (a.f_mvm == 2) {
-        if ((err = cudaFuncSetAttribute(cac_general_kernel<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem)) != cudaSuccess)
+        if ((err = ensure_dynamic_smem<cac_general_kernel<N, 2>>(smem)) != cudaSuccess)
             return err;
         cac_general_kernel<N, 2><<<a.n_problems, threads, smem, s>>>(a);
     } else if (a.f_mvm == 1) {
-        if ((err = cudaFuncSetAttribute(cac_general_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem)) != cudaSuccess)
+        if ((err = ensure_dynamic_smem<cac_general_kernel<N, 1>>(smem)) != cudaSuccess)
             return err;
         cac_general_kernel<N, 1><<<a.n_problems, threads, smem, s>>>(a);
     } else {
-        if ((err = cudaFuncSetAttribute(cac_general_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem)) != cudaSuccess)
+        if ((err = ensure_dynamic_smem<cac_general_kernel<N, 0>>(smem)) != cudaSuccess)
             return err;
         cac_general_kernel<N, 0><<<a.n_problems, threads, smem, s>>>(a);
     }
@@ -1976,7 +2008,7 @@ cudaError_t launch_gram_tc_impl(const GramArgs& a, cudaStream_t s) {
     } else {
         const size_t smem = (size_t)4 * 2 * kMaxNr * NT * sizeof(float);
         cudaError_t err =
-            cudaFuncSetAttribute(gram_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            ensure_dynamic_smem<gram_tc_kernel<NT>>(smem);
         if (err != cudaSuccess) return err;
         gram_tc_kernel<NT><<<(a.n_chan + 3) / 4, 128, smem, s>>>(a);
         return cudaGetLastError();
@@ -2054,7 +2086,7 @@ template <int NT>
 cudaError_t launch_select_impl(const SelectArgs& a, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
     const size_t smem = (size_t)4 * (2 * kMaxNr * NT + 4 * kMaxNr) * sizeof(float);
-    cudaError_t err = cudaFuncSetAttribute(select_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = ensure_dynamic_smem<select_kernel<NT>>(smem);
     if (err != cudaSuccess) return err;
     select_kernel<NT><<<(a.n_problems + 3) / 4, 128, smem, s>>>(a);
     return cudaGetLastError();
@@ -2238,10 +2270,13 @@ __global__ void __launch_bounds__(32) vpp_inverse_ir_kernel(VppInvArgs a) {
     const int n_t = a.n_t;
     const int cc = lane / LPC, part = lane % LPC;
     const bool active = cc < NU;
-    // complex matrices, element (row i, column j) at [i * NU + j]
-    float2* Kh = fsm2;             // K = Kh + Kl
-    float2* Kl = Kh + NU * NU;
-    float2* Lc = Kl + NU * NU;     // FP32 Cholesky factor of Kh; diagonal holds 1 / L_ii
+    // complex matrices, element (row i, column j) at [i * NU + j]; K's rows are
+    // padded to KS = NU + 1 so that the two lanes of a column, reading rows i and
+    // i + 1 in the residual, fall in different banks
+    constexpr int KS = NU + 1;
+    float2* Kh = fsm2;             // K = Kh + Kl, [NU][KS]
+    float2* Kl = Kh + NU * KS;
+    float2* Lc = Kl + NU * KS;     // FP32 Cholesky factor of Kh; diagonal holds 1 / L_ii
     float2* Hf = Lc + NU * NU;     // H [NU][n_t], until K is formed; then
     float2* Xh = Hf;               // X = Xh + Xl
     float2* Xl = Xh + NU * NU;
@@ -2266,15 +2301,15 @@ __global__ void __launch_bounds__(32) vpp_inverse_ir_kernel(VppInvArgs a) {
             }
         }
         const DF re = df_add(DF{sr, 0.0f}, er, 0.0f), im = df_add(DF{si, 0.0f}, ei, 0.0f);
-        Kh[i * NU + j] = make_float2(re.hi, im.hi);
-        Kl[i * NU + j] = make_float2(re.lo, im.lo);
-        Kh[j * NU + i] = make_float2(re.hi, -im.hi);
-        Kl[j * NU + i] = make_float2(re.lo, -im.lo);
+        Kh[i * KS + j] = make_float2(re.hi, im.hi);
+        Kl[i * KS + j] = make_float2(re.lo, im.lo);
+        Kh[j * KS + i] = make_float2(re.hi, -im.hi);
+        Kl[j * KS + i] = make_float2(re.lo, -im.lo);
     }
     __syncwarp();
     for (int j = 0; j < NU; ++j) {
         if (lane == j) {
-            float d = Kh[j * NU + j].x;
+            float d = Kh[j * KS + j].x;
             for (int k = 0; k < j; ++k) {
                 const float2 l = Lc[j * NU + k];
                 d = fmarn(-l.x, l.x, d);
@@ -2288,7 +2323,7 @@ __global__ void __launch_bounds__(32) vpp_inverse_ir_kernel(VppInvArgs a) {
         const float rjj = Lc[j * NU + j].x;
         if (lane > j && lane < NU) {
             const int i = lane;
-            float2 v = Kh[i * NU + j];
+            float2 v = Kh[i * KS + j];
             for (int k = 0; k < j; ++k) {  // v -= L_ik conj(L_jk)
                 const float2 x = Lc[i * NU + k], y = Lc[j * NU + k];
                 v.x = fmarn(-x.x, y.x, v.x);
@@ -2357,7 +2392,7 @@ __global__ void __launch_bounds__(32) vpp_inverse_ir_kernel(VppInvArgs a) {
                 // exactly to about 2^-48; e also takes - (Kh Xl + Kl Xh) in FP32
                 float sr = i == cc ? 1.0f : 0.0f, si = 0.0f, er = 0.0f, ei = 0.0f;
                 for (int j = 0; j < NU; ++j) {
-                    const float2 kh = Kh[i * NU + j], kl = Kl[i * NU + j];
+                    const float2 kh = Kh[i * KS + j], kl = Kl[i * KS + j];
                     const float2 xh = Xh[j * NU + cc], xl = Xl[j * NU + cc];
                     two_sum_prod(sr, er, -kh.x, xh.x);
                     two_sum_prod(sr, er, kh.y, xh.y);
@@ -2410,9 +2445,9 @@ template <int NU>
 cudaError_t launch_vpp_inverse_ir_impl(const VppInvArgs& a, cudaStream_t s) {
     if (a.n_chan <= 0) return cudaSuccess;
     if (a.refine < 1 || a.refine > kVppRefineMax) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(3 * NU * NU + std::max(NU * a.n_t, 3 * NU * NU)) * sizeof(float2);
+    const size_t smem = (size_t)(2 * NU * (NU + 1) + NU * NU + std::max(NU * a.n_t, 3 * NU * NU)) * sizeof(float2);
     cudaError_t err =
-        cudaFuncSetAttribute(vpp_inverse_ir_kernel<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_dynamic_smem<vpp_inverse_ir_kernel<NU>>(smem);
     if (err != cudaSuccess) return err;
     vpp_inverse_ir_kernel<NU><<<a.n_chan, 32, smem, s>>>(a);
     return cudaGetLastError();
@@ -2548,8 +2583,7 @@ template <int NT>
 cudaError_t launch_build_detect_impl(const BuildArgs& a, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
     const size_t smem = (size_t)kBuildWarps * build_smem_floats<NT>(a.n_r) * sizeof(float);
-    cudaError_t err = cudaFuncSetAttribute(build_detect_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    cudaError_t err = ensure_dynamic_smem<build_detect_kernel<NT>>(smem);
     if (err != cudaSuccess) return err;
     const int blocks = (a.n_problems + kBuildWarps - 1) / kBuildWarps;
     build_detect_kernel<NT><<<blocks, kBuildWarps * 32, smem, s>>>(a);
@@ -2598,8 +2632,7 @@ template <int NT>
 cudaError_t launch_vpp_inverse_impl(const VppInvArgs& a, cudaStream_t s) {
     if (a.n_chan <= 0) return cudaSuccess;
     const size_t smem = (size_t)(2 * NT * a.n_t + 8 * NT * NT) * sizeof(double);
-    cudaError_t err = cudaFuncSetAttribute(vpp_inverse_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    cudaError_t err = ensure_dynamic_smem<vpp_inverse_kernel<NT>>(smem);
     if (err != cudaSuccess) return err;
     vpp_inverse_kernel<NT><<<a.n_chan, 32, smem, s>>>(a);
     return cudaGetLastError();
