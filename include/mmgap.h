@@ -328,7 +328,7 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
  * Launch shape of the CIM-CAC solver for n_t users (no counterpart in the
  * paper, which runs one thread per anneal).  Shapes 0-4 and 6 give
  * bit-identical results; they differ only in speed:
- *   0 default for the size (packed one-thread-per-anneal where compiled)
+ *   0 default for the size (6 for 16 users, 3 for 4 and 8, 1 elsewhere)
  *   1 plain: one thread per anneal, scalar FP32 (the paper's design point)
  *   2 tuned kernel, one thread per anneal, scalar FP32
  *   3 tuned kernel, one thread per anneal, packed FP32 pairs

@@ -58,7 +58,8 @@ cudaError_t launch_random_ising(int16_t* Aq, int16_t* hq, int n, int n_problems,
 int mmgap::resolve_variant(int n_t, int f_mvm, int requested) {
     const bool tuned = (n_t == 4 || n_t == 8 || n_t == 16) && (f_mvm == 1 || f_mvm == 2);
     if (!tuned) return kVariantPlain;
-    if (requested <= kVariantAuto || requested >= kVariantCount) return kVariantTpa1Packed;
+    if (requested <= kVariantAuto || requested >= kVariantCount)  // the measured fastest exact shape
+        return n_t == 16 ? kVariantPairPacked : kVariantTpa1Packed;
     if (requested == kVariantTensorCore && n_t == 4) return kVariantTpa1Packed;
     return requested;
 }
