@@ -340,7 +340,10 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
  * the coupling field of a warp's 32 anneals computed on the tensor cores
  * (mma.sync m16n8k16, couplings and u split into FP16 pairs, FP32
  * accumulation; about 2^-21 of sum |A||u| from the FP32 field), for n_t in
- * {8, 16} (MMGAP_EUNSUPPORTED otherwise); the autotuner never picks it.
+ * {8, 16} (MMGAP_EUNSUPPORTED otherwise); shape 7 is the same refresh with
+ * two threads per anneal (half the registers per thread; b^T u summed as two
+ * halves, so not bit-identical to shape 5 either).  The autotuner never
+ * picks 5 or 7.
  * The choice is per context and applies to detect, precode and solve_ising
  * calls.
  */
@@ -354,11 +357,11 @@ mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* v
  * n_t users on n_problems random Q14 problems (0 = 8192; clamped to the
  * workspace) with *params, keep the fastest for this context and return it
  * in *variant_out.
- * ms_out (may be NULL, else 7 floats) receives [0] the best time and [v] the
+ * ms_out (may be NULL, else 8 floats) receives [0] the best time and [v] the
  * time of shape v (-1 if not compiled or not bit-identical).  Synchronises the device; uses the workspace.
  */
 mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
-                            float ms_out[7]);
+                            float ms_out[8]);
 
 /*
  * Batched persistent launch of mixed-size uplink jobs (no counterpart in the

@@ -60,7 +60,7 @@ int mmgap::resolve_variant(int n_t, int f_mvm, int requested) {
     if (!tuned) return kVariantPlain;
     if (requested <= kVariantAuto || requested >= kVariantCount)  // the measured fastest exact shape
         return n_t == 16 ? kVariantPairPacked : kVariantTpa1Packed;
-    if (requested == kVariantTensorCore && n_t == 4) return kVariantTpa1Packed;
+    if ((requested == kVariantTensorCore || requested == kVariantTensorCore2) && n_t == 4) return kVariantTpa1Packed;
     return requested;
 }
 
@@ -924,7 +924,7 @@ mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant) {
     if (!ctx) return MMGAP_EINVAL;
     if (!nt_supported(n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d", n_t);
     if (variant < 0 || variant >= kVariantCount) return fail(ctx, MMGAP_EINVAL, "variant=%d", variant);
-    if (variant == kVariantTensorCore && n_t != 8 && n_t != 16)
+    if ((variant == kVariantTensorCore || variant == kVariantTensorCore2) && n_t != 8 && n_t != 16)
         return fail(ctx, MMGAP_EUNSUPPORTED, "tensor-core refresh needs n_t 8 or 16");
     ctx->variant[n_t] = variant;
     return MMGAP_OK;
@@ -938,7 +938,7 @@ mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* v
 }
 
 mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
-                            float ms_out[7]) {
+                            float ms_out[8]) {
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;

@@ -53,14 +53,15 @@ enum SolverVariant : int {
     kVariantTpa2Packed = 4,  // tuned kernel, two threads per anneal, packed FP32 pairs
     kVariantTensorCore = 5,  // field refresh on tensor cores (FP16 split, FP32 accumulation): not bit-identical
     kVariantPairPacked = 6,  // tuned kernel, one thread per anneal, refresh shared by lane pairs
-    kVariantCount = 7
+    kVariantTensorCore2 = 7, // field refresh on tensor cores, two threads per anneal: not bit-identical
+    kVariantCount = 8
 };
 
 // Variant used for n_t users and refresh period f_mvm when `requested` is
 // kVariantAuto or not compiled for that size.
 int resolve_variant(int n_t, int f_mvm, int requested);
 // Shapes whose results are bit-identical to the plain kernel's (the autotuner's candidates).
-constexpr bool variant_exact(int v) { return v != kVariantTensorCore; }
+constexpr bool variant_exact(int v) { return v != kVariantTensorCore && v != kVariantTensorCore2; }
 
 struct BuildArgs {
     const float* H;            // complex [n_chan][n_r][n_t]

@@ -956,7 +956,9 @@ struct TcShape {
     static constexpr int KT = n / 16;     // K steps (columns j)
     static constexpr int UW = n / 2 + 4;  // 32-bit words per row of U^T (FP16 pairs), padded
     static constexpr int MW = n + 4;      // floats per row of M^T, padded
-    static constexpr int WARP_WORDS = 2 * 32 * UW > 32 * MW ? 2 * 32 * UW : 32 * MW;
+    // exchange buffer of a warp with AW anneals (32 / threads per anneal)
+    static constexpr int warp_words(int AW) { return 2 * AW * UW > AW * MW ? 2 * AW * UW : AW * MW; }
+    static constexpr int WARP_WORDS = warp_words(32);
     static constexpr int AF_WORDS = MT * KT * 2 * 4 * 32;  // A fragments, hi and lo
 };
 
@@ -993,44 +995,58 @@ __device__ __forceinline__ void tc_stage_fragments(const int16_t* sAq, uint32_t*
     }
 }
 
-// Tensor-core refresh + L frozen Euler steps (packed FP32) of one anneal per lane.
-template <int NT, int L>
+// Tensor-core refresh + L frozen Euler steps (packed FP32).  TPA threads per
+// anneal (1 or 2): the warp's 32 / TPA anneals are the N columns of the MMA;
+// thread q of an anneal owns rows [q NS, (q+1) NS) (NS = n / TPA), writes
+// them into its anneal's row of U^T, reads them back from M^T, and keeps the
+// auxiliary spin redundantly (mu_a: this thread's part of b^T u plus the
+// partner's, by shuffle; the same sum on both threads).
+template <int NT, int L, int TPA = 1>
 __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, const float* snd, uint32_t* wsm,
-                                         float (&x1)[2 * NT], float (&x2)[2 * NT], float (&e1)[2 * NT],
-                                         float (&e2)[2 * NT], float& xa, float& ea, int lane, int Lrt, float mscale,
-                                         const EulerConsts& k) {
+                                         float (&x1)[2 * NT / TPA], float (&x2)[2 * NT / TPA],
+                                         float (&e1)[2 * NT / TPA], float (&e2)[2 * NT / TPA], float& xa,
+                                         float& ea, int lane, int Lrt, float mscale, const EulerConsts& k) {
     using S = TcShape<NT>;
     constexpr int n = S::n;
+    constexpr int NS = n / TPA;      // rows per thread
+    constexpr int AW = 32 / TPA;     // anneals per warp
+    constexpr int NTL = AW / 8;      // N tiles
+    static_assert(TPA == 1 || TPA == 2, "one or two threads per anneal");
+    static_assert(NS % 8 == 0, "whole uint4 stores of U^T");
     asm volatile("" ::: "memory");
+    const int q = lane % TPA, rl = lane / TPA, row0 = q * NS;
     uint32_t* sUh = wsm;
-    uint32_t* sUl = wsm + 32 * S::UW;
+    uint32_t* sUl = wsm + AW * S::UW;
     float* sM = reinterpret_cast<float*>(wsm);
-    // u = x1 + x2 and mu_a = b^T u (FP32, ascending j); FP16 split of 2^5 u into row `lane` of U^T
+    // u = x1 + x2 and this thread's part of mu_a = b^T u (FP32, ascending j); FP16 split of 2^5 u into
+    // this thread's half of row rl of U^T
     float mua = 0.0f;
 #pragma unroll
-    for (int w4 = 0; w4 < n / 8; ++w4) {
+    for (int w4 = 0; w4 < NS / 8; ++w4) {
         uint32_t hv[4], lv[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int j = 8 * w4 + 2 * t;
             const float2 u2 = __fadd2_rn(make_float2(x1[j], x1[j + 1]), make_float2(x2[j], x2[j + 1]));
-            mua = fmarn(sh[j], u2.x, mua);
-            mua = fmarn(sh[j + 1], u2.y, mua);
+            mua = fmarn(sh[row0 + j], u2.x, mua);
+            mua = fmarn(sh[row0 + j + 1], u2.y, mua);
             const float2 us = __fmul2_rn(u2, make_float2(32.0f, 32.0f));
             hv[t] = h2pack(us.x, us.y);
             const float2 hf = h2unpack(hv[t]);
             lv[t] = h2pack(__fsub_rn(us.x, hf.x), __fsub_rn(us.y, hf.y));
         }
-        *reinterpret_cast<uint4*>(sUh + lane * S::UW + 4 * w4) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<uint4*>(sUl + lane * S::UW + 4 * w4) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+        const int wo = rl * S::UW + row0 / 2 + 4 * w4;
+        *reinterpret_cast<uint4*>(sUh + wo) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(sUl + wo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
     }
+    if constexpr (TPA == 2) mua = addrn(mua, __shfl_xor_sync(0xffffffffu, mua, 1));
     __syncwarp();
     const int g = lane >> 2, tg = lane & 3;
-    float acc[S::MT][4][4];
+    float acc[S::MT][NTL][4];
 #pragma unroll
     for (int mt = 0; mt < S::MT; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < NTL; ++nt)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[mt][nt][c] = 0.0f;
 #pragma unroll
@@ -1044,7 +1060,7 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
                 al[mt][r] = sAf[(((mt * S::KT + kk) * 2 + 1) * 4 + r) * 32 + lane];
             }
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
+        for (int nt = 0; nt < NTL; ++nt) {
             const int row = (nt * 8 + g) * S::UW + kk * 8 + tg;
             const uint32_t bh[2] = {sUh[row], sUh[row + 4]};
             const uint32_t bl[2] = {sUl[row], sUl[row + 4]};
@@ -1060,7 +1076,7 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
 #pragma unroll
     for (int mt = 0; mt < S::MT; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
+        for (int nt = 0; nt < NTL; ++nt) {
             const int r0 = nt * 8 + 2 * tg, i0 = mt * 16 + g;
             sM[r0 * S::MW + i0] = acc[mt][nt][0];
             sM[(r0 + 1) * S::MW + i0] = acc[mt][nt][1];
@@ -1068,10 +1084,10 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
             sM[(r0 + 1) * S::MW + i0 + 8] = acc[mt][nt][3];
         }
     __syncwarp();
-    float m[n];
+    float m[NS];
 #pragma unroll
-    for (int i4 = 0; i4 < n / 4; ++i4) {
-        const float4 v = *reinterpret_cast<const float4*>(sM + lane * S::MW + 4 * i4);
+    for (int i4 = 0; i4 < NS / 4; ++i4) {
+        const float4 v = *reinterpret_cast<const float4*>(sM + rl * S::MW + row0 + 4 * i4);
         const float2 lo = __fmul2_rn(make_float2(v.x, v.y), make_float2(mscale, mscale));
         const float2 hi = __fmul2_rn(make_float2(v.z, v.w), make_float2(mscale, mscale));
         m[4 * i4] = lo.x;
@@ -1084,9 +1100,9 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
     const float2 cdt = make_float2(k.cdt, k.cdt), c1 = make_float2(k.c1, k.c1);
     const float2 cz = make_float2(k.cz, k.cz), c2 = make_float2(k.c2, k.c2);
 #pragma unroll
-    for (int i = 0; i < n; i += 2) {
-        const float2 hh = *reinterpret_cast<const float2*>(sh + i);
-        const float2 nd = *reinterpret_cast<const float2*>(snd + i);
+    for (int i = 0; i < NS; i += 2) {
+        const float2 hh = *reinterpret_cast<const float2*>(sh + row0 + i);
+        const float2 nd = *reinterpret_cast<const float2*>(snd + row0 + i);
         const float2 c = __ffma2_rn(hh, xa2, make_float2(m[i], m[i + 1]));
         float2 X1 = make_float2(x1[i], x1[i + 1]), X2 = make_float2(x2[i], x2[i + 1]);
         float2 E1 = make_float2(e1[i], e1[i + 1]), E2 = make_float2(e2[i], e2[i + 1]);
@@ -1123,12 +1139,12 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
     constexpr int NS = n / TPA;
     static_assert(n % TPA == 0 && NS % 4 == 0, "rows per thread must be a multiple of 4");
     static_assert(F > 0, "compile-time refresh period");
-    static_assert(!TC || (TPA == 1 && PACKED && n % 16 == 0), "tensor-core refresh: one thread per anneal, n % 16 == 0");
+    static_assert(!TC || (TPA <= 2 && PACKED && n % 16 == 0), "tensor-core refresh: 1 or 2 threads per anneal");
     __shared__ __align__(16) SolveSmem<NT> sm;
     __shared__ long long skey[4 * TPA];
     __shared__ int sdiv[4 * TPA];
     __shared__ __align__(16) uint32_t tc_af[TC ? TcShape<NT>::AF_WORDS : 1];
-    extern __shared__ __align__(16) uint32_t tc_ws[];  // TC: TcShape<NT>::WARP_WORDS per warp (dynamic)
+    extern __shared__ __align__(16) uint32_t tc_ws[];  // TC: TcShape<NT>::warp_words(32 / TPA) per warp (dynamic)
     const int p = blockIdx.x;
     const int tid = threadIdx.x, T = blockDim.x;
     const int q = tid % TPA, run = tid / TPA;
@@ -1180,11 +1196,12 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
     const int S = a.steps;
     int t = 0;
     if constexpr (TC) {
-        uint32_t* wsm = tc_ws + warp * TcShape<NT>::WARP_WORDS;
+        uint32_t* wsm = tc_ws + warp * TcShape<NT>::warp_words(32 / TPA);
         const float mscale = mulrn(k.ce, 0x1p-5f);  // eps dt, and the 2^5 of u
 #pragma unroll 1
-        for (; t + F <= S; t += F) tc_block<NT, F>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, F, mscale, k);
-        if (t < S) tc_block<NT, 0>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, S - t, mscale, k);
+        for (; t + F <= S; t += F)
+            tc_block<NT, F, TPA>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, F, mscale, k);
+        if (t < S) tc_block<NT, 0, TPA>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, S - t, mscale, k);
     } else {
 #pragma unroll 1
         for (; t + F <= S; t += F)
@@ -2606,7 +2623,14 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
         case kVariantTensorCore:
             if constexpr (NT % 8 == 0) {
                 cac_solve_tuned_kernel<NT, F, 1, true, true>
-                    <<<a.n_problems, runs, (size_t)(runs / 32) * TcShape<NT>::WARP_WORDS * 4, s>>>(a);
+                    <<<a.n_problems, runs, (size_t)(runs / 32) * TcShape<NT>::warp_words(32) * 4, s>>>(a);
+                break;
+            }
+            [[fallthrough]];
+        case kVariantTensorCore2:
+            if constexpr (NT % 8 == 0) {
+                cac_solve_tuned_kernel<NT, F, 2, true, true>
+                    <<<a.n_problems, 2 * runs, (size_t)(2 * runs / 32) * TcShape<NT>::warp_words(16) * 4, s>>>(a);
                 break;
             }
             [[fallthrough]];

@@ -36,28 +36,30 @@ def mm():
     ctx.close()
 
 
+@pytest.mark.parametrize("shape", [5, 7])
 @pytest.mark.parametrize("n_t,f,runs", [(8, 1, 32), (8, 2, 64), (16, 2, 32), (16, 1, 128)])
-def test_short_anneals_agree_and_energies_are_exact(mm, n_t, f, runs):
+def test_short_anneals_agree_and_energies_are_exact(mm, shape, n_t, f, runs):
     pkg, ctx = mm
     n = 2 * n_t
     Aq, hq = synth.random_ising(40 + n_t + f, 1500, n)
     prm = pkg.Params.default(steps=7, f_mvm=f, runs=runs)
     res = {}
-    for v in (3, 5):
+    for v in (3, shape):
         ctx.set_solver_variant(n_t, v)
         res[v] = ctx.solve_ising(T(Aq), T(hq), prm, 9)
     ctx.set_solver_variant(n_t, 0)
     torch.cuda.synchronize()
-    d3, d5 = res[3]["d"].cpu().numpy(), res[5]["d"].cpu().numpy()
+    d3, d5 = res[3]["d"].cpu().numpy(), res[shape]["d"].cpu().numpy()
     same = np.all(d3 == d5, axis=1).mean()
     assert same >= 0.99, same
-    E5 = res[5]["E"].cpu().numpy()
+    E5 = res[shape]["E"].cpu().numpy()
     for p in range(0, 1500, 7):
         assert E5[p] == oracle.energy_q(Aq[p], hq[p], d5[p]), p
 
 
+@pytest.mark.parametrize("shape", [5, 7])
 @pytest.mark.parametrize("n_t,mb,snr,model,hold", [(16, 4, 16.0, "iid", "subcarrier"), (8, 4, 15.0, "kron", "prb")])
-def test_detection_ber_equals_the_fp32_path(mm, n_t, mb, snr, model, hold):
+def test_detection_ber_equals_the_fp32_path(mm, shape, n_t, mb, snr, model, hold):
     """16x16 16-QAM i.i.d. and 8x8 16-QAM Kronecker, 32 anneals x 200 steps:
     the bit-error counts of the two refreshes differ by less than four
     standard deviations of a binomial count (and by less than 12 %)."""
@@ -67,7 +69,7 @@ def test_detection_ber_equals_the_fp32_path(mm, n_t, mb, snr, model, hold):
     prm = pkg.Params.default()
     H, y, nv, ci = (T(w[k]) for k in ("H", "y", "noise_var", "chan_index"))
     errs = {}
-    for v in (3, 5):
+    for v in (3, shape):
         ctx.set_solver_variant(n_t, v)
         out = ctx.detect(H, y, nv, mb, prm, 5, chan_index=ci, want_guess=(v == 3))
         torch.cuda.synchronize()
@@ -79,7 +81,7 @@ def test_detection_ber_equals_the_fp32_path(mm, n_t, mb, snr, model, hold):
             errs["mmse"] = synth.bit_errors(mmse, w["sym"], mb)
     ctx.set_solver_variant(n_t, 0)
     nbits = P * n_t * mb
-    e3, e5 = errs[3], errs[5]
+    e3, e5 = errs[3], errs[shape]
     sd = np.sqrt(e3 * (1 - e3 / nbits))
     assert abs(e5 - e3) <= 4 * sd and abs(e5 - e3) <= 0.12 * e3, (e3, e5, sd)
     assert e5 < errs["mmse"]
@@ -87,8 +89,9 @@ def test_detection_ber_equals_the_fp32_path(mm, n_t, mb, snr, model, hold):
 
 def test_refused_where_not_built_and_never_autotuned(mm):
     pkg, ctx = mm
-    with pytest.raises(pkg.MMGaPError) as e:
-        ctx.set_solver_variant(4, 5)
-    assert e.value.status == 5
+    for shape in (5, 7):
+        with pytest.raises(pkg.MMGaPError) as e:
+            ctx.set_solver_variant(4, shape)
+        assert e.value.status == 5
     v, ms = ctx.autotune(pkg.Params.default(steps=40), 16, 2048)
-    assert v in (1, 2, 3, 4, 6) and 5 not in ms
+    assert v in (1, 2, 3, 4, 6) and 5 not in ms and 7 not in ms
