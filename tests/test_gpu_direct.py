@@ -159,3 +159,22 @@ def test_direct_mapping_arguments(mm):
     job = ctx.detect_job(T(w["H"]), T(w["y"]), T(w["noise_var"]), 6, 1, out, T(w["chan_index"]), mapping=1)
     with pytest.raises(pkg.MMGaPError):
         pkg.Batch(0, pkg.Params.default(), [job])
+
+
+def test_direct_chunked_workspace_is_deterministic(mm):
+    """A workspace that holds a few problems per chunk gives the same bits as one chunk."""
+    pkg, ctx = mm
+    w = synth.uplink(77, 8, 8, 4, n_sub=6, n_sym=4, snr_db=14.0)
+    prm = pkg.Params.default(steps=60)
+    outs = []
+    for ws in (24 * 1024, 0):
+        with pkg.Context(0, workspace_bytes=ws) as c:
+            o = c.detect(T(w["H"]), T(w["y"]), T(w["noise_var"]), 4, prm, 5, chan_index=T(w["chan_index"]),
+                         want_energy=True, want_guess=True, want_offset=True, want_ndiv=True, mapping=1)
+            torch.cuda.synchronize()
+            outs.append({k: v.cpu().numpy() for k, v in o.items()})
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    for p in (0, 11, 23):
+        r = oracle.detect_direct(w["H"][w["chan_index"][p]], w["y"][p], w["noise_var"][p], 4, oparams(prm), 5, p)
+        assert np.array_equal(outs[0]["sym"][p], r["sym"]) and outs[0]["energy"][p] == r["E"], p

@@ -121,3 +121,26 @@ def test_precode_with_refined_inverse_matches_fp64_path(mm, nu, mb):
     assert v_eq.mean() >= 0.97, v_eq.mean()
     assert np.allclose(pg[v_eq], pr[v_eq], rtol=1e-5, atol=0)
     assert abs(pg.sum() / pr.sum() - 1.0) < 0.01
+
+
+@pytest.mark.parametrize("inv_precision", [0, 1])
+def test_precode_chunked_workspace_is_deterministic(mm, inv_precision):
+    """A workspace that holds the channel inverses and a few problems per chunk gives the same bits as
+    one chunk; the FP64 path also equals the oracle."""
+    pkg, ctx = mm
+    d = synth.downlink(31, 8, 8, 4, n_sub=10, n_sym=4)
+    prm = pkg.Params.default(steps=60)
+    outs = []
+    for ws in (16 * 1024, 0):
+        with pkg.Context(0, workspace_bytes=ws) as c:
+            o = c.precode(T(d["H"]), T(d["u_sym"]), 4, prm, 3, chan_index=T(d["chan_index"]), want_energy=True,
+                          want_ndiv=True, inv_precision=inv_precision)
+            torch.cuda.synchronize()
+            outs.append({k: v.cpu().numpy() for k, v in o.items()})
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    if inv_precision == 0:
+        fields = ("runs", "steps", "f_mvm", "dt", "p", "a", "zeta", "eps", "sigma0", "x_max")
+        ref = oracle.precode_batch(d["H"], d["u_sym"], 4, oracle.Params(**{f: getattr(prm, f) for f in fields}), 3,
+                                   d["chan_index"])
+        assert np.array_equal(outs[0]["v"], ref["v"]) and np.array_equal(outs[0]["energy"], ref["E"])
