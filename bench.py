@@ -1153,28 +1153,33 @@ def main():
               "frac_problems_identical": float(np.mean(np.all(tsym == sym, axis=1))),
               "algorithmic_tflops": solver_flops(P, n_t, args.runs, args.solver_steps, args.f_mvm) /
               (tc_solve / 1e3) / 1e12, "shape": "tensor-core (5)"}
-        # the same refresh with two threads per anneal (shape 7)
-        ctx.set_solver_variant(n_t, 7)
-        for _ in range(2):
-            flush.zero_()
-            ctx.detect_jobs([tjob], prm)
-        torch.cuda.synchronize()
-        t7, s7 = [], []
-        for i in range(args.steps):
-            flush.zero_()
-            starts[i].record(stream)
-            ctx.detect_jobs([tjob], prm)
-            ends[i].record(stream)
-            s7.append(ctx.stage_times()[1])
-        torch.cuda.synchronize()
-        t7 = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
-        ctx.set_solver_variant(n_t, variant)
-        sym7 = tout["sym"].cpu().numpy()
-        tc["tpa2"] = {"ms_per_step": statistics.mean(t7), "value": world * P / (statistics.mean(t7) / 1e3),
-                      "solve_ms": statistics.mean(s7), "speedup_vs_exact": ms_per_step / statistics.mean(t7),
-                      "ber": synth.bit_errors(sym7, w["sym"], mb) / nbits,
-                      "frac_problems_identical": float(np.mean(np.all(sym7 == sym, axis=1))),
-                      "shape": "tensor-core, two threads per anneal (7)"}
+        # the same refresh with two threads per anneal (shape 7), and as tcgen05
+        # MMAs with the accumulator in tensor memory (shape 8)
+        for sv, key, label in ((7, "tpa2", "tensor-core, two threads per anneal (7)"),
+                               (8, "tcgen05", "tcgen05 MMA, FP32 accumulator in tensor memory (8)")):
+            ctx.set_solver_variant(n_t, sv)
+            for _ in range(2):
+                flush.zero_()
+                ctx.detect_jobs([tjob], prm)
+            torch.cuda.synchronize()
+            tv, sv_ms = [], []
+            for i in range(args.steps):
+                flush.zero_()
+                starts[i].record(stream)
+                ctx.detect_jobs([tjob], prm)
+                ends[i].record(stream)
+                sv_ms.append(ctx.stage_times()[1])
+            torch.cuda.synchronize()
+            tv = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+            ctx.set_solver_variant(n_t, variant)
+            symv = tout["sym"].cpu().numpy()
+            tc[key] = {"ms_per_step": statistics.mean(tv), "value": world * P / (statistics.mean(tv) / 1e3),
+                       "solve_ms": statistics.mean(sv_ms), "speedup_vs_exact": ms_per_step / statistics.mean(tv),
+                       "ber": synth.bit_errors(symv, w["sym"], mb) / nbits,
+                       "frac_problems_identical": float(np.mean(np.all(symv == sym, axis=1))),
+                       "algorithmic_tflops": solver_flops(P, n_t, args.runs, args.solver_steps, args.f_mvm) /
+                       (statistics.mean(sv_ms) / 1e3) / 1e12, "shape": label}
+        tc["device_errors"] = ctx.device_errors()
 
     # the batched persistent launch (fused build + anneal per warp, replayed
     # from a CUDA graph) on the same slot

@@ -320,7 +320,10 @@ mmgap_status mmgap_set_timing(mmgap_ctx* ctx, int enable);
 mmgap_status mmgap_stage_times(mmgap_ctx* ctx, float ms_out[4], int* n_chunks_out);
 
 /* Device-side error word of this context (bit 0: a channel index outside
- * [0, n_chan) was met; the problem was computed as all-zero couplings).
+ * [0, n_chan) was met; the problem was computed as all-zero couplings;
+ * bit 1: a wait of solver shape 8 on its tensor-core product expired; the
+ * problems of that CTA returned their guesses with every anneal counted as
+ * diverged).
  * Synchronises the device; clears the word if `clear` is non-zero. */
 mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
 
@@ -342,8 +345,11 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
  * accumulation; about 2^-21 of sum |A||u| from the FP32 field), for n_t in
  * {8, 16} (MMGAP_EUNSUPPORTED otherwise); shape 7 is the same refresh with
  * two threads per anneal (half the registers per thread; b^T u summed as two
- * halves, so not bit-identical to shape 5 either).  The autotuner never
- * picks 5 or 7.
+ * halves, so not bit-identical to shape 5 either).  Shape 8 forms the same
+ * FP16-split product with tcgen05 MMAs (Blackwell fifth-generation tensor
+ * cores): CTAs of 128 anneals (128 / runs problems), the product's FP32
+ * accumulator in tensor memory, read back by each anneal's thread; n_t in
+ * {8, 16} (runs = 96 runs shape 5).  The autotuner never picks 5, 7 or 8.
  * The choice is per context and applies to detect, precode and solve_ising
  * calls.
  */

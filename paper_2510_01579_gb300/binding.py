@@ -127,7 +127,7 @@ ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_l
                "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy")
 
 VARIANT_NAMES = {0: "default", 1: "plain", 2: "tpa1", 3: "tpa1-packed", 4: "tpa2-packed", 5: "tensor-core",
-                 6: "pair-packed", 7: "tensor-core-tpa2"}
+                 6: "pair-packed", 7: "tensor-core-tpa2", 8: "tcgen05"}
 
 
 @dataclasses.dataclass

@@ -60,7 +60,7 @@ int mmgap::resolve_variant(int n_t, int f_mvm, int requested) {
     if (!tuned) return kVariantPlain;
     if (requested <= kVariantAuto || requested >= kVariantCount)  // the measured fastest exact shape
         return n_t == 16 ? kVariantPairPacked : kVariantTpa1Packed;
-    if ((requested == kVariantTensorCore || requested == kVariantTensorCore2) && n_t == 4) return kVariantTpa1Packed;
+    if (variant_tensor_core(requested) && n_t == 4) return kVariantTpa1Packed;
     return requested;
 }
 
@@ -521,6 +521,7 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     if (level_max < 0 || (level_max > 0 && !g)) return fail(ctx, MMGAP_EINVAL, "level_max needs g");
     CurrentDevice cd(ctx->device);
     SolveArgs a{};
+    a.err = ctx->dev_err;
     a.Aq = A_q;
     a.hq = h_q;
     a.g = g;
@@ -629,6 +630,7 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
             if (e != cudaSuccess) return cuda_fail(ctx, e, "build_detect launch");
             if ((st = timing_mark(ctx, 1, s)) != MMGAP_OK) return st;
             SolveArgs a{};
+            a.err = ctx->dev_err;
             a.Aq = Aq;
             a.hq = hq;
             a.g = g;
@@ -711,6 +713,7 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
             if (e != cudaSuccess) return cuda_fail(ctx, e, "vpp_build launch");
             if ((st = timing_mark(ctx, 1, s)) != MMGAP_OK) return st;
             SolveArgs a{};
+            a.err = ctx->dev_err;
             a.Aq = Aq;
             a.hq = hq;
             a.g = nullptr;
@@ -827,6 +830,7 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
         b.hq = hq;
         b.Gc_pre = gc ? (J.chan_index ? gc : gc + (size_t)p0 * 2 * J.n_t * J.n_t) : nullptr;
         SolveArgs a{};
+        a.err = ctx->dev_err;
         a.Aq = Aq;
         a.hq = hq;
         a.level_max = (1 << (J.mod_bits >> 1)) - 1;
@@ -902,6 +906,7 @@ mmgap_status mmgap_anneal_spins(mmgap_ctx* ctx, const mmgap_params* params, int 
     if (!A_q || !h_q || !spins_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q, h_q or spins_out");
     CurrentDevice cd(ctx->device);
     SolveArgs a{};
+    a.err = ctx->dev_err;
     a.Aq = A_q;
     a.hq = h_q;
     a.n_problems = n_problems;
@@ -924,7 +929,7 @@ mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant) {
     if (!ctx) return MMGAP_EINVAL;
     if (!nt_supported(n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d", n_t);
     if (variant < 0 || variant >= kVariantCount) return fail(ctx, MMGAP_EINVAL, "variant=%d", variant);
-    if ((variant == kVariantTensorCore || variant == kVariantTensorCore2) && n_t != 8 && n_t != 16)
+    if (variant_tensor_core(variant) && n_t != 8 && n_t != 16)
         return fail(ctx, MMGAP_EUNSUPPORTED, "tensor-core refresh needs n_t 8 or 16");
     ctx->variant[n_t] = variant;
     return MMGAP_OK;
@@ -958,6 +963,7 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     cudaError_t e = launch_random_ising(Aq, hq, n, n_problems, 0x5eedULL, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "random problems");
     SolveArgs a{};
+    a.err = ctx->dev_err;
     a.Aq = Aq;
     a.hq = hq;
     a.n_problems = n_problems;
@@ -973,7 +979,7 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     float best = 1e30f;
     int best_v = kVariantPlain;
     for (int v = kVariantPlain; v < kVariantCount; ++v) {
-        if (ms_out) ms_out[v] = -1.0f;
+        if (ms_out && v < 8) ms_out[v] = -1.0f;  // ms_out has one slot per exact shape (0-7)
         if (!variant_exact(v)) continue;                             // bit-identical shapes only
         if (resolve_variant(n_t, params->f_mvm, v) != v) continue;  // not compiled for this size
         a.variant = v;
@@ -989,7 +995,7 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
             ms = r == 0 ? m : std::min(ms, m);
         }
         if (e != cudaSuccess) break;
-        if (ms_out) ms_out[v] = ms;
+        if (ms_out && v < 8) ms_out[v] = ms;
         if (ms < best) {
             best = ms;
             best_v = v;

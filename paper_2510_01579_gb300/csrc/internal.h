@@ -42,6 +42,7 @@ struct SolveArgs {
     int variant;               // SolverVariant; 0 = the size's default
     int8_t* x_out;             // [P][n] selected lattice point g + 2d, or nullptr
     uint64_t* spins_out;       // [P][runs][2] final sign bits per anneal (plain kernel), or nullptr
+    int* err;                  // device error word (bit 1: a tcgen05 wait expired), or nullptr
 };
 
 // Launch shapes of the solver.  All produce bit-identical results.
@@ -54,14 +55,18 @@ enum SolverVariant : int {
     kVariantTensorCore = 5,  // field refresh on tensor cores (FP16 split, FP32 accumulation): not bit-identical
     kVariantPairPacked = 6,  // tuned kernel, one thread per anneal, refresh shared by lane pairs
     kVariantTensorCore2 = 7, // field refresh on tensor cores, two threads per anneal: not bit-identical
-    kVariantCount = 8
+    kVariantUmma = 8,        // field refresh by tcgen05 UMMA into tensor memory: not bit-identical
+    kVariantCount = 9
 };
 
 // Variant used for n_t users and refresh period f_mvm when `requested` is
 // kVariantAuto or not compiled for that size.
 int resolve_variant(int n_t, int f_mvm, int requested);
 // Shapes whose results are bit-identical to the plain kernel's (the autotuner's candidates).
-constexpr bool variant_exact(int v) { return v != kVariantTensorCore && v != kVariantTensorCore2; }
+constexpr bool variant_exact(int v) {
+    return v != kVariantTensorCore && v != kVariantTensorCore2 && v != kVariantUmma;
+}
+constexpr bool variant_tensor_core(int v) { return !variant_exact(v); }
 
 struct BuildArgs {
     const float* H;            // complex [n_chan][n_r][n_t]

@@ -1,9 +1,11 @@
-"""Tensor-core field refresh (solver launch shape 5).
+"""Tensor-core field refresh (solver launch shapes 5, 7 and 8).
 
 A precision variant of the CIM-CAC solver: the field m = A u of the 32
 anneals of a warp is one mma.sync product with FP16-split operands and FP32
-accumulation, so its results are not bit-identical to the FP32 path's.  What
-is required of it:
+accumulation (shape 5; shape 7 with two threads per anneal), or the same
+product for a CTA's 128 anneals as tcgen05 MMAs with the accumulator in
+tensor memory (shape 8), so its results are not bit-identical to the FP32
+path's.  What is required of it:
   * the selection stays exact: every reported energy is the integer energy of
     the reported offsets (checked with the oracle's energy);
   * over a few steps, where the FP32 path's rounding has not yet been
@@ -36,12 +38,14 @@ def mm():
     ctx.close()
 
 
-@pytest.mark.parametrize("shape", [5, 7])
-@pytest.mark.parametrize("n_t,f,runs", [(8, 1, 32), (8, 2, 64), (16, 2, 32), (16, 1, 128)])
+@pytest.mark.parametrize("shape", [5, 7, 8])
+@pytest.mark.parametrize("n_t,f,runs", [(8, 1, 32), (8, 2, 64), (16, 2, 32), (16, 1, 128), (16, 2, 64),
+                                        (8, 2, 128)])
 def test_short_anneals_agree_and_energies_are_exact(mm, shape, n_t, f, runs):
+    """1,501 problems (a ragged last CTA for shape 8's 128 / runs problems per CTA)."""
     pkg, ctx = mm
     n = 2 * n_t
-    Aq, hq = synth.random_ising(40 + n_t + f, 1500, n)
+    Aq, hq = synth.random_ising(40 + n_t + f, 1501, n)
     prm = pkg.Params.default(steps=7, f_mvm=f, runs=runs)
     res = {}
     for v in (3, shape):
@@ -53,11 +57,36 @@ def test_short_anneals_agree_and_energies_are_exact(mm, shape, n_t, f, runs):
     same = np.all(d3 == d5, axis=1).mean()
     assert same >= 0.99, same
     E5 = res[shape]["E"].cpu().numpy()
-    for p in range(0, 1500, 7):
+    for p in list(range(0, 1501, 7)) + [1499, 1500]:
         assert E5[p] == oracle.energy_q(Aq[p], hq[p], d5[p]), p
+    assert ctx.device_errors() == 0
 
 
-@pytest.mark.parametrize("shape", [5, 7])
+@pytest.mark.parametrize("n_t", [8, 16])
+def test_tcgen05_long_anneals_and_96_runs(mm, n_t):
+    """Shape 8 over full 200-step anneals (every refresh through tensor memory):
+    energies stay exact and no wait expires; 96 anneals (not a divisor of the
+    128-row tile) run shape 5's kernel, bit for bit."""
+    pkg, ctx = mm
+    n = 2 * n_t
+    Aq, hq = synth.random_ising(90 + n_t, 777, n)
+    ctx.set_solver_variant(n_t, 8)
+    r8 = ctx.solve_ising(T(Aq), T(hq), pkg.Params.default(), 4)
+    r96 = ctx.solve_ising(T(Aq), T(hq), pkg.Params.default(runs=96), 4)
+    ctx.set_solver_variant(n_t, 5)
+    r5 = ctx.solve_ising(T(Aq), T(hq), pkg.Params.default(runs=96), 4)
+    ctx.set_solver_variant(n_t, 0)
+    torch.cuda.synchronize()
+    assert ctx.device_errors() == 0
+    d8, E8 = r8["d"].cpu().numpy(), r8["E"].cpu().numpy()
+    for p in range(0, 777, 11):
+        assert E8[p] == oracle.energy_q(Aq[p], hq[p], d8[p]), p
+    assert (E8 <= 0).all()
+    for key in r5:
+        assert torch.equal(r96[key], r5[key]), key
+
+
+@pytest.mark.parametrize("shape", [5, 7, 8])
 @pytest.mark.parametrize("n_t,mb,snr,model,hold", [(16, 4, 16.0, "iid", "subcarrier"), (8, 4, 15.0, "kron", "prb")])
 def test_detection_ber_equals_the_fp32_path(mm, shape, n_t, mb, snr, model, hold):
     """16x16 16-QAM i.i.d. and 8x8 16-QAM Kronecker, 32 anneals x 200 steps:
@@ -89,9 +118,9 @@ def test_detection_ber_equals_the_fp32_path(mm, shape, n_t, mb, snr, model, hold
 
 def test_refused_where_not_built_and_never_autotuned(mm):
     pkg, ctx = mm
-    for shape in (5, 7):
+    for shape in (5, 7, 8):
         with pytest.raises(pkg.MMGaPError) as e:
             ctx.set_solver_variant(4, shape)
         assert e.value.status == 5
     v, ms = ctx.autotune(pkg.Params.default(steps=40), 16, 2048)
-    assert v in (1, 2, 3, 4, 6) and 5 not in ms and 7 not in ms
+    assert v in (1, 2, 3, 4, 6) and 5 not in ms and 7 not in ms and 8 not in ms
