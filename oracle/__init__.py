@@ -453,7 +453,7 @@ _lib.orc_build_direct32.argtypes = [C.c_int, C.c_int, C.c_int, _f32p, _f32p, C.c
 _lib.orc_general_field.argtypes = [C.c_int, _f32p, _f32p, _f32p, _f32p]
 _lib.orc_cac_solve_general.argtypes = [C.c_int, _i16p, _i16p, _nullable(_i8p), C.POINTER(CParams), C.c_uint64,
                                        C.c_uint64, _i8p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                                       C.POINTER(C.c_int32), _nullable(_i32p)]
+                                       C.POINTER(C.c_int32), _nullable(_i32p), _nullable(_f32p)]
 _lib.orc_detect_direct.argtypes = [C.c_int, C.c_int, C.c_int, _f32p, _f32p, C.c_float, C.POINTER(CParams),
                                    C.c_uint64, C.c_uint64, _u8p, _i32p, _i8p, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
@@ -518,21 +518,24 @@ def general_field(Jf, cf, x) -> np.ndarray:
     return mu
 
 
-def cac_solve_general(Jq, cq, s_ref, params: Params, seed, problem, want_energies=False):
+def cac_solve_general(Jq, cq, s_ref, params: Params, seed, problem, want_energies=False, want_states=False):
     N = len(cq)
     s = np.zeros(N, np.int8)
     E, run, nd = C.c_int32(), C.c_int32(), C.c_int32()
     Er = np.zeros(params.runs, np.int32) if want_energies else None
+    xf = np.zeros(params.runs * (N + 1), np.float32) if want_states else None
     sr = None if s_ref is None else np.ascontiguousarray(s_ref, np.int8)
     cp = params.c()
     st = _lib.orc_cac_solve_general(N, np.ascontiguousarray(Jq, np.int16).ravel(), np.ascontiguousarray(cq, np.int16),
                                     sr, C.byref(cp), int(seed), int(problem), s, C.byref(E), C.byref(run),
-                                    C.byref(nd), Er)
+                                    C.byref(nd), Er, xf)
     if st:
         raise ValueError("invalid solver arguments")
     out = dict(s=s, E=E.value, run=run.value, n_div=nd.value)
     if want_energies:
         out["E_runs"] = Er
+    if want_states:
+        out["x_final"] = xf.reshape(params.runs, N + 1)
     return out
 
 

@@ -1552,11 +1552,12 @@ void orc_general_field(int N, const float* Jf, const float* cf, const float* x, 
  * lowest (E, candidate index).
  * Outputs: s_out [N], E_out, run_out (-1: s_ref, or no valid candidate when
  * s_ref is NULL, then s = +1 and E = E(+1)), n_div_out; optional E_runs [R]
- * (INT32_MAX for diverged anneals).
+ * (INT32_MAX for diverged anneals) and x_final [R][N+1] (final amplitudes,
+ * the auxiliary spin last).
  */
 int orc_cac_solve_general(int N, const int16_t* Jq, const int16_t* cq, const int8_t* s_ref, const orc_params* P,
                           uint64_t seed, uint64_t problem, int8_t* s_out, int32_t* E_out, int32_t* run_out,
-                          int32_t* n_div_out, int32_t* E_runs)
+                          int32_t* n_div_out, int32_t* E_runs, float* x_final)
 {
     if (N < 1 || P->runs < 1 || P->steps < 0 || P->f_mvm < 1) return ORC_EINVAL;
     orc_consts C;
@@ -1588,6 +1589,7 @@ int orc_cac_solve_general(int N, const int16_t* Jq, const int16_t* cq, const int
             if (t % P->f_mvm == 0) orc_general_field(N, Jf, cf, x, mu);
             for (int k = 0; k <= N; ++k) euler_spin(&x[k], &eh[k], mu[k], &C);
         }
+        if (x_final) memcpy(x_final + (size_t)r * (N + 1), x, sizeof(float) * (size_t)(N + 1));
         int valid = 1;
         for (int k = 0; k <= N; ++k)
             if (!(fabsf(x[k]) <= P->x_max) || !(eh[k] > 0.0f)) valid = 0;
@@ -1631,7 +1633,7 @@ int orc_detect_direct(int n_r, int n_t, int mod_bits, const float* H, const floa
     int se;
     orc_build_direct32(n_r, n_t, mod_bits, H, y, noise_var, g, NULL, NULL, &se, Jq, cq);
     orc_direct_spins(n_t, mod_bits, g, sref);
-    orc_cac_solve_general(N, Jq, cq, sref, P, seed, problem, s, E, run, n_div, NULL);
+    orc_cac_solve_general(N, Jq, cq, sref, P, seed, problem, s, E, run, n_div, NULL, NULL);
     orc_direct_lattice(n_t, mod_bits, s, x);
     int8_t* zero = (int8_t*)calloc((size_t)n, 1);
     orc_decode_detect(n_t, mod_bits, x, zero, sym);

@@ -114,6 +114,36 @@ def test_general_field_is_the_dense_product():
         assert np.all(np.abs(mu - ref) <= bound)
 
 
+@pytest.mark.parametrize("N,f,steps", [(8, 1, 40), (16, 2, 40), (24, 3, 40), (64, 2, 40), (96, 1, 30)])
+def test_general_trajectory_matches_fp64_euler(N, f, steps):
+    """Short anneals of the general solver equal a forward-Euler integration of
+    Eqs. 10-11 in FP64 written here: the N + 1 amplitudes coupled by
+    [[J, c], [c^T, 0]] (J = J_q 2^-14 with zero diagonal, the field c reaching
+    the spins through the auxiliary spin), the field frozen for f_mvm steps,
+    from the same Philox amplitudes, to 5e-3 relative.  The FP32 rounding the
+    horizon accumulates stays below 8e-4 (96 spins); a flipped c or a halved J
+    miss by more than 5."""
+    Jq, cq = synth.random_ising(800 + N, 1, N)
+    Jq, cq = Jq[0].copy(), cq[0]
+    np.fill_diagonal(Jq, 0)
+    prm = oracle.Params(runs=3, steps=steps, f_mvm=f)
+    r = oracle.cac_solve_general(Jq, cq, None, prm, 9, 4, want_states=True)
+    K = np.zeros((N + 1, N + 1))
+    K[:N, :N] = Jq * 2.0 ** -14
+    K[:N, N] = K[N, :N] = cq * 2.0 ** -14
+    xs = oracle.cac_consts(prm).xs
+    dt, p, a, zeta, eps = prm.dt, prm.p, prm.a, prm.zeta, prm.eps
+    for run in range(3):
+        x = np.array([float(oracle.initial_x(9, 4, run, k, xs)) for k in range(N + 1)])
+        e = np.ones(N + 1)
+        for t in range(steps):
+            if t % f == 0:
+                mu = K @ x
+            x, e = x + dt * ((p - 1) * x - x ** 3 + eps * e * mu), e + dt * (-zeta * (x ** 2 - a) * e)
+        got = r["x_final"][run].astype(np.float64)
+        assert np.all(np.abs(got - x) <= 5e-3 * (np.abs(x) + 1e-3)), run
+
+
 def test_general_anneal_finds_small_ground_states():
     """Random small problems (N = 6): 64 anneals reach the brute-force minimum
     of the exact quantised energy, and the reported energy is that of the

@@ -263,6 +263,39 @@ def test_decoupled_dynamics_closed_form(p):
     assert np.allclose(np.log(e), -0.5 * (intw - 1.0 * T), rtol=3e-2, atol=3e-2)
 
 
+@pytest.mark.parametrize("n,f,steps", [(4, 1, 40), (8, 2, 40), (16, 3, 41), (32, 2, 40), (32, 1, 60)])
+def test_coupled_trajectory_matches_fp64_euler(n, f, steps):
+    """Short coupled anneals: the oracle's FP32 amplitudes after S steps equal a
+    forward-Euler integration of Eqs. 10-11 in FP64 written here from the
+    paper's definitions -- J from the block structure of Eq. 9 / Fig. 5 (the
+    two halves coupled by A, each half's self-coupling with a zero diagonal,
+    the auxiliary spin coupled by b = h), the field J x frozen for f_mvm steps
+    (Sec. 3.2.1), x and e updated together from the old values -- from the same
+    Philox amplitudes, to 5e-4 relative.  The FP32 rounding the horizon
+    accumulates stays below 4e-5; a kept diagonal, a flipped b, a field
+    refreshed one step late or e updated from the new x each miss by > 0.08."""
+    rng = np.random.default_rng(70 + n + f)
+    A = rng.integers(-2 ** 14, 2 ** 14 + 1, (n, n))
+    A = np.triu(A) + np.triu(A, 1).T
+    h = rng.integers(-2 ** 14, 2 ** 14 + 1, n)
+    prm = o.Params(runs=3, steps=steps, f_mvm=f)
+    r = o.cac_solve(A.astype(np.int16), h.astype(np.int16), None, 0, prm, 11, 5, want_states=True)
+    Ad, hd = A * 2.0 ** -14, h * 2.0 ** -14
+    At = Ad - np.diag(np.diag(Ad))
+    J = np.block([[At, Ad, hd[:, None]], [Ad, At, hd[:, None]], [hd[None, :], hd[None, :], np.zeros((1, 1))]])
+    xs = o.cac_consts(prm).xs
+    dt, p, a, zeta, eps = prm.dt, prm.p, prm.a, prm.zeta, prm.eps
+    for run in range(3):
+        x = np.array([float(o.initial_x(11, 5, run, k, xs)) for k in range(2 * n + 1)])
+        e = np.ones(2 * n + 1)
+        for t in range(steps):
+            if t % f == 0:
+                mu = J @ x
+            x, e = x + dt * ((p - 1) * x - x ** 3 + eps * e * mu), e + dt * (-zeta * (x ** 2 - a) * e)
+        got = r["x_final"][run].astype(np.float64)
+        assert np.all(np.abs(got - x) <= 5e-4 * (np.abs(x) + 1e-3)), run
+
+
 # ------------------------------------------------------ energy and selection
 def test_integer_energy_matches_ml_objective():
     """E(d) = d^T G_q d - h_q^T d equals (||z - 2 Hs d||^2 - ||z||^2) 2^14 / (4 sigma)
