@@ -15,8 +15,11 @@ numpy wrappers over ``oracle.c`` (plain single-threaded C):
   integer results (guesses, quantised couplings, spins, symbols) can be
   compared bit for bit.
 
-Parity unpinned: the CIM-CAC trajectory has no worked example in the paper;
-it is pinned by closed forms and identities only (see tests/test_oracle_*).
+The CIM-CAC trajectory has no worked example in the paper.  It is pinned by
+closed forms (eps = 0), the dense-J identity of the half-size field, and, over
+short horizons, by an FP64 forward-Euler integration of Eqs. 10-11 written in
+the tests; beyond those horizons the FP32 trajectory has no independent
+reference (see tests/test_oracle_*).
 """
 from __future__ import annotations
 

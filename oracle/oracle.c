@@ -24,10 +24,12 @@
  * Compile with -ffp-contract=off (no implicit contraction of a*b+c) and without
  * -ffast-math; fmaf()/fma() are the only fused operations.
  *
- * Parity unpinned: the CIM-CAC trajectory itself (Eqs. 10-11 under the forward
- * Euler reading) has no worked example in the paper; it is pinned only through
- * closed forms (eps = 0 decoupled dynamics), the dense-J identity of the
- * half-size coupling field (Fig. 5) and statistical behaviour.
+ * The CIM-CAC trajectory (Eqs. 10-11 under the forward Euler reading) has no
+ * worked example in the paper.  It is pinned by closed forms (eps = 0
+ * decoupled dynamics), the dense-J identity of the half-size coupling field
+ * (Fig. 5), an FP64 integration of Eqs. 10-11 over short anneals (error
+ * bound) and statistical behaviour; beyond short horizons the FP32 trajectory
+ * has no independent reference.
  */
 #include <math.h>
 #include <stdint.h>
