@@ -643,9 +643,20 @@ def run_critical(args):
         out = {"sym": torch.empty((1, n_t), dtype=torch.uint8, device=dev)}
         job = ctx.detect_job(H, y, nv, mb, 11, out, ci)
         r = {}
-        for v in (1, 2, 3, 4):
+        for v in (1, 2, 3, 4, 6, 9, 10):
+            if (v == 9 and n_t < 8) or (v == 10 and n_t < 16):
+                continue
             ctx.set_solver_variant(n_t, v)
             r["mmgap_" + VARIANT_NAMES[v]] = timed(lambda: ctx.detect_jobs([job], prm))
+            # the same call's stages (per-stage CUDA events): builder and solver
+            ctx.set_timing(True)
+            st = []
+            for _ in range(10):
+                ctx.detect_jobs([job], prm)
+                st.append(ctx.stage_times())
+            ctx.set_timing(False)
+            r["mmgap_" + VARIANT_NAMES[v]].update(
+                build_us=statistics.median(s[0] for s in st) * 1e3, solve_us=statistics.median(s[1] for s in st) * 1e3)
         ctx.set_solver_variant(n_t, 0)
         for st in (1, 2):
             r[f"mmgap_e{st}"] = timed(lambda: ctx.detect_e(H, y, nv, mb, prm, 11, stages=st, chan_index=ci))

@@ -329,7 +329,7 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
 
 /*
  * Launch shape of the CIM-CAC solver for n_t users (no counterpart in the
- * paper, which runs one thread per anneal).  Shapes 0-4 and 6 give
+ * paper, which runs one thread per anneal).  Shapes 0-4, 6, 9 and 10 give
  * bit-identical results; they differ only in speed:
  *   0 default for the size (6 for 16 users, 3 for 4 and 8, 1 elsewhere)
  *   1 plain: one thread per anneal, scalar FP32 (the paper's design point)
@@ -338,7 +338,10 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
  *   4 tuned kernel, two threads per anneal (shuffle-gathered field), packed
  *   6 tuned kernel, one thread per anneal, packed, the field refresh shared
  *     by lane pairs (each coupling read once for two anneals)
- * Shapes 2-4 and 6 exist for n_t in {4, 8, 16} with f_mvm in {1, 2};
+ *   9 tuned kernel, four threads per anneal, packed (n_t 8 and 16; 4 runs 4)
+ *  10 tuned kernel, eight threads per anneal, packed (n_t 16; 8 runs 9,
+ *     4 runs 4) -- shapes for latency, when few problems leave SMs idle
+ * Shapes 2-4, 6, 9 and 10 exist for n_t in {4, 8, 16} with f_mvm in {1, 2};
  * elsewhere 1 runs.  Shape 5 is a precision variant, not bit-identical: shape 3 with
  * the coupling field of a warp's 32 anneals computed on the tensor cores
  * (mma.sync m16n8k16, couplings and u split into FP16 pairs, FP32
@@ -355,19 +358,19 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
  */
 mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant);
 
-/* The shape (1-4) a call with n_t users and refresh period f_mvm would run. */
+/* The shape a call with n_t users and refresh period f_mvm would run. */
 mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* variant_out);
 
 /*
- * Autotuner: time every compiled bit-identical solver shape (1-4, 6) for
+ * Autotuner: time every compiled bit-identical solver shape (1-4, 6, 9, 10) for
  * n_t users on n_problems random Q14 problems (0 = 8192; clamped to the
  * workspace) with *params, keep the fastest for this context and return it
  * in *variant_out.
- * ms_out (may be NULL, else 8 floats) receives [0] the best time and [v] the
+ * ms_out (may be NULL, else 16 floats) receives [0] the best time and [v] the
  * time of shape v (-1 if not compiled or not bit-identical).  Synchronises the device; uses the workspace.
  */
 mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
-                            float ms_out[8]);
+                            float ms_out[16]);
 
 /*
  * Batched persistent launch of mixed-size uplink jobs (no counterpart in the

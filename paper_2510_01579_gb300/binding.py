@@ -127,7 +127,7 @@ ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_l
                "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy")
 
 VARIANT_NAMES = {0: "default", 1: "plain", 2: "tpa1", 3: "tpa1-packed", 4: "tpa2-packed", 5: "tensor-core",
-                 6: "pair-packed", 7: "tensor-core-tpa2", 8: "tcgen05"}
+                 6: "pair-packed", 7: "tensor-core-tpa2", 8: "tcgen05", 9: "tpa4-packed", 10: "tpa8-packed"}
 
 
 @dataclasses.dataclass
@@ -421,10 +421,10 @@ class Context:
     def autotune(self, params: Params, n_t: int, n_problems: int = 0):
         """Time every compiled launch shape, keep the fastest; returns (shape, {shape: ms})."""
         v = C.c_int()
-        ms = (C.c_float * 8)()
+        ms = (C.c_float * 16)()
         cp = params._c()
         self._raise(_lib.mmgap_autotune(self._h, C.byref(cp), n_t, n_problems, C.byref(v), ms))
-        return v.value, {i: ms[i] for i in range(1, 8) if ms[i] >= 0}
+        return v.value, {i: ms[i] for i in range(1, 16) if ms[i] >= 0}
 
     def set_timing(self, enable: bool):
         self._raise(_lib.mmgap_set_timing(self._h, 1 if enable else 0))

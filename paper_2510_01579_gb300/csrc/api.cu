@@ -61,6 +61,9 @@ int mmgap::resolve_variant(int n_t, int f_mvm, int requested) {
     if (requested <= kVariantAuto || requested >= kVariantCount)  // the measured fastest exact shape
         return n_t == 16 ? kVariantPairPacked : kVariantTpa1Packed;
     if (variant_tensor_core(requested) && n_t == 4) return kVariantTpa1Packed;
+    // more threads per anneal need at least 4 rows (one float4 of couplings) per thread
+    if (requested == kVariantTpa8Packed && n_t < 16) return n_t == 8 ? kVariantTpa4Packed : kVariantTpa2Packed;
+    if (requested == kVariantTpa4Packed && n_t < 8) return kVariantTpa2Packed;
     return requested;
 }
 
@@ -943,7 +946,7 @@ mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* v
 }
 
 mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
-                            float ms_out[8]) {
+                            float ms_out[16]) {
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
@@ -978,8 +981,10 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     cudaEventCreate(&t1);
     float best = 1e30f;
     int best_v = kVariantPlain;
+    static_assert(kVariantCount <= 16, "mmgap_autotune reports 16 slots");
+    if (ms_out)
+        for (int v = 0; v < 16; ++v) ms_out[v] = -1.0f;
     for (int v = kVariantPlain; v < kVariantCount; ++v) {
-        if (ms_out && v < 8) ms_out[v] = -1.0f;  // ms_out has one slot per exact shape (0-7)
         if (!variant_exact(v)) continue;                             // bit-identical shapes only
         if (resolve_variant(n_t, params->f_mvm, v) != v) continue;  // not compiled for this size
         a.variant = v;
@@ -995,7 +1000,7 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
             ms = r == 0 ? m : std::min(ms, m);
         }
         if (e != cudaSuccess) break;
-        if (ms_out && v < 8) ms_out[v] = ms;
+        if (ms_out) ms_out[v] = ms;
         if (ms < best) {
             best = ms;
             best_v = v;

@@ -56,7 +56,9 @@ enum SolverVariant : int {
     kVariantPairPacked = 6,  // tuned kernel, one thread per anneal, refresh shared by lane pairs
     kVariantTensorCore2 = 7, // field refresh on tensor cores, two threads per anneal: not bit-identical
     kVariantUmma = 8,        // field refresh by tcgen05 UMMA into tensor memory: not bit-identical
-    kVariantCount = 9
+    kVariantTpa4Packed = 9,  // tuned kernel, four threads per anneal, packed FP32 pairs (n_t 8, 16)
+    kVariantTpa8Packed = 10, // tuned kernel, eight threads per anneal, packed FP32 pairs (n_t 16)
+    kVariantCount = 11
 };
 
 // Variant used for n_t users and refresh period f_mvm when `requested` is

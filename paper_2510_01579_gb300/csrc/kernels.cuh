@@ -3080,6 +3080,14 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
         case kVariantTpa1: cac_solve_tuned_kernel<NT, F, 1, false><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa1Packed: cac_solve_tuned_kernel<NT, F, 1, true><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa2Packed: cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a); break;
+        case kVariantTpa4Packed:  // (smaller sizes are resolved to shape 4 before launch)
+            if constexpr (NT >= 8) cac_solve_tuned_kernel<NT, F, 4, true><<<a.n_problems, 4 * runs, 0, s>>>(a);
+            else cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
+            break;
+        case kVariantTpa8Packed:
+            if constexpr (NT >= 16) cac_solve_tuned_kernel<NT, F, 8, true><<<a.n_problems, 8 * runs, 0, s>>>(a);
+            else cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
+            break;
         case kVariantPairPacked:
             cac_solve_tuned_kernel<NT, F, 1, true, false, true><<<a.n_problems, runs, 0, s>>>(a);
             break;
