@@ -331,7 +331,9 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
  * Launch shape of the CIM-CAC solver for n_t users (no counterpart in the
  * paper, which runs one thread per anneal).  Shapes 0-4, 6, 9 and 10 give
  * bit-identical results; they differ only in speed:
- *   0 default for the size (6 for 16 users, 3 for 4 and 8, 1 elsewhere)
+ *   0 default for the size and the call: calls of at most one problem per
+ *     SM run 10 (16 users) or 9 (8 users), of at most two per SM 4, larger
+ *     calls 6 (16 users) or 3 (4 and 8 users; 4 users always), 1 elsewhere
  *   1 plain: one thread per anneal, scalar FP32 (the paper's design point)
  *   2 tuned kernel, one thread per anneal, scalar FP32
  *   3 tuned kernel, one thread per anneal, packed FP32 pairs
@@ -358,7 +360,8 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
  */
 mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant);
 
-/* The shape a call with n_t users and refresh period f_mvm would run. */
+/* The shape a large call (more than two problems per SM) with n_t users and
+ * refresh period f_mvm would run. */
 mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* variant_out);
 
 /*

@@ -27,6 +27,7 @@ struct mmgap_ctx {
     std::vector<cudaEvent_t> events;  // 4 per chunk: start, built, solved, output
     int n_chunks = 0;
     int variant[17] = {};             // solver launch shape per n_t (0 = default)
+    int n_sm = 0;                     // SMs of the device
 };
 
 namespace mmgap {
@@ -55,11 +56,19 @@ cudaError_t launch_random_ising(int16_t* Aq, int16_t* hq, int n, int n_problems,
 }
 }  // namespace mmgap
 
-int mmgap::resolve_variant(int n_t, int f_mvm, int requested) {
+int mmgap::resolve_variant(int n_t, int f_mvm, int requested, int n_problems, int n_sm) {
     const bool tuned = (n_t == 4 || n_t == 8 || n_t == 16) && (f_mvm == 1 || f_mvm == 2);
     if (!tuned) return kVariantPlain;
-    if (requested <= kVariantAuto || requested >= kVariantCount)  // the measured fastest exact shape
-        return n_t == 16 ? kVariantPairPacked : kVariantTpa1Packed;
+    if (requested <= kVariantAuto || requested >= kVariantCount) {
+        // Measured on GB300 (detect of P problems, 32 x 200 anneals): up to one problem per SM,
+        // 8 (16 users) or 4 (8 users) threads per anneal are 1.5x faster than the throughput
+        // shapes; up to two per SM, two threads per anneal; beyond that the throughput shapes.
+        if (n_problems >= 0 && n_sm > 0 && n_t >= 8) {
+            if (n_problems <= n_sm) return n_t == 16 ? kVariantTpa8Packed : kVariantTpa4Packed;
+            if (n_problems <= 2 * n_sm) return kVariantTpa2Packed;
+        }
+        return n_t == 16 ? kVariantPairPacked : kVariantTpa1Packed;  // the measured fastest for large calls
+    }
     if (variant_tensor_core(requested) && n_t == 4) return kVariantTpa1Packed;
     // more threads per anneal need at least 4 rows (one float4 of couplings) per thread
     if (requested == kVariantTpa8Packed && n_t < 16) return n_t == 8 ? kVariantTpa4Packed : kVariantTpa2Packed;
@@ -389,6 +398,10 @@ mmgap_status mmgap_create(mmgap_ctx** out, int device, size_t workspace_bytes) {
     if (!ctx) return MMGAP_ENOMEM;
     ctx->device = device;
     CurrentDevice cd(device);
+    if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->n_sm = 0;  // unknown: the throughput shapes for every call
+    }
     ctx->ws_bytes = workspace_bytes ? workspace_bytes : ((size_t)256 << 20);
     if (cudaMalloc(&ctx->ws, ctx->ws_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -525,6 +538,7 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     CurrentDevice cd(ctx->device);
     SolveArgs a{};
     a.err = ctx->dev_err;
+    a.n_sm = ctx->n_sm;
     a.Aq = A_q;
     a.hq = h_q;
     a.g = g;
@@ -634,6 +648,7 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
             if ((st = timing_mark(ctx, 1, s)) != MMGAP_OK) return st;
             SolveArgs a{};
             a.err = ctx->dev_err;
+            a.n_sm = ctx->n_sm;
             a.Aq = Aq;
             a.hq = hq;
             a.g = g;
@@ -717,6 +732,7 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
             if ((st = timing_mark(ctx, 1, s)) != MMGAP_OK) return st;
             SolveArgs a{};
             a.err = ctx->dev_err;
+            a.n_sm = ctx->n_sm;
             a.Aq = Aq;
             a.hq = hq;
             a.g = nullptr;
@@ -834,6 +850,7 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
         b.Gc_pre = gc ? (J.chan_index ? gc : gc + (size_t)p0 * 2 * J.n_t * J.n_t) : nullptr;
         SolveArgs a{};
         a.err = ctx->dev_err;
+        a.n_sm = ctx->n_sm;
         a.Aq = Aq;
         a.hq = hq;
         a.level_max = (1 << (J.mod_bits >> 1)) - 1;
@@ -910,6 +927,7 @@ mmgap_status mmgap_anneal_spins(mmgap_ctx* ctx, const mmgap_params* params, int 
     CurrentDevice cd(ctx->device);
     SolveArgs a{};
     a.err = ctx->dev_err;
+    a.n_sm = ctx->n_sm;
     a.Aq = A_q;
     a.hq = h_q;
     a.n_problems = n_problems;
@@ -967,6 +985,7 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     if (e != cudaSuccess) return cuda_fail(ctx, e, "random problems");
     SolveArgs a{};
     a.err = ctx->dev_err;
+    a.n_sm = ctx->n_sm;
     a.Aq = Aq;
     a.hq = hq;
     a.n_problems = n_problems;

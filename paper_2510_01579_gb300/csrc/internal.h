@@ -43,6 +43,7 @@ struct SolveArgs {
     int8_t* x_out;             // [P][n] selected lattice point g + 2d, or nullptr
     uint64_t* spins_out;       // [P][runs][2] final sign bits per anneal (plain kernel), or nullptr
     int* err;                  // device error word (bit 1: a tcgen05 wait expired), or nullptr
+    int n_sm;                  // SMs of the device (0: unknown); picks latency shapes for small calls
 };
 
 // Launch shapes of the solver.  All produce bit-identical results.
@@ -62,8 +63,10 @@ enum SolverVariant : int {
 };
 
 // Variant used for n_t users and refresh period f_mvm when `requested` is
-// kVariantAuto or not compiled for that size.
-int resolve_variant(int n_t, int f_mvm, int requested);
+// kVariantAuto or not compiled for that size.  With the call's problem count
+// and the device's SM count known, kVariantAuto takes the latency shapes when
+// the call leaves SMs idle.
+int resolve_variant(int n_t, int f_mvm, int requested, int n_problems = -1, int n_sm = 0);
 // Shapes whose results are bit-identical to the plain kernel's (the autotuner's candidates).
 constexpr bool variant_exact(int v) {
     return v != kVariantTensorCore && v != kVariantTensorCore2 && v != kVariantUmma;

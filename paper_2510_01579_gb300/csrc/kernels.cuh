@@ -3121,7 +3121,7 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
 template <int NT>
 cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
-    const int v = a.spins_out ? (int)kVariantPlain : resolve_variant(NT, a.f_mvm, a.variant);
+    const int v = a.spins_out ? (int)kVariantPlain : resolve_variant(NT, a.f_mvm, a.variant, a.n_problems, a.n_sm);
     if (a.f_mvm == 2) return launch_tuned<NT, 2>(a, runs, v, s);
     if (a.f_mvm == 1) return launch_tuned<NT, 1>(a, runs, v, s);
     cac_solve_kernel<NT, 0><<<a.n_problems, runs, 0, s>>>(a);

@@ -369,6 +369,30 @@ def test_solver_shapes_bit_exact(mm, nt, variant, f_mvm, steps, runs):
     assert np.array_equal(got["ndiv"].cpu().numpy(), ref["n_div"])
 
 
+@pytest.mark.parametrize("nt,P", [(16, 5), (16, 200), (16, 400), (8, 5), (8, 200), (8, 400)])
+def test_default_shape_by_call_size_is_bit_identical(mm, nt, P):
+    """The default shape depends on the call's size (latency shapes when SMs
+    would idle); every choice gives the bits of the throughput shape and,
+    on sampled problems, the oracle's."""
+    pkg, ctx = mm
+    w = synth.uplink(650 + nt + P, nt, nt, 4, n_sub=P, n_sym=1, snr_db=14.0)
+    prm = pkg.Params.default(steps=60)
+    ctx.set_solver_variant(nt, 0)
+    auto = _detect(ctx, w, prm, 21)
+    ctx.set_solver_variant(nt, 6 if nt == 16 else 3)
+    try:
+        fixed = _detect(ctx, w, prm, 21)
+    finally:
+        ctx.set_solver_variant(nt, 0)
+    assert np.array_equal(auto["sym"], fixed["sym"]) and np.array_equal(auto["energy"], fixed["energy"])
+    for p in (0, P // 2, P - 1):
+        c = int(w["chan_index"][p])
+        bld = oracle.build_detect32(w["H"][c], w["y"][p], w["noise_var"][p], 4)
+        r = oracle.cac_solve(bld["Aq"], bld["hq"], bld["g"], 3, oparams(prm), 21, p)
+        assert np.array_equal(auto["sym"][p], oracle.decode_detect(nt, 4, bld["g"], r["d"])), p
+        assert auto["energy"][p] == r["E"], p
+
+
 def test_autotuner_picks_a_compiled_shape(mm):
     pkg, _ = mm
     with pkg.Context(0) as ctx:
