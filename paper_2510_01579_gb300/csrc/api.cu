@@ -475,6 +475,7 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear) {
 
 mmgap_status mmgap_build_detect(mmgap_ctx* ctx, const mmgap_detect_job* job, int16_t* A_q_out, int16_t* h_q_out,
                                 int8_t* g_out, float* G_out, float* h_out, int32_t* sigma_exp_out, void* stream) {
+    NvtxRange nvtx_range("mmgap_build_detect");
     if (!ctx) return MMGAP_EINVAL;
     if (!job) return fail(ctx, MMGAP_EINVAL, "job is NULL");
     mmgap_status st = check_detect_job(ctx, *job, false);
@@ -526,6 +527,7 @@ mmgap_status mmgap_build_detect(mmgap_ctx* ctx, const mmgap_detect_job* job, int
 mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n, int n_problems, const int16_t* A_q,
                                const int16_t* h_q, const int8_t* g, int level_max, uint64_t seed, int8_t* d_out,
                                int32_t* E_out, int32_t* run_out, int32_t* ndiv_out, void* stream) {
+    NvtxRange nvtx_range("mmgap_solve_ising");
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
@@ -563,6 +565,7 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
 mmgap_status mmgap_solve_general(mmgap_ctx* ctx, const mmgap_params* params, int N, int n_problems,
                                  const int16_t* J_q, const int16_t* c_q, const int8_t* s_ref, uint64_t seed,
                                  int8_t* s_out, int32_t* E_out, int32_t* run_out, int32_t* ndiv_out, void* stream) {
+    NvtxRange nvtx_range("mmgap_solve_general");
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
@@ -593,6 +596,7 @@ mmgap_status mmgap_solve_general(mmgap_ctx* ctx, const mmgap_params* params, int
 
 mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job* jobs, int n_jobs,
                           void* stream) {
+    NvtxRange nvtx_range("mmgap_detect");
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
@@ -682,6 +686,7 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
 
 mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_precode_job* jobs, int n_jobs,
                            void* stream) {
+    NvtxRange nvtx_range("mmgap_precode");
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
@@ -775,6 +780,7 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
 
 mmgap_status mmgap_vpp_inverse(mmgap_ctx* ctx, int n_u, int n_t, int n_chan, const float* H, int inv_precision,
                                double* Q_out, int32_t* status_out, void* stream) {
+    NvtxRange nvtx_range("mmgap_vpp_inverse");
     if (!ctx) return MMGAP_EINVAL;
     if (!nt_supported(n_u)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_u=%d: supported 1, 2, 3, 4, 8, 16", n_u);
     if (n_t < n_u || n_t > kMaxNr) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d out of [n_u, %d]", n_t, kMaxNr);
@@ -799,6 +805,7 @@ mmgap_status mmgap_vpp_inverse(mmgap_ctx* ctx, int n_u, int n_t, int n_chan, con
 
 mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mmgap_detect_job* job, int stages,
                             int32_t* best_out, float* obj_out, int8_t* cand_out, void* stream) {
+    NvtxRange nvtx_range("mmgap_detect_e");
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
@@ -916,6 +923,7 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
 
 mmgap_status mmgap_anneal_spins(mmgap_ctx* ctx, const mmgap_params* params, int n, int n_problems, const int16_t* A_q,
                                 const int16_t* h_q, uint64_t seed, uint64_t* spins_out, void* stream) {
+    NvtxRange nvtx_range("mmgap_anneal_spins");
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
@@ -965,6 +973,7 @@ mmgap_status mmgap_get_solver_variant(mmgap_ctx* ctx, int n_t, int f_mvm, int* v
 
 mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t, int n_problems, int* variant_out,
                             float ms_out[16]) {
+    NvtxRange nvtx_range("mmgap_autotune");
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;

@@ -487,6 +487,7 @@ mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_param
 }
 
 mmgap_status mmgap_batch_run(mmgap_batch* b, int use_graph, void* stream) {
+    NvtxRange nvtx_range("mmgap_batch_run");
     if (!b) return MMGAP_EINVAL;
     int prev = -1;
     cudaGetDevice(&prev);

@@ -84,6 +84,7 @@ bool nt_ok(int nt) { return nt == 1 || nt == 2 || nt == 3 || nt == 4 || nt == 8 
 extern "C" {
 
 mmgap_status mmgap_detect_static(const mmgap_params* params, const mmgap_detect_job* job, void* stream) {
+    NvtxRange nvtx_range("mmgap_detect_static");
     if (!params || !job) return MMGAP_EINVAL;
     const mmgap_params& P = *params;
     if (!(P.runs == 32 || P.runs == 64 || P.runs == 96 || P.runs == 128)) return MMGAP_EUNSUPPORTED;

@@ -5,8 +5,19 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace mmgap {
+
+// NVTX range over one library call (visible in Nsight timelines; a no-op
+// without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 // Derived constants of the Euler discretisation of Eqs. 10-11, each rounded
 // once to FP32 from a double expression of the float parameters.

@@ -180,9 +180,12 @@ void dispatch_loop(mmgap_server* s) {
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return group[a].n_t() > group[b].n_t(); });
         cudaError_t e = cudaSuccess;
-        if (L.runner.stage(group.data(), order.data(), (int)group.size()) != 0) e = cudaErrorInvalidValue;
-        if (e == cudaSuccess) e = L.runner.run(s->params, L.stream, s->use_graph);
-        if (e == cudaSuccess) e = cudaLaunchHostFunc(L.stream, on_group_done, new Callback{s, li});
+        {
+            NvtxRange nvtx_range("mmgap_server_group");
+            if (L.runner.stage(group.data(), order.data(), (int)group.size()) != 0) e = cudaErrorInvalidValue;
+            if (e == cudaSuccess) e = L.runner.run(s->params, L.stream, s->use_graph);
+            if (e == cudaSuccess) e = cudaLaunchHostFunc(L.stream, on_group_done, new Callback{s, li});
+        }
         lock.lock();
         if (e != cudaSuccess) {
             fprintf(stderr, "mmgap_server: launch failed: %s\n", cudaGetErrorString(e));
