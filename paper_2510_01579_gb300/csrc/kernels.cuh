@@ -1315,7 +1315,9 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
 // thread writes its anneal's 2^5 u (u = x1 + x2, split into an FP16 pair) as
 // one row of U^T in shared memory; one thread issues D = U^T C^T with C the
 // PP problems' couplings c 2^-14 (an exact FP16 pair) stacked along N, so
-// N = PP n and the cross-problem blocks of D are computed but never read.
+// N = PP n and the cross-problem blocks of D are computed but never read --
+// unless the tile's problems carry identical couplings (one channel), when
+// one C serves all of them and N = n.
 // D = Uh Cl + Ul Ch + Uh Ch accumulates in FP32 in tensor memory (TMEM); its
 // row r is anneal r, and one tcgen05.ld hands each thread its own row -- the
 // field m of its problem's n columns -- with no shared-memory round trip.
@@ -1607,8 +1609,13 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
         const int q = e / n, i = e % n;
         snd[e] = -mulrn(mulrn((float)sAq[(q * n + i) * n + i], 0x1p-14f), k.ce);
     }
+    // A tile whose problems carry bitwise-identical couplings (one channel, one
+    // normaliser: the common case when a channel serves consecutive problems)
+    // multiplies by one C: N = n instead of PP n, every warp reading columns 0..n-1.
+    int differ = 0;
+    for (int e = tid; e < (PP - 1) * n * n; e += 128) differ |= sAq[n * n + e] != sAq[e % (n * n)];
     tc05_fence_before();
-    __syncthreads();
+    const bool shared_c = __syncthreads_or(differ) == 0;
     tc05_fence_after();
     const uint32_t tmem = tmem_slot;
 
@@ -1638,8 +1645,8 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
     uint8_t* su_l = usm + L.off_ul();
     const uint32_t a_h = smem_u32(su_h), a_l = smem_u32(su_l);
     const uint32_t c_h = smem_u32(usm + L.off_ch()), c_l = smem_u32(usm + L.off_cl());
-    const uint32_t idesc = umma_idesc_f16(N);
-    const uint32_t my_cols = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(pl * n);
+    const uint32_t idesc = umma_idesc_f16(shared_c ? n : N);
+    const uint32_t my_cols = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(shared_c ? 0 : pl * n);
     const float mscale = mulrn(k.ce, 0x1p-5f);  // eps dt, and the 2^5 of u
     const float* shp = sh + pl * n;
     const float* sndp = snd + pl * n;

@@ -62,6 +62,31 @@ def test_short_anneals_agree_and_energies_are_exact(mm, shape, n_t, f, runs):
     assert ctx.device_errors() == 0
 
 
+@pytest.mark.parametrize("n_t,runs", [(8, 32), (16, 32), (16, 64)])
+def test_tcgen05_shared_couplings(mm, n_t, runs):
+    """Shape 8 on problems whose couplings repeat in runs of 6 (a channel serving
+    consecutive problems; fields differ): tiles inside a run multiply by one C,
+    tiles across runs by the stacked C's; both agree with the FP32 path over
+    short anneals and report exact energies."""
+    pkg, ctx = mm
+    n = 2 * n_t
+    Aq, hq = synth.random_ising(120 + n_t + runs, 1203, n)
+    Aq = np.ascontiguousarray(Aq[(np.arange(1203) // 6) * 6])
+    prm = pkg.Params.default(steps=7, runs=runs)
+    res = {}
+    for v in (3, 8):
+        ctx.set_solver_variant(n_t, v)
+        res[v] = ctx.solve_ising(T(Aq), T(hq), prm, 12)
+    ctx.set_solver_variant(n_t, 0)
+    torch.cuda.synchronize()
+    d3, d8 = res[3]["d"].cpu().numpy(), res[8]["d"].cpu().numpy()
+    assert np.all(d3 == d8, axis=1).mean() >= 0.99
+    E8 = res[8]["E"].cpu().numpy()
+    for p in list(range(0, 1203, 5)) + [1202]:
+        assert E8[p] == oracle.energy_q(Aq[p], hq[p], d8[p]), p
+    assert ctx.device_errors() == 0
+
+
 @pytest.mark.parametrize("n_t", [8, 16])
 def test_tcgen05_long_anneals_and_96_runs(mm, n_t):
     """Shape 8 over full 200-step anneals (every refresh through tensor memory):
