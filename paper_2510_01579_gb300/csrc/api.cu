@@ -981,7 +981,7 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     const int n = 2 * n_t;
     if (n_problems <= 0) n_problems = 8192;
     const size_t per = (size_t)n * n * 2 + (size_t)n * 2 + (size_t)n + 32;
-    const size_t cap = (ctx->ws_bytes - 4 * kAlign) / per;
+    const size_t cap = ctx->ws_bytes > 4 * kAlign ? (ctx->ws_bytes - 4 * kAlign) / per : 0;
     if (cap < 1) return fail(ctx, MMGAP_ENOMEM, "workspace too small for autotuning");
     if ((size_t)n_problems > cap) n_problems = (int)cap;
     CurrentDevice cd(ctx->device);
@@ -1004,9 +1004,11 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     a.k = euler_consts(*params);
     a.d_out = d;
     a.E_out = E;
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) {
+        if (t0) cudaEventDestroy(t0);
+        return cuda_fail(ctx, e, "cudaEventCreate");
+    }
     float best = 1e30f;
     int best_v = kVariantPlain;
     static_assert(kVariantCount <= 16, "mmgap_autotune reports 16 slots");
