@@ -1184,6 +1184,8 @@ def main():
             tv = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
             ctx.set_solver_variant(n_t, variant)
             symv = tout["sym"].cpu().numpy()
+            if sv == 8:
+                sym_tcgen05 = symv.copy()
             tc[key] = {"ms_per_step": statistics.mean(tv), "value": world * P / (statistics.mean(tv) / 1e3),
                        "solve_ms": statistics.mean(sv_ms), "speedup_vs_exact": ms_per_step / statistics.mean(tv),
                        "ber": synth.bit_errors(symv, w["sym"], mb) / nbits,
@@ -1198,11 +1200,15 @@ def main():
     if not args.no_batch:
         from paper_2510_01579_gb300 import Batch
         batched = {}
-        for mode, persistent in (("grid", False), ("persistent", True)):
+        modes = [("grid", False, False), ("persistent", True, False)]
+        if tc is not None:  # the tcgen05 tiles (precision variant): equal to per-job shape 8
+            modes.append(("tensor_core", False, True))
+        for mode, persistent, tcm in modes:
             bout = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
                     "energy": torch.empty(P, dtype=torch.int32, device=dev)}
             bjob = ctx.detect_job(H, y, nv, mb, 77, bout, ci)
-            with Batch(local, prm, [bjob], keepalive=(H, y, nv, ci, bout), persistent=persistent) as batch:
+            with Batch(local, prm, [bjob], keepalive=(H, y, nv, ci, bout), persistent=persistent,
+                       tensor_core=tcm) as batch:
                 for _ in range(args.warmup):
                     flush.zero_()
                     batch.run(use_graph=True)
@@ -1214,7 +1220,7 @@ def main():
                     ends[i].record(stream)
                 torch.cuda.synchronize()
                 bt = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
-            if not torch.equal(bout["sym"].cpu(), torch.from_numpy(sym)):
+            if not torch.equal(bout["sym"].cpu(), torch.from_numpy(sym_tcgen05 if tcm else sym)):
                 raise RuntimeError("batched and per-job paths disagree")
             bsrt = sorted(bt)
             batched[mode] = {"ms_per_step": statistics.mean(bt), "value": world * P / (statistics.mean(bt) / 1e3),

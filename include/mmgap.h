@@ -397,9 +397,9 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
  */
 typedef struct mmgap_batch mmgap_batch;
 #define MMGAP_BATCH_PERSISTENT 1 /* flags: persistent solver warps on an atomic counter (else one CTA per problem) */
-#define MMGAP_BATCH_TENSOR_CORE 2 /* flags: tensor-core field refresh for 8 and 16 users (solver shape 5: a
-                                     precision variant, results as mmgap_detect with that shape; implies
-                                     one CTA per problem) */
+#define MMGAP_BATCH_TENSOR_CORE 2 /* flags: tcgen05 field refresh for 8 and 16 users (solver shape 8: a
+                                     precision variant, results as mmgap_detect with that shape; 128-thread
+                                     CTAs over tiles of 4 problems of one job; not persistent) */
 mmgap_status mmgap_batch_create(mmgap_batch** batch, int device, const mmgap_params* params,
                                 const mmgap_detect_job* jobs, int n_jobs, int flags);
 mmgap_status mmgap_batch_run(mmgap_batch* batch, int use_graph, void* stream);

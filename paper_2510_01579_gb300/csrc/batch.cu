@@ -36,9 +36,8 @@ int build_floats_for(int nt, int n_r) {
 
 template <int NTMAX>
 const void* solve_ptr(int f, bool persistent, bool tc) {
-    if (tc)  // the tensor-core refresh runs in grid mode (its exchange buffer is per CTA)
-        return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1, true>
-                      : (const void*)batch_solve_grid_kernel<NTMAX, 2, true>;
+    if (tc)  // tcgen05 tiles of 4 problems (solver shape 8)
+        return f == 1 ? (const void*)batch_solve_umma_kernel<NTMAX, 1> : (const void*)batch_solve_umma_kernel<NTMAX, 2>;
     if (persistent)
         return f == 1 ? (const void*)batch_solve_kernel<NTMAX, 1> : (const void*)batch_solve_kernel<NTMAX, 2>;
     return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1> : (const void*)batch_solve_grid_kernel<NTMAX, 2>;
@@ -144,6 +143,22 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
     grid_ = std::max(1, per_sm) * sms;
     build_grid_max_ = std::max(1, bper_sm) * sms;
+    if (tc_) {
+        // the tiles resident on an SM share its 512 TMEM columns (128 per 16-user tile, 64 per
+        // 8-user tile): pad shared memory so that no more of them fit
+        int smem_sm = 0;
+        if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device)) != cudaSuccess)
+            return e;
+        const int ncols = ntmax >= 16 ? 128 : 64;
+        size_t smem = ntmax >= 16 ? batch_umma_bytes<16>() : batch_umma_bytes<8>();
+        const size_t floor_bytes = (size_t)smem_sm / (size_t)(512 / ncols + 1) + 1;
+        if (smem < floor_bytes) smem = (floor_bytes + 127) & ~(size_t)127;
+        umma_smem_ = smem;
+        for (int f : {1, 2})
+            if ((e = cudaFuncSetAttribute(pick_solve(ntmax, f, false, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess)
+                return e;
+    }
     return cudaSuccess;
 }
 
@@ -174,13 +189,14 @@ int BatchRunner::stage(const mmgap_detect_job* jobs, const int* order, int n_job
 int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
     if (n_jobs > capacity_) return -1;
     pre_.clear();
-    long long first = 0;
+    long long first = 0, tiles = 0;
     size_t off = 0;
     for (int i = 0; i < n_jobs; ++i) {
         const GroupJob& G = jobs[order ? order[i] : i];
         BatchJob& B = h_jobs_[i];
         B = BatchJob{};
         B.first = first;
+        B.tile_first = tiles;
         B.b.err = err_word_;
         if (G.det) {
             const mmgap_detect_job& J = *G.det;
@@ -211,6 +227,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
             B.offset_out = J.offset_out;
             B.ndiv_out = J.ndiv_out;
             first += J.n_problems;
+            tiles += (J.n_problems + 3) / 4;
         } else {
             const mmgap_precode_job& J = *G.pre;
             const size_t n = 2 * (size_t)J.n_u, P = (size_t)J.n_problems;
@@ -238,6 +255,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
             B.energy_out = J.energy_out;
             B.ndiv_out = J.ndiv_out;
             first += J.n_problems;
+            tiles += (J.n_problems + 3) / 4;
             if (J.n_problems > 0) pre_.push_back(R);
         }
     }
@@ -246,6 +264,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
     h_head_->pad = 0;
     h_head_->total = first;
     h_head_->counter = 0;
+    h_head_->tiles = tiles;
     return 0;
 }
 
@@ -317,6 +336,11 @@ void BatchRunner::grids(unsigned* build_grid, unsigned* solve_grid) const {
     const long long total = h_head_ ? h_head_->total : capacity_problems_;
     const long long bb = (std::max(1LL, total) + kBuildWarps - 1) / kBuildWarps;
     *build_grid = (unsigned)std::min<long long>(bb, build_grid_max_);
+    if (tc_) {  // tiles of 4 problems, at most one partial tile per job
+        const long long tiles = h_head_ ? h_head_->tiles : (capacity_problems_ + 3) / 4 + capacity_;
+        *solve_grid = (unsigned)std::max(1LL, tiles);
+        return;
+    }
     *solve_grid = persistent_ ? (unsigned)grid_ : (unsigned)std::max(1LL, total);
 }
 
@@ -347,8 +371,8 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3(bg), dim3(kBuildWarps * 32), args, build_smem_, s)) !=
         cudaSuccess)
         return e;
-    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, persistent_, tc_), dim3(sg),
-                            dim3(persistent_ ? kBatchWarps * 32 : 32), args, 0, s);
+    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, persistent_, tc_), dim3(sg), dim3(solve_block()), args,
+                            solve_smem(), s);
 }
 
 cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_graph) {
@@ -409,8 +433,8 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         cudaKernelNodeParams ks{};
         ks.func = (void*)pick_solve(ntmax_, P.f_mvm, persistent_, tc_);
         ks.gridDim = dim3(sg);
-        ks.blockDim = dim3(persistent_ ? kBatchWarps * 32 : 32);
-        ks.sharedMemBytes = 0;
+        ks.blockDim = dim3(solve_block());
+        ks.sharedMemBytes = (unsigned)solve_smem();
         ks.kernelParams = args;
         if ((e = cudaGraphExecKernelNodeSetParams(exec_, solve_node_, &ks)) != cudaSuccess) return e;
     }

@@ -35,8 +35,8 @@ class BatchRunner {
     // coupling scratch; err_word receives out-of-range channel indices.
     // persistent: the solver runs warps that pull problems from an atomic
     // counter; otherwise one 32-thread CTA per problem.  tensor_core: the
-    // field refresh of 8- and 16-user problems on tensor cores (solver shape
-    // 5, a precision variant; grid mode).
+    // field refresh of 8- and 16-user problems as tcgen05 MMAs (solver shape
+    // 8, a precision variant; 128-thread CTAs over 4-problem tiles).
     cudaError_t init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r, int ntmax,
                      int* err_word, bool persistent, bool tensor_core = false);
     void release();
@@ -65,9 +65,12 @@ class BatchRunner {
     cudaError_t precode_after(cudaStream_t s);
     std::vector<Precode> pre_;
     void grids(unsigned* build_grid, unsigned* solve_grid) const;
+    unsigned solve_block() const { return tc_ ? 128u : (persistent_ ? 4u * 32u : 32u); }
+    size_t solve_smem() const { return tc_ ? umma_smem_ : 0; }
     int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0, grid_ = 0, build_grid_max_ = 1;
     bool persistent_ = false;
-    bool tc_ = false;  // tensor-core field refresh for 8 and 16 users (grid mode)
+    bool tc_ = false;  // tcgen05 field refresh for 8 and 16 users (4-problem tiles)
+    size_t umma_smem_ = 0;  // dynamic shared memory of the tcgen05 solver
     long long capacity_problems_ = 0;
     size_t build_smem_ = 0, scratch_bytes_ = 0;
     char* scratch_ = nullptr;

@@ -1554,11 +1554,35 @@ __device__ __forceinline__ bool umma_block(uint8_t* su_h, uint8_t* su_l, uint32_
     return true;
 }
 
+// One CTA-tile of shape 8: the 128 / runs problems starting at T's base,
+// annealed, selected and written.  Called by all 128 threads of the CTA with
+// `usm` the CTA's dynamic shared memory (UmmaSmem<NT>(128 / runs).bytes()).
+struct UmmaTile {
+    const int16_t* Aq;      // couplings of the tile's first problem ([n][n] per problem)
+    const int16_t* hq;      // fields ([n] per problem)
+    const int8_t* g;        // guesses ([n] per problem) or nullptr (0)
+    int n_live;             // problems of the tile that exist (the rest run on zeros)
+    uint64_t problem0;      // Philox problem index of the first problem
+    uint32_t key0, key1;
+    int level_max;          // clip offsets to the alphabet (0: no clipping)
+    int steps;
+    EulerConsts k;
+    int* err;               // device error word or nullptr
+    // outputs for the tile's first problem (each may be nullptr)
+    int8_t* d_out;          // [n] offsets (0 where the guess was kept)
+    int32_t* E_out;
+    int32_t* run_out;
+    int32_t* ndiv_out;
+    int8_t* x_out;          // [n] g + 2d
+    int8_t* guess_out;      // [n] g
+    uint8_t* sym_out;       // [n_t] decoded symbols
+    int mod_bits;
+};
+
 template <int NT, int F>
-__global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int runs) {
+__device__ __forceinline__ void umma_tile(const UmmaTile& a, int runs, uint8_t* usm) {
     constexpr int n = 2 * NT;
     static_assert(n % 16 == 0 && F > 0, "tcgen05 refresh: n a multiple of 16, compile-time refresh period");
-    extern __shared__ __align__(128) uint8_t usm[];
     __shared__ __align__(8) uint64_t mbar_store;
     __shared__ uint32_t tmem_slot;
     __shared__ long long skey[4];
@@ -1569,8 +1593,7 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
     const uint32_t ncols = N < 32 ? 32u : (uint32_t)N;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pl = tid / runs, run = tid % runs;
-    const int p = blockIdx.x * PP + pl;
-    const bool live = p < a.n_problems;
+    const bool live = pl < a.n_live;
     const EulerConsts k = a.k;
     int16_t* sAq = reinterpret_cast<int16_t*>(usm + L.off_aq());
     int16_t* shq = reinterpret_cast<int16_t*>(usm + L.off_hq());
@@ -1578,17 +1601,13 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
     float* snd = reinterpret_cast<float*>(usm + L.off_nd());
     int8_t* sg = reinterpret_cast<int8_t*>(usm + L.off_g());
     // stage the PP problems (a missing tail problem is all zeros)
-    for (int e = tid; e < PP * n * n; e += 128) {
-        const int q = e / (n * n), pq = blockIdx.x * PP + q;
-        sAq[e] = pq < a.n_problems ? a.Aq[(size_t)pq * n * n + (e - q * n * n)] : (int16_t)0;
-    }
+    for (int e = tid; e < PP * n * n; e += 128) sAq[e] = e / (n * n) < a.n_live ? a.Aq[e] : (int16_t)0;
     for (int e = tid; e < PP * n; e += 128) {
-        const int q = e / n, pq = blockIdx.x * PP + q;
-        const bool have = pq < a.n_problems;
-        const int16_t v = have ? a.hq[(size_t)pq * n + (e - q * n)] : (int16_t)0;
+        const bool have = e / n < a.n_live;
+        const int16_t v = have ? a.hq[e] : (int16_t)0;
         shq[e] = v;
         sh[e] = mulrn(mulrn((float)v, 0x1p-14f), k.ce);
-        sg[e] = have && a.g ? a.g[(size_t)pq * n + (e - q * n)] : (int8_t)0;
+        sg[e] = have && a.g ? a.g[e] : (int8_t)0;
     }
     if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), ncols);
     const uint32_t mbar = smem_u32(&mbar_store);
@@ -1622,7 +1641,7 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
     // Philox initial amplitudes (the same counters as every other shape)
     float x1[n], x2[n], e1[n], e2[n], xa, ea = 1.0f;
     {
-        const uint64_t pg = a.problem_offset + (uint64_t)p;
+        const uint64_t pg = a.problem0 + (uint64_t)pl;
         const uint32_t c2 = (uint32_t)pg, c3 = (uint32_t)(pg >> 32);
 #pragma unroll
         for (int b = 0; b < n / 4; ++b) {
@@ -1729,6 +1748,7 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
     }
     const int best_run = (int)(best & 0xffffffffLL);
     if (live && run == best_run) {
+        const int p = pl;  // within the tile
         if (a.d_out) {
 #pragma unroll
             for (int i = 0; i < n; ++i) a.d_out[(size_t)p * n + i] = keep ? (int8_t)d[i] : (int8_t)0;
@@ -1741,6 +1761,10 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
 #pragma unroll
             for (int i = 0; i < n; ++i) a.x_out[(size_t)p * n + i] = (int8_t)((int)g[i] + 2 * (keep ? d[i] : 0));
         }
+        if (a.guess_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) a.guess_out[(size_t)p * n + i] = g[i];
+        }
         if (a.sym_out) {
             const int side = 1 << (a.mod_bits >> 1), Lv = side - 1;
             uint8_t* so = a.sym_out + (size_t)p * NT;
@@ -1752,6 +1776,36 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
             }
         }
     }
+}
+
+template <int NT, int F>
+__global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int runs) {
+    constexpr int n = 2 * NT;
+    extern __shared__ __align__(128) uint8_t usm[];
+    const int PP = 128 / runs;
+    const int base = blockIdx.x * PP;
+    auto at = [&](auto* ptr, size_t per) { return ptr ? ptr + (size_t)base * per : ptr; };
+    UmmaTile t;
+    t.Aq = a.Aq + (size_t)base * n * n;
+    t.hq = a.hq + (size_t)base * n;
+    t.g = at(a.g, n);
+    t.n_live = min(PP, a.n_problems - base);
+    t.problem0 = a.problem_offset + (uint64_t)base;
+    t.key0 = a.key0;
+    t.key1 = a.key1;
+    t.level_max = a.level_max;
+    t.steps = a.steps;
+    t.k = a.k;
+    t.err = a.err;
+    t.d_out = at(a.d_out, n);
+    t.E_out = at(a.E_out, 1);
+    t.run_out = at(a.run_out, 1);
+    t.ndiv_out = at(a.ndiv_out, 1);
+    t.x_out = at(a.x_out, n);
+    t.guess_out = nullptr;
+    t.sym_out = at(a.sym_out, NT);
+    t.mod_bits = a.mod_bits;
+    umma_tile<NT, F>(t, runs, usm);
 }
 
 // =========================================================================
@@ -1771,6 +1825,7 @@ struct BatchJob {
                             // batch: no clipping (guess 0), offsets to offset_out, no symbols
     uint32_t key0, key1;
     long long first;        // batch index of the job's problem 0
+    long long tile_first;   // tensor-core solver: index of the job's first 4-problem tile
     int16_t* Aq;            // scratch [P][n][n]
     int16_t* hq;            // scratch [P][n]
     int8_t* g;              // scratch [P][n]
@@ -1786,6 +1841,7 @@ struct BatchHeader {
     int pad;
     long long total;             // problems in the batch
     unsigned long long counter;  // next problem to hand out (reset before each run)
+    long long tiles;             // 4-problem tiles of the tensor-core solver (no tile spans two jobs)
 };
 
 struct BatchArgs {
@@ -1839,13 +1895,10 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 8) batch_build_kernel(BatchA
     }
 }
 
-// Anneal one problem already built into sm (Aq, hq, g) with one warp.  TC:
-// the tensor-core field refresh (solver shape 5; tc_af / tc_ws hold the A
-// fragments and the warp's exchange buffer), for 8 and 16 users.
-template <int NT, int F, bool TC = false>
+// Anneal one problem already built into sm (Aq, hq, g) with one warp.
+template <int NT, int F>
 __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const BatchJob& J, int p, int lane,
-                                                 SolveSmem<NT>& sm, uint32_t* tc_af = nullptr,
-                                                 uint32_t* tc_ws = nullptr) {
+                                                 SolveSmem<NT>& sm) {
     constexpr int n = 2 * NT;
     const EulerConsts k = A.k;
     for (int e = lane; e < n * n; e += 32) sm.A[e] = mulrn(mulrn((float)sm.Aq[e], 0x1p-14f), k.ce);
@@ -1875,14 +1928,7 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
     }
     const int S = A.steps;
     int t = 0;
-    if constexpr (TC && NT % 8 == 0) {
-        tc_stage_fragments<NT>(sm.Aq, tc_af, lane, 32);
-        __syncwarp();
-        const float mscale = mulrn(k.ce, 0x1p-5f);
-#pragma unroll 1
-        for (; t + F <= S; t += F) tc_block<NT, F>(tc_af, sm.h, sm.nd, tc_ws, x1, x2, e1, e2, xa, ea, lane, F, mscale, k);
-        if (t < S) tc_block<NT, 0>(tc_af, sm.h, sm.nd, tc_ws, x1, x2, e1, e2, xa, ea, lane, S - t, mscale, k);
-    } else {
+    {
         // 16 users: the paired refresh (faster there, same bits); fewer users: one anneal per lane
         constexpr bool kPair = NT == 16;
 #pragma unroll 1
@@ -1952,10 +1998,9 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
     __syncwarp();  // the warp's shared memory is reused by its next problem
 }
 
-template <int NT, int F, bool TC = false>
+template <int NT, int F>
 __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const BatchJob& J, int p, int lane,
-                                                    unsigned char* solve_mem, uint32_t* tc_af = nullptr,
-                                                    uint32_t* tc_ws = nullptr) {
+                                                    unsigned char* solve_mem) {
     constexpr int n = 2 * NT;
     SolveSmem<NT>& sm = *reinterpret_cast<SolveSmem<NT>*>(solve_mem);
     const int16_t* Aq = J.Aq + (size_t)p * n * n;
@@ -1965,26 +2010,23 @@ __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const Ba
         sm.g[i] = J.g ? J.g[(size_t)p * n + i] : (int8_t)0;
     }
     __syncwarp();
-    batch_solve_warp<NT, F, TC>(A, J, p, lane, sm, tc_af, tc_ws);
+    batch_solve_warp<NT, F>(A, J, p, lane, sm);
 }
 
 // Grid solver over the batch: one 32-thread CTA per problem (the hardware
 // CTA scheduler balances sizes); CTAs past the staged total exit.
-template <int NTMAX, int F, bool TC = false>
+template <int NTMAX, int F>
 __global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
     __shared__ __align__(16) unsigned char ssm[batch_solve_bytes<NTMAX>()];
-    constexpr bool kTc = TC && NTMAX >= 8;
-    __shared__ __align__(16) uint32_t tc_af[kTc ? TcShape<NTMAX>::AF_WORDS : 1];
-    __shared__ __align__(16) uint32_t tc_ws[kTc ? TcShape<NTMAX>::WARP_WORDS : 1];
     const long long w = blockIdx.x;
     if (w >= A.head->total) return;
     const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
     const int p = (int)(w - J.first);
     const int lane = threadIdx.x;
     if (J.nt == 16) {
-        if constexpr (NTMAX >= 16) batch_solve_problem<16, F, kTc>(A, J, p, lane, ssm, tc_af, tc_ws);
+        if constexpr (NTMAX >= 16) batch_solve_problem<16, F>(A, J, p, lane, ssm);
     } else if (J.nt == 8) {
-        if constexpr (NTMAX >= 8) batch_solve_problem<8, F, kTc>(A, J, p, lane, ssm, tc_af, tc_ws);
+        if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, ssm);
     } else {
         batch_solve_problem<4, F>(A, J, p, lane, ssm);
     }
@@ -2013,6 +2055,66 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchArgs A) {
         } else {
             batch_solve_problem<4, F>(A, J, p, lane, mine);
         }
+    }
+}
+
+// Batched tensor-core solver (tcgen05, solver shape 8): one 128-thread CTA
+// per tile of 4 consecutive problems of one job; 8- and 16-user tiles run
+// umma_tile (the same tiles as mmgap_detect with shape 8, so the same bits),
+// 4-user tiles one exact warp per problem.
+template <int NTMAX>
+__host__ __device__ constexpr size_t batch_umma_bytes() {
+    constexpr size_t u = NTMAX >= 8 ? (size_t)UmmaSmem<NTMAX >= 16 ? 16 : 8>(4).bytes() : 0;
+    constexpr size_t w = 4 * batch_solve_bytes<4>();
+    return u > w ? u : w;
+}
+
+template <int NTMAX, int F>
+__global__ void __launch_bounds__(128) batch_solve_umma_kernel(BatchArgs A) {
+    extern __shared__ __align__(128) uint8_t usm[];
+    const long long t = blockIdx.x;
+    if (t >= A.head->tiles) return;
+    int lo = 0, hi = A.head->n_jobs - 1;  // last job whose tiles start at or before t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.jobs[mid].tile_first <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchJob& J = A.jobs[lo];
+    const int base = (int)(t - J.tile_first) * 4;
+    const int live = min(4, J.b.n_problems - base);
+    if (J.nt >= 8) {
+        if constexpr (NTMAX >= 8) {
+            const int nt = J.nt, n = 2 * nt;
+            UmmaTile u;
+            u.Aq = J.Aq + (size_t)base * n * n;
+            u.hq = J.hq + (size_t)base * n;
+            u.g = J.g ? J.g + (size_t)base * n : nullptr;
+            u.n_live = live;
+            u.problem0 = (uint64_t)base;
+            u.key0 = J.key0;
+            u.key1 = J.key1;
+            u.level_max = J.kind == 0 ? (1 << (J.b.mod_bits >> 1)) - 1 : 0;
+            u.steps = A.steps;
+            u.k = A.k;
+            u.err = J.b.err;
+            u.d_out = J.offset_out ? J.offset_out + (size_t)base * n : nullptr;
+            u.E_out = J.energy_out ? J.energy_out + base : nullptr;
+            u.run_out = nullptr;
+            u.ndiv_out = J.ndiv_out ? J.ndiv_out + base : nullptr;
+            u.x_out = nullptr;
+            u.guess_out = J.guess_out ? J.guess_out + (size_t)base * n : nullptr;
+            u.sym_out = J.sym_out ? J.sym_out + (size_t)base * nt : nullptr;
+            u.mod_bits = J.b.mod_bits;
+            if (nt == 16) {
+                if constexpr (NTMAX >= 16) umma_tile<16, F>(u, 32, usm);
+            } else {
+                umma_tile<8, F>(u, 32, usm);
+            }
+        }
+    } else {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (warp < live) batch_solve_problem<4, F>(A, J, base + warp, lane, usm + warp * batch_solve_bytes<4>());
     }
 }
 

@@ -171,8 +171,9 @@ def test_server_rejects_sizes_above_its_limits():
 
 def test_tensor_core_server_equals_per_job_tensor_core_shape():
     """A server (and a batch) with the tensor-core refresh returns, for 8- and
-    16-user jobs, exactly what mmgap_detect returns with solver shape 5, and
-    for 4-user jobs what the exact shapes return."""
+    16-user jobs, exactly what mmgap_detect returns with solver shape 8 (the
+    same 4-problem tcgen05 tiles), and for 4-user jobs what the exact shapes
+    return."""
     import paper_2510_01579_gb300 as pkg
     prm = pkg.Params.default(steps=80)
     with pkg.Context(0) as ctx:
@@ -181,7 +182,7 @@ def test_tensor_core_server_equals_per_job_tensor_core_shape():
         for w, t, o, job in jobs:
             n_t = w["n_t"]
             if n_t in (8, 16):
-                ctx.set_solver_variant(n_t, 5)
+                ctx.set_solver_variant(n_t, 8)
             r = {k: torch.empty_like(v) for k, v in o.items()}
             ctx.detect_jobs([ctx.detect_job(t[0], t[1], t[2], w["mod_bits"], job.seed, r, t[3])], prm)
             ctx.set_solver_variant(n_t, 0)
