@@ -177,6 +177,32 @@ def test_detect_small_config_bit_exact_and_ml(mm):
     assert hits >= 60
 
 
+def test_qpsk_ber_ordering_over_snr(mm):
+    """8x8 QPSK, 96 problems per SNR (i.i.d. CN(0,1)), 32 x 200 anneals: MMGaP
+    never has a larger ML objective than the MMSE guess (the selection energy
+    is exact up to the couplings' Q14 rounding), its bit errors stay close to
+    exhaustive 4^8 ML's at every SNR (QPSK: the delta neighbourhood covers the
+    alphabet) and below MMSE's wherever MMSE makes errors."""
+    pkg, ctx = mm
+    prm = pkg.Params.default()
+    for snr in (0.0, 5.0, 10.0, 15.0):
+        w = synth.uplink(int(30 + snr), 8, 8, 2, n_sub=96, n_sym=1, snr_db=snr, hold="problem")
+        got = _detect(ctx, w, prm, 13)
+        g = got["guess"].astype(int)
+        mmse = ((g[:, :8] + 1) // 2) * 2 + (g[:, 8:] + 1) // 2
+        ml = np.zeros_like(w["sym"])
+        for p in range(96):
+            H, y = w["H"][p].astype(np.complex128), w["y"][p].astype(np.complex128)
+            _, x = oracle.ml_exhaustive(H, y, 2)
+            ml[p] = ((x[:8] + 1) // 2) * 2 + (x[8:] + 1) // 2
+            obj = lambda s: np.linalg.norm(y - H @ synth.symbols_to_complex(s, 2)) ** 2
+            # (up to the Q14 rounding of the energy that decides the selection)
+            assert obj(got["sym"][p]) <= obj(mmse[p]) * (1 + 1e-3) + 1e-3, (snr, p)
+        e_ml, e_mm, e_mmse = (synth.bit_errors(s, w["sym"], 2) for s in (ml, got["sym"], mmse))
+        assert e_mm <= 1.5 * e_ml + 4, (snr, e_ml, e_mm)
+        assert e_mm < e_mmse or e_mmse == 0, (snr, e_mm, e_mmse)
+
+
 def test_detect_prb_kronecker_bit_exact(mm):
     """8x8 16-QAM, Kronecker rho = 0.5, channel held per PRB (12 subcarriers x
     14 symbols), an SNR sweep across problems."""
