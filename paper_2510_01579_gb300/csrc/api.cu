@@ -1,6 +1,6 @@
 // C-ABI front end of the MMGaP hot path: argument checking, workspace
 // chunking, size dispatch and per-stage timing.  All arithmetic of the path
-// runs in the kernels of kernels.cuh.
+// runs in the kernels of the csrc/*.cuh headers (listed in kernels.cuh).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

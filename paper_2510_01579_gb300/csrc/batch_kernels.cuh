@@ -1,0 +1,320 @@
+// Batched launch of mixed-size jobs: builder over the job table, grid / persistent
+// solvers and the tcgen05 tile solver.
+#pragma once
+#include "build.cuh"
+#include "solve.cuh"
+#include "umma.cuh"
+
+namespace mmgap {
+
+// =========================================================================
+// Batched launch of mixed-size uplink jobs, in two kernels replayed as one
+// graph.  The builder runs one warp per problem over the whole batch (all
+// jobs, all sizes) into batch scratch; the solver is persistent: warps pull
+// problems from one atomic counter over a device job table (largest users
+// first), stage the problem's Q14 couplings in shared memory and anneal it
+// with 32 anneals on the warp's 32 lanes (one thread per anneal, packed
+// FP32).  Results equal the per-job path bit for bit: the Philox counters use
+// each problem's index within its own job.
+// =========================================================================
+struct BatchJob {
+    BuildArgs b;            // inputs, n_r, mod_bits, n_problems, n_chan, kappa, err
+    int nt;
+    int kind;               // 0 detection (built by the batch builder); 1 VPP, built before the
+                            // batch: no clipping (guess 0), offsets to offset_out, no symbols
+    uint32_t key0, key1;
+    long long first;        // batch index of the job's problem 0
+    long long tile_first;   // tensor-core solver: index of the job's first 4-problem tile
+    int16_t* Aq;            // scratch [P][n][n]
+    int16_t* hq;            // scratch [P][n]
+    int8_t* g;              // scratch [P][n]
+    uint8_t* sym_out;
+    int32_t* energy_out;
+    int8_t* guess_out;
+    int8_t* offset_out;
+    int32_t* ndiv_out;
+};
+
+struct BatchHeader {
+    int n_jobs;
+    int pad;
+    long long total;             // problems in the batch
+    unsigned long long counter;  // next problem to hand out (reset before each run)
+    long long tiles;             // 4-problem tiles of the tensor-core solver (no tile spans two jobs)
+};
+
+struct BatchArgs {
+    const BatchJob* jobs;
+    BatchHeader* head;
+    int steps;
+    EulerConsts k;
+    int build_floats;       // builder shared memory per warp (floats)
+};
+
+template <int NTMAX>
+__host__ __device__ constexpr size_t batch_solve_bytes() {
+    return (sizeof(SolveSmem<NTMAX>) + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ int batch_find_job(const BatchJob* jobs, int n_jobs, long long w) {
+    int lo = 0, hi = n_jobs - 1;  // last job with first <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].first <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Builder over the whole batch: warp w of the grid builds problem w.
+template <int NTMAX>
+__global__ void __launch_bounds__(kBuildWarps * 32, 8) batch_build_kernel(BatchArgs A) {
+    extern __shared__ __align__(16) float bws[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long total = A.head->total;
+    const int n_jobs = A.head->n_jobs;
+    float* ws = bws + warp * A.build_floats;
+    for (long long w = (long long)blockIdx.x * kBuildWarps + warp; w < total;
+         w += (long long)gridDim.x * kBuildWarps) {
+        const BatchJob& J = A.jobs[batch_find_job(A.jobs, n_jobs, w)];
+        if (J.kind != 0) continue;  // built before the batch
+        const int p = (int)(w - J.first);
+        const int n = 2 * J.nt;
+        BuildOut o{J.Aq + (size_t)p * n * n, J.hq + (size_t)p * n, J.g + (size_t)p * n, nullptr, nullptr, nullptr};
+        // a register copy of the job's arguments: read through the reference, every field would be
+        // reloaded from global memory after each of the builder's global stores
+        const BuildArgs b = J.b;
+        if (J.nt == 16) {
+            if constexpr (NTMAX >= 16) build_problem_warp<16>(b, p, lane, ws, o);
+        } else if (J.nt == 8) {
+            if constexpr (NTMAX >= 8) build_problem_warp<8>(b, p, lane, ws, o);
+        } else {
+            build_problem_warp<4>(b, p, lane, ws, o);
+        }
+    }
+}
+
+// Anneal one problem already built into sm (Aq, hq, g) with one warp.
+template <int NT, int F>
+__device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const BatchJob& J, int p, int lane,
+                                                 SolveSmem<NT>& sm) {
+    constexpr int n = 2 * NT;
+    const EulerConsts k = A.k;
+    for (int e = lane; e < n * n; e += 32) sm.A[e] = mulrn(mulrn((float)sm.Aq[e], 0x1p-14f), k.ce);
+    for (int i = lane; i < n; i += 32) sm.h[i] = mulrn(mulrn((float)sm.hq[i], 0x1p-14f), k.ce);
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) sm.nd[i] = -sm.A[i * n + i];
+    __syncwarp();
+    const int run = lane;
+    float x1[n], x2[n], e1[n], e2[n], xa, ea = 1.0f;
+    {
+        const uint32_t c2 = (uint32_t)p, c3 = 0u;
+#pragma unroll
+        for (int b = 0; b < n / 4; ++b) {
+            const U4 w1 = philox4x32_10(U4{(uint32_t)b, (uint32_t)run, c2, c3}, J.key0, J.key1);
+            const U4 w2 = philox4x32_10(U4{(uint32_t)((n >> 2) + b), (uint32_t)run, c2, c3}, J.key0, J.key1);
+            const uint32_t v1[4] = {w1.x, w1.y, w1.z, w1.w}, v2[4] = {w2.x, w2.y, w2.z, w2.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                x1[4 * b + t] = mulrn((float)((int)(v1[t] >> 8) - 8388608), k.xs);
+                x2[4 * b + t] = mulrn((float)((int)(v2[t] >> 8) - 8388608), k.xs);
+                e1[4 * b + t] = 1.0f;
+                e2[4 * b + t] = 1.0f;
+            }
+        }
+        const U4 wa = philox4x32_10(U4{(uint32_t)((2 * n) >> 2), (uint32_t)run, c2, c3}, J.key0, J.key1);
+        xa = mulrn((float)((int)(wa.x >> 8) - 8388608), k.xs);
+    }
+    const int S = A.steps;
+    int t = 0;
+    {
+        // 16 users: the paired refresh (faster there, same bits); fewer users: one anneal per lane
+        constexpr bool kPair = NT == 16;
+#pragma unroll 1
+        for (; t + F <= S; t += F)
+            tuned_block<n, n, 1, true, F, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, F, k);
+        if (t < S)
+            tuned_block<n, n, 1, true, 0, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, S - t, k);
+    }
+
+    bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+        valid = valid && (fabsf(x1[i]) <= k.x_max) && (e1[i] > 0.0f) && (fabsf(x2[i]) <= k.x_max) && (e2[i] > 0.0f);
+    const int level_max = J.kind == 0 ? (1 << (J.b.mod_bits >> 1)) - 1 : 0;  // 0: no clipping
+    const int sa = xa >= 0.0f ? 1 : -1;
+    int d[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int s1 = x1[i] >= 0.0f ? 1 : -1, s2 = x2[i] >= 0.0f ? 1 : -1;
+        int di = sa * (s1 + s2) / 2;
+        const int xv = (int)sm.g[i] + 2 * di;
+        if (level_max > 0 && (xv > level_max || xv < -level_max)) di = 0;
+        d[i] = di;
+    }
+    int E = 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) r += (int)sm.Aq[i * n + j] * d[j];
+        E -= d[i] * r;
+        E -= (int)sm.hq[i] * d[i];
+    }
+    const bool keep = valid && E <= 0;
+    const int Ec = keep ? E : 0;
+    long long key = (long long)Ec * 4294967296LL + (long long)run;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long other = __shfl_xor_sync(0xffffffffu, key, o);
+        key = other < key ? other : key;
+    }
+    const int ndiv = __popc(__ballot_sync(0xffffffffu, !valid));
+    const int best_run = (int)(key & 0xffffffffLL);
+    if (run == best_run) {
+        const int bestE = (int)((key - (long long)best_run) / 4294967296LL);
+        if (J.energy_out) J.energy_out[p] = bestE;
+        if (J.ndiv_out) J.ndiv_out[p] = ndiv;
+        if (J.offset_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) J.offset_out[(size_t)p * n + i] = keep ? (int8_t)d[i] : (int8_t)0;
+        }
+        if (J.guess_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) J.guess_out[(size_t)p * n + i] = sm.g[i];
+        }
+        if (J.sym_out) {
+            const int side = 1 << (J.b.mod_bits >> 1), L = side - 1;
+            uint8_t* so = J.sym_out + (size_t)p * NT;
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                const int xr = (int)sm.g[i] + 2 * (keep ? d[i] : 0);
+                const int xi = (int)sm.g[NT + i] + 2 * (keep ? d[NT + i] : 0);
+                so[i] = (uint8_t)(((xr + L) / 2) * side + (xi + L) / 2);
+            }
+        }
+    }
+    __syncwarp();  // the warp's shared memory is reused by its next problem
+}
+
+template <int NT, int F>
+__device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const BatchJob& J, int p, int lane,
+                                                    unsigned char* solve_mem) {
+    constexpr int n = 2 * NT;
+    SolveSmem<NT>& sm = *reinterpret_cast<SolveSmem<NT>*>(solve_mem);
+    const int16_t* Aq = J.Aq + (size_t)p * n * n;
+    for (int e = lane; e < n * n; e += 32) sm.Aq[e] = Aq[e];
+    for (int i = lane; i < n; i += 32) {
+        sm.hq[i] = J.hq[(size_t)p * n + i];
+        sm.g[i] = J.g ? J.g[(size_t)p * n + i] : (int8_t)0;
+    }
+    __syncwarp();
+    batch_solve_warp<NT, F>(A, J, p, lane, sm);
+}
+
+// Grid solver over the batch: one 32-thread CTA per problem (the hardware
+// CTA scheduler balances sizes); CTAs past the staged total exit.
+template <int NTMAX, int F>
+__global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
+    __shared__ __align__(16) unsigned char ssm[batch_solve_bytes<NTMAX>()];
+    const long long w = blockIdx.x;
+    if (w >= A.head->total) return;
+    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
+    const int p = (int)(w - J.first);
+    const int lane = threadIdx.x;
+    if (J.nt == 16) {
+        if constexpr (NTMAX >= 16) batch_solve_problem<16, F>(A, J, p, lane, ssm);
+    } else if (J.nt == 8) {
+        if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, ssm);
+    } else {
+        batch_solve_problem<4, F>(A, J, p, lane, ssm);
+    }
+}
+
+// Persistent solver over the batch: one warp per problem, problems handed
+// out by an atomic counter.
+template <int NTMAX, int F>
+__global__ void __launch_bounds__(128) batch_solve_kernel(BatchArgs A) {
+    __shared__ __align__(16) unsigned char ssm[4 * batch_solve_bytes<NTMAX>()];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* mine = ssm + (size_t)warp * batch_solve_bytes<NTMAX>();
+    const int n_jobs = A.head->n_jobs;
+    const long long total = A.head->total;
+    for (;;) {
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(&A.head->counter, 1ULL);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if ((long long)w >= total) break;
+        const BatchJob& J = A.jobs[batch_find_job(A.jobs, n_jobs, (long long)w)];
+        const int p = (int)((long long)w - J.first);
+        if (J.nt == 16) {
+            if constexpr (NTMAX >= 16) batch_solve_problem<16, F>(A, J, p, lane, mine);
+        } else if (J.nt == 8) {
+            if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, mine);
+        } else {
+            batch_solve_problem<4, F>(A, J, p, lane, mine);
+        }
+    }
+}
+
+// Batched tensor-core solver (tcgen05, solver shape 8): one 128-thread CTA
+// per tile of 4 consecutive problems of one job; 8- and 16-user tiles run
+// umma_tile (the same tiles as mmgap_detect with shape 8, so the same bits),
+// 4-user tiles one exact warp per problem.
+template <int NTMAX>
+__host__ __device__ constexpr size_t batch_umma_bytes() {
+    constexpr size_t u = NTMAX >= 8 ? (size_t)UmmaSmem<NTMAX >= 16 ? 16 : 8>(4).bytes() : 0;
+    constexpr size_t w = 4 * batch_solve_bytes<4>();
+    return u > w ? u : w;
+}
+
+template <int NTMAX, int F>
+__global__ void __launch_bounds__(128) batch_solve_umma_kernel(BatchArgs A) {
+    extern __shared__ __align__(128) uint8_t usm[];
+    const long long t = blockIdx.x;
+    if (t >= A.head->tiles) return;
+    int lo = 0, hi = A.head->n_jobs - 1;  // last job whose tiles start at or before t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.jobs[mid].tile_first <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchJob& J = A.jobs[lo];
+    const int base = (int)(t - J.tile_first) * 4;
+    const int live = min(4, J.b.n_problems - base);
+    if (J.nt >= 8) {
+        if constexpr (NTMAX >= 8) {
+            const int nt = J.nt, n = 2 * nt;
+            UmmaTile u;
+            u.Aq = J.Aq + (size_t)base * n * n;
+            u.hq = J.hq + (size_t)base * n;
+            u.g = J.g ? J.g + (size_t)base * n : nullptr;
+            u.n_live = live;
+            u.problem0 = (uint64_t)base;
+            u.key0 = J.key0;
+            u.key1 = J.key1;
+            u.level_max = J.kind == 0 ? (1 << (J.b.mod_bits >> 1)) - 1 : 0;
+            u.steps = A.steps;
+            u.k = A.k;
+            u.err = J.b.err;
+            u.d_out = J.offset_out ? J.offset_out + (size_t)base * n : nullptr;
+            u.E_out = J.energy_out ? J.energy_out + base : nullptr;
+            u.run_out = nullptr;
+            u.ndiv_out = J.ndiv_out ? J.ndiv_out + base : nullptr;
+            u.x_out = nullptr;
+            u.guess_out = J.guess_out ? J.guess_out + (size_t)base * n : nullptr;
+            u.sym_out = J.sym_out ? J.sym_out + (size_t)base * nt : nullptr;
+            u.mod_bits = J.b.mod_bits;
+            if (nt == 16) {
+                if constexpr (NTMAX >= 16) umma_tile<16, F>(u, 32, usm);
+            } else {
+                umma_tile<8, F>(u, 32, usm);
+            }
+        }
+    } else {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (warp < live) batch_solve_problem<4, F>(A, J, base + warp, lane, usm + warp * batch_solve_bytes<4>());
+    }
+}
+
+}  // namespace mmgap

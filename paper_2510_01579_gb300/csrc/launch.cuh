@@ -1,0 +1,130 @@
+// Host-side launchers of every kernel (grid sizes, dynamic shared memory, shapes).
+#pragma once
+#include "build.cuh"
+#include "solve.cuh"
+#include "umma.cuh"
+#include "batch_kernels.cuh"
+#include "direct.cuh"
+#include "gram_select.cuh"
+#include "vpp.cuh"
+
+namespace mmgap {
+
+// ------------------------------------------------------------- launchers
+template <int NT>
+cudaError_t launch_build_detect_impl(const BuildArgs& a, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    const size_t smem = (size_t)kBuildWarps * build_smem_floats<NT>(a.n_r) * sizeof(float);
+    cudaError_t err = ensure_dynamic_smem<build_detect_kernel<NT>>(smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = (a.n_problems + kBuildWarps - 1) / kBuildWarps;
+    build_detect_kernel<NT><<<blocks, kBuildWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Tuned kernels exist for n_t in {4, 8, 16} and f_mvm in {1, 2}.
+__host__ __device__ constexpr bool tuned_size(int NT) { return NT == 4 || NT == 8 || NT == 16; }
+
+// Shape 8: CTAs of 128 anneals.  The CTAs resident on an SM share its 512
+// TMEM columns, so shared memory is padded where needed to keep at most
+// 512 / ncols of them on one SM (registers already allow fewer here).
+template <int NT, int F>
+cudaError_t launch_umma(const SolveArgs& a, int runs, cudaStream_t s) {
+    const int pp = 128 / runs;
+    const int N = pp * 2 * NT;
+    const int ncols = N < 32 ? 32 : N;
+    const int max_ctas = 512 / ncols;
+    int dev = 0, smem_sm = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (err != cudaSuccess) return err;
+    size_t smem = (size_t)UmmaSmem<NT>(pp).bytes();
+    const size_t floor_bytes = (size_t)smem_sm / (size_t)(max_ctas + 1) + 1;  // (max_ctas + 1) CTAs no longer fit
+    if (smem < floor_bytes) smem = (floor_bytes + 127) & ~(size_t)127;
+    err = ensure_dynamic_smem<cac_solve_umma_kernel<NT, F>>(smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = (a.n_problems + pp - 1) / pp;
+    cac_solve_umma_kernel<NT, F><<<blocks, 128, smem, s>>>(a, runs);
+    return cudaGetLastError();
+}
+
+template <int NT, int F>
+cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t s) {
+    if constexpr (tuned_size(NT)) {
+        switch (variant) {
+        case kVariantTpa1: cac_solve_tuned_kernel<NT, F, 1, false><<<a.n_problems, runs, 0, s>>>(a); break;
+        case kVariantTpa1Packed: cac_solve_tuned_kernel<NT, F, 1, true><<<a.n_problems, runs, 0, s>>>(a); break;
+        case kVariantTpa2Packed: cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a); break;
+        case kVariantTpa4Packed:  // (smaller sizes are resolved to shape 4 before launch)
+            if constexpr (NT >= 8) cac_solve_tuned_kernel<NT, F, 4, true><<<a.n_problems, 4 * runs, 0, s>>>(a);
+            else cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
+            break;
+        case kVariantTpa8Packed:
+            if constexpr (NT >= 16) cac_solve_tuned_kernel<NT, F, 8, true><<<a.n_problems, 8 * runs, 0, s>>>(a);
+            else cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
+            break;
+        case kVariantPairPacked:
+            cac_solve_tuned_kernel<NT, F, 1, true, false, true><<<a.n_problems, runs, 0, s>>>(a);
+            break;
+        case kVariantUmma:
+            if constexpr (NT % 8 == 0) {
+                if (runs != 96) return launch_umma<NT, F>(a, runs, s);
+            }
+            [[fallthrough]];  // 96 anneals do not tile the 128 rows: shape 5
+        case kVariantTensorCore:
+            if constexpr (NT % 8 == 0) {
+                cac_solve_tuned_kernel<NT, F, 1, true, true>
+                    <<<a.n_problems, runs, (size_t)(runs / 32) * TcShape<NT>::warp_words(32) * 4, s>>>(a);
+                break;
+            }
+            [[fallthrough]];
+        case kVariantTensorCore2:
+            if constexpr (NT % 8 == 0) {
+                cac_solve_tuned_kernel<NT, F, 2, true, true>
+                    <<<a.n_problems, 2 * runs, (size_t)(2 * runs / 32) * TcShape<NT>::warp_words(16) * 4, s>>>(a);
+                break;
+            }
+            [[fallthrough]];
+        default: cac_solve_kernel<NT, F><<<a.n_problems, runs, 0, s>>>(a); break;
+        }
+    } else {
+        cac_solve_kernel<NT, F><<<a.n_problems, runs, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    const int v = a.spins_out ? (int)kVariantPlain : resolve_variant(NT, a.f_mvm, a.variant, a.n_problems, a.n_sm);
+    if (a.f_mvm == 2) return launch_tuned<NT, 2>(a, runs, v, s);
+    if (a.f_mvm == 1) return launch_tuned<NT, 1>(a, runs, v, s);
+    cac_solve_kernel<NT, 0><<<a.n_problems, runs, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_vpp_inverse_impl(const VppInvArgs& a, cudaStream_t s) {
+    if (a.n_chan <= 0) return cudaSuccess;
+    const size_t smem = (size_t)(2 * NT * a.n_t + 8 * NT * NT) * sizeof(double);
+    cudaError_t err = ensure_dynamic_smem<vpp_inverse_kernel<NT>>(smem);
+    if (err != cudaSuccess) return err;
+    vpp_inverse_kernel<NT><<<a.n_chan, 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_vpp_build_impl(const VppBuildArgs& a, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    vpp_build_kernel<NT><<<(a.n_problems + 3) / 4, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_vpp_output_impl(const VppOutArgs& a, cudaStream_t s) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    vpp_output_kernel<NT><<<(a.n_problems + 3) / 4, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mmgap

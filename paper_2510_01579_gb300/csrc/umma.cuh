@@ -1,0 +1,508 @@
+// tcgen05 field refresh (solver shape 8): UMMA into tensor memory, per-job kernel.
+#pragma once
+#include "solve.cuh"
+
+namespace mmgap {
+
+// =========================================================================
+// tcgen05 field refresh (solver shape 8; a precision variant like shape 5,
+// the same FP16-split product, on the fifth-generation tensor cores).
+// One CTA of 128 threads is the 128 rows of one UMMA tile: PP = 128 / runs
+// problems of `runs` anneals, one thread per anneal.  At each refresh every
+// thread writes its anneal's 2^5 u (u = x1 + x2, split into an FP16 pair) as
+// one row of U^T in shared memory; one thread issues D = U^T C^T with C the
+// PP problems' couplings c 2^-14 (an exact FP16 pair) stacked along N, so
+// N = PP n and the cross-problem blocks of D are computed but never read --
+// unless the tile's problems carry identical couplings (one channel), when
+// one C serves all of them and N = n.
+// D = Uh Cl + Ul Ch + Uh Ch accumulates in FP32 in tensor memory (TMEM); its
+// row r is anneal r, and one tcgen05.ld hands each thread its own row -- the
+// field m of its problem's n columns -- with no shared-memory round trip.
+// Both operands are K-major without swizzle: core matrices of 8 rows x 16
+// bytes, 128 B apart along K (LBO) and 16 n B apart per 8 rows (SBO).
+// Every wait on the MMA's completion barrier is bounded (kUmmaWaitNs); on
+// expiry the CTA stops annealing, reports its problems' guesses as if every
+// anneal had diverged, sets bit 1 of the device error word, waits once more
+// (bounded) for the MMA in flight and frees its TMEM.
+// =========================================================================
+
+constexpr unsigned long long kUmmaWaitNs = 200000000ull;  // 0.2 s; an MMA here takes microseconds
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4),
+// descriptor version 1, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B FP16, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         int accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc05_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc05_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of parity `parity` to complete; false if it has not
+// within kUmmaWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(mbar, parity))
+        if (global_ns() - t0 > kUmmaWaitNs) return false;
+    return true;
+}
+
+// TMEM allocation and release (whole warp, converged).
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// This thread's TMEM lane, NC consecutive 32-bit columns from taddr, and the
+// wait for the load in the same statement (the registers are not read before it).
+__device__ __forceinline__ void tmem_ld_row(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_row(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        " tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory layout of one CTA (bytes), for PP problems of n = 2 NT spins.
+template <int NT>
+struct UmmaSmem {
+    static constexpr int n = 2 * NT;
+    static constexpr int SBO = 16 * n;              // bytes per 8-row group of a K-major FP16 plane
+    static constexpr int U_PLANE = 128 * 2 * n;     // U^T: 128 rows x n FP16
+    int pp;
+    __host__ __device__ constexpr UmmaSmem(int pp_) : pp(pp_) {}
+    __host__ __device__ constexpr int c_plane() const { return pp * n * 2 * n; }  // C: PP n rows x n FP16
+    __host__ __device__ constexpr int off_uh() const { return 0; }
+    __host__ __device__ constexpr int off_ul() const { return U_PLANE; }
+    __host__ __device__ constexpr int off_ch() const { return 2 * U_PLANE; }
+    __host__ __device__ constexpr int off_cl() const { return 2 * U_PLANE + c_plane(); }
+    __host__ __device__ constexpr int off_aq() const { return 2 * U_PLANE + 2 * c_plane(); }   // int16 [PP][n][n]
+    __host__ __device__ constexpr int off_hq() const { return off_aq() + pp * n * n * 2; }    // int16 [PP][n]
+    __host__ __device__ constexpr int off_h() const { return off_hq() + pp * n * 2; }         // float [PP][n]
+    __host__ __device__ constexpr int off_nd() const { return off_h() + pp * n * 4; }         // float [PP][n]
+    __host__ __device__ constexpr int off_g() const { return off_nd() + pp * n * 4; }         // int8 [PP][n]
+    __host__ __device__ constexpr int bytes() const { return off_g() + ((pp * n + 15) & ~15); }
+};
+
+// Refresh through the tensor cores + L frozen Euler steps (L == 0: runtime
+// Lrt).  Returns false, without stepping, once any thread of the CTA has met
+// an expired wait (the decision is CTA-uniform).
+template <int NT, int L>
+__device__ __forceinline__ bool umma_block(uint8_t* su_h, uint8_t* su_l, uint32_t a_h, uint32_t a_l, uint32_t c_h,
+                                           uint32_t c_l, uint32_t idesc, uint32_t d_tmem, uint32_t my_cols,
+                                           uint32_t mbar, uint32_t& phase, bool& failed, const float* sh,
+                                           const float* snd, float (&x1)[2 * NT], float (&x2)[2 * NT],
+                                           float (&e1)[2 * NT], float (&e2)[2 * NT], float& xa, float& ea, int tid,
+                                           int Lrt, float mscale, const EulerConsts& k) {
+    constexpr int n = 2 * NT;
+    constexpr int SBO = UmmaSmem<NT>::SBO;
+    asm volatile("" ::: "memory");
+    // u = x1 + x2, mu_a = b^T u (FP32, ascending j), FP16 split of 2^5 u into row tid of U^T
+    float mua = 0.0f;
+    const int rowoff = (tid >> 3) * SBO + (tid & 7) * 16;
+#pragma unroll
+    for (int c = 0; c < n / 8; ++c) {
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = 8 * c + 2 * t;
+            const float2 u2 = __fadd2_rn(make_float2(x1[j], x1[j + 1]), make_float2(x2[j], x2[j + 1]));
+            mua = fmarn(sh[j], u2.x, mua);
+            mua = fmarn(sh[j + 1], u2.y, mua);
+            const float2 us = __fmul2_rn(u2, make_float2(32.0f, 32.0f));
+            hv[t] = h2pack(us.x, us.y);
+            const float2 hf = h2unpack(hv[t]);
+            lv[t] = h2pack(__fsub_rn(us.x, hf.x), __fsub_rn(us.y, hf.y));
+        }
+        *reinterpret_cast<uint4*>(su_h + rowoff + 128 * c) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(su_l + rowoff + 128 * c) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+    fence_async_smem();  // the generic-proxy rows become visible to the tensor cores
+    tc05_fence_before();
+    const int stop = __syncthreads_or(failed ? 1 : 0);
+    tc05_fence_after();
+    if (stop) return false;
+    if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < n / 16; ++kk) {  // K steps of 16: two core matrices, 256 B
+            const uint32_t o = 256u * kk;
+            const uint64_t ah = umma_desc(a_h + o, 128, SBO), al = umma_desc(a_l + o, 128, SBO);
+            const uint64_t ch = umma_desc(c_h + o, 128, SBO), cl = umma_desc(c_l + o, 128, SBO);
+            umma_f16(d_tmem, ah, cl, idesc, kk > 0);  // small terms first
+            umma_f16(d_tmem, al, ch, idesc, 1);
+            umma_f16(d_tmem, ah, ch, idesc, 1);
+        }
+        umma_commit(mbar);
+    }
+    const bool ok = mbar_wait_bounded(mbar, phase);
+    if (!ok) {
+        failed = true;
+        return true;  // the next barrier (or the caller's) stops the CTA
+    }
+    phase ^= 1u;
+    tc05_fence_after();
+    float m[n];
+    tmem_ld_row(my_cols, m);
+    const float2 xa2 = make_float2(xa, xa);
+    const float2 ms2 = make_float2(mscale, mscale);
+    const float2 cdt = make_float2(k.cdt, k.cdt), c1 = make_float2(k.c1, k.c1);
+    const float2 cz = make_float2(k.cz, k.cz), c2 = make_float2(k.c2, k.c2);
+#pragma unroll
+    for (int i = 0; i < n; i += 2) {
+        const float2 mm = __fmul2_rn(make_float2(m[i], m[i + 1]), ms2);
+        const float2 hh = *reinterpret_cast<const float2*>(sh + i);
+        const float2 nd = *reinterpret_cast<const float2*>(snd + i);
+        const float2 c = __ffma2_rn(hh, xa2, mm);
+        float2 X1 = make_float2(x1[i], x1[i + 1]), X2 = make_float2(x2[i], x2[i + 1]);
+        float2 E1 = make_float2(e1[i], e1[i + 1]), E2 = make_float2(e2[i], e2[i + 1]);
+        const float2 mu1 = __ffma2_rn(nd, X1, c);
+        const float2 mu2 = __ffma2_rn(nd, X2, c);
+        if constexpr (L > 0) {
+#pragma unroll
+            for (int s = 0; s < L; ++s) {
+                euler_pair(X1, E1, mu1, cdt, c1, cz, c2);
+                euler_pair(X2, E2, mu2, cdt, c1, cz, c2);
+            }
+        } else {
+#pragma unroll 1
+            for (int s = 0; s < Lrt; ++s) {
+                euler_pair(X1, E1, mu1, cdt, c1, cz, c2);
+                euler_pair(X2, E2, mu2, cdt, c1, cz, c2);
+            }
+        }
+        x1[i] = X1.x; x1[i + 1] = X1.y; x2[i] = X2.x; x2[i + 1] = X2.y;
+        e1[i] = E1.x; e1[i + 1] = E1.y; e2[i] = E2.x; e2[i + 1] = E2.y;
+    }
+    if constexpr (L > 0) {
+#pragma unroll
+        for (int s = 0; s < L; ++s) euler_spin(xa, ea, mua, k);
+    } else {
+#pragma unroll 1
+        for (int s = 0; s < Lrt; ++s) euler_spin(xa, ea, mua, k);
+    }
+    return true;
+}
+
+// One CTA-tile of shape 8: the 128 / runs problems starting at T's base,
+// annealed, selected and written.  Called by all 128 threads of the CTA with
+// `usm` the CTA's dynamic shared memory (UmmaSmem<NT>(128 / runs).bytes()).
+struct UmmaTile {
+    const int16_t* Aq;      // couplings of the tile's first problem ([n][n] per problem)
+    const int16_t* hq;      // fields ([n] per problem)
+    const int8_t* g;        // guesses ([n] per problem) or nullptr (0)
+    int n_live;             // problems of the tile that exist (the rest run on zeros)
+    uint64_t problem0;      // Philox problem index of the first problem
+    uint32_t key0, key1;
+    int level_max;          // clip offsets to the alphabet (0: no clipping)
+    int steps;
+    EulerConsts k;
+    int* err;               // device error word or nullptr
+    // outputs for the tile's first problem (each may be nullptr)
+    int8_t* d_out;          // [n] offsets (0 where the guess was kept)
+    int32_t* E_out;
+    int32_t* run_out;
+    int32_t* ndiv_out;
+    int8_t* x_out;          // [n] g + 2d
+    int8_t* guess_out;      // [n] g
+    uint8_t* sym_out;       // [n_t] decoded symbols
+    int mod_bits;
+};
+
+template <int NT, int F>
+__device__ __forceinline__ void umma_tile(const UmmaTile& a, int runs, uint8_t* usm) {
+    constexpr int n = 2 * NT;
+    static_assert(n % 16 == 0 && F > 0, "tcgen05 refresh: n a multiple of 16, compile-time refresh period");
+    __shared__ __align__(8) uint64_t mbar_store;
+    __shared__ uint32_t tmem_slot;
+    __shared__ long long skey[4];
+    __shared__ int sdiv[4];
+    const int PP = 128 / runs;
+    const UmmaSmem<NT> L(PP);
+    const int N = PP * n;
+    const uint32_t ncols = N < 32 ? 32u : (uint32_t)N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int pl = tid / runs, run = tid % runs;
+    const bool live = pl < a.n_live;
+    const EulerConsts k = a.k;
+    int16_t* sAq = reinterpret_cast<int16_t*>(usm + L.off_aq());
+    int16_t* shq = reinterpret_cast<int16_t*>(usm + L.off_hq());
+    float* sh = reinterpret_cast<float*>(usm + L.off_h());
+    float* snd = reinterpret_cast<float*>(usm + L.off_nd());
+    int8_t* sg = reinterpret_cast<int8_t*>(usm + L.off_g());
+    // stage the PP problems (a missing tail problem is all zeros)
+    for (int e = tid; e < PP * n * n; e += 128) sAq[e] = e / (n * n) < a.n_live ? a.Aq[e] : (int16_t)0;
+    for (int e = tid; e < PP * n; e += 128) {
+        const bool have = e / n < a.n_live;
+        const int16_t v = have ? a.hq[e] : (int16_t)0;
+        shq[e] = v;
+        sh[e] = mulrn(mulrn((float)v, 0x1p-14f), k.ce);
+        sg[e] = have && a.g ? a.g[e] : (int8_t)0;
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), ncols);
+    const uint32_t mbar = smem_u32(&mbar_store);
+    if (tid == 0) mbar_init(mbar, 1);
+    __syncthreads();
+    // couplings c 2^-14 as FP16 pairs (exact: at most 15 significant bits), -diag(A)
+    for (int e = tid; e < PP * n * (n / 2); e += 128) {
+        const int row = e / (n / 2), j = 2 * (e % (n / 2));  // row = q n + i
+        const float a0 = (float)sAq[row * n + j] * 0x1p-14f, a1 = (float)sAq[row * n + j + 1] * 0x1p-14f;
+        const uint32_t hi = h2pack(a0, a1);
+        const float2 hf = h2unpack(hi);
+        const uint32_t lo = h2pack(a0 - hf.x, a1 - hf.y);
+        const int off = (row >> 3) * UmmaSmem<NT>::SBO + (j >> 3) * 128 + (row & 7) * 16 + (j & 7) * 2;
+        *reinterpret_cast<uint32_t*>(usm + L.off_ch() + off) = hi;
+        *reinterpret_cast<uint32_t*>(usm + L.off_cl() + off) = lo;
+    }
+    for (int e = tid; e < PP * n; e += 128) {
+        const int q = e / n, i = e % n;
+        snd[e] = -mulrn(mulrn((float)sAq[(q * n + i) * n + i], 0x1p-14f), k.ce);
+    }
+    // A tile whose problems carry bitwise-identical couplings (one channel, one
+    // normaliser: the common case when a channel serves consecutive problems)
+    // multiplies by one C: N = n instead of PP n, every warp reading columns 0..n-1.
+    int differ = 0;
+    for (int e = tid; e < (PP - 1) * n * n; e += 128) differ |= sAq[n * n + e] != sAq[e % (n * n)];
+    tc05_fence_before();
+    const bool shared_c = __syncthreads_or(differ) == 0;
+    tc05_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    // Philox initial amplitudes (the same counters as every other shape)
+    float x1[n], x2[n], e1[n], e2[n], xa, ea = 1.0f;
+    {
+        const uint64_t pg = a.problem0 + (uint64_t)pl;
+        const uint32_t c2 = (uint32_t)pg, c3 = (uint32_t)(pg >> 32);
+#pragma unroll
+        for (int b = 0; b < n / 4; ++b) {
+            const U4 w1 = philox4x32_10(U4{(uint32_t)b, (uint32_t)run, c2, c3}, a.key0, a.key1);
+            const U4 w2 = philox4x32_10(U4{(uint32_t)((n >> 2) + b), (uint32_t)run, c2, c3}, a.key0, a.key1);
+            const uint32_t v1[4] = {w1.x, w1.y, w1.z, w1.w}, v2[4] = {w2.x, w2.y, w2.z, w2.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                x1[4 * b + t] = mulrn((float)((int)(v1[t] >> 8) - 8388608), k.xs);
+                x2[4 * b + t] = mulrn((float)((int)(v2[t] >> 8) - 8388608), k.xs);
+                e1[4 * b + t] = 1.0f;
+                e2[4 * b + t] = 1.0f;
+            }
+        }
+        const U4 wa = philox4x32_10(U4{(uint32_t)((2 * n) >> 2), (uint32_t)run, c2, c3}, a.key0, a.key1);
+        xa = mulrn((float)((int)(wa.x >> 8) - 8388608), k.xs);
+    }
+
+    uint8_t* su_h = usm + L.off_uh();
+    uint8_t* su_l = usm + L.off_ul();
+    const uint32_t a_h = smem_u32(su_h), a_l = smem_u32(su_l);
+    const uint32_t c_h = smem_u32(usm + L.off_ch()), c_l = smem_u32(usm + L.off_cl());
+    const uint32_t idesc = umma_idesc_f16(shared_c ? n : N);
+    const uint32_t my_cols = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(shared_c ? 0 : pl * n);
+    const float mscale = mulrn(k.ce, 0x1p-5f);  // eps dt, and the 2^5 of u
+    const float* shp = sh + pl * n;
+    const float* sndp = snd + pl * n;
+    uint32_t phase = 0;
+    bool failed = false;
+    const int S = a.steps;
+    int t = 0;
+    bool go = true;
+#pragma unroll 1
+    for (; go && t + F <= S; t += F)
+        go = umma_block<NT, F>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed, shp, sndp,
+                               x1, x2, e1, e2, xa, ea, tid, F, mscale, k);
+    if (go && t < S)
+        umma_block<NT, 0>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed, shp, sndp, x1,
+                          x2, e1, e2, xa, ea, tid, S - t, mscale, k);
+    tc05_fence_before();
+    const bool cta_failed = __syncthreads_or(failed ? 1 : 0) != 0;
+    if (cta_failed) {
+        // one more bounded wait for the MMA in flight, then report
+        if (tid == 0) {
+            mbar_wait_bounded(mbar, phase);
+            if (a.err) atomicOr(a.err, 2);
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc05_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+
+    bool valid = !cta_failed && (fabsf(xa) <= k.x_max) && (ea > 0.0f);
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+        valid = valid && (fabsf(x1[i]) <= k.x_max) && (e1[i] > 0.0f) && (fabsf(x2[i]) <= k.x_max) && (e2[i] > 0.0f);
+    const int sa = xa >= 0.0f ? 1 : -1;
+    const int8_t* g = sg + pl * n;
+    int d[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int s1 = x1[i] >= 0.0f ? 1 : -1, s2 = x2[i] >= 0.0f ? 1 : -1;
+        int di = sa * (s1 + s2) / 2;
+        if (a.level_max > 0) {
+            const int xv = (int)g[i] + 2 * di;
+            if (xv > a.level_max || xv < -a.level_max) di = 0;
+        }
+        d[i] = di;
+    }
+    // exact quantised energy of this anneal's offsets
+    const int16_t* Aq = sAq + pl * n * n;
+    const int16_t* hq = shq + pl * n;
+    int E = 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) r += (int)Aq[i * n + j] * d[j];
+        E -= d[i] * r;
+        E -= (int)hq[i] * d[i];
+    }
+    const bool keep = valid && E <= 0;
+    const int Ec = keep ? E : 0;
+    long long key = (long long)Ec * 4294967296LL + (long long)run;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long other = __shfl_xor_sync(0xffffffffu, key, o);
+        key = other < key ? other : key;
+    }
+    const unsigned divmask = __ballot_sync(0xffffffffu, !valid);
+    if (lane == 0) {
+        skey[warp] = key;
+        sdiv[warp] = __popc(divmask);
+    }
+    __syncthreads();
+    const int wpp = runs / 32, w0 = pl * wpp;  // this problem's warps
+    long long best = skey[w0];
+    int ndiv = sdiv[w0];
+    for (int w = 1; w < wpp; ++w) {
+        best = skey[w0 + w] < best ? skey[w0 + w] : best;
+        ndiv += sdiv[w0 + w];
+    }
+    const int best_run = (int)(best & 0xffffffffLL);
+    if (live && run == best_run) {
+        const int p = pl;  // within the tile
+        if (a.d_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) a.d_out[(size_t)p * n + i] = keep ? (int8_t)d[i] : (int8_t)0;
+        }
+        const int bestE = (int)((best - (long long)best_run) / 4294967296LL);
+        if (a.E_out) a.E_out[p] = bestE;
+        if (a.run_out) a.run_out[p] = best_run;
+        if (a.ndiv_out) a.ndiv_out[p] = ndiv;
+        if (a.x_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) a.x_out[(size_t)p * n + i] = (int8_t)((int)g[i] + 2 * (keep ? d[i] : 0));
+        }
+        if (a.guess_out) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) a.guess_out[(size_t)p * n + i] = g[i];
+        }
+        if (a.sym_out) {
+            const int side = 1 << (a.mod_bits >> 1), Lv = side - 1;
+            uint8_t* so = a.sym_out + (size_t)p * NT;
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                const int xr = (int)g[i] + 2 * (keep ? d[i] : 0);
+                const int xi = (int)g[NT + i] + 2 * (keep ? d[NT + i] : 0);
+                so[i] = (uint8_t)(((xr + Lv) / 2) * side + (xi + Lv) / 2);
+            }
+        }
+    }
+}
+
+template <int NT, int F>
+__global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int runs) {
+    constexpr int n = 2 * NT;
+    extern __shared__ __align__(128) uint8_t usm[];
+    const int PP = 128 / runs;
+    const int base = blockIdx.x * PP;
+    auto at = [&](auto* ptr, size_t per) { return ptr ? ptr + (size_t)base * per : ptr; };
+    UmmaTile t;
+    t.Aq = a.Aq + (size_t)base * n * n;
+    t.hq = a.hq + (size_t)base * n;
+    t.g = at(a.g, n);
+    t.n_live = min(PP, a.n_problems - base);
+    t.problem0 = a.problem_offset + (uint64_t)base;
+    t.key0 = a.key0;
+    t.key1 = a.key1;
+    t.level_max = a.level_max;
+    t.steps = a.steps;
+    t.k = a.k;
+    t.err = a.err;
+    t.d_out = at(a.d_out, n);
+    t.E_out = at(a.E_out, 1);
+    t.run_out = at(a.run_out, 1);
+    t.ndiv_out = at(a.ndiv_out, 1);
+    t.x_out = at(a.x_out, n);
+    t.guess_out = nullptr;
+    t.sym_out = at(a.sym_out, NT);
+    t.mod_bits = a.mod_bits;
+    umma_tile<NT, F>(t, runs, usm);
+}
+
+}  // namespace mmgap
