@@ -444,9 +444,12 @@ class Context:
 
 class Batch:
     """mmgap_batch: a fixed set of uplink jobs of mixed sizes run by one
-    persistent kernel launch (optionally replayed from a CUDA graph).  The
-    jobs' tensors must stay alive (and at the same addresses) for the life of
-    the batch; their contents may change between runs."""
+    builder and one solver launch (optionally replayed from a CUDA graph):
+    one CTA per problem, persistent warps (persistent=True), or tcgen05 tiles
+    of 4 problems for 8 and 16 users (tensor_core=True, the precision variant
+    of solver shape 8).  The jobs' tensors must stay alive (and at the same
+    addresses) for the life of the batch; their contents may change between
+    runs."""
 
     def __init__(self, device: int, params: Params, jobs, keepalive=(), persistent: bool = False,
                  tensor_core: bool = False):
