@@ -88,6 +88,28 @@ def test_tcgen05_shared_couplings(mm, n_t, runs):
 
 
 @pytest.mark.parametrize("n_t", [8, 16])
+def test_tcgen05_results_do_not_depend_on_tiling(mm, n_t):
+    """Shape 8 groups 4 problems per CTA from each chunk's start; a workspace
+    that forces chunks of a few problems regroups them (and changes which tiles
+    share one coupling operand), yet every problem's bits stay the same: each
+    product element depends only on its own row and column."""
+    pkg, ctx = mm
+    w = synth.uplink(300 + n_t, n_t, n_t, 4, n_sub=9, n_sym=14, snr_db=14.0)
+    prm = pkg.Params.default(steps=60)
+    outs = []
+    for ws in (96 * 1024 if n_t == 16 else 24 * 1024, 0):
+        with pkg.Context(0, workspace_bytes=ws) as c:
+            c.set_solver_variant(n_t, 8)
+            o = c.detect(T(w["H"]), T(w["y"]), T(w["noise_var"]), 4, prm, 5, chan_index=T(w["chan_index"]),
+                         want_energy=True, want_offset=True, want_ndiv=True)
+            torch.cuda.synchronize()
+            assert c.device_errors() == 0
+            outs.append({k: v.cpu().numpy() for k, v in o.items()})
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+@pytest.mark.parametrize("n_t", [8, 16])
 def test_tcgen05_long_anneals_and_96_runs(mm, n_t):
     """Shape 8 over full 200-step anneals (every refresh through tensor memory):
     energies stay exact and no wait expires; 96 anneals (not a divisor of the
