@@ -1,4 +1,5 @@
-// tcgen05 field refresh (solver shape 8): UMMA into tensor memory, per-job kernel.
+// tcgen05 field refresh (solver shape 8): the 128-anneal tile (umma_tile, also run by the batched
+// launch) and the per-job kernel.
 #pragma once
 #include "solve.cuh"
 
