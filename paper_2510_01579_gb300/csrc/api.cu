@@ -142,6 +142,7 @@ cudaError_t dispatch_nt(int nt, Args&&... args) {
 }
 
 template <int NT> struct OpBuild { static cudaError_t run(const BuildArgs& a, cudaStream_t s) { return launch_build_detect<NT>(a, s); } };
+template <int NT> struct OpFactor { static cudaError_t run(const ChanFactorArgs& a, cudaStream_t s) { return launch_chan_factor<NT>(a, s); } };
 template <int NT> struct OpSolve { static cudaError_t run(const SolveArgs& a, int r, cudaStream_t s) { return launch_solve<NT>(a, r, s); } };
 template <int NT> struct OpVppInv { static cudaError_t run(const VppInvArgs& a, cudaStream_t s) { return launch_vpp_inverse<NT>(a, s); } };
 template <int NT> struct OpVppInvIr { static cudaError_t run(const VppInvArgs& a, cudaStream_t s) { return launch_vpp_inverse_ir<NT>(a, s); } };
@@ -620,8 +621,42 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
         float* gc = nullptr;
         size_t gc_bytes = 0;
         if ((st = job_gram(ctx, J, s, &gc, &gc_bytes)) != MMGAP_OK) return st;
-        char* base = ctx->ws + gc_bytes;
-        const size_t avail = ctx->ws_bytes - gc_bytes;
+        // Channels that serve several problems (the symbols of a subcarrier, the
+        // resource elements of a PRB) are factorised once: the builder of a
+        // problem whose rho equals its channel's reads the factor instead of
+        // repeating the column-sequential Cholesky (the same bits).  Skipped when
+        // the workspace cannot hold the factors and one problem besides.
+        size_t fac_bytes = 0;
+        const float* L_pre = nullptr;
+        const float* rho_pre = nullptr;
+        const int32_t* chol_pre = nullptr;
+        if (!gc && J.chan_index && J.n_chan < J.n_problems) {
+            const size_t nc = (size_t)J.n_chan;
+            const size_t lb = align_up(nc * 2 * J.n_t * J.n_t * sizeof(float)), rb = align_up(nc * 4);
+            if (gc_bytes + lb + 3 * rb + per + 3 * kAlign <= ctx->ws_bytes) {
+                char* fb = ctx->ws + gc_bytes;
+                ChanFactorArgs f{};
+                f.H = J.H;
+                f.chan_index = J.chan_index;
+                f.noise_var = J.noise_var;
+                f.n_r = J.n_r;
+                f.n_problems = J.n_problems;
+                f.n_chan = J.n_chan;
+                qam_kappa(J.mod_bits, &f.kappa, &f.kappa2);
+                f.L_out = (float*)fb;
+                f.rho_out = (float*)(fb + lb);
+                f.chol_out = (int32_t*)(fb + lb + rb);
+                f.first = (int32_t*)(fb + lb + 2 * rb);
+                cudaError_t e = dispatch_nt<OpFactor>(J.n_t, f, s);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "chan_factor launch");
+                L_pre = f.L_out;
+                rho_pre = f.rho_out;
+                chol_pre = f.chol_out;
+                fac_bytes = lb + 3 * rb;
+            }
+        }
+        char* base = ctx->ws + gc_bytes + fac_bytes;
+        const size_t avail = ctx->ws_bytes - gc_bytes - fac_bytes;
         // chunk so that three aligned regions of chunk size fit the workspace
         long long chunk = (long long)(avail / (per + 3 * kAlign));
         if (chunk < 1) return fail(ctx, MMGAP_ENOMEM, "workspace of %zu bytes holds no problem", ctx->ws_bytes);
@@ -634,6 +669,9 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
             if (p0 > 0 && (st = timing_mark(ctx, 0, s)) != MMGAP_OK) return st;
             BuildArgs b{};
             b.Gc_pre = gc ? (J.chan_index ? gc : gc + (size_t)p0 * 2 * J.n_t * J.n_t) : nullptr;
+            b.L_pre = L_pre;
+            b.rho_pre = rho_pre;
+            b.chol_pre = chol_pre;
             b.H = J.chan_index ? J.H : J.H + (size_t)p0 * 2 * J.n_r * J.n_t;
             b.chan_index = J.chan_index ? J.chan_index + p0 : nullptr;
             b.y = J.y + (size_t)p0 * 2 * J.n_r;

@@ -27,48 +27,14 @@ struct BuildOut {
     int32_t* sigma_exp; // or nullptr
 };
 
-// Build problem p of `a` with one warp; ws = build_smem_floats<NT>(n_r)
-// floats of this warp's shared memory.
+// Tasks t in [t0, t1) of a warp: t < NT^2 the Gram element (i, j) = (t / NT,
+// t % NT) of G_c = Hs^H Hs (upper triangle, mirrored), t >= NT^2 the matched
+// filter m_i = (Hs^H y)_i, i = t - NT^2.  Each value's FMA order is fixed, so
+// it does not depend on which lane (or which kernel) computes it.
 template <int NT>
-__device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, int lane, float* ws, const BuildOut& o) {
-    constexpr int n = 2 * NT;
-    const int n_r = a.n_r;
-    float* Hs = ws;
-    float* Gc = Hs + 2 * n_r * NT;
-    float* Lc = Gc + 2 * NT * NT;
-    float* yv = Lc + 2 * NT * NT;
-    float* zv = yv + 2 * n_r;
-    float* mv = zv + 2 * n_r;  // matched filter [NT] c
-    float* gv = mv + 2 * NT;   // g as floats [2NT]
-    int* flag = reinterpret_cast<int*>(gv + 2 * NT);
-    int* perm = flag + 4;      // position -> user (SIC)
-    float* dg = reinterpret_cast<float*>(perm + NT);  // current Schur diagonal per user (SIC)
-
-    const int c = a.chan_index ? a.chan_index[p] : p;
-    if (c < 0 || c >= a.n_chan) {  // bad channel index: flag it, emit an all-zero problem
-        if (lane == 0) atomicOr(a.err, kErrChanIndex);
-        if (o.Aq)
-            for (int e = lane; e < n * n; e += 32) o.Aq[e] = 0;
-        for (int e = lane; e < n; e += 32) {
-            if (o.hq) o.hq[e] = 0;
-            o.g[e] = 0;
-        }
-        __syncwarp();
-        return;
-    }
-    const float* Hg = a.H + (size_t)c * 2 * n_r * NT;
-    const float* yg = a.y + (size_t)p * 2 * n_r;
-    for (int e = lane; e < 2 * n_r * NT; e += 32) Hs[e] = mulrn(a.kappa, Hg[e]);
-    for (int e = lane; e < 2 * n_r; e += 32) yv[e] = yg[e];
-    if (lane == 0) flag[0] = 0;
-    __syncwarp();
-
-    // Gram G_c = Hs^H Hs (upper triangle + Hermitian mirror) and m = Hs^H y.
-    // With a precomputed (tensor-core) Gram only the matched filter is formed here.
-    const float* Gpre = a.Gc_pre ? a.Gc_pre + (size_t)c * 2 * NT * NT : nullptr;
-    if (Gpre)
-        for (int e = lane; e < 2 * NT * NT; e += 32) Gc[e] = Gpre[e];
-    for (int t = lane + (Gpre ? NT * NT : 0); t < NT * NT + NT; t += 32) {
+__device__ __forceinline__ void gram_mf_warp(const float* Hs, const float* yv, int n_r, float* Gc, float* mv, int t0,
+                                             int t1, int lane) {
+    for (int t = t0 + lane; t < t1; t += 32) {
         if (t < NT * NT) {
             const int i = t / NT, j = t % NT;
             if (i > j) continue;
@@ -111,6 +77,132 @@ __device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, in
             mv[2 * i + 1] = im;
         }
     }
+}
+
+// Cholesky of B = G_c + rho I (Eq. 3), left-looking, one column per step;
+// lane j the pivot, lanes i > j the rest.  MMSE factors in natural order;
+// MMSE-SIC (Sec. 3.2.2) pivots on the smallest current Schur diagonal (ties:
+// first position), rows of L being positions (perm: position -> user).  L goes
+// to Lc (lower triangle); flag[0] is set on a failed pivot (the pivot is then
+// taken as 1).  Whole warp.
+template <int NT>
+__device__ __forceinline__ void cholesky_warp(const float* Gc, float rho, bool sic, float* Lc, int* flag, int* perm,
+                                              float* dg, int lane) {
+    if (lane < NT) {
+        perm[lane] = lane;
+        dg[lane] = addrn(Gc[2 * (lane * NT + lane)], rho);
+    }
+    __syncwarp();
+    for (int j = 0; j < NT; ++j) {
+        if (sic) {
+            if (lane == 0) {
+                int best = j;
+                for (int i = j + 1; i < NT; ++i)
+                    if (dg[perm[i]] < dg[perm[best]]) best = i;
+                flag[1] = best;
+                const int t = perm[j];
+                perm[j] = perm[best];
+                perm[best] = t;
+            }
+            __syncwarp();
+            const int best = flag[1];
+            if (lane < j && best != j) {  // swap the computed part of rows j and best
+                const float r0 = Lc[2 * (j * NT + lane)], r1 = Lc[2 * (j * NT + lane) + 1];
+                Lc[2 * (j * NT + lane)] = Lc[2 * (best * NT + lane)];
+                Lc[2 * (j * NT + lane) + 1] = Lc[2 * (best * NT + lane) + 1];
+                Lc[2 * (best * NT + lane)] = r0;
+                Lc[2 * (best * NT + lane) + 1] = r1;
+            }
+            __syncwarp();
+        }
+        const int u = sic ? perm[j] : j;
+        if (lane == j) {
+            float d;
+            if (sic) {
+                d = dg[u];
+            } else {
+                d = addrn(Gc[2 * (j * NT + j)], rho);
+                for (int k = 0; k < j; ++k) {
+                    const float lr = Lc[2 * (j * NT + k)], li = Lc[2 * (j * NT + k) + 1];
+                    d = fmarn(-lr, lr, d);
+                    d = fmarn(-li, li, d);
+                }
+            }
+            const bool ok = (d > 0.0f) && !isinf(d);
+            if (!ok) flag[0] = 1;
+            Lc[2 * (j * NT + j)] = ok ? __fsqrt_rn(d) : 1.0f;
+            Lc[2 * (j * NT + j) + 1] = 0.0f;
+        }
+        __syncwarp();
+        const float ljj = Lc[2 * (j * NT + j)];
+        if (lane > j && lane < NT) {
+            const int i = lane;
+            const int v = sic ? perm[i] : i;
+            float re = Gc[2 * (v * NT + u)], im = Gc[2 * (v * NT + u) + 1];
+            for (int k = 0; k < j; ++k) {
+                const float ar = Lc[2 * (i * NT + k)], ai = Lc[2 * (i * NT + k) + 1];
+                const float br = Lc[2 * (j * NT + k)], bi = Lc[2 * (j * NT + k) + 1];
+                re = fmarn(-ar, br, re);
+                re = fmarn(-ai, bi, re);
+                im = fmarn(-ai, br, im);
+                im = fmarn(ar, bi, im);
+            }
+            const float lr = __fdiv_rn(re, ljj), li = __fdiv_rn(im, ljj);
+            Lc[2 * (i * NT + j)] = lr;
+            Lc[2 * (i * NT + j) + 1] = li;
+            if (sic) {
+                float dv = dg[v];
+                dv = fmarn(-lr, lr, dv);
+                dv = fmarn(-li, li, dv);
+                dg[v] = dv;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Build problem p of `a` with one warp; ws = build_smem_floats<NT>(n_r)
+// floats of this warp's shared memory.
+template <int NT>
+__device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, int lane, float* ws, const BuildOut& o) {
+    constexpr int n = 2 * NT;
+    const int n_r = a.n_r;
+    float* Hs = ws;
+    float* Gc = Hs + 2 * n_r * NT;
+    float* Lc = Gc + 2 * NT * NT;
+    float* yv = Lc + 2 * NT * NT;
+    float* zv = yv + 2 * n_r;
+    float* mv = zv + 2 * n_r;  // matched filter [NT] c
+    float* gv = mv + 2 * NT;   // g as floats [2NT]
+    int* flag = reinterpret_cast<int*>(gv + 2 * NT);
+    int* perm = flag + 4;      // position -> user (SIC)
+    float* dg = reinterpret_cast<float*>(perm + NT);  // current Schur diagonal per user (SIC)
+
+    const int c = a.chan_index ? a.chan_index[p] : p;
+    if (c < 0 || c >= a.n_chan) {  // bad channel index: flag it, emit an all-zero problem
+        if (lane == 0) atomicOr(a.err, kErrChanIndex);
+        if (o.Aq)
+            for (int e = lane; e < n * n; e += 32) o.Aq[e] = 0;
+        for (int e = lane; e < n; e += 32) {
+            if (o.hq) o.hq[e] = 0;
+            o.g[e] = 0;
+        }
+        __syncwarp();
+        return;
+    }
+    const float* Hg = a.H + (size_t)c * 2 * n_r * NT;
+    const float* yg = a.y + (size_t)p * 2 * n_r;
+    for (int e = lane; e < 2 * n_r * NT; e += 32) Hs[e] = mulrn(a.kappa, Hg[e]);
+    for (int e = lane; e < 2 * n_r; e += 32) yv[e] = yg[e];
+    if (lane == 0) flag[0] = 0;
+    __syncwarp();
+
+    // Gram G_c = Hs^H Hs (upper triangle + Hermitian mirror) and m = Hs^H y.
+    // With a precomputed (tensor-core) Gram only the matched filter is formed here.
+    const float* Gpre = a.Gc_pre ? a.Gc_pre + (size_t)c * 2 * NT * NT : nullptr;
+    if (Gpre)
+        for (int e = lane; e < 2 * NT * NT; e += 32) Gc[e] = Gpre[e];
+    gram_mf_warp<NT>(Hs, yv, n_r, Gc, mv, Gpre ? NT * NT : 0, NT * NT + NT, lane);
     __syncwarp();
 
     const int side = 1 << (a.mod_bits >> 1);
@@ -128,82 +220,17 @@ __device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, in
         }
         __syncwarp();
     } else {
-        // Cholesky of B = G_c + rho I (rho = noise_var kappa^2), left-looking, one
-        // column per step; lane j the pivot, lanes i > j the rest.  MMSE (Eq. 3)
-        // factors in natural order; MMSE-SIC (Sec. 3.2.2) pivots on the smallest
-        // current Schur diagonal (ties: first position), rows of L being positions.
+        // Cholesky of B = G_c + rho I, rho = noise_var kappa^2 (cholesky_warp)
         const bool sic = a.guess_mode == 1;
         const float rho = mulrn(a.noise_var[p], a.kappa2);
-        if (lane < NT) {
-            perm[lane] = lane;
-            dg[lane] = addrn(Gc[2 * (lane * NT + lane)], rho);
-        }
-        __syncwarp();
-        for (int j = 0; j < NT; ++j) {
-            if (sic) {
-                if (lane == 0) {
-                    int best = j;
-                    for (int i = j + 1; i < NT; ++i)
-                        if (dg[perm[i]] < dg[perm[best]]) best = i;
-                    flag[1] = best;
-                    const int t = perm[j];
-                    perm[j] = perm[best];
-                    perm[best] = t;
-                }
-                __syncwarp();
-                const int best = flag[1];
-                if (lane < j && best != j) {  // swap the computed part of rows j and best
-                    const float r0 = Lc[2 * (j * NT + lane)], r1 = Lc[2 * (j * NT + lane) + 1];
-                    Lc[2 * (j * NT + lane)] = Lc[2 * (best * NT + lane)];
-                    Lc[2 * (j * NT + lane) + 1] = Lc[2 * (best * NT + lane) + 1];
-                    Lc[2 * (best * NT + lane)] = r0;
-                    Lc[2 * (best * NT + lane) + 1] = r1;
-                }
-                __syncwarp();
-            }
-            const int u = sic ? perm[j] : j;
-            if (lane == j) {
-                float d;
-                if (sic) {
-                    d = dg[u];
-                } else {
-                    d = addrn(Gc[2 * (j * NT + j)], rho);
-                    for (int k = 0; k < j; ++k) {
-                        const float lr = Lc[2 * (j * NT + k)], li = Lc[2 * (j * NT + k) + 1];
-                        d = fmarn(-lr, lr, d);
-                        d = fmarn(-li, li, d);
-                    }
-                }
-                const bool ok = (d > 0.0f) && !isinf(d);
-                if (!ok) flag[0] = 1;
-                Lc[2 * (j * NT + j)] = ok ? __fsqrt_rn(d) : 1.0f;
-                Lc[2 * (j * NT + j) + 1] = 0.0f;
-            }
+        if (!sic && a.L_pre && a.rho_pre[c] == rho) {
+            // this channel's factor, made once by chan_factor_kernel with the same rho: the same bits
+            const float* Lg = a.L_pre + (size_t)c * 2 * NT * NT;
+            for (int e = lane; e < 2 * NT * NT; e += 32) Lc[e] = Lg[e];
+            if (lane == 0) flag[0] = a.chol_pre[c];
             __syncwarp();
-            const float ljj = Lc[2 * (j * NT + j)];
-            if (lane > j && lane < NT) {
-                const int i = lane;
-                const int v = sic ? perm[i] : i;
-                float re = Gc[2 * (v * NT + u)], im = Gc[2 * (v * NT + u) + 1];
-                for (int k = 0; k < j; ++k) {
-                    const float ar = Lc[2 * (i * NT + k)], ai = Lc[2 * (i * NT + k) + 1];
-                    const float br = Lc[2 * (j * NT + k)], bi = Lc[2 * (j * NT + k) + 1];
-                    re = fmarn(-ar, br, re);
-                    re = fmarn(-ai, bi, re);
-                    im = fmarn(-ai, br, im);
-                    im = fmarn(ar, bi, im);
-                }
-                const float lr = __fdiv_rn(re, ljj), li = __fdiv_rn(im, ljj);
-                Lc[2 * (i * NT + j)] = lr;
-                Lc[2 * (i * NT + j) + 1] = li;
-                if (sic) {
-                    float dv = dg[v];
-                    dv = fmarn(-lr, lr, dv);
-                    dv = fmarn(-li, li, dv);
-                    dg[v] = dv;
-                }
-            }
-            __syncwarp();
+        } else {
+            cholesky_warp<NT>(Gc, rho, sic, Lc, flag, perm, dg, lane);
         }
         const bool chol_failed = flag[0] != 0;
 
@@ -341,6 +368,58 @@ __global__ void __launch_bounds__(kBuildWarps * 32) build_detect_kernel(BuildArg
     o.h32 = a.h32 ? a.h32 + (size_t)p * n : nullptr;
     o.sigma_exp = a.sigma_exp ? a.sigma_exp + p : nullptr;
     build_problem_warp<NT>(a, p, lane, smem + warp * build_smem_floats<NT>(a.n_r), o);
+}
+
+// First problem of each channel (atomic minimum over the problems).
+template <int NT>
+__global__ void chan_first_kernel(ChanFactorArgs a) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.n_problems; p += gridDim.x * blockDim.x) {
+        const int c = a.chan_index[p];
+        if (c >= 0 && c < a.n_chan) atomicMin(a.first + c, p);
+    }
+}
+
+// One warp per channel: Hs = kappa H, the Gram and the MMSE Cholesky factor
+// with rho of the channel's first problem -- the same functions and shared
+// memory layout as build_problem_warp, so a problem with that rho finds the
+// bits its own factorisation would give.
+template <int NT>
+__global__ void __launch_bounds__(kBuildWarps * 32) chan_factor_kernel(ChanFactorArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kBuildWarps + warp;
+    if (c >= a.n_chan) return;  // warp-uniform
+    const int p0 = a.first[c];
+    if (p0 < 0 || p0 >= a.n_problems) {
+        if (lane == 0) a.rho_out[c] = __int_as_float(0x7fc00000);  // NaN: no problem compares equal
+        return;
+    }
+    const int n_r = a.n_r;
+    float* ws = smem + warp * build_smem_floats<NT>(n_r);
+    float* Hs = ws;
+    float* Gc = Hs + 2 * n_r * NT;
+    float* Lc = Gc + 2 * NT * NT;
+    float* yv = Lc + 2 * NT * NT;
+    float* zv = yv + 2 * n_r;
+    float* mv = zv + 2 * n_r;
+    float* gv = mv + 2 * NT;
+    int* flag = reinterpret_cast<int*>(gv + 2 * NT);
+    int* perm = flag + 4;
+    float* dg = reinterpret_cast<float*>(perm + NT);
+    const float* Hg = a.H + (size_t)c * 2 * n_r * NT;
+    for (int e = lane; e < 2 * n_r * NT; e += 32) Hs[e] = mulrn(a.kappa, Hg[e]);
+    if (lane == 0) flag[0] = 0;
+    __syncwarp();
+    gram_mf_warp<NT>(Hs, yv, n_r, Gc, mv, 0, NT * NT, lane);
+    __syncwarp();
+    const float rho = mulrn(a.noise_var[p0], a.kappa2);
+    cholesky_warp<NT>(Gc, rho, false, Lc, flag, perm, dg, lane);
+    float* Lg = a.L_out + (size_t)c * 2 * NT * NT;
+    for (int e = lane; e < 2 * NT * NT; e += 32) Lg[e] = Lc[e];
+    if (lane == 0) {
+        a.rho_out[c] = rho;
+        a.chol_out[c] = flag[0];
+    }
 }
 
 }  // namespace mmgap

@@ -96,6 +96,11 @@ struct BuildArgs {
     float kappa, kappa2;
     int* err;                  // device error word (bit 0: channel index out of range)
     const float* Gc_pre;       // optional precomputed Gram of kappa H per channel, complex [n_chan][n_t][n_t]
+    // optional MMSE Cholesky factor of each channel (chan_factor_kernel), used by a problem whose
+    // rho = noise_var kappa^2 equals the channel's: L complex [n_chan][n_t][n_t], rho, failed-pivot flag
+    const float* L_pre;
+    const float* rho_pre;
+    const int32_t* chol_pre;
     int guess_mode;            // 0: MMSE, 1: MMSE-SIC (sorted Cholesky), 2: given g_in
     const int8_t* g_in;        // [P][n] lattice guesses for guess_mode 2
     // outputs
@@ -105,6 +110,20 @@ struct BuildArgs {
     float* G32;                // [P][n][n] or nullptr
     float* h32;                // [P][n] or nullptr
     int32_t* sigma_exp;        // [P] or nullptr
+};
+
+// Per-channel MMSE factorisation ahead of the builder: for every channel, the
+// Cholesky factor of G_c + rho I with rho from the channel's first problem.
+struct ChanFactorArgs {
+    const float* H;            // complex [n_chan][n_r][n_t]
+    const int32_t* chan_index; // [P]
+    const float* noise_var;    // [P]
+    int n_r, n_problems, n_chan;
+    float kappa, kappa2;
+    int32_t* first;            // scratch [n_chan]: first problem of each channel
+    float* L_out;              // complex [n_chan][n_t][n_t]
+    float* rho_out;            // [n_chan] (NaN for a channel no problem uses)
+    int32_t* chol_out;         // [n_chan] 1 if a pivot failed
 };
 
 // Direct (binary-weighted) spin mapping: the delta build's MMSE guess, Gram
@@ -211,6 +230,7 @@ struct VppOutArgs {
 // Launchers, one set per n_t (defined in inst_nt<N>.cu).  Return the launch
 // error (cudaSuccess on success).
 template <int NT> cudaError_t launch_build_detect(const BuildArgs& a, cudaStream_t s);
+template <int NT> cudaError_t launch_chan_factor(const ChanFactorArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_solve(const SolveArgs& a, int runs, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_inverse(const VppInvArgs& a, cudaStream_t s);
 template <int NT> cudaError_t launch_vpp_inverse_ir(const VppInvArgs& a, cudaStream_t s);

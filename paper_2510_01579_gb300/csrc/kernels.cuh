@@ -34,6 +34,9 @@
     template <> cudaError_t launch_build_detect<NT>(const BuildArgs& a, cudaStream_t s) {                      \
         return launch_build_detect_impl<NT>(a, s);                                                             \
     }                                                                                                          \
+    template <> cudaError_t launch_chan_factor<NT>(const ChanFactorArgs& a, cudaStream_t s) {                  \
+        return launch_chan_factor_impl<NT>(a, s);                                                              \
+    }                                                                                                          \
     template <> cudaError_t launch_solve<NT>(const SolveArgs& a, int runs, cudaStream_t s) {                   \
         return launch_solve_impl<NT>(a, runs, s);                                                              \
     }                                                                                                          \

@@ -22,6 +22,19 @@ cudaError_t launch_build_detect_impl(const BuildArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int NT>
+cudaError_t launch_chan_factor_impl(const ChanFactorArgs& a, cudaStream_t s) {
+    if (a.n_chan <= 0 || a.n_problems <= 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(a.first, 0x7f, (size_t)a.n_chan * sizeof(int32_t), s);  // > any index
+    if (err != cudaSuccess) return err;
+    chan_first_kernel<NT><<<(a.n_problems + 255) / 256, 256, 0, s>>>(a);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const size_t smem = (size_t)kBuildWarps * build_smem_floats<NT>(a.n_r) * sizeof(float);
+    if ((err = ensure_dynamic_smem<chan_factor_kernel<NT>>(smem)) != cudaSuccess) return err;
+    chan_factor_kernel<NT><<<(a.n_chan + kBuildWarps - 1) / kBuildWarps, kBuildWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 // Tuned kernels exist for n_t in {4, 8, 16} and f_mvm in {1, 2}.
 __host__ __device__ constexpr bool tuned_size(int NT) { return NT == 4 || NT == 8 || NT == 16; }
 

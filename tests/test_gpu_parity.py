@@ -230,6 +230,30 @@ def test_detect_chunked_workspace_is_deterministic(mm):
     assert np.array_equal(a["sym"], ref["sym"])
 
 
+@pytest.mark.parametrize("n_t,hold", [(16, "subcarrier"), (8, "prb")])
+def test_detect_per_channel_factorisation(mm, n_t, hold):
+    """Channels shared by several problems are factorised once; problems whose
+    noise variance differs from their channel's first problem factorise for
+    themselves.  With half the noise variances changed, every problem still
+    equals the oracle (which factorises per problem), and a workspace too small
+    for the per-channel factors (so no sharing at all) gives the same bits."""
+    pkg, ctx = mm
+    w = synth.uplink(660 + n_t, n_t, n_t, 4, n_sub=24, n_sym=14, snr_db=14.0, hold=hold)
+    nv = w["noise_var"].copy()
+    nv[1::2] *= np.float32(1.5)
+    w = dict(w, noise_var=nv)
+    prm = pkg.Params.default(steps=60)
+    got = _detect(ctx, w, prm, 9)
+    small = 3 * 1024 if n_t == 8 else 40 * 1024  # holds a problem but not the per-channel factors
+    with pkg.Context(0, workspace_bytes=small) as c2:
+        got2 = _detect(c2, w, prm, 9)
+    for k in got:
+        assert np.array_equal(got[k], got2[k]), k
+    ref = oracle.detect_batch(w["H"], w["y"], w["noise_var"], 4, oparams(prm), 9, w["chan_index"])
+    assert np.array_equal(got["sym"], ref["sym"]) and np.array_equal(got["energy"], ref["E"])
+    assert np.array_equal(got["guess"], ref["g"].astype(np.int8))
+
+
 def test_detect_mixed_jobs_one_call(mm):
     """Jobs of different sizes in one call equal their separate calls."""
     pkg, ctx = mm
