@@ -1266,7 +1266,10 @@ def main():
             "tensor_core_refresh": tc,
             "batched_path": batched,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 2 * chunks, "clocks": clk, "wall_s": wall}
+            # per call: builder + solver per chunk, and the per-channel factorisation (first-problem and
+            # factor kernels) once when channels serve several problems (as here: H per subcarrier or PRB)
+            "gpu_launches": 2 * chunks + (2 * args.steps if w["H"].shape[0] < P else 0), "clocks": clk,
+            "wall_s": wall}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
