@@ -103,6 +103,11 @@ size_t BatchRunner::precode_scratch_bytes(const mmgap_precode_job& J) {
            salign(n_chan * J.n_u * J.n_u * 16) + salign(n_chan * 4);
 }
 
+size_t BatchRunner::factor_bytes(int n_t, int n_chan) {
+    const size_t nc = (size_t)std::max(0, n_chan);
+    return salign(nc * 2 * n_t * n_t * sizeof(float)) + 3 * salign(nc * 4);
+}
+
 size_t BatchRunner::scratch_bytes(int n_t, int n_problems) {
     const size_t n = 2 * (size_t)n_t, P = (size_t)n_problems;
     return salign(P * n * n * 2) + salign(P * n * 2) + salign(P * n);
@@ -260,6 +265,40 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
         }
     }
     if (first > capacity_problems_) return -3;
+    // second pass: per-channel factors for detection jobs whose channels serve
+    // several problems, as far as the remaining scratch allows
+    fac_.clear();
+    for (int i = 0; i < n_jobs; ++i) {
+        const GroupJob& G = jobs[order ? order[i] : i];
+        if (!G.det) continue;
+        const mmgap_detect_job& J = *G.det;
+        if (!J.chan_index || J.n_chan >= J.n_problems || J.n_problems == 0) continue;
+        const size_t fb = factor_bytes(J.n_t, J.n_chan);
+        if (off + fb > scratch_bytes_) continue;
+        const size_t nc = (size_t)J.n_chan, lb = salign(nc * 2 * J.n_t * J.n_t * sizeof(float)), rb = salign(nc * 4);
+        char* base = scratch_ + off;
+        off += fb;
+        BatchJob& B = h_jobs_[i];
+        Factor F{};
+        F.n_t = J.n_t;
+        ChanFactorArgs& f = F.args;
+        f.H = J.H;
+        f.chan_index = J.chan_index;
+        f.noise_var = J.noise_var;
+        f.n_r = J.n_r;
+        f.n_problems = J.n_problems;
+        f.n_chan = J.n_chan;
+        f.kappa = B.b.kappa;
+        f.kappa2 = B.b.kappa2;
+        f.L_out = (float*)base;
+        f.rho_out = (float*)(base + lb);
+        f.chol_out = (int32_t*)(base + lb + rb);
+        f.first = (int32_t*)(base + lb + 2 * rb);
+        B.b.L_pre = f.L_out;
+        B.b.rho_pre = f.rho_out;
+        B.b.chol_pre = f.chol_out;
+        fac_.push_back(F);
+    }
     h_head_->n_jobs = n_jobs;
     h_head_->pad = 0;
     h_head_->total = first;
@@ -287,6 +326,19 @@ cudaError_t vpp_output_nu(int n_u, const VppOutArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t BatchRunner::factor_before(cudaStream_t s) {
+    for (const Factor& F : fac_) {
+        cudaError_t e;
+        switch (F.n_t) {
+        case 16: e = launch_chan_factor<16>(F.args, s); break;
+        case 8: e = launch_chan_factor<8>(F.args, s); break;
+        default: e = launch_chan_factor<4>(F.args, s); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t BatchRunner::precode_before(cudaStream_t s) {
     for (const Precode& R : pre_) {
@@ -376,7 +428,9 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
 }
 
 cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_graph) {
-    cudaError_t e = precode_before(s);
+    cudaError_t e = factor_before(s);
+    if (e != cudaSuccess) return e;
+    e = precode_before(s);
     if (e != cudaSuccess) return e;
     if ((e = run_batch(P, s, use_graph)) != cudaSuccess) return e;
     return precode_after(s);
@@ -474,6 +528,8 @@ mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_param
         max_n_r = std::max(max_n_r, jobs[i].n_r);
         total += jobs[i].n_problems;
         scratch += BatchRunner::scratch_bytes(jobs[i].n_t, jobs[i].n_problems);
+        if (jobs[i].chan_index && jobs[i].n_chan < jobs[i].n_problems)
+            scratch += BatchRunner::factor_bytes(jobs[i].n_t, jobs[i].n_chan);
     }
     int prev = -1;
     cudaGetDevice(&prev);

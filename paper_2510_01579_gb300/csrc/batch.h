@@ -27,6 +27,10 @@ class BatchRunner {
 
     // Scratch bytes (Q14 couplings, field, guess) of one job.
     static size_t scratch_bytes(int n_t, int n_problems);
+    // Scratch bytes of the per-channel MMSE factors of a detection job whose
+    // n_chan channels serve several problems each (optional: staged when the
+    // scratch has room after every job's own scratch).
+    static size_t factor_bytes(int n_t, int n_chan);
     // Scratch bytes of one precoding job: couplings, field, offsets, the
     // channel inverses and their flags.
     static size_t precode_scratch_bytes(const mmgap_precode_job& J);
@@ -62,6 +66,12 @@ class BatchRunner {
     cudaError_t enqueue(const mmgap_params& P, cudaStream_t s);
     cudaError_t run_batch(const mmgap_params& P, cudaStream_t s, bool use_graph);
     cudaError_t precode_before(cudaStream_t s);
+    cudaError_t factor_before(cudaStream_t s);  // per-channel factorisation of the staged jobs
+    struct Factor {
+        int n_t;
+        ChanFactorArgs args;
+    };
+    std::vector<Factor> fac_;
     cudaError_t precode_after(cudaStream_t s);
     std::vector<Precode> pre_;
     void grids(unsigned* build_grid, unsigned* solve_grid) const;
