@@ -26,7 +26,7 @@ struct mmgap_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> events;  // 4 per chunk: start, built, solved, output
     int n_chunks = 0;
-    int variant[17] = {};             // solver launch shape per n_t (0 = default)
+    int variant[33] = {};             // solver launch shape per n_t (0 = default)
     int n_sm = 0;                     // SMs of the device
 };
 
@@ -128,6 +128,9 @@ mmgap_status check_params(mmgap_ctx* ctx, const mmgap_params* P) {
     return MMGAP_OK;
 }
 
+// Operations that also exist for 32 users (delta-mapping detection and the solver only).
+template <template <int> class Op> struct Has32 { static constexpr bool value = false; };
+
 template <template <int> class Op, class... Args>
 cudaError_t dispatch_nt(int nt, Args&&... args) {
     switch (nt) {
@@ -137,6 +140,9 @@ cudaError_t dispatch_nt(int nt, Args&&... args) {
     case 4: return Op<4>::run(args...);
     case 8: return Op<8>::run(args...);
     case 16: return Op<16>::run(args...);
+    case 32:
+        if constexpr (Has32<Op>::value) return Op<32>::run(args...);
+        else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }
@@ -150,6 +156,9 @@ template <int NT> struct OpVppBuild { static cudaError_t run(const VppBuildArgs&
 template <int NT> struct OpVppOut { static cudaError_t run(const VppOutArgs& a, cudaStream_t s) { return launch_vpp_output<NT>(a, s); } };
 template <int NT> struct OpGram { static cudaError_t run(const GramArgs& a, cudaStream_t s) { return launch_gram_tc<NT>(a, s); } };
 template <int NT> struct OpSelect { static cudaError_t run(const SelectArgs& a, cudaStream_t s) { return launch_select<NT>(a, s); } };
+template <> struct Has32<OpBuild> { static constexpr bool value = true; };
+template <> struct Has32<OpFactor> { static constexpr bool value = true; };
+template <> struct Has32<OpSolve> { static constexpr bool value = true; };
 
 // QAM normalisation kappa = 1/sqrt(2 (M-1)/3) and kappa^2, rounded once to float.
 void qam_kappa(int mod_bits, float* kappa, float* kappa2) {
@@ -193,7 +202,10 @@ mmgap_status timing_mark(mmgap_ctx* ctx, int stage, cudaStream_t s) {
 }
 
 mmgap_status check_detect_job(mmgap_ctx* ctx, const mmgap_detect_job& j, bool need_sym) {
-    if (!nt_supported(j.n_t)) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d: supported 1, 2, 3, 4, 8, 16", j.n_t);
+    if (!nt_supported(j.n_t) && j.n_t != 32)
+        return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=%d: supported 1, 2, 3, 4, 8, 16, 32", j.n_t);
+    if (j.n_t == 32 && (j.mapping != MMGAP_MAPPING_DELTA || j.gram_precision != 0))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=32: delta mapping with the FP32 Gram only");
     if (j.n_r < 1 || j.n_r > kMaxNr) return fail(ctx, MMGAP_EUNSUPPORTED, "n_r=%d out of [1, %d]", j.n_r, kMaxNr);
     if (!(j.mod_bits == 2 || j.mod_bits == 4 || j.mod_bits == 6))
         return fail(ctx, MMGAP_EUNSUPPORTED, "mod_bits=%d: supported 2, 4, 6", j.mod_bits);
@@ -532,8 +544,9 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     if (!ctx) return MMGAP_EINVAL;
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
-    if (n < 2 || (n & 1) || !nt_supported(n / 2))
-        return fail(ctx, MMGAP_EUNSUPPORTED, "n=%d: supported 2, 4, 6, 8, 16, 32", n);
+    if (n < 2 || (n & 1) || (!nt_supported(n / 2) && n != 64))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "n=%d: supported 2, 4, 6, 8, 16, 32, 64", n);
+    if (n == 64 && params->f_mvm > 2) return fail(ctx, MMGAP_EUNSUPPORTED, "n=64: f_mvm 1 or 2");
     if (n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
     if (n_problems == 0) return MMGAP_OK;
     if (!A_q || !h_q || !d_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q, h_q or d_out");
@@ -602,8 +615,10 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, MMGAP_EINVAL, "bad jobs array");
-    for (int j = 0; j < n_jobs; ++j)
+    for (int j = 0; j < n_jobs; ++j) {
         if ((st = check_detect_job(ctx, jobs[j], true)) != MMGAP_OK) return st;
+        if (jobs[j].n_t == 32 && params->f_mvm > 2) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=32: f_mvm 1 or 2");
+    }
     CurrentDevice cd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const EulerConsts k = euler_consts(*params);
@@ -850,6 +865,7 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
     if (!job) return fail(ctx, MMGAP_EINVAL, "job is NULL");
     if ((st = check_detect_job(ctx, *job, true)) != MMGAP_OK) return st;
     if (job->mapping != MMGAP_MAPPING_DELTA) return fail(ctx, MMGAP_EUNSUPPORTED, "MMGaP-E uses the delta mapping");
+    if (job->n_t == 32) return fail(ctx, MMGAP_EUNSUPPORTED, "MMGaP-E: n_t up to 16");
     if (stages < 1 || stages > 8) return fail(ctx, MMGAP_EINVAL, "stages=%d out of [1, 8]", stages);
     const mmgap_detect_job& J = *job;
     if (J.n_problems == 0) return MMGAP_OK;

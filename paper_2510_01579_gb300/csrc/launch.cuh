@@ -109,11 +109,31 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
 template <int NT>
 cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
-    const int v = a.spins_out ? (int)kVariantPlain : resolve_variant(NT, a.f_mvm, a.variant, a.n_problems, a.n_sm);
-    if (a.f_mvm == 2) return launch_tuned<NT, 2>(a, runs, v, s);
-    if (a.f_mvm == 1) return launch_tuned<NT, 1>(a, runs, v, s);
-    cac_solve_kernel<NT, 0><<<a.n_problems, runs, 0, s>>>(a);
-    return cudaGetLastError();
+    if constexpr (NT == 32) {
+        // 32 users (n = 64): one launch shape, four threads per anneal with u through a shared-memory
+        // row per anneal; f_mvm 1 or 2 and no spin dump (the API refuses the rest)
+        if (a.spins_out || (a.f_mvm != 1 && a.f_mvm != 2)) return cudaErrorInvalidValue;
+        const size_t smem = (size_t)runs * (2 * NT + 4) * sizeof(float);
+        cudaError_t err;
+        if (a.f_mvm == 2) {
+            if ((err = ensure_dynamic_smem<cac_solve_tuned_kernel<32, 2, 4, true, false, false, true>>(smem)) !=
+                cudaSuccess)
+                return err;
+            cac_solve_tuned_kernel<32, 2, 4, true, false, false, true><<<a.n_problems, 4 * runs, smem, s>>>(a);
+        } else {
+            if ((err = ensure_dynamic_smem<cac_solve_tuned_kernel<32, 1, 4, true, false, false, true>>(smem)) !=
+                cudaSuccess)
+                return err;
+            cac_solve_tuned_kernel<32, 1, 4, true, false, false, true><<<a.n_problems, 4 * runs, smem, s>>>(a);
+        }
+        return cudaGetLastError();
+    } else {
+        const int v = a.spins_out ? (int)kVariantPlain : resolve_variant(NT, a.f_mvm, a.variant, a.n_problems, a.n_sm);
+        if (a.f_mvm == 2) return launch_tuned<NT, 2>(a, runs, v, s);
+        if (a.f_mvm == 1) return launch_tuned<NT, 1>(a, runs, v, s);
+        cac_solve_kernel<NT, 0><<<a.n_problems, runs, 0, s>>>(a);
+        return cudaGetLastError();
+    }
 }
 
 template <int NT>

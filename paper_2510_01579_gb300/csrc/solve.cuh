@@ -310,10 +310,13 @@ __device__ __forceinline__ void euler_pair(float2& x, float2& e, float2 mu, floa
 // (the partner's u_j arrives by shuffle), so each coupling loaded from shared
 // memory feeds two fused multiply-adds; the halves are then swapped.  Every
 // m_i is still the ascending-j FMA chain from 0, so results are unchanged.
-template <int n, int NS, int TPA, bool PACKED, int L, bool PAIR = false>
+// SMEMU (more than two threads per anneal, 32 users): the anneal's u goes
+// through its padded shared-memory row `urow` instead of warp shuffles, since
+// the gathered 2n values would not fit the registers.
+template <int n, int NS, int TPA, bool PACKED, int L, bool PAIR = false, bool SMEMU = false>
 __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, const float* snd, float (&x1)[NS],
                                             float (&x2)[NS], float (&e1)[NS], float (&e2)[NS], float& xa, float& ea,
-                                            int q, int lane, int Lrt, const EulerConsts& k) {
+                                            int q, int lane, int Lrt, const EulerConsts& k, float* urow = nullptr) {
     asm volatile("" ::: "memory");  // keep the coupling loads inside the time loop
     const int row0 = q * NS;
     // u = x1 + x2 of this thread's rows, then of the whole anneal
@@ -329,9 +332,15 @@ __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, co
 #pragma unroll
         for (int i = 0; i < NS; ++i) uo[i] = addrn(x1[i], x2[i]);
     }
-    float u[TPA == 1 ? 1 : n];
+    float u[TPA == 1 || SMEMU ? 1 : n];
     if constexpr (TPA == 1) {
         // uo is the whole anneal's u; used directly below
+    } else if constexpr (SMEMU) {
+        static_assert(TPA > 2 && NS % 4 == 0, "shared-memory u: rows in whole float4s");
+#pragma unroll
+        for (int i = 0; i < NS; i += 4)
+            *reinterpret_cast<float4*>(urow + row0 + i) = make_float4(uo[i], uo[i + 1], uo[i + 2], uo[i + 3]);
+        __syncwarp();
     } else if constexpr (TPA == 2) {
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -395,6 +404,7 @@ __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, co
     for (int j = 0; j < n; ++j) {
         float uj;
         if constexpr (TPA == 1) uj = uo[j];
+        else if constexpr (SMEMU) uj = urow[j];
         else uj = u[j];
         mua = fmarn(sh[j], uj, mua);
         const float4* row = reinterpret_cast<const float4*>(sA + j * n + row0);
@@ -418,6 +428,7 @@ __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, co
         }
     }
     }
+    if constexpr (SMEMU) __syncwarp();  // every read of urow is done before the next refresh rewrites it
     // frozen field: c = m + b x_a, mu1 = c - diag(A) x1, mu2 = c - diag(A) x2
     if constexpr (PACKED) {
         const float2 xa2 = make_float2(xa, xa);
@@ -703,7 +714,7 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
     }
 }
 
-template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false>
+template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false, bool SMEMU = false>
 __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a) {
     constexpr int n = 2 * NT;
     constexpr int NS = n / TPA;
@@ -714,7 +725,8 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
     __shared__ long long skey[4 * TPA];
     __shared__ int sdiv[4 * TPA];
     __shared__ __align__(16) uint32_t tc_af[TC ? TcShape<NT>::AF_WORDS : 1];
-    extern __shared__ __align__(16) uint32_t tc_ws[];  // TC: TcShape<NT>::warp_words(32 / TPA) per warp (dynamic)
+    // dynamic: TC, TcShape<NT>::warp_words(32 / TPA) per warp; SMEMU, a row of n + 4 floats per anneal
+    extern __shared__ __align__(16) uint32_t tc_ws[];
     const int p = blockIdx.x;
     const int tid = threadIdx.x, T = blockDim.x;
     const int q = tid % TPA, run = tid / TPA;
@@ -773,11 +785,14 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
             tc_block<NT, F, TPA>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, F, mscale, k);
         if (t < S) tc_block<NT, 0, TPA>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, S - t, mscale, k);
     } else {
+        float* urow = SMEMU ? reinterpret_cast<float*>(tc_ws) + run * (n + 4) : nullptr;
 #pragma unroll 1
         for (; t + F <= S; t += F)
-            tuned_block<n, NS, TPA, PACKED, F, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
+            tuned_block<n, NS, TPA, PACKED, F, PAIR, SMEMU>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k,
+                                                            urow);
         if (t < S)
-            tuned_block<n, NS, TPA, PACKED, 0, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
+            tuned_block<n, NS, TPA, PACKED, 0, PAIR, SMEMU>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t,
+                                                            k, urow);
     }
 
     // validity over the whole anneal
