@@ -110,10 +110,11 @@ template <int NT>
 cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
     if constexpr (NT == 32) {
-        // 32 users (n = 64): one launch shape, four threads per anneal with u through a shared-memory
-        // row per anneal; f_mvm 1 or 2 and no spin dump (the API refuses the rest)
-        if (a.spins_out || (a.f_mvm != 1 && a.f_mvm != 2)) return cudaErrorInvalidValue;
-        const size_t smem = (size_t)runs * (2 * NT + 4) * sizeof(float);
+        // 32 users (n = 64): one launch shape, four warps per 32 anneals (one 16-row block each) with
+        // u through double-buffered shared-memory rows; f_mvm 1 or 2 and no spin dump (the API refuses
+        // the rest)
+        if (a.spins_out || (a.f_mvm != 1 && a.f_mvm != 2) || runs % 32 != 0) return cudaErrorInvalidValue;
+        const size_t smem = 2 * (size_t)runs * (2 * NT + 4) * sizeof(float);
         cudaError_t err;
         if (a.f_mvm == 2) {
             if ((err = ensure_dynamic_smem<cac_solve_tuned_kernel<32, 2, 4, true, false, false, true>>(smem)) !=
