@@ -663,7 +663,7 @@ def run_ul32(args):
             "ber": {"mmgap": ber, "mmse": ber_mmse},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "cac_solve, 32 users (four threads per anneal, u through shared memory)"},
+                         "kernel": "cac_solve_rows (32 users: two anneals x 8 rows per thread)"},
             "clocks": clk}
     print(json.dumps(line), flush=True)
     ctx.close()

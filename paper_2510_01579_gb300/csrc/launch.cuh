@@ -2,6 +2,7 @@
 #pragma once
 #include "build.cuh"
 #include "solve.cuh"
+#include "solve_rows.cuh"
 #include "umma.cuh"
 #include "batch_kernels.cuh"
 #include "direct.cuh"
@@ -110,22 +111,17 @@ template <int NT>
 cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
     if constexpr (NT == 32) {
-        // 32 users (n = 64): one launch shape, four warps per 32 anneals (one 16-row block each) with
-        // u through double-buffered shared-memory rows; f_mvm 1 or 2 and no spin dump (the API refuses
-        // the rest)
+        // 32 users (n = 64): the row-block kernel (two anneals x 8 rows per thread, four warps per 32
+        // anneals); f_mvm 1 or 2 and no spin dump (the API refuses the rest)
         if (a.spins_out || (a.f_mvm != 1 && a.f_mvm != 2) || runs % 32 != 0) return cudaErrorInvalidValue;
-        const size_t smem = 2 * (size_t)runs * (2 * NT + 4) * sizeof(float);
+        const size_t smem = rows_dyn_bytes(2 * NT, runs);
         cudaError_t err;
         if (a.f_mvm == 2) {
-            if ((err = ensure_dynamic_smem<cac_solve_tuned_kernel<32, 2, 4, true, false, false, true>>(smem)) !=
-                cudaSuccess)
-                return err;
-            cac_solve_tuned_kernel<32, 2, 4, true, false, false, true><<<a.n_problems, 4 * runs, smem, s>>>(a);
+            if ((err = ensure_dynamic_smem<cac_solve_rows_kernel<32, 2>>(smem)) != cudaSuccess) return err;
+            cac_solve_rows_kernel<32, 2><<<a.n_problems, 4 * runs, smem, s>>>(a);
         } else {
-            if ((err = ensure_dynamic_smem<cac_solve_tuned_kernel<32, 1, 4, true, false, false, true>>(smem)) !=
-                cudaSuccess)
-                return err;
-            cac_solve_tuned_kernel<32, 1, 4, true, false, false, true><<<a.n_problems, 4 * runs, smem, s>>>(a);
+            if ((err = ensure_dynamic_smem<cac_solve_rows_kernel<32, 1>>(smem)) != cudaSuccess) return err;
+            cac_solve_rows_kernel<32, 1><<<a.n_problems, 4 * runs, smem, s>>>(a);
         }
         return cudaGetLastError();
     } else {

@@ -310,17 +310,10 @@ __device__ __forceinline__ void euler_pair(float2& x, float2& e, float2 mu, floa
 // (the partner's u_j arrives by shuffle), so each coupling loaded from shared
 // memory feeds two fused multiply-adds; the halves are then swapped.  Every
 // m_i is still the ascending-j FMA chain from 0, so results are unchanged.
-// SMEMU (row blocks across warps, 32 users): the TPA threads of an anneal
-// sit in TPA different warps at the same lane, warp q holding rows
-// [q NS, (q+1) NS) of 32 anneals, so every coupling load of a warp is one
-// broadcast address.  The anneal's u goes through its padded shared-memory
-// row `urow` (double-buffered by the caller), published to the TPA warps by
-// the named barrier `bar`.
-template <int n, int NS, int TPA, bool PACKED, int L, bool PAIR = false, bool SMEMU = false>
+template <int n, int NS, int TPA, bool PACKED, int L, bool PAIR = false>
 __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, const float* snd, float (&x1)[NS],
                                             float (&x2)[NS], float (&e1)[NS], float (&e2)[NS], float& xa, float& ea,
-                                            int q, int lane, int Lrt, const EulerConsts& k, float* urow = nullptr,
-                                            int bar = 0) {
+                                            int q, int lane, int Lrt, const EulerConsts& k) {
     asm volatile("" ::: "memory");  // keep the coupling loads inside the time loop
     const int row0 = q * NS;
     // u = x1 + x2 of this thread's rows, then of the whole anneal
@@ -336,15 +329,9 @@ __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, co
 #pragma unroll
         for (int i = 0; i < NS; ++i) uo[i] = addrn(x1[i], x2[i]);
     }
-    float u[TPA == 1 || SMEMU ? 1 : n];
+    float u[TPA == 1 ? 1 : n];
     if constexpr (TPA == 1) {
         // uo is the whole anneal's u; used directly below
-    } else if constexpr (SMEMU) {
-        static_assert(TPA > 2 && NS % 4 == 0, "shared-memory u: rows in whole float4s");
-#pragma unroll
-        for (int i = 0; i < NS; i += 4)
-            *reinterpret_cast<float4*>(urow + row0 + i) = make_float4(uo[i], uo[i + 1], uo[i + 2], uo[i + 3]);
-        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(32 * TPA) : "memory");
     } else if constexpr (TPA == 2) {
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -404,18 +391,11 @@ __device__ __forceinline__ void tuned_block(const float* sA, const float* sh, co
             m[H + i] = half ? mo[i] : other;
         }
     } else {
-    float4 u4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // SMEMU: u[j..j+3] in one conflict-free load
 #pragma unroll
     for (int j = 0; j < n; ++j) {
         float uj;
-        if constexpr (TPA == 1) {
-            uj = uo[j];
-        } else if constexpr (SMEMU) {
-            if ((j & 3) == 0) u4 = *reinterpret_cast<const float4*>(urow + j);
-            uj = (j & 3) == 0 ? u4.x : (j & 3) == 1 ? u4.y : (j & 3) == 2 ? u4.z : u4.w;
-        } else {
-            uj = u[j];
-        }
+        if constexpr (TPA == 1) uj = uo[j];
+        else uj = u[j];
         mua = fmarn(sh[j], uj, mua);
         const float4* row = reinterpret_cast<const float4*>(sA + j * n + row0);
 #pragma unroll
@@ -723,7 +703,7 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
     }
 }
 
-template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false, bool SMEMU = false>
+template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false>
 __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a) {
     constexpr int n = 2 * NT;
     constexpr int NS = n / TPA;
@@ -734,15 +714,11 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
     __shared__ long long skey[4 * TPA];
     __shared__ int sdiv[4 * TPA];
     __shared__ __align__(16) uint32_t tc_af[TC ? TcShape<NT>::AF_WORDS : 1];
-    // dynamic: TC, TcShape<NT>::warp_words(32 / TPA) per warp; SMEMU, two buffers of a row of n + 4
-    // floats per anneal
-    extern __shared__ __align__(16) uint32_t tc_ws[];
+    extern __shared__ __align__(16) uint32_t tc_ws[];  // TC: TcShape<NT>::warp_words(32 / TPA) per warp (dynamic)
     const int p = blockIdx.x;
     const int tid = threadIdx.x, T = blockDim.x;
+    const int q = tid % TPA, run = tid / TPA;
     const int lane = tid & 31, warp = tid >> 5;
-    // SMEMU: warp w holds rows block w % TPA of anneals 32 (w / TPA) + lane
-    const int q = SMEMU ? warp % TPA : tid % TPA;
-    const int run = SMEMU ? (warp / TPA) * 32 + lane : tid / TPA;
     const int row0 = q * NS;
     const EulerConsts k = a.k;
     {
@@ -797,33 +773,20 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
             tc_block<NT, F, TPA>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, F, mscale, k);
         if (t < S) tc_block<NT, 0, TPA>(tc_af, sm.h, sm.nd, wsm, x1, x2, e1, e2, xa, ea, lane, S - t, mscale, k);
     } else {
-        const int ubuf = (T / TPA) * (n + 4);  // floats per buffer
-        float* urow = SMEMU ? reinterpret_cast<float*>(tc_ws) + run * (n + 4) : nullptr;
-        const int bar = 1 + warp / TPA;        // named barrier of this anneal group's TPA warps
-        int b = 0;
 #pragma unroll 1
-        for (; t + F <= S; t += F, b ^= 1)
-            tuned_block<n, NS, TPA, PACKED, F, PAIR, SMEMU>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k,
-                                                            urow + b * ubuf, bar);
+        for (; t + F <= S; t += F)
+            tuned_block<n, NS, TPA, PACKED, F, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
         if (t < S)
-            tuned_block<n, NS, TPA, PACKED, 0, PAIR, SMEMU>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t,
-                                                            k, urow + b * ubuf, bar);
+            tuned_block<n, NS, TPA, PACKED, 0, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
     }
-    // SMEMU: the anneal's TPA threads exchange validity, offsets and energy through shared memory
-    uint32_t* xv = tc_ws;                                                        // [TPA][runs] validity
-    uint64_t* xc = reinterpret_cast<uint64_t*>(tc_ws + 2 * TPA * (T / TPA));    // [TPA][runs] codes
-    int* xe = reinterpret_cast<int*>(tc_ws + TPA * (T / TPA));                  // [TPA][runs] energies
-    if constexpr (SMEMU) __syncthreads();  // every read of the u rows is done
 
     // validity over the whole anneal
     bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
 #pragma unroll
     for (int i = 0; i < NS; ++i)
         valid = valid && (fabsf(x1[i]) <= k.x_max) && (e1[i] > 0.0f) && (fabsf(x2[i]) <= k.x_max) && (e2[i] > 0.0f);
-    if constexpr (!SMEMU) {
 #pragma unroll
-        for (int o = 1; o < TPA; o <<= 1) valid = __shfl_xor_sync(0xffffffffu, (int)valid, o) && valid;
-    }
+    for (int o = 1; o < TPA; o <<= 1) valid = __shfl_xor_sync(0xffffffffu, (int)valid, o) && valid;
     // offsets of this thread's rows, then the whole anneal's (2-bit codes)
     const int sa = xa >= 0.0f ? 1 : -1;
     int dmine[NS];
@@ -839,21 +802,12 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
         dmine[i] = di;
         code |= (uint64_t)(di & 3) << (2 * i);
     }
-    if constexpr (SMEMU) {
-        xv[q * (T / TPA) + run] = valid ? 1u : 0u;
-        xc[q * (T / TPA) + run] = code;
-        __syncthreads();
-#pragma unroll
-        for (int qq = 0; qq < TPA; ++qq) valid = valid && xv[qq * (T / TPA) + run] != 0u;
-    }
     int d[n];
     {
         const int base = lane & ~(TPA - 1);
 #pragma unroll
         for (int qq = 0; qq < TPA; ++qq) {
-            const uint64_t c = TPA == 1 ? code
-                               : SMEMU  ? xc[qq * (T / TPA) + run]
-                                        : __shfl_sync(0xffffffffu, code, base | qq);
+            const uint64_t c = TPA == 1 ? code : __shfl_sync(0xffffffffu, code, base | qq);
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
                 const int v = (int)((c >> (2 * i)) & 3u);
@@ -871,16 +825,8 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
         E -= dmine[i] * r;
         E -= (int)sm.hq[row0 + i] * dmine[i];
     }
-    if constexpr (SMEMU) {
-        xe[q * (T / TPA) + run] = E;
-        __syncthreads();
-        E = 0;
 #pragma unroll
-        for (int qq = 0; qq < TPA; ++qq) E += xe[qq * (T / TPA) + run];
-    } else {
-#pragma unroll
-        for (int o = 1; o < TPA; o <<= 1) E += __shfl_xor_sync(0xffffffffu, E, o);
-    }
+    for (int o = 1; o < TPA; o <<= 1) E += __shfl_xor_sync(0xffffffffu, E, o);
     const bool keep = valid && E <= 0;
     const int Ec = keep ? E : 0;
     long long key = (long long)Ec * 4294967296LL + (long long)run;
