@@ -609,16 +609,19 @@ def run_mmgap_e(args):
 
 
 def run_ul32(args):
-    """32x32 16-QAM slot (the high-connectivity case; i.i.d. Rayleigh, 18 dB,
-    H per subcarrier): slot time through mmgap_detect, its build / solve split
-    from the library's stage events, BER against MMSE, and the solver's FP32
-    roofline.  The L2 is flushed between slots."""
+    """32x32 16-QAM slot of the high-connectivity evaluation (Sec. 5: 10 MHz at
+    30 kHz = 288 subcarriers x 14 symbols, N_a = 128 anneals; i.i.d. Rayleigh,
+    18 dB, H per subcarrier): slot time through mmgap_detect, its build / solve
+    split from the library's stage events, BER against MMSE, and the solver's
+    FP32 roofline (--subcarriers and --runs change the 288 and 128).  The L2
+    is flushed between slots."""
     import torch
 
     from paper_2510_01579_gb300 import Context, Params
     dev = torch.device("cuda", 0)
+    n_sub = args.subcarriers
     prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=min(args.f_mvm, 2))
-    w = synth.uplink(rank_seed(0) + 320, 32, 32, 4, n_sub=args.subcarriers, snr_db=18.0, hold="subcarrier")
+    w = synth.uplink(rank_seed(0) + 320, 32, 32, 4, n_sub=n_sub, snr_db=18.0, hold="subcarrier")
     H, y, nv, ci = (torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index"))
     P = w["y"].shape[0]
     ctx = Context(0, workspace_bytes=1 << 30)
@@ -656,7 +659,7 @@ def run_ul32(args):
     line = {"metric": "32x32 16-QAM detection throughput", "value": P / (ms / 1e3), "unit": "problems/s",
             "n_gpus": 1, "steps": n_steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "ul32x32_16qam_slot", "problems_per_step": P, "runs": prm.runs,
+            "config": {"workload": "ul32x32_16qam_slot", "subcarriers": n_sub, "problems_per_step": P, "runs": prm.runs,
                        "solver_steps": prm.steps, "f_mvm": prm.f_mvm, "snr_db": 18.0,
                        "l2": "flushed between steps (256 MiB write)"},
             "stage_ms": {"build": statistics.mean(build), "solve": solve_avg},
@@ -995,7 +998,7 @@ def main():
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load as a fraction of capacity")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: length of the arrival trace")
     ap.add_argument("--lanes", type=int, default=4, help="serve: concurrent launch groups (streams)")
-    ap.add_argument("--runs", type=int, default=32)
+    ap.add_argument("--runs", type=int, default=None, help="anneals per problem (32; 128 for the 32x32 workload)")
     ap.add_argument("--solver-steps", type=int, default=200)
     ap.add_argument("--f-mvm", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1006,9 +1009,15 @@ def main():
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core field refresh variant")
     ap.add_argument("--no-batch", action="store_true", help="skip timing the batched persistent launch")
     ap.add_argument("--ref-budget", type=float, default=1.5, help="seconds of oracle work per core per step")
-    ap.add_argument("--subcarriers", type=int, default=synth.SUBCARRIERS_100MHZ_30KHZ,
-                    help="subcarriers per slot (3276 = 100 MHz at 30 kHz; smaller only for profiling)")
+    ap.add_argument("--subcarriers", type=int, default=None,
+                    help="subcarriers per slot (3276 = 100 MHz at 30 kHz; 288 = 10 MHz for the 32x32 workload)")
     args = ap.parse_args()
+    # the 32x32 high-connectivity evaluation (Sec. 5) is a 10 MHz slot with N_a = 128 anneals
+    ul32 = args.workload == "ul32x32_16qam_slot"
+    if args.runs is None:
+        args.runs = 128 if ul32 else 32
+    if args.subcarriers is None:
+        args.subcarriers = synth.SUBCARRIERS_10MHZ_30KHZ if ul32 else synth.SUBCARRIERS_100MHZ_30KHZ
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

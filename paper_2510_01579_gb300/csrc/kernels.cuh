@@ -19,6 +19,7 @@
 //   common.cuh        Philox, IEEE helpers, dynamic shared-memory limits
 //   build.cuh         builder (Gram, MMSE / SIC guess, field, Q14)
 //   solve.cuh         CIM-CAC solver and its bit-identical launch shapes
+//   solve_rows.cuh    CIM-CAC solver for 32 users (row blocks, two anneals per thread)
 //   umma.cuh          tcgen05 field refresh (solver shape 8)
 //   batch_kernels.cuh batched launch over a job table
 //   direct.cuh        direct spin mapping: builder and general solver

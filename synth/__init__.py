@@ -23,6 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 SUBCARRIERS_100MHZ_30KHZ = 3276
+SUBCARRIERS_10MHZ_30KHZ = 288  # 24 PRBs: the high-connectivity 32x32 evaluation (Sec. 5)
 SYMBOLS_PER_SLOT = 14
 SUBCARRIERS_PER_PRB = 12
 
