@@ -77,8 +77,8 @@ typedef struct {
  * One uplink detection job: n_problems problems (resource elements) of the
  * same size (Sec. 3.2: inputs are H and y per problem, Fig. 4).
  *   n_t in {1, 2, 3, 4, 8, 16, 32} users, n_r in [1, 64] antennas; 32 users
- *   (the 32x32 high-connectivity case) only with the delta mapping, the
- *   FP32 Gram and f_mvm in {1, 2}, and not in MMGaP-E,
+ *   (the 32x32 high-connectivity case) only with the delta mapping and the
+ *   FP32 Gram, and not in MMGaP-E,
  *   mod_bits in {2, 4, 6} (QPSK, 16-QAM, 64-QAM; symbol index q maps to the
  *   lattice point (2 (q / sqrt(M)) - L) + i (2 (q % sqrt(M)) - L),
  *   L = sqrt(M) - 1, scaled by 1/sqrt(2 (M - 1) / 3)).
@@ -226,7 +226,7 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
 /*
  * Solver boundary (Sec. 2.3, Sec. 3.2): anneal n_problems quantised
  * delta-Ising problems of half-size n (2n + 1 spins, n = 2 n_t,
- * n in {2, 4, 6, 8, 16, 32, 64}; n = 64 needs f_mvm in {1, 2}).
+ * n in {2, 4, 6, 8, 16, 32, 64}).
  *   A_q: int16 [n_problems][n][n] symmetric Q14 half-size block A = -G
  *        (Fig. 5(a): J = [[A~, A, b], [A, A~, b], [b^T, b^T, 0]])
  *   h_q: int16 [n_problems][n] Q14 auxiliary block b
@@ -251,7 +251,8 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
  * bit 63 set iff the anneal diverged.  P_diverge and P_error of the paper's
  * (dt, f_mvm) study follow from comparing these words across parameter sets
  * with equal N_I dt.  Uses the workspace for the discarded selection.
- * n in {2, 4, 6, 8, 16, 32} (n = 64 is refused: MMGAP_EUNSUPPORTED).
+ * n in {2, 4, 6, 8, 16, 32}: n = 64 is refused with MMGAP_EUNSUPPORTED, since
+ * its 129 spins do not fit the 127 state bits of the two words.
  */
 mmgap_status mmgap_anneal_spins(mmgap_ctx* ctx, const mmgap_params* params, int n, int n_problems,
                                 const int16_t* A_q, const int16_t* h_q, uint64_t seed, uint64_t* spins_out,

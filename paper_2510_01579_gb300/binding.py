@@ -26,7 +26,7 @@ _lib = C.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EBUSY = range(7)
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED", 6: "EBUSY"}
 
-# User counts of every call; detect / build_detect (delta mapping, FP32 Gram, f_mvm 1 or 2) and
+# User counts of every call; detect / build_detect (delta mapping, FP32 Gram) and
 # solve_ising (n = 64) also take 32 users.
 SUPPORTED_NT = (1, 2, 3, 4, 8, 16)
 

@@ -546,7 +546,6 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     if (st != MMGAP_OK) return st;
     if (n < 2 || (n & 1) || (!nt_supported(n / 2) && n != 64))
         return fail(ctx, MMGAP_EUNSUPPORTED, "n=%d: supported 2, 4, 6, 8, 16, 32, 64", n);
-    if (n == 64 && params->f_mvm > 2) return fail(ctx, MMGAP_EUNSUPPORTED, "n=64: f_mvm 1 or 2");
     if (n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
     if (n_problems == 0) return MMGAP_OK;
     if (!A_q || !h_q || !d_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q, h_q or d_out");
@@ -615,10 +614,8 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, MMGAP_EINVAL, "bad jobs array");
-    for (int j = 0; j < n_jobs; ++j) {
+    for (int j = 0; j < n_jobs; ++j)
         if ((st = check_detect_job(ctx, jobs[j], true)) != MMGAP_OK) return st;
-        if (jobs[j].n_t == 32 && params->f_mvm > 2) return fail(ctx, MMGAP_EUNSUPPORTED, "n_t=32: f_mvm 1 or 2");
-    }
     CurrentDevice cd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const EulerConsts k = euler_consts(*params);

@@ -112,16 +112,20 @@ cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
     if constexpr (NT == 32) {
         // 32 users (n = 64): the row-block kernel (two anneals x 8 rows per thread, four warps per 32
-        // anneals); f_mvm 1 or 2 and no spin dump (the API refuses the rest)
-        if (a.spins_out || (a.f_mvm != 1 && a.f_mvm != 2) || runs % 32 != 0) return cudaErrorInvalidValue;
+        // anneals); f_mvm 1 and 2 compiled in, others at run time; no spin dump (129 spins do not fit
+        // the 128-bit state words, and the API refuses it)
+        if (a.spins_out || a.f_mvm < 1 || runs % 32 != 0) return cudaErrorInvalidValue;
         const size_t smem = rows_dyn_bytes(2 * NT, runs);
         cudaError_t err;
         if (a.f_mvm == 2) {
             if ((err = ensure_dynamic_smem<cac_solve_rows_kernel<32, 2>>(smem)) != cudaSuccess) return err;
             cac_solve_rows_kernel<32, 2><<<a.n_problems, 4 * runs, smem, s>>>(a);
-        } else {
+        } else if (a.f_mvm == 1) {
             if ((err = ensure_dynamic_smem<cac_solve_rows_kernel<32, 1>>(smem)) != cudaSuccess) return err;
             cac_solve_rows_kernel<32, 1><<<a.n_problems, 4 * runs, smem, s>>>(a);
+        } else {
+            if ((err = ensure_dynamic_smem<cac_solve_rows_kernel<32, 0>>(smem)) != cudaSuccess) return err;
+            cac_solve_rows_kernel<32, 0><<<a.n_problems, 4 * runs, smem, s>>>(a);
         }
         return cudaGetLastError();
     } else {

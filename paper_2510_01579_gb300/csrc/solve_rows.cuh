@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
     constexpr int n = 2 * NT;
     constexpr int NRB = n / kRowsNs;  // row blocks per anneal
     static_assert(n == 64, "two 8-row blocks per warp and four warps per 32 anneals: n = 64");
-    static_assert(F > 0, "compile-time refresh period");
+    static_assert(F >= 0, "refresh period: compile-time F > 0, or F = 0 for a.f_mvm at run time");
     __shared__ __align__(16) SolveSmem<NT> sm;
     __shared__ long long skey[16];
     __shared__ int sdiv[16];
@@ -204,11 +204,12 @@ __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
     const int ubuf = R * (n + 4);  // floats per buffer
     const int bar = 1 + grp;
     const int S = a.steps;
+    const int f = F > 0 ? F : a.f_mvm;
     int t = 0, b = 0;
 #pragma unroll 1
-    for (; t + F <= S; t += F, b ^= 1)
+    for (; t + f <= S; t += f, b ^= 1)
         rows_block<n, F>(sm.A, sm.h, sm.nd, row0, x1, x2, e1, e2, xa, ea, ubase + b * ubuf + run[0] * (n + 4),
-                         ubase + b * ubuf + run[1] * (n + 4), bar, F, k);
+                         ubase + b * ubuf + run[1] * (n + 4), bar, f, k);
     if (t < S)
         rows_block<n, 0>(sm.A, sm.h, sm.nd, row0, x1, x2, e1, e2, xa, ea, ubase + b * ubuf + run[0] * (n + 4),
                          ubase + b * ubuf + run[1] * (n + 4), bar, S - t, k);

@@ -39,7 +39,7 @@ def _detect(ctx, w, prm, seed):
 
 
 @pytest.mark.parametrize("n_r,mb,runs,f_mvm,steps", [(32, 2, 32, 2, 150), (32, 4, 128, 1, 80), (48, 4, 64, 2, 100),
-                                                     (32, 6, 96, 2, 60)])
+                                                     (32, 6, 96, 2, 60), (32, 4, 32, 3, 100), (64, 4, 64, 5, 77)])
 def test_detect_32x32_bit_exact(mm, n_r, mb, runs, f_mvm, steps):
     """Shared channels (three symbols per subcarrier) go through the
     per-channel factorisation; noise variances of every other problem differ
@@ -72,7 +72,7 @@ def test_detect_32x32_small_workspace_same_bits(mm):
         assert np.array_equal(got[k], got2[k]), k
 
 
-@pytest.mark.parametrize("runs,f_mvm", [(32, 2), (64, 1), (128, 2)])
+@pytest.mark.parametrize("runs,f_mvm", [(32, 2), (64, 1), (128, 2), (32, 4), (96, 3)])
 def test_solve_ising_n64_bit_exact(mm, runs, f_mvm):
     """Random Appendix-style instances at n = 64: a stable step and one large
     enough that anneals diverge (the counts and the all-diverged result must
@@ -109,14 +109,11 @@ def test_32_users_refused_outside_the_delta_path(mm):
     w = synth.uplink(3400, 32, 32, 2, n_sub=2, n_sym=1, snr_db=10.0, hold="problem")
     H, y, nv = T(w["H"]), T(w["y"]), T(w["noise_var"])
     cases = [
-        lambda: ctx.detect(H, y, nv, 2, pkg.Params.default(f_mvm=3), 1),
         lambda: ctx.detect(H, y, nv, 2, pkg.Params.default(), 1, mapping=1),
         lambda: ctx.detect(H, y, nv, 2, pkg.Params.default(), 1, gram_precision=1),
         lambda: ctx.detect_e(H, y, nv, 2, pkg.Params.default(), 1),
         lambda: ctx.anneal_spins(T(np.zeros((1, 64, 64), np.int16)), T(np.zeros((1, 64), np.int16)),
                                  pkg.Params.default(), 1),
-        lambda: ctx.solve_ising(T(np.zeros((1, 64, 64), np.int16)), T(np.zeros((1, 64), np.int16)),
-                                pkg.Params.default(f_mvm=4), 1),
         lambda: ctx.set_solver_variant(32, 1),
     ]
     for i, c in enumerate(cases):
