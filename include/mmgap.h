@@ -383,8 +383,12 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
  * Batched persistent launch of mixed-size uplink jobs (no counterpart in the
  * paper, which launches one fixed-size grid per kernel).
  *
- * mmgap_batch_create validates the jobs (n_t in {4, 8, 16}, n_r <= 64,
+ * mmgap_batch_create validates the jobs (n_t in {4, 8, 16, 32}, n_r <= 64,
  * runs = 32, f_mvm in {1, 2}) and uploads a job table (largest users first).
+ * 32-user jobs stay out of the table: each run launches their builder and
+ * row-block solver (the kernels mmgap_detect uses for 32 users) ahead of the
+ * table's kernels, outside the graph, always exact (MMGAP_BATCH_TENSOR_CORE
+ * applies to the table's jobs).
  * A run is one builder kernel over every problem of every job (the Sec. 3.2
  * pre-processing, one warp per resource element) into batch-owned scratch,
  * then one solver kernel that anneals each problem with 32 anneals on the 32

@@ -60,6 +60,22 @@ const void* pick_build(int ntmax) {
 }
 
 constexpr int kBatchWarps = 4;
+
+// Constants of the Euler discretisation of Eqs. 10-11, each computed in
+// double from the float parameters and rounded once to float (the same
+// values as the per-job entry points use).
+EulerConsts batch_consts(const mmgap_params& P) {
+    const double dt = P.dt, p = P.p, aa = P.a, zeta = P.zeta, eps = P.eps;
+    EulerConsts k;
+    k.c1 = (float)(1.0 + dt * (p - 1.0));
+    k.cdt = (float)(-dt);
+    k.cz = (float)(-(dt * zeta));
+    k.c2 = (float)(1.0 + (dt * zeta) * aa);
+    k.ce = (float)(eps * dt);
+    k.xs = (float)((double)P.sigma0 * 0x1p-23);
+    k.x_max = P.x_max;
+    return k;
+}
 constexpr size_t kScratchAlign = 256;
 size_t salign(size_t v) { return (v + kScratchAlign - 1) / kScratchAlign * kScratchAlign; }
 
@@ -73,7 +89,7 @@ const char* BatchRunner::check_params(const mmgap_params& P) {
 }
 
 const char* BatchRunner::check_job(const mmgap_detect_job& J) {
-    if (!batch_nt(J.n_t)) return "batched launch supports n_t 4, 8, 16";
+    if (!batch_nt(J.n_t) && J.n_t != 32) return "batched launch supports n_t 4, 8, 16, 32";
     if (J.n_r < 1 || J.n_r > kMaxNr) return "n_r out of [1, 64]";
     if (!(J.mod_bits == 2 || J.mod_bits == 4 || J.mod_bits == 6)) return "mod_bits must be 2, 4 or 6";
     if (J.n_problems < 0) return "n_problems < 0";
@@ -194,11 +210,56 @@ int BatchRunner::stage(const mmgap_detect_job* jobs, const int* order, int n_job
 int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
     if (n_jobs > capacity_) return -1;
     pre_.clear();
+    wide_.clear();
     long long first = 0, tiles = 0;
     size_t off = 0;
+    int n_table = 0;
+    std::vector<int> slot((size_t)std::max(0, n_jobs));  // table index, or -1 - (index into wide_)
     for (int i = 0; i < n_jobs; ++i) {
         const GroupJob& G = jobs[order ? order[i] : i];
-        BatchJob& B = h_jobs_[i];
+        if (G.det && G.det->n_t == 32) {
+            const mmgap_detect_job& J = *G.det;
+            const size_t n = 64, P = (size_t)J.n_problems;
+            if (off + scratch_bytes(32, J.n_problems) > scratch_bytes_) return -2;
+            Wide W{};
+            BuildArgs& b = W.b;
+            b.H = J.H;
+            b.chan_index = J.chan_index;
+            b.y = J.y;
+            b.noise_var = J.noise_var;
+            b.n_r = J.n_r;
+            b.mod_bits = J.mod_bits;
+            b.n_problems = J.n_problems;
+            b.n_chan = J.chan_index ? J.n_chan : J.n_problems;
+            const double M = (double)(1 << J.mod_bits);
+            b.kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
+            b.kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
+            b.err = err_word_;
+            b.Aq = (int16_t*)(scratch_ + off);
+            b.hq = (int16_t*)(scratch_ + off + salign(P * n * n * 2));
+            b.g = (int8_t*)(scratch_ + off + salign(P * n * n * 2) + salign(P * n * 2));
+            off += scratch_bytes(32, J.n_problems);
+            SolveArgs& a = W.a;
+            a.err = err_word_;
+            a.Aq = b.Aq;
+            a.hq = b.hq;
+            a.g = b.g;
+            a.level_max = (1 << (J.mod_bits >> 1)) - 1;
+            a.n_problems = J.n_problems;
+            a.key0 = (uint32_t)J.seed;
+            a.key1 = (uint32_t)(J.seed >> 32);
+            a.d_out = J.offset_out;
+            a.E_out = J.energy_out;
+            a.ndiv_out = J.ndiv_out;
+            a.sym_out = J.sym_out;
+            a.mod_bits = J.mod_bits;
+            W.guess_out = J.guess_out;
+            slot[i] = -1 - (int)wide_.size();
+            if (J.n_problems > 0) wide_.push_back(W);
+            continue;
+        }
+        slot[i] = n_table;
+        BatchJob& B = h_jobs_[n_table++];
         B = BatchJob{};
         B.first = first;
         B.tile_first = tiles;
@@ -275,10 +336,11 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
         if (!J.chan_index || J.n_chan >= J.n_problems || J.n_problems == 0) continue;
         const size_t fb = factor_bytes(J.n_t, J.n_chan);
         if (off + fb > scratch_bytes_) continue;
+        if (slot[i] < 0 && J.n_problems == 0) continue;  // (empty wide jobs are not staged)
         const size_t nc = (size_t)J.n_chan, lb = salign(nc * 2 * J.n_t * J.n_t * sizeof(float)), rb = salign(nc * 4);
         char* base = scratch_ + off;
         off += fb;
-        BatchJob& B = h_jobs_[i];
+        BuildArgs& B = slot[i] >= 0 ? h_jobs_[slot[i]].b : wide_[(size_t)(-1 - slot[i])].b;
         Factor F{};
         F.n_t = J.n_t;
         ChanFactorArgs& f = F.args;
@@ -288,18 +350,18 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
         f.n_r = J.n_r;
         f.n_problems = J.n_problems;
         f.n_chan = J.n_chan;
-        f.kappa = B.b.kappa;
-        f.kappa2 = B.b.kappa2;
+        f.kappa = B.kappa;
+        f.kappa2 = B.kappa2;
         f.L_out = (float*)base;
         f.rho_out = (float*)(base + lb);
         f.chol_out = (int32_t*)(base + lb + rb);
         f.first = (int32_t*)(base + lb + 2 * rb);
-        B.b.L_pre = f.L_out;
-        B.b.rho_pre = f.rho_out;
-        B.b.chol_pre = f.chol_out;
+        B.L_pre = f.L_out;
+        B.rho_pre = f.rho_out;
+        B.chol_pre = f.chol_out;
         fac_.push_back(F);
     }
-    h_head_->n_jobs = n_jobs;
+    h_head_->n_jobs = n_table;
     h_head_->pad = 0;
     h_head_->total = first;
     h_head_->counter = 0;
@@ -327,10 +389,28 @@ cudaError_t vpp_output_nu(int n_u, const VppOutArgs& a, cudaStream_t s) {
 
 }  // namespace
 
+cudaError_t BatchRunner::wide_before(const mmgap_params& P, cudaStream_t s) {
+    const EulerConsts k = batch_consts(P);
+    for (Wide& W : wide_) {
+        cudaError_t e = launch_build_detect<32>(W.b, s);
+        if (e != cudaSuccess) return e;
+        W.a.steps = P.steps;
+        W.a.f_mvm = P.f_mvm;
+        W.a.k = k;
+        if ((e = launch_solve<32>(W.a, P.runs, s)) != cudaSuccess) return e;
+        if (W.guess_out &&
+            (e = cudaMemcpyAsync(W.guess_out, W.b.g, (size_t)W.b.n_problems * 64, cudaMemcpyDeviceToDevice, s)) !=
+                cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t BatchRunner::factor_before(cudaStream_t s) {
     for (const Factor& F : fac_) {
         cudaError_t e;
         switch (F.n_t) {
+        case 32: e = launch_chan_factor<32>(F.args, s); break;
         case 16: e = launch_chan_factor<16>(F.args, s); break;
         case 8: e = launch_chan_factor<8>(F.args, s); break;
         default: e = launch_chan_factor<4>(F.args, s); break;
@@ -408,14 +488,7 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     a.jobs = d_jobs_;
     a.head = d_head_;
     a.steps = P.steps;
-    const double dt = P.dt, p = P.p, aa = P.a, zeta = P.zeta, eps = P.eps;
-    a.k.c1 = (float)(1.0 + dt * (p - 1.0));
-    a.k.cdt = (float)(-dt);
-    a.k.cz = (float)(-(dt * zeta));
-    a.k.c2 = (float)(1.0 + (dt * zeta) * aa);
-    a.k.ce = (float)(eps * dt);
-    a.k.xs = (float)((double)P.sigma0 * 0x1p-23);
-    a.k.x_max = P.x_max;
+    a.k = batch_consts(P);
     a.build_floats = build_floats_;
     void* args[] = {&a};
     unsigned bg, sg;
@@ -432,7 +505,8 @@ cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_gra
     if (e != cudaSuccess) return e;
     e = precode_before(s);
     if (e != cudaSuccess) return e;
-    if ((e = run_batch(P, s, use_graph)) != cudaSuccess) return e;
+    if ((e = wide_before(P, s)) != cudaSuccess) return e;
+    if (h_head_->n_jobs > 0 && (e = run_batch(P, s, use_graph)) != cudaSuccess) return e;
     return precode_after(s);
 }
 
@@ -524,9 +598,11 @@ mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_param
             fprintf(stderr, "mmgap_batch_create: job %d: %s\n", i, why);
             return MMGAP_EUNSUPPORTED;
         }
-        ntmax = std::max(ntmax, jobs[i].n_t);
-        max_n_r = std::max(max_n_r, jobs[i].n_r);
-        total += jobs[i].n_problems;
+        if (jobs[i].n_t != 32) {  // (32-user jobs run their own launches: not in the table's kernels)
+            ntmax = std::max(ntmax, jobs[i].n_t);
+            max_n_r = std::max(max_n_r, jobs[i].n_r);
+            total += jobs[i].n_problems;
+        }
         scratch += BatchRunner::scratch_bytes(jobs[i].n_t, jobs[i].n_problems);
         if (jobs[i].chan_index && jobs[i].n_chan < jobs[i].n_problems)
             scratch += BatchRunner::factor_bytes(jobs[i].n_t, jobs[i].n_chan);

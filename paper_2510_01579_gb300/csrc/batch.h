@@ -48,9 +48,10 @@ class BatchRunner {
     // returns 0, or < 0 if the jobs exceed the table, scratch or problem capacity.
     int stage(const mmgap_detect_job* jobs, const int* order, int n_jobs);
     int stage(const GroupJob* jobs, const int* order, int n_jobs);
-    // Launch on s: each precoding job's channel inverse and VPP build, then
-    // the batch (table upload, builder, solver; or the graph of them), then
-    // each precoding job's output kernel.
+    // Launch on s: the per-channel factorisations, each precoding job's
+    // channel inverse and VPP build, each 32-user job's build and row-block
+    // solve, then the batch of the other jobs (table upload, builder,
+    // solver; or the graph of them), then each precoding job's output kernel.
     cudaError_t run(const mmgap_params& P, cudaStream_t s, bool use_graph);
     int grid() const { return grid_; }
 
@@ -74,6 +75,15 @@ class BatchRunner {
     std::vector<Factor> fac_;
     cudaError_t precode_after(cudaStream_t s);
     std::vector<Precode> pre_;
+    // 32-user detection jobs: outside the job table (the mixed-size kernels
+    // stop at 16 users), with their own builder and row-block solver launches
+    struct Wide {
+        BuildArgs b;
+        SolveArgs a;
+        int8_t* guess_out;
+    };
+    std::vector<Wide> wide_;
+    cudaError_t wide_before(const mmgap_params& P, cudaStream_t s);
     void grids(unsigned* build_grid, unsigned* solve_grid) const;
     unsigned solve_block() const { return tc_ ? 128u : (persistent_ ? 4u * 32u : 32u); }
     size_t solve_smem() const { return tc_ ? umma_smem_ : 0; }

@@ -99,3 +99,41 @@ def test_batch_rejects_unsupported_shapes():
         job8 = ctx.detect_job(T(w8["H"]), T(w8["y"]), T(w8["noise_var"]), 2, 1, o8, T(w8["chan_index"]))
         with pytest.raises(pkg.MMGaPError):
             pkg.Batch(0, pkg.Params.default(runs=64), [job8])
+
+
+@pytest.mark.parametrize("persistent,tensor_core,graph", [(False, False, True), (True, False, False),
+                                                          (False, True, True)])
+def test_batch_with_32_user_jobs(persistent, tensor_core, graph):
+    """32-user jobs ride along a batch (their own build and row-block solve
+    launches ahead of the table's kernels) and equal the per-job path bit for
+    bit, next to 16- and 8-user jobs; a batch of 32-user jobs alone too."""
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=70)
+    ws = [synth.uplink(91, 32, 32, 4, n_sub=6, n_sym=14, snr_db=18.0),                  # 32x32, H per subcarrier
+          synth.uplink(92, 16, 16, 4, n_sub=8, n_sym=14, snr_db=16.0),
+          synth.uplink(93, 40, 32, 2, n_sub=3, n_sym=5, snr_db=10.0, hold="problem"),   # 40x32 QPSK, H per problem
+          synth.uplink(94, 8, 8, 2, n_sub=12, n_sym=14, snr_db=8.0, model="kron", hold="prb")]
+    with pkg.Context(0) as ctx:
+        for sel in ([0, 1, 2, 3], [2, 0]):
+            tens, outs, jobs, refs = [], [], [], []
+            for i in sel:
+                w = ws[i]
+                t = (T(w["H"]), T(w["y"]), T(w["noise_var"]), T(w["chan_index"]))
+                P = w["y"].shape[0]
+                o = _outs(P, w["n_t"])
+                tens.append(t)
+                outs.append(o)
+                jobs.append(ctx.detect_job(*t[:3], w["mod_bits"], 700 + i, o, t[3]))
+                r = _outs(P, w["n_t"])
+                ctx.detect_jobs([ctx.detect_job(*t[:3], w["mod_bits"], 700 + i, r, t[3])], prm)
+                refs.append(r)
+            with pkg.Batch(0, prm, jobs, keepalive=(tens, outs), persistent=persistent,
+                           tensor_core=tensor_core) as b:
+                for _ in range(2):  # a second run (graph replay) gives the same bits
+                    b.run(use_graph=graph)
+                    torch.cuda.synchronize()
+                    for j, i in enumerate(sel):
+                        if tensor_core and ws[i]["n_t"] != 32:
+                            continue  # (the tcgen05 refresh is a precision variant for the smaller jobs)
+                        for k in refs[j]:
+                            assert torch.equal(outs[j][k], refs[j][k]), (sel, i, k)
