@@ -436,7 +436,8 @@ mmgap_status mmgap_batch_destroy(mmgap_batch* batch);
  * on the host's steady clock.  deadline_us > 0 counts jobs over it;
  * inject_delay_us > 0 delays every launch on the host (fault injection for
  * tests: a stalled dispatcher).  Limits as mmgap_batch_create (n_t in
- * {4, 8, 16} up to max_n_t, n_r <= max_n_r, runs = 32, f_mvm in {1, 2}).
+ * {4, 8, 16, 32} up to max_n_t, n_r <= max_n_r, runs = 32, f_mvm in
+ * {1, 2}); max_n_t in {4, 8, 16, 32}; precoding jobs up to 16 users.
  */
 typedef struct mmgap_server mmgap_server;
 typedef struct {

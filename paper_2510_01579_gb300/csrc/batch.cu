@@ -132,6 +132,7 @@ size_t BatchRunner::scratch_bytes(int n_t, int n_problems) {
 cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r,
                               int ntmax, int* err_word, bool persistent, bool tensor_core) {
     device_ = device;
+    ntmax = std::min(ntmax, 16);  // the table's kernels; 32-user jobs run their own launches
     tc_ = tensor_core && ntmax >= 8;
     persistent_ = persistent && !tc_;
     capacity_ = capacity_jobs;

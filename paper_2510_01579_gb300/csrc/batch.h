@@ -35,8 +35,9 @@ class BatchRunner {
     // channel inverses and their flags.
     static size_t precode_scratch_bytes(const mmgap_precode_job& J);
     // Device job table for up to capacity_jobs jobs and capacity_problems
-    // problems with n_r <= max_n_r and n_t <= ntmax, `scratch` bytes of
-    // coupling scratch; err_word receives out-of-range channel indices.
+    // problems with n_r <= max_n_r and n_t <= ntmax (the table's kernels are
+    // sized for min(ntmax, 16); 32-user jobs stay outside the table), `scratch`
+    // bytes of coupling scratch; err_word receives out-of-range channel indices.
     // persistent: the solver runs warps that pull problems from an atomic
     // counter; otherwise one 32-thread CTA per problem.  tensor_core: the
     // field refresh of 8- and 16-user problems as tcgen05 MMAs (solver shape

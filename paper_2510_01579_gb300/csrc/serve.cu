@@ -215,7 +215,7 @@ mmgap_status mmgap_server_create(mmgap_server** out, int device, const mmgap_par
     }
     if (cfg->n_lanes < 1 || cfg->n_lanes > 16 || cfg->scratch_bytes == 0 || cfg->max_jobs_per_group < 1 ||
         cfg->max_problems_per_group < 1 || cfg->max_n_r < 1 || cfg->max_n_r > 64 ||
-        !(cfg->max_n_t == 4 || cfg->max_n_t == 8 || cfg->max_n_t == 16))
+        !(cfg->max_n_t == 4 || cfg->max_n_t == 8 || cfg->max_n_t == 16 || cfg->max_n_t == 32))
         return MMGAP_EINVAL;
     int prev = -1;
     cudaGetDevice(&prev);

@@ -204,3 +204,30 @@ def test_tensor_core_server_equals_per_job_tensor_core_shape():
         for (w, t, o, job), r in zip(jobs, refs):
             for k in o:
                 assert torch.equal(o[k], r[k]), (w["n_t"], k)
+
+
+def test_server_with_32_user_jobs():
+    """A server sized for 32 users: 32x32 jobs grouped with smaller ones equal
+    their mmgap_detect results bit for bit."""
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(steps=60)
+    specs = [(32, 4, 40, "iid", "subcarrier"), (16, 4, 200, "iid", "subcarrier"), (32, 2, 25, "iid", "problem"),
+             (8, 2, 300, "kron", "prb")]
+    with pkg.Context(0) as ctx:
+        jobs = _jobs(ctx, specs)
+        refs = []
+        for w, t, o, job in jobs:
+            r = {k: torch.empty_like(v) for k, v in o.items()}
+            ctx.detect_jobs([ctx.detect_job(t[0], t[1], t[2], w["mod_bits"], job.seed, r, t[3])], prm)
+            refs.append(r)
+        torch.cuda.synchronize()
+        with pkg.Server(0, prm, scratch_bytes=8 << 20, n_lanes=2, max_jobs_per_group=2, max_n_t=32,
+                        max_n_r=32) as srv:
+            tickets = [srv.submit(job) for _, _, _, job in jobs]
+            for tk in tickets:
+                srv.wait(tk, timeout_us=60_000_000)
+            st = srv.stats()
+        for (w, t, o, job), r in zip(jobs, refs):
+            for k in o:
+                assert torch.equal(o[k], r[k]), (w["n_t"], k)
+        assert st["completed"] == len(jobs)
