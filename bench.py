@@ -646,6 +646,17 @@ def run_ul32(args):
         build.append(st[0])
         solve.append(st[1])
     clk = clocks.stop()
+    # one problem alone (the critical path of a single 32x32 resource element): median of 50 calls
+    H1, y1, nv1 = H[ci[0].item():ci[0].item() + 1], y[:1], nv[:1]
+    for _ in range(3):
+        ctx.detect(H1, y1, nv1, 4, prm, 3)
+    lat = []
+    for _ in range(50):
+        a.record(stream)
+        ctx.detect(H1, y1, nv1, 4, prm, 3)
+        b.record(stream)
+        torch.cuda.synchronize()
+        lat.append(a.elapsed_time(b) * 1e3)
     nbits = P * 32 * 4
     g = r["guess"].cpu().numpy().astype(int)
     mm = ((g[:, :32] + 3) // 2) * 4 + (g[:, 32:] + 3) // 2
@@ -663,6 +674,7 @@ def run_ul32(args):
                        "solver_steps": prm.steps, "f_mvm": prm.f_mvm, "snr_db": 18.0,
                        "l2": "flushed between steps (256 MiB write)"},
             "stage_ms": {"build": statistics.mean(build), "solve": solve_avg},
+            "single_problem_us": {"p50": statistics.median(lat), "max": max(lat)},
             "ber": {"mmgap": ber, "mmse": ber_mmse},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,

@@ -494,7 +494,7 @@ mmgap_status mmgap_server_destroy(mmgap_server* server);
  * device memory, as for mmgap_detect; the call runs on the current device.
  *
  * Limit: the job must fit the array, i.e. align256(P n^2 2) + align256(P n 2)
- * + align256(P n) <= 8 MiB with n = 2 n_t (about 3,900 problems of 16 users,
+ * + align256(P n) <= 8 MiB with n = 2 n_t (about 1,000 problems of 32 users, 3,900 of 16 users,
  * 14,900 of 8 users); a larger job returns MMGAP_ENOMEM (with a message on
  * stderr) and launches nothing.  Split it.
  * The first call on a device looks up the array's device address (with that

@@ -71,13 +71,14 @@ cudaError_t dispatch_nt(int nt, Args&&... args) {
     case 4: return Op<4>::run(args...);
     case 8: return Op<8>::run(args...);
     case 16: return Op<16>::run(args...);
+    case 32: return Op<32>::run(args...);  // (both operations exist for 32 users)
     default: return cudaErrorInvalidValue;
     }
 }
 template <int NT> struct OpBuild { static cudaError_t run(const BuildArgs& a, cudaStream_t s) { return launch_build_detect<NT>(a, s); } };
 template <int NT> struct OpSolve { static cudaError_t run(const SolveArgs& a, int r, cudaStream_t s) { return launch_solve<NT>(a, r, s); } };
 
-bool nt_ok(int nt) { return nt == 1 || nt == 2 || nt == 3 || nt == 4 || nt == 8 || nt == 16; }
+bool nt_ok(int nt) { return nt == 1 || nt == 2 || nt == 3 || nt == 4 || nt == 8 || nt == 16 || nt == 32; }
 
 }  // namespace
 

@@ -107,6 +107,27 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
     return cudaGetLastError();
 }
 
+// 32 users, few problems: a cluster of CL CTAs of 32 anneals per problem.
+template <int F, int CL>
+cudaError_t launch_rows_cluster(const SolveArgs& a, cudaStream_t s) {
+    const size_t smem = rows_dyn_bytes(64, 32);
+    cudaError_t err = ensure_dynamic_smem<cac_solve_rows_kernel<32, F, CL>>(smem);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(a.n_problems * CL));
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cac_solve_rows_kernel<32, F, CL>, a);
+}
+
 template <int NT>
 cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
     if (a.n_problems <= 0) return cudaSuccess;
@@ -115,6 +136,14 @@ cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
         // anneals); f_mvm 1 and 2 compiled in, others at run time; no spin dump (129 spins do not fit
         // the 128-bit state words, and the API refuses it)
         if (a.spins_out || a.f_mvm < 1 || runs % 32 != 0) return cudaErrorInvalidValue;
+        // latency: when the problems' 32-anneal groups fit the SMs, each problem is a cluster of
+        // runs / 32 CTAs (same results: anneal indices and the arg-min key are the problem's)
+        const int cl = runs / 32;
+        if (cl > 1 && (a.f_mvm == 1 || a.f_mvm == 2) && a.n_sm > 0 && (long long)a.n_problems * cl <= a.n_sm) {
+            if (cl == 2) return a.f_mvm == 2 ? launch_rows_cluster<2, 2>(a, s) : launch_rows_cluster<1, 2>(a, s);
+            if (cl == 3) return a.f_mvm == 2 ? launch_rows_cluster<2, 3>(a, s) : launch_rows_cluster<1, 3>(a, s);
+            return a.f_mvm == 2 ? launch_rows_cluster<2, 4>(a, s) : launch_rows_cluster<1, 4>(a, s);
+        }
         const size_t smem = rows_dyn_bytes(2 * NT, runs);
         cudaError_t err;
         if (a.f_mvm == 2) {

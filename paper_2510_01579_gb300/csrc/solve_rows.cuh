@@ -1,6 +1,8 @@
 // CIM-CAC solver for 32 users (n = 64, Eqs. 10-11, Fig. 5): row blocks of
 // two anneals per thread.  Bit-identical to the one-thread-per-anneal kernel.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "solve.cuh"
 
 namespace mmgap {
@@ -136,7 +138,10 @@ __host__ __device__ constexpr size_t rows_dyn_bytes(int n, int runs) {
     return 2 * (size_t)runs * (size_t)(n + 4) * sizeof(float);
 }
 
-template <int NT, int F>
+// CL > 1 (latency: few problems): a cluster of CL CTAs per problem, each
+// with R / CL of its anneals on its own SM; the arg-min and the divergence
+// count are combined through distributed shared memory.
+template <int NT, int F, int CL = 1>
 __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
     constexpr int n = 2 * NT;
     constexpr int NRB = n / kRowsNs;  // row blocks per anneal
@@ -146,14 +151,16 @@ __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
     __shared__ long long skey[16];
     __shared__ int sdiv[16];
     extern __shared__ __align__(16) uint32_t rows_ws[];
-    const int p = blockIdx.x;
+    const int p = blockIdx.x / CL;
+    const int crank = CL > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
     const int tid = threadIdx.x, T = blockDim.x;
-    const int R = T / 4;  // anneals
+    const int R = T / 4;  // anneals of this CTA
     const int lane = tid & 31, warp = tid >> 5;
     const int grp = warp >> 2;                        // group of 32 anneals
     const int rb = 2 * (warp & 3) + (lane >> 4);     // row block
     const int row0 = rb * kRowsNs;
-    const int run[2] = {grp * 32 + (lane & 15), grp * 32 + (lane & 15) + 16};
+    const int run[2] = {grp * 32 + (lane & 15), grp * 32 + (lane & 15) + 16};  // this CTA's anneals
+    const int grun[2] = {crank * R + run[0], crank * R + run[1]};              // the problem's anneal index
     const EulerConsts k = a.k;
     {
         const int16_t* Aq = a.Aq + (size_t)p * n * n;
@@ -183,9 +190,9 @@ __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
         for (int t = 0; t < 2; ++t) {
 #pragma unroll
             for (int b = 0; b < kRowsNs / 4; ++b) {
-                const U4 w1 = philox4x32_10(U4{(uint32_t)((row0 >> 2) + b), (uint32_t)run[t], c2, c3}, a.key0, a.key1);
+                const U4 w1 = philox4x32_10(U4{(uint32_t)((row0 >> 2) + b), (uint32_t)grun[t], c2, c3}, a.key0, a.key1);
                 const U4 w2 =
-                    philox4x32_10(U4{(uint32_t)(((n + row0) >> 2) + b), (uint32_t)run[t], c2, c3}, a.key0, a.key1);
+                    philox4x32_10(U4{(uint32_t)(((n + row0) >> 2) + b), (uint32_t)grun[t], c2, c3}, a.key0, a.key1);
                 const uint32_t v1[4] = {w1.x, w1.y, w1.z, w1.w}, v2[4] = {w2.x, w2.y, w2.z, w2.w};
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
                     e2[t][4 * b + s] = 1.0f;
                 }
             }
-            const U4 wa = philox4x32_10(U4{(uint32_t)((2 * n) >> 2), (uint32_t)run[t], c2, c3}, a.key0, a.key1);
+            const U4 wa = philox4x32_10(U4{(uint32_t)((2 * n) >> 2), (uint32_t)grun[t], c2, c3}, a.key0, a.key1);
             xa[t] = mulrn((float)((int)(wa.x >> 8) - 8388608), k.xs);
         }
     }
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
 #pragma unroll
         for (int r = 0; r < NRB; ++r) E += xe[r * R + run[s]];
         keep[s] = valid[s] && E <= 0;
-        const long long ks = (long long)(keep[s] ? E : 0) * 4294967296LL + (long long)run[s];
+        const long long ks = (long long)(keep[s] ? E : 0) * 4294967296LL + (long long)grun[s];
         key = ks < key ? ks : key;
     }
 #pragma unroll
@@ -304,10 +311,30 @@ __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
         best = skey[w] < best ? skey[w] : best;
         ndiv += sdiv[w];
     }
+    if constexpr (CL > 1) {
+        __shared__ long long ckey;
+        __shared__ int cdiv;
+        cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+        if (tid == 0) {
+            ckey = best;
+            cdiv = ndiv;
+        }
+        cluster.sync();
+        best = 0x7fffffffffffffffLL;
+        ndiv = 0;
+#pragma unroll
+        for (int r = 0; r < CL; ++r) {
+            const long long kr = *cluster.map_shared_rank(&ckey, (unsigned)r);
+            best = kr < best ? kr : best;
+            ndiv += *cluster.map_shared_rank(&cdiv, (unsigned)r);
+        }
+        cluster.sync();  // no CTA leaves while another still reads its shared memory
+    }
     const int best_run = (int)(best & 0xffffffffLL);
+    const int best_local = best_run - crank * R;  // (in the CTA that holds the winner)
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        if (run[s] != best_run) continue;
+        if (grun[s] != best_run) continue;
         if (a.d_out) {
 #pragma unroll
             for (int i = 0; i < kRowsNs; ++i)
@@ -319,7 +346,7 @@ __global__ void __launch_bounds__(512) cac_solve_rows_kernel(SolveArgs a) {
             if (a.run_out) a.run_out[p] = best_run;
             if (a.ndiv_out) a.ndiv_out[p] = ndiv;
             auto dj = [&](int j) {  // the winning anneal's offset of row j (0 unless kept)
-                const int v = (int)((xc[(j / kRowsNs) * R + best_run] >> (2 * (j % kRowsNs))) & 3u);
+                const int v = (int)((xc[(j / kRowsNs) * R + best_local] >> (2 * (j % kRowsNs))) & 3u);
                 return keep[s] ? (v == 3 ? -1 : v) : 0;
             };
             if (a.x_out) {

@@ -120,3 +120,18 @@ def test_32_users_refused_outside_the_delta_path(mm):
         with pytest.raises(pkg.MMGaPError) as e:
             c()
         assert e.value.status == 5, i
+
+
+@pytest.mark.parametrize("runs", [64, 96, 128])
+def test_cluster_split_small_calls_equal_large_calls(mm, runs):
+    """A call whose problems' 32-anneal groups fit the SMs runs each problem as
+    a cluster of runs/32 CTAs (combined through distributed shared memory);
+    the same problems inside a larger call (one CTA each) give the same bits."""
+    pkg, ctx = mm
+    w = synth.uplink(3500 + runs, 32, 32, 4, n_sub=200, n_sym=1, snr_db=16.0, hold="problem")
+    prm = pkg.Params.default(runs=runs, steps=60)
+    big = _detect(ctx, w, prm, 8)  # 200 problems x runs/32 CTAs > the SM count: one CTA per problem
+    small = _detect(ctx, dict(w, H=w["H"][:5], y=w["y"][:5], noise_var=w["noise_var"][:5],
+                              chan_index=w["chan_index"][:5]), prm, 8)
+    for k in big:
+        assert np.array_equal(small[k], big[k][:5]), k

@@ -38,7 +38,8 @@ def test_static_scratch_matches_context_path_two_calls_in_a_row():
     import paper_2510_01579_gb300 as pkg
     prm = pkg.Params.default(steps=120)
     cases = [synth.uplink(61, 16, 16, 4, n_sub=20, n_sym=10, snr_db=14.0),      # 200 problems, 16 users
-             synth.uplink(62, 8, 8, 2, n_sub=30, n_sym=10, snr_db=8.0, model="kron", hold="prb")]  # 300, 8 users
+             synth.uplink(62, 8, 8, 2, n_sub=30, n_sym=10, snr_db=8.0, model="kron", hold="prb"),  # 300, 8 users
+             synth.uplink(64, 32, 32, 4, n_sub=12, n_sym=10, snr_db=18.0)]     # 120 problems, 32 users
     with pkg.Context(0) as ctx:
         for i, w in enumerate(cases):
             P, n_t = w["y"].shape[0], w["n_t"]
