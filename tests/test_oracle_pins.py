@@ -162,7 +162,8 @@ def _build_pair(rng, n_r, n_t, mb, nv):
     return H32, y32, b32, b64
 
 
-@pytest.mark.parametrize("n_r,n_t,mb", [(8, 8, 4), (16, 16, 4), (16, 16, 6), (12, 8, 2), (4, 4, 6)])
+@pytest.mark.parametrize("n_r,n_t,mb", [(8, 8, 4), (16, 16, 4), (16, 16, 6), (12, 8, 2), (4, 4, 6), (32, 32, 4),
+                                        (48, 32, 2)])
 def test_fp32_build_within_error_bound(n_r, n_t, mb):
     """FP32 Gram and field agree with FP64 within 1e-5 normwise:
     |dG_ij| <= 1e-5 sum_k |Hs_ki||Hs_kj| and |dh_i| <= 1e-5 sum_k |Hs_ki| (|z_k| + sum_j |Hs_kj g_j|)."""
@@ -263,7 +264,8 @@ def test_decoupled_dynamics_closed_form(p):
     assert np.allclose(np.log(e), -0.5 * (intw - 1.0 * T), rtol=3e-2, atol=3e-2)
 
 
-@pytest.mark.parametrize("n,f,steps", [(4, 1, 40), (8, 2, 40), (16, 3, 41), (32, 2, 40), (32, 1, 60)])
+@pytest.mark.parametrize("n,f,steps", [(4, 1, 40), (8, 2, 40), (16, 3, 41), (32, 2, 40), (32, 1, 60), (64, 2, 40),
+                                         (64, 3, 31)])
 def test_coupled_trajectory_matches_fp64_euler(n, f, steps):
     """Short coupled anneals: the oracle's FP32 amplitudes after S steps equal a
     forward-Euler integration of Eqs. 10-11 in FP64 written here from the
@@ -301,7 +303,7 @@ def test_integer_energy_matches_ml_objective():
     """E(d) = d^T G_q d - h_q^T d equals (||z - 2 Hs d||^2 - ||z||^2) 2^14 / (4 sigma)
     up to the code roundings (<= 1/2 each), the objective taken from Eq. 2."""
     rng = np.random.default_rng(51)
-    for (n_t, mb) in [(2, 4), (4, 4), (8, 6), (8, 2)]:
+    for (n_t, mb) in [(2, 4), (4, 4), (8, 6), (8, 2), (32, 4)]:
         H, y = _rand_problem(rng, n_t, n_t, mb, 0.1)
         b = o.build_detect64(H, y, 0.1, mb)
         se, Aq, hq = o.quantise64(b["G"], b["h"])
