@@ -135,3 +135,55 @@ def test_cluster_split_small_calls_equal_large_calls(mm, runs):
                               chan_index=w["chan_index"][:5]), prm, 8)
     for k in big:
         assert np.array_equal(small[k], big[k][:5]), k
+
+
+@pytest.mark.parametrize("n_r,mb,hold", [(32, 4, "subcarrier"), (64, 6, "problem"), (8, 2, "problem")])
+def test_builder_32_users_bit_exact(mm, n_r, mb, hold):
+    """Q14 couplings, field, guess, FP32 Gram and field and the normaliser of
+    the 32-user builder equal the oracle's FP32 mirror (n_r = 8 < n_t: the
+    regularised Gram of an under-determined system)."""
+    pkg, ctx = mm
+    w = synth.uplink(3600 + n_r + mb, n_r, 32, mb, n_sub=5, n_sym=2, snr_db=15.0, hold=hold)
+    out = ctx.build_detect(T(w["H"]), T(w["y"]), T(w["noise_var"]), mb, chan_index=T(w["chan_index"]))
+    torch.cuda.synchronize()
+    for p in range(w["y"].shape[0]):
+        c = int(w["chan_index"][p])
+        b = oracle.build_detect32(w["H"][c], w["y"][p], w["noise_var"][p], mb)
+        assert np.array_equal(out["A_q"][p].cpu().numpy(), b["Aq"]), p
+        assert np.array_equal(out["h_q"][p].cpu().numpy(), b["hq"]), p
+        assert np.array_equal(out["g"][p].cpu().numpy(), b["g"].astype(np.int8)), p
+        assert np.array_equal(out["G"][p].cpu().numpy(), b["G32"]), p
+        assert np.array_equal(out["h"][p].cpu().numpy(), b["h32"]), p
+        assert int(out["sigma_exp"][p]) == b["sigma_exp"]
+
+
+def test_32_users_degenerate_empty_and_bad_index(mm):
+    """All-zero channel, a noise-free rank-deficient channel (the Cholesky
+    pivot fails: guess from x_mmse = 0), an empty job, and an out-of-range
+    channel index (flagged in the device error word)."""
+    pkg, ctx = mm
+    rng = np.random.default_rng(32)
+    H = np.zeros((2, 32, 32), np.complex64)
+    H[1] = (rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))).astype(np.complex64)
+    H[1][:, 31] = H[1][:, 30]
+    y = (rng.standard_normal((2, 32)) + 1j * rng.standard_normal((2, 32))).astype(np.complex64)
+    nv = np.zeros(2, np.float32)
+    out = ctx.build_detect(T(H), T(y), T(nv), 4)
+    prm = pkg.Params.default(steps=40)
+    det = ctx.detect(T(H), T(y), T(nv), 4, prm, 6, want_energy=True)
+    torch.cuda.synchronize()
+    ref = oracle.detect_batch(H, y, nv, 4, oracle.Params(steps=40), 6, np.arange(2, dtype=np.int32))
+    for p in range(2):
+        b = oracle.build_detect32(H[p], y[p], nv[p], 4)
+        assert np.array_equal(out["A_q"][p].cpu().numpy(), b["Aq"])
+        assert np.array_equal(out["g"][p].cpu().numpy(), b["g"].astype(np.int8))
+    assert not out["A_q"][0].any()
+    assert np.array_equal(det["sym"].cpu().numpy(), ref["sym"])
+    assert np.array_equal(det["energy"].cpu().numpy(), ref["E"])
+    empty = ctx.detect(T(H), T(y[:0]), T(nv[:0]), 4, prm, 1)
+    assert empty["sym"].shape == (0, 32)
+    ctx.device_errors(clear=True)
+    w = synth.uplink(3700, 32, 32, 2, n_sub=3, n_sym=1)
+    ctx.detect(T(w["H"]), T(w["y"]), T(w["noise_var"]), 2, prm, 1, chan_index=T(np.array([0, 9, 1], np.int32)))
+    torch.cuda.synchronize()
+    assert ctx.device_errors(clear=True) & 1
