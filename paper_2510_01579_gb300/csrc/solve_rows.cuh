@@ -18,7 +18,7 @@ namespace mmgap {
 // row split.  The anneals' u vectors go through double-buffered padded
 // shared-memory rows published by a named barrier of the group's warps.
 // Every m_i stays the ascending-j FMA chain from 0, so the results equal the
-// reference kernel's bit for bit.
+// one-thread-per-anneal kernel's (and the oracle's) bit for bit.
 // =========================================================================
 constexpr int kRowsNs = 8;  // rows per thread
 
