@@ -1028,7 +1028,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=-1,
-                    help="solver launch shape (1 plain .. 4); default: autotuned at set-up")
+                    help="solver launch shape (1 plain, 2-4, 6, 9, 10 exact; 5, 7, 8 tensor-core precision variants); default: autotuned at set-up")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-problem kernel")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core field refresh variant")
     ap.add_argument("--no-batch", action="store_true", help="skip timing the batched persistent launch")
