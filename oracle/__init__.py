@@ -56,7 +56,7 @@ class CParams(C.Structure):
     _fields_ = [("runs", C.c_int), ("steps", C.c_int), ("f_mvm", C.c_int),
                 ("dt", C.c_float), ("p", C.c_float), ("a", C.c_float),
                 ("zeta", C.c_float), ("eps", C.c_float), ("sigma0", C.c_float),
-                ("x_max", C.c_float)]
+                ("x_max", C.c_float), ("early_exit", C.c_int)]
 
 
 class CConsts(C.Structure):
@@ -77,10 +77,11 @@ class Params:
     eps: float = 0.5
     sigma0: float = 0.1
     x_max: float = 1000.0
+    early_exit: int = 0  # K > 0: stop at the first K-th refresh point with no sign change since the last
 
     def c(self) -> CParams:
         return CParams(self.runs, self.steps, self.f_mvm, self.dt, self.p, self.a,
-                       self.zeta, self.eps, self.sigma0, self.x_max)
+                       self.zeta, self.eps, self.sigma0, self.x_max, self.early_exit)
 
 
 _lib.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
@@ -114,6 +115,7 @@ _lib.orc_anneal.argtypes = [C.c_int, _f32p, _f32p, C.POINTER(CParams), C.POINTER
 _lib.orc_cac_solve.argtypes = [C.c_int, _i16p, _i16p, _nullable(_i32p), C.c_int, C.POINTER(CParams),
                                C.c_uint64, C.c_uint64, _i8p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32), _nullable(_f32p), _nullable(_i32p)]
+_lib.orc_cac_solve_steps.argtypes = _lib.orc_cac_solve.argtypes + [_nullable(_i32p)]
 _lib.orc_decode_detect.argtypes = [C.c_int, C.c_int, _i32p, _i8p, _u8p]
 _lib.orc_vpp_inverse64.argtypes = [C.c_int, C.c_int, _f64p, _f64p]
 _lib.orc_build_precode.argtypes = [C.c_int, C.c_int, C.c_int, _f64p, _u8p, _nullable(_f64p), _nullable(_f64p),
@@ -122,7 +124,7 @@ _lib.orc_precode_output.argtypes = [C.c_int, C.c_int, C.c_int, _f64p, _f64p, _u8
                                     C.POINTER(C.c_float)]
 _lib.orc_detect_batch.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _nullable(_i32p), _f32p, _f32p, _f32p,
                                   C.POINTER(CParams), C.c_uint64, _u8p, _i32p, _i32p, _i32p, _nullable(_i32p),
-                                  _nullable(_i8p)]
+                                  _nullable(_i8p), _nullable(_i32p)]
 
 _lib.orc_sic_guess32.argtypes = [C.c_int, C.c_int, C.c_int, _f32p, _f32p, C.c_float, _i32p, _nullable(_i32p)]
 _lib.orc_ml_objective32.restype = C.c_float
@@ -303,12 +305,13 @@ def cac_solve(Aq, hq, g, level_max, params: Params, seed, problem, want_states=F
     Er = np.zeros(params.runs, np.int32) if want_states else None
     gi = None if g is None else np.ascontiguousarray(g, np.int32)
     cp = params.c()
-    st = _lib.orc_cac_solve(n, np.ascontiguousarray(Aq, np.int16).ravel(), np.ascontiguousarray(hq, np.int16), gi,
-                            int(level_max), C.byref(cp), int(seed), int(problem), d, C.byref(E), C.byref(run),
-                            C.byref(nd), xf, Er)
+    taken = np.zeros(1, np.int32)
+    st = _lib.orc_cac_solve_steps(n, np.ascontiguousarray(Aq, np.int16).ravel(), np.ascontiguousarray(hq, np.int16),
+                                  gi, int(level_max), C.byref(cp), int(seed), int(problem), d, C.byref(E),
+                                  C.byref(run), C.byref(nd), xf, Er, taken)
     if st:
         raise ValueError("invalid solver arguments")
-    out = dict(d=d, E=E.value, run=run.value, n_div=nd.value)
+    out = dict(d=d, E=E.value, run=run.value, n_div=nd.value, steps=int(taken[0]))
     if want_states:
         out["x_final"] = xf.reshape(params.runs, N)
         out["E_runs"] = Er
@@ -366,11 +369,13 @@ def detect_batch(H, y, noise_var, mod_bits, params: Params, seed, chan_index=Non
     nd = np.zeros(P, np.int32)
     g = np.zeros(P * n, np.int32)
     d = np.zeros(P * n, np.int8)
+    steps = np.zeros(P, np.int32)
     ci = None if chan_index is None else np.ascontiguousarray(chan_index, np.int32)
     cp = params.c()
     _lib.orc_detect_batch(n_r, n_t, mod_bits, P, ci, _c64(H), _c64(y),
-                          np.ascontiguousarray(noise_var, np.float32), C.byref(cp), int(seed), sym, E, run, nd, g, d)
-    return dict(sym=sym.reshape(P, n_t), E=E, run=run, n_div=nd, g=g.reshape(P, n), d=d.reshape(P, n))
+                          np.ascontiguousarray(noise_var, np.float32), C.byref(cp), int(seed), sym, E, run, nd, g, d,
+                          steps)
+    return dict(sym=sym.reshape(P, n_t), E=E, run=run, n_div=nd, g=g.reshape(P, n), d=d.reshape(P, n), steps=steps)
 
 
 def solve_batch(Aq, hq, g, level_max, params: Params, seed):

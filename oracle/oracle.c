@@ -659,6 +659,9 @@ typedef struct {
     float p, a, zeta, eps; /* CIM-CAC parameters of Eqs. 10-11 */
     float sigma0; /* initial amplitudes uniform in [-sigma0, sigma0) */
     float x_max;  /* divergence bound on |x| at the end of an anneal */
+    int early_exit; /* K > 0: stop a problem's anneals at the first K-th refresh
+                       point where no spin sign of any of them changed since the
+                       previous one (anneal_early_exit); 0 = off */
 } orc_params;
 
 typedef struct {
@@ -753,6 +756,53 @@ void orc_anneal(int n, const float* Af, const float* hf, const orc_params* P, co
 }
 
 /*
+ * The R anneals of one problem with early exit (a budget lever; the paper
+ * anneals every run for a fixed N_I steps, Appendix A).  The anneals advance
+ * together, one refresh interval at a time, each exactly as orc_anneal
+ * advances it.  Every K-th refresh point, t = j K f_mvm with 0 < t < S
+ * (K = P->early_exit), is a check point: the spin signs s_k = [x_k >= 0] of
+ * every anneal (all 2n+1 spins) are compared with their signs at the previous
+ * check point t - K f_mvm (the initial state for the first).  If no sign of
+ * any anneal changed, the anneals stop at t: their state at t is final and no
+ * refresh is made there.
+ * X, EH: [R][2n+1] in/out.  Returns the Euler steps taken (<= S).
+ */
+static int anneal_early_exit(int n, const float* Af, const float* hf, const orc_params* P, const orc_consts* C,
+                             float* X, float* EH)
+{
+    const int N = 2 * n + 1, R = P->runs, S = P->steps, f = P->f_mvm, K = P->early_exit;
+    unsigned char* sg = (unsigned char*)malloc((size_t)R * N);
+    float* mu = (float*)malloc(sizeof(float) * (size_t)N);
+    for (int i = 0; i < R * N; ++i) sg[i] = X[i] >= 0.0f;
+    int taken = S;
+    for (int t = 0; t < S; t += f) {
+        if (t > 0 && (t / f) % K == 0) {
+            int changed = 0;
+            for (int i = 0; i < R * N; ++i) {
+                const unsigned char s = X[i] >= 0.0f;
+                if (s != sg[i]) changed = 1;
+                sg[i] = s;
+            }
+            if (!changed) {
+                taken = t;
+                break;
+            }
+        }
+        const int L = (S - t < f) ? S - t : f;
+        for (int r = 0; r < R; ++r) {
+            float* x = X + (size_t)r * N;
+            float* eh = EH + (size_t)r * N;
+            orc_coupling_field(n, Af, hf, x, mu);
+            for (int s = 0; s < L; ++s)
+                for (int k = 0; k < N; ++k) euler_spin(&x[k], &eh[k], mu[k], C);
+        }
+    }
+    free(sg);
+    free(mu);
+    return taken;
+}
+
+/*
  * Solve one delta-Ising problem with R anneals and keep the best candidate.
  *
  * Aq [n][n], hq [n]: Q14 couplings (A = -G block, b = h).
@@ -764,14 +814,18 @@ void orc_anneal(int n, const float* Af, const float* hf, const orc_params* P, co
  * returns the guess (d = 0, E = 0) instead (Sec. 3.2 solver kernel); the best
  * candidate is the lowest (E, run index) (Sec. 3.2 post-processing).
  *
+ * With P->early_exit = K > 0 the anneals stop together as anneal_early_exit
+ * states; selection is unchanged.
+ *
  * Outputs: d_out [n], E_out, run_out, n_div_out; optional x_final [R][2n+1],
- * E_runs [R] (raw energy of each anneal's clipped offset, INT32_MAX if diverged).
+ * E_runs [R] (raw energy of each anneal's clipped offset, INT32_MAX if diverged),
+ * steps_out (Euler steps the anneals took).
  */
-int orc_cac_solve(int n, const int16_t* Aq, const int16_t* hq, const int* g, int level_max, const orc_params* P,
-                  uint64_t seed, uint64_t problem, int8_t* d_out, int32_t* E_out, int32_t* run_out,
-                  int32_t* n_div_out, float* x_final, int32_t* E_runs)
+int orc_cac_solve_steps(int n, const int16_t* Aq, const int16_t* hq, const int* g, int level_max,
+                        const orc_params* P, uint64_t seed, uint64_t problem, int8_t* d_out, int32_t* E_out,
+                        int32_t* run_out, int32_t* n_div_out, float* x_final, int32_t* E_runs, int32_t* steps_out)
 {
-    if (n < 1 || P->runs < 1 || P->steps < 0 || P->f_mvm < 1) return ORC_EINVAL;
+    if (n < 1 || P->runs < 1 || P->steps < 0 || P->f_mvm < 1 || P->early_exit < 0) return ORC_EINVAL;
     const int N = 2 * n + 1;
     orc_consts C;
     orc_cac_consts(P, &C);
@@ -787,13 +841,34 @@ int orc_cac_solve(int n, const int16_t* Aq, const int16_t* hq, const int* g, int
     int32_t bestE = 0;
     int bestRun = -1, ndiv = 0;
     memset(d_out, 0, (size_t)n);
+    /* with early exit the anneals run together first; their final states are
+       then scored one by one below */
+    float* XE = NULL;
+    float* EE = NULL;
+    int taken = P->steps;
+    if (P->early_exit > 0) {
+        XE = (float*)malloc(sizeof(float) * (size_t)P->runs * N);
+        EE = (float*)malloc(sizeof(float) * (size_t)P->runs * N);
+        for (int r = 0; r < P->runs; ++r)
+            for (int k = 0; k < N; ++k) {
+                XE[(size_t)r * N + k] = orc_initial_x(seed, problem, r, k, C.xs);
+                EE[(size_t)r * N + k] = 1.0f;
+            }
+        taken = anneal_early_exit(n, Af, hf, P, &C, XE, EE);
+    }
+    if (steps_out) *steps_out = taken;
 
     for (int r = 0; r < P->runs; ++r) {
-        for (int k = 0; k < N; ++k) {
-            x[k] = orc_initial_x(seed, problem, r, k, C.xs);
-            eh[k] = 1.0f;
+        if (XE) {
+            memcpy(x, XE + (size_t)r * N, sizeof(float) * (size_t)N);
+            memcpy(eh, EE + (size_t)r * N, sizeof(float) * (size_t)N);
+        } else {
+            for (int k = 0; k < N; ++k) {
+                x[k] = orc_initial_x(seed, problem, r, k, C.xs);
+                eh[k] = 1.0f;
+            }
+            orc_anneal(n, Af, hf, P, &C, x, eh);
         }
-        orc_anneal(n, Af, hf, P, &C, x, eh);
         if (x_final) memcpy(x_final + (size_t)r * N, x, sizeof(float) * (size_t)N);
         int valid = 1;
         for (int k = 0; k < N; ++k)
@@ -822,8 +897,16 @@ int orc_cac_solve(int n, const int16_t* Aq, const int16_t* hq, const int* g, int
     *E_out = bestE;
     *run_out = bestRun;
     *n_div_out = ndiv;
-    free(Af); free(hf); free(x); free(eh); free(d);
+    free(Af); free(hf); free(x); free(eh); free(d); free(XE); free(EE);
     return ORC_OK;
+}
+
+int orc_cac_solve(int n, const int16_t* Aq, const int16_t* hq, const int* g, int level_max, const orc_params* P,
+                  uint64_t seed, uint64_t problem, int8_t* d_out, int32_t* E_out, int32_t* run_out,
+                  int32_t* n_div_out, float* x_final, int32_t* E_runs)
+{
+    return orc_cac_solve_steps(n, Aq, hq, g, level_max, P, seed, problem, d_out, E_out, run_out, n_div_out, x_final,
+                               E_runs, NULL);
 }
 
 /* Decoded uplink symbol of user i: lattice x = g + 2d per real dimension,
@@ -1089,11 +1172,11 @@ void orc_precode_output(int n_u, int n_t, int mod_bits, const double* H, const d
  * H: [n_chan][n_r][n_t] complex float, chan_index: [P] (NULL = identity),
  * y: [P][n_r] complex float, noise_var: [P].  Problem p uses Philox counter
  * space (seed, p).  Outputs: sym [P][n_t], E [P], run [P], n_div [P],
- * optional g [P][n], d [P][n].
+ * optional g [P][n], d [P][n], steps [P] (Euler steps taken).
  */
 int orc_detect_batch(int n_r, int n_t, int mod_bits, int P, const int32_t* chan_index, const float* H,
                      const float* y, const float* noise_var, const orc_params* prm, uint64_t seed, uint8_t* sym,
-                     int32_t* E, int32_t* run, int32_t* n_div, int32_t* g_out, int8_t* d_out)
+                     int32_t* E, int32_t* run, int32_t* n_div, int32_t* g_out, int8_t* d_out, int32_t* steps_out)
 {
     const int n = 2 * n_t;
     int* g = (int*)malloc(sizeof(int) * (size_t)n);
@@ -1106,8 +1189,8 @@ int orc_detect_batch(int n_r, int n_t, int mod_bits, int P, const int32_t* chan_
         int se;
         orc_build_detect32(n_r, n_t, mod_bits, H + (size_t)c * 2 * n_r * n_t, y + (size_t)p * 2 * n_r,
                            noise_var[p], NULL, g, NULL, NULL, &se, Aq, hq);
-        int st = orc_cac_solve(n, Aq, hq, g, orc_qam_level_max(mod_bits), prm, seed, (uint64_t)p, d, &E[p], &run[p],
-                               &n_div[p], NULL, NULL);
+        int st = orc_cac_solve_steps(n, Aq, hq, g, orc_qam_level_max(mod_bits), prm, seed, (uint64_t)p, d, &E[p],
+                                     &run[p], &n_div[p], NULL, NULL, steps_out ? &steps_out[p] : NULL);
         if (st != ORC_OK) status = st;
         orc_decode_detect(n_t, mod_bits, g, d, sym + (size_t)p * n_t);
         if (g_out)

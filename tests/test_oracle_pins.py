@@ -319,6 +319,40 @@ def test_integer_energy_matches_ml_objective():
             assert abs(E - ref) <= bound
 
 
+def _final_e(b, prm, seed, problem, run):
+    """Error variables of one anneal at its end, from the plain integrator."""
+    c = o.cac_consts(prm)
+    n = len(b["hq"])
+    Af = (b["Aq"].astype(np.float32) * np.float32(2.0 ** -14)).astype(np.float32) * np.float32(c.ce)
+    hf = (b["hq"].astype(np.float32) * np.float32(2.0 ** -14)).astype(np.float32) * np.float32(c.ce)
+    x0 = np.array([o.initial_x(seed, problem, run, k, c.xs) for k in range(2 * n + 1)], np.float32)
+    x, e = o.anneal(Af.astype(np.float32), hf.astype(np.float32), prm, x0, np.ones(2 * n + 1, np.float32))
+    return e
+
+
+def test_solver_counts_a_nonpositive_error_variable_as_diverged():
+    """An anneal whose error variable ends <= 0 (finite amplitudes) is not a
+    candidate: E_runs marks it, the divergence count includes it, and the
+    selection falls back as for |x| > x_max.  p = 4 drives x^2 towards 3, where
+    1 + dt zeta (a - x^2) < 0 (a = 0.01, zeta = 25) flips the sign of e every
+    step while |e| decays."""
+    rng = np.random.default_rng(62)
+    prm = o.Params(runs=32, steps=61, p=4.0, a=0.01, zeta=25.0)
+    seen = 0
+    for _ in range(4):
+        H32, y32, b32, _ = _build_pair(rng, 4, 4, 4, 0.05)
+        r = o.cac_solve(b32["Aq"], b32["hq"], b32["g"], 3, prm, 5, 2, want_states=True)
+        for run in range(prm.runs):
+            e = _final_e(b32, prm, 5, 2, run)
+            x = r["x_final"][run]
+            assert np.all(np.isfinite(x)) and np.all(np.abs(x) <= prm.x_max)
+            bad = not np.all(e > 0)
+            seen += bad
+            assert (r["E_runs"][run] == 2 ** 31 - 1) == bad
+        assert r["n_div"] == sum(not np.all(_final_e(b32, prm, 5, 2, q) > 0) for q in range(prm.runs))
+    assert seen > 0
+
+
 def test_solver_selection_rules():
     """Spins -> offset (d = s_a(s1+s2)/2, clipped), MMSE fallback (E > 0 or
     diverged -> guess) and arg-min over (E, run) of Sec. 3.2."""
@@ -335,7 +369,7 @@ def test_solver_selection_rules():
             d = s[2 * n] * (s[:n] + s[n:2 * n]) // 2
             xl = b32["g"] + 2 * d
             d[np.abs(xl) > 3] = 0
-            valid = np.all(np.abs(x) <= prm.x_max)
+            valid = np.all(np.abs(x) <= prm.x_max) and np.all(_final_e(b32, prm, 9, 4, run) > 0)
             E = o.energy_q(b32["Aq"], b32["hq"], d.astype(np.int8)) if valid else None
             assert r["E_runs"][run] == (E if valid else 2 ** 31 - 1)
             cands.append((E, run, d) if (valid and E <= 0) else (0, run, np.zeros(n, int)))
