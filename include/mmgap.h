@@ -63,6 +63,17 @@ typedef enum {
  * (Appendix A, P_diverge) and replaced by the guess.
  * Limits: runs in {32, 64, 96, 128}; steps in [0, 1<<20]; f_mvm in [1, 64];
  * dt > 0.
+ * early_exit: 0 = every anneal runs all `steps` steps (the paper's fixed N_I).
+ *   K > 0 = early exit, a budget lever with no counterpart in the paper: a
+ *   problem's anneals advance together, and every K-th field refresh, at
+ *   t = j K f_mvm (0 < t < steps), the signs [x >= 0] of all spins of all of
+ *   its anneals are compared with their signs at t - K f_mvm; if none changed,
+ *   all of the problem's anneals stop at t (their state there is final) and
+ *   selection proceeds as usual.  Results stay bit-exact with the CPU oracle
+ *   under the same rule.  Supported by mmgap_detect (delta mapping, up to 16
+ *   users, the bit-identical solver shapes), mmgap_detect_e, mmgap_precode,
+ *   mmgap_solve_ising (n <= 32) and mmgap_detect_static; the other calls and
+ *   the tensor-core shapes 5, 7 and 8 return MMGAP_EUNSUPPORTED when K > 0.
  */
 typedef struct {
     int32_t runs;
@@ -71,6 +82,7 @@ typedef struct {
     float dt, p, a, zeta, eps;
     float sigma0;
     float x_max;
+    int32_t early_exit;
 } mmgap_params;
 
 /*
@@ -89,13 +101,30 @@ typedef struct {
  *   noise_var: float [n_problems], noise variance per receive antenna
  *              (rho of Eq. 3 with unit symbol energy)
  *   seed:      Philox4x32-10 key; problem k of the job draws from counter
- *              space (., run, k).
+ *              space (., run, problem_offset + k).
+ *   problem_offset: index of the job's problem 0 in that counter space; 0 for
+ *              a whole job.  A job cut into shards (contiguous PRB ranges of
+ *              one slot on several GPUs, Sec. 3.2) gives each shard the index
+ *              of its first problem, and the shards' results then equal the
+ *              whole job's bit for bit.
  * Outputs (NULL = not wanted, except sym_out):
  *   sym_out:    uint8 [n_problems][n_t] detected QAM symbol indices
  *   energy_out: int32 [n_problems] selected quantised energy (<= 0; 0 = guess)
  *   guess_out:  int8 [n_problems][2 n_t] MMSE lattice guess (re block, im block)
  *   offset_out: int8 [n_problems][2 n_t] selected offset d in {-1, 0, 1}
  *   ndiv_out:   int32 [n_problems] diverged anneals
+ *   steps_out:  int32 [n_problems] Euler steps the problem's anneals took
+ *               (params->steps unless early exit stopped them); mmgap_detect
+ *               and mmgap_detect_static only (the batch and the server
+ *               refuse it)
+ * guess_in: int8 [n_problems][2 n_t] (re block, im block) lattice guess that
+ *   replaces the MMSE guess (Sec. 3.2: the guess is an input of the
+ *   pre-processing); NULL = MMSE.  Each entry must be an alphabet point, odd
+ *   with |g| <= sqrt(M) - 1; the builder sets bit 2 of the device error word
+ *   for any other value (the problem is built around it as given).  Honoured
+ *   by mmgap_detect, mmgap_build_detect, mmgap_detect_static, the batch and
+ *   the server with the delta mapping; refused (MMGAP_EUNSUPPORTED) with the
+ *   direct mapping and by mmgap_detect_e (which makes its own guesses).
  * gram_precision: 0 = FP32 Gram in the fixed operation order (bit-exact
  *   against the CPU oracle); 1 = BF16, 2 = FP16 and 3 = split BF16 (each
  *   operand as bf16 hi + bf16 lo, products hi*hi + hi*lo + lo*hi) on tensor
@@ -137,6 +166,9 @@ typedef struct {
     int32_t* ndiv_out;
     int32_t gram_precision;
     int32_t mapping;
+    const int8_t* guess_in;
+    int32_t* steps_out;
+    uint64_t problem_offset;
 } mmgap_detect_job;
 
 /*
@@ -174,8 +206,8 @@ typedef struct {
 } mmgap_precode_job;
 
 /* Fill *p with the library defaults: runs 32, steps 200, f_mvm 2, dt 0.02,
- * p 1.2, a 1.0, zeta 3.0, eps 0.5, sigma0 0.1, x_max 1000.  p/a/zeta/eps were
- * chosen on the CPU oracle (the paper does not print them). */
+ * p 1.2, a 1.0, zeta 3.0, eps 0.5, sigma0 0.1, x_max 1000, early_exit 0.
+ * p/a/zeta/eps were chosen on the CPU oracle (the paper does not print them). */
 mmgap_status mmgap_default_params(mmgap_params* p);
 
 /* Create a context on CUDA device `device` owning `workspace_bytes` of device
@@ -327,7 +359,8 @@ mmgap_status mmgap_stage_times(mmgap_ctx* ctx, float ms_out[4], int* n_chunks_ou
  * [0, n_chan) was met; the problem was computed as all-zero couplings;
  * bit 1: a wait of solver shape 8 on its tensor-core product expired; the
  * problems of that CTA returned their guesses with every anneal counted as
- * diverged).
+ * diverged; bit 2: a caller-supplied guess (guess_in) held a value that is
+ * not an alphabet point).
  * Synchronises the device; clears the word if `clear` is non-zero. */
 mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
 
@@ -484,25 +517,29 @@ mmgap_status mmgap_server_destroy(mmgap_server* server);
  * Uplink detection that allocates nothing (no counterpart in the paper; this
  * is a service to callers that cannot allocate device memory: a running
  * real-time slot loop, where cudaMalloc may synchronise the device and miss
- * the slot, a plug-in inside an application that owns all device memory, or
- * code being recorded into a CUDA graph).
+ * the slot, or a plug-in inside an application that owns all device memory).
  *
  * Computes exactly what mmgap_detect computes for one job, without a
  * context: the scratch between the build and solve kernels comes from an
  * 8 MiB array compiled into the library (every GPU that loads the library
- * holds it until the process exits).  Inputs and outputs are the caller's
- * device memory, as for mmgap_detect; the call runs on the current device.
+ * holds it until the process exits; with CUDA's lazy module loading the
+ * memory is taken on the first call on each device).  Inputs and outputs are
+ * the caller's device memory, as for mmgap_detect; the call runs on the
+ * current device.  guess_in, steps_out and params->early_exit (up to 16 users)
+ * are honoured as by mmgap_detect.
  *
  * Limit: the job must fit the array, i.e. align256(P n^2 2) + align256(P n 2)
  * + align256(P n) <= 8 MiB with n = 2 n_t (about 1,000 problems of 32 users, 3,900 of 16 users,
  * 14,900 of 8 users); a larger job returns MMGAP_ENOMEM (with a message on
  * stderr) and launches nothing.  Split it.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.
- * Every call shares the one array, which keeps the last call's contents, so
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race: serialise them.  A channel index out of range gives an all-zero
- * problem, as for mmgap_detect, but is not reported.
+ * The first call on a device looks up the array's device address and the
+ * device's SM count (with that device current); make that first call before
+ * any stream capture.
+ * Every call shares the one array, which keeps the last call's contents (each
+ * call writes every byte it reads before reading it), so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race: serialise
+ * them.  A channel index out of range gives an all-zero problem, as for
+ * mmgap_detect, but is not reported (there is no error word).
  * Returns MMGAP_EINVAL / MMGAP_EUNSUPPORTED for bad arguments, MMGAP_ECUDA
  * for a CUDA error.
  */

@@ -40,7 +40,7 @@ class MMGaPError(RuntimeError):
 class _Params(C.Structure):
     _fields_ = [("runs", C.c_int32), ("steps", C.c_int32), ("f_mvm", C.c_int32), ("dt", C.c_float),
                 ("p", C.c_float), ("a", C.c_float), ("zeta", C.c_float), ("eps", C.c_float),
-                ("sigma0", C.c_float), ("x_max", C.c_float)]
+                ("sigma0", C.c_float), ("x_max", C.c_float), ("early_exit", C.c_int32)]
 
 
 class _DetectJob(C.Structure):
@@ -48,7 +48,8 @@ class _DetectJob(C.Structure):
                 ("n_chan", C.c_int32), ("chan_index", C.c_void_p), ("H", C.c_void_p), ("y", C.c_void_p),
                 ("noise_var", C.c_void_p), ("seed", C.c_uint64), ("sym_out", C.c_void_p),
                 ("energy_out", C.c_void_p), ("guess_out", C.c_void_p), ("offset_out", C.c_void_p),
-                ("ndiv_out", C.c_void_p), ("gram_precision", C.c_int32), ("mapping", C.c_int32)]
+                ("ndiv_out", C.c_void_p), ("gram_precision", C.c_int32), ("mapping", C.c_int32),
+                ("guess_in", C.c_void_p), ("steps_out", C.c_void_p), ("problem_offset", C.c_uint64)]
 
 
 class _PrecodeJob(C.Structure):
@@ -145,6 +146,7 @@ class Params:
     eps: float
     sigma0: float
     x_max: float
+    early_exit: int = 0
 
     @classmethod
     def default(cls, **overrides) -> "Params":
@@ -156,7 +158,7 @@ class Params:
 
     def _c(self) -> _Params:
         return _Params(self.runs, self.steps, self.f_mvm, self.dt, self.p, self.a, self.zeta, self.eps,
-                       self.sigma0, self.x_max)
+                       self.sigma0, self.x_max, self.early_exit)
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -216,10 +218,11 @@ class Context:
     # ------------------------------------------------------------------ API
     def detect(self, H, y, noise_var, mod_bits: int, params: Params, seed: int, chan_index=None,
                want_energy=False, want_guess=False, want_offset=False, want_ndiv=False, gram_precision: int = 0,
-               mapping: int = 0):
+               mapping: int = 0, guess=None, want_steps=False):
         """Uplink detection of P problems.  H: complex64 (n_chan, n_r, n_t),
         y: complex64 (P, n_r), noise_var: float32 (P,), chan_index: int32 (P,)
-        or None.  Returns a dict of CUDA tensors (sym uint8 (P, n_t), ...)."""
+        or None, guess: int8 (P, 2 n_t) lattice guess replacing MMSE, or None.
+        Returns a dict of CUDA tensors (sym uint8 (P, n_t), ...)."""
         n_chan, n_r, n_t = H.shape
         P = y.shape[0]
         dev = self.device
@@ -227,7 +230,10 @@ class Context:
         _check(y, "y", torch.complex64, (P, n_r), dev)
         _check(noise_var, "noise_var", torch.float32, (P,), dev)
         _check(chan_index, "chan_index", torch.int32, (P,), dev)
+        _check(guess, "guess", torch.int8, (P, 2 * n_t), dev)
         out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev)}
+        if want_steps:
+            out["steps"] = torch.empty(P, dtype=torch.int32, device=dev)
         if want_energy:
             out["energy"] = torch.empty(P, dtype=torch.int32, device=dev)
         if want_guess:
@@ -236,7 +242,7 @@ class Context:
             out["offset"] = torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)
         if want_ndiv:
             out["ndiv"] = torch.empty(P, dtype=torch.int32, device=dev)
-        job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index, gram_precision, mapping)
+        job = self.detect_job(H, y, noise_var, mod_bits, seed, out, chan_index, gram_precision, mapping, guess)
         self.detect_jobs([job], params)
         return out
 
@@ -263,11 +269,15 @@ class Context:
         return out
 
     def detect_job(self, H, y, noise_var, mod_bits, seed, out, chan_index=None, gram_precision=0,
-                   mapping=0) -> _DetectJob:
+                   mapping=0, guess=None, problem_offset=0) -> _DetectJob:
+        """A detection job descriptor over device tensors.  out: dict with "sym" and optional
+        "energy", "guess", "offset", "ndiv", "steps"; guess: int8 (P, 2 n_t) input guess or None;
+        problem_offset: Philox counter index of problem 0 (a shard of a larger job)."""
         n_chan, n_r, n_t = H.shape
         return _DetectJob(n_r, n_t, mod_bits, y.shape[0], n_chan, _ptr(chan_index), _ptr(H), _ptr(y),
                           _ptr(noise_var), seed, _ptr(out["sym"]), _ptr(out.get("energy")), _ptr(out.get("guess")),
-                          _ptr(out.get("offset")), _ptr(out.get("ndiv")), gram_precision, mapping)
+                          _ptr(out.get("offset")), _ptr(out.get("ndiv")), gram_precision, mapping, _ptr(guess),
+                          _ptr(out.get("steps")), problem_offset)
 
     def detect_jobs(self, jobs, params: Params, stream=None):
         arr = (_DetectJob * len(jobs))(*jobs)
@@ -377,7 +387,7 @@ class Context:
         return out
 
     def build_detect(self, H, y, noise_var, mod_bits: int, chan_index=None, want_float=True, gram_precision=0,
-                     mapping=0):
+                     mapping=0, guess=None):
         """Builder only: quantised Ising coefficients of P detection problems (delta form:
         A_q (P, n, n), h_q (P, n); direct form, mapping=1: J_q (P, N, N), c_q (P, N) in the same keys)."""
         n_chan, n_r, n_t = H.shape
@@ -395,8 +405,9 @@ class Context:
             out["G"] = torch.empty((P, n, n), dtype=torch.float32, device=dev)
             out["h"] = torch.empty((P, n), dtype=torch.float32, device=dev)
             out["sigma_exp"] = torch.empty(P, dtype=torch.int32, device=dev)
+        _check(guess, "guess", torch.int8, (P, 2 * n_t), dev)
         job = _DetectJob(n_r, n_t, mod_bits, P, n_chan, _ptr(chan_index), _ptr(H), _ptr(y), _ptr(noise_var), 0,
-                         None, None, None, None, None, gram_precision, mapping)
+                         None, None, None, None, None, gram_precision, mapping, _ptr(guess), None)
         self._raise(_lib.mmgap_build_detect(self._h, C.byref(job), _ptr(out["A_q"]), _ptr(out["h_q"]),
                                             _ptr(out["g"]), _ptr(out.get("G")), _ptr(out.get("h")),
                                             _ptr(out.get("sigma_exp")), self._stream()))

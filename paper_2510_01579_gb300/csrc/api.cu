@@ -56,6 +56,28 @@ cudaError_t launch_random_ising(int16_t* Aq, int16_t* hq, int n, int n_problems,
 }
 }  // namespace mmgap
 
+// Constants of the Euler discretisation of Eqs. 10-11, each computed in
+// double from the float parameters and rounded once to float.
+EulerConsts mmgap::euler_consts(float dt_f, float p_f, float a_f, float zeta_f, float eps_f, float sigma0,
+                                float x_max) {
+    const double dt = dt_f, p = p_f, a = a_f, zeta = zeta_f, eps = eps_f;
+    EulerConsts k;
+    k.c1 = (float)(1.0 + dt * (p - 1.0));
+    k.cdt = (float)(-dt);
+    k.cz = (float)(-(dt * zeta));
+    k.c2 = (float)(1.0 + (dt * zeta) * a);
+    k.ce = (float)(eps * dt);
+    k.xs = (float)((double)sigma0 * 0x1p-23);
+    k.x_max = x_max;
+    return k;
+}
+
+void mmgap::qam_kappa(int mod_bits, float* kappa, float* kappa2) {
+    const double M = (double)(1 << mod_bits);
+    *kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
+    *kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
+}
+
 int mmgap::resolve_variant(int n_t, int f_mvm, int requested, int n_problems, int n_sm) {
     const bool tuned = (n_t == 4 || n_t == 8 || n_t == 16) && (f_mvm == 1 || f_mvm == 2);
     if (!tuned) return kVariantPlain;
@@ -100,19 +122,8 @@ mmgap_status cuda_fail(mmgap_ctx* ctx, cudaError_t e, const char* what) {
 
 bool nt_supported(int nt) { return nt == 1 || nt == 2 || nt == 3 || nt == 4 || nt == 8 || nt == 16; }
 
-// Constants of the Euler discretisation of Eqs. 10-11, each computed in
-// double from the float parameters and rounded once to float.
 EulerConsts euler_consts(const mmgap_params& P) {
-    const double dt = P.dt, p = P.p, a = P.a, zeta = P.zeta, eps = P.eps;
-    EulerConsts k;
-    k.c1 = (float)(1.0 + dt * (p - 1.0));
-    k.cdt = (float)(-dt);
-    k.cz = (float)(-(dt * zeta));
-    k.c2 = (float)(1.0 + (dt * zeta) * a);
-    k.ce = (float)(eps * dt);
-    k.xs = (float)((double)P.sigma0 * 0x1p-23);
-    k.x_max = P.x_max;
-    return k;
+    return mmgap::euler_consts(P.dt, P.p, P.a, P.zeta, P.eps, P.sigma0, P.x_max);
 }
 
 mmgap_status check_params(mmgap_ctx* ctx, const mmgap_params* P) {
@@ -125,6 +136,16 @@ mmgap_status check_params(mmgap_ctx* ctx, const mmgap_params* P) {
     if (!std::isfinite(P->p) || !std::isfinite(P->a) || !std::isfinite(P->zeta) || !std::isfinite(P->eps) ||
         !std::isfinite(P->sigma0) || !(P->x_max > 0.0f))
         return fail(ctx, MMGAP_EINVAL, "non-finite solver parameter or x_max <= 0");
+    if (P->early_exit < 0) return fail(ctx, MMGAP_EINVAL, "early_exit=%d must be >= 0", P->early_exit);
+    return MMGAP_OK;
+}
+
+// Early exit runs on the bit-identical solver shapes up to 16 users.
+mmgap_status check_early_exit(mmgap_ctx* ctx, const mmgap_params* P, int n_t) {
+    if (P->early_exit == 0) return MMGAP_OK;
+    if (n_t > 16) return fail(ctx, MMGAP_EUNSUPPORTED, "early exit: up to 16 users");
+    if (variant_tensor_core(resolve_variant(n_t, P->f_mvm, ctx->variant[n_t])))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "early exit runs on the bit-identical solver shapes, not 5, 7 or 8");
     return MMGAP_OK;
 }
 
@@ -160,12 +181,6 @@ template <> struct Has32<OpBuild> { static constexpr bool value = true; };
 template <> struct Has32<OpFactor> { static constexpr bool value = true; };
 template <> struct Has32<OpSolve> { static constexpr bool value = true; };
 
-// QAM normalisation kappa = 1/sqrt(2 (M-1)/3) and kappa^2, rounded once to float.
-void qam_kappa(int mod_bits, float* kappa, float* kappa2) {
-    const double M = (double)(1 << mod_bits);
-    *kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
-    *kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
-}
 
 struct CurrentDevice {
     int prev = -1;
@@ -221,6 +236,8 @@ mmgap_status check_detect_job(mmgap_ctx* ctx, const mmgap_detect_job& j, bool ne
     if (j.mapping != MMGAP_MAPPING_DELTA && j.mapping != MMGAP_MAPPING_DIRECT)
         return fail(ctx, MMGAP_EINVAL, "mapping=%d: 0 delta, 1 direct", j.mapping);
     if (j.mapping == MMGAP_MAPPING_DIRECT) {
+        if (j.guess_in) return fail(ctx, MMGAP_EUNSUPPORTED, "direct mapping: the guess is the MMSE guess");
+        if (j.steps_out) return fail(ctx, MMGAP_EUNSUPPORTED, "direct mapping: no steps_out");
         if (!(j.n_t == 4 || j.n_t == 8 || j.n_t == 16))
             return fail(ctx, MMGAP_EUNSUPPORTED, "direct mapping: n_t=%d, supported 4, 8, 16", j.n_t);
         if (j.gram_precision != 0) return fail(ctx, MMGAP_EUNSUPPORTED, "direct mapping builds the Gram in FP32");
@@ -305,7 +322,7 @@ mmgap_status detect_direct_job(mmgap_ctx* ctx, const mmgap_params* params, const
         a.f_mvm = params->f_mvm;
         a.key0 = (uint32_t)J.seed;
         a.key1 = (uint32_t)(J.seed >> 32);
-        a.problem_offset = (uint64_t)p0;
+        a.problem_offset = J.problem_offset + (uint64_t)p0;
         a.k = k;
         a.E_out = J.energy_out ? J.energy_out + p0 : nullptr;
         a.ndiv_out = J.ndiv_out ? J.ndiv_out + p0 : nullptr;
@@ -399,6 +416,7 @@ mmgap_status mmgap_default_params(mmgap_params* p) {
     p->eps = 0.5f;
     p->sigma0 = 0.1f;
     p->x_max = 1000.0f;
+    p->early_exit = 0;
     return MMGAP_OK;
 }
 
@@ -522,6 +540,8 @@ mmgap_status mmgap_build_detect(mmgap_ctx* ctx, const mmgap_detect_job* job, int
     a.n_chan = job->n_chan;
     qam_kappa(job->mod_bits, &a.kappa, &a.kappa2);
     a.err = ctx->dev_err;
+    a.guess_mode = job->guess_in ? 2 : 0;
+    a.g_in = job->guess_in;
     a.Aq = A_q_out;
     a.hq = h_q_out;
     a.g = g_out;
@@ -550,6 +570,7 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     if (n_problems == 0) return MMGAP_OK;
     if (!A_q || !h_q || !d_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q, h_q or d_out");
     if (level_max < 0 || (level_max > 0 && !g)) return fail(ctx, MMGAP_EINVAL, "level_max needs g");
+    if ((st = check_early_exit(ctx, params, n / 2)) != MMGAP_OK) return st;
     CurrentDevice cd(ctx->device);
     SolveArgs a{};
     a.err = ctx->dev_err;
@@ -569,6 +590,7 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     a.E_out = E_out;
     a.run_out = run_out;
     a.ndiv_out = ndiv_out;
+    a.early_exit = params->early_exit;
     a.variant = ctx->variant[n / 2];
     cudaError_t e = dispatch_nt<OpSolve>(n / 2, a, params->runs, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
@@ -583,6 +605,7 @@ mmgap_status mmgap_solve_general(mmgap_ctx* ctx, const mmgap_params* params, int
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
     if (!general_supported(N)) return fail(ctx, MMGAP_EUNSUPPORTED, "N=%d: supported 8, 16, 24, 32, 48, 64, 96", N);
+    if (params->early_exit) return fail(ctx, MMGAP_EUNSUPPORTED, "the general solver has no early exit");
     if ((st = check_general_runs(ctx, params, N)) != MMGAP_OK) return st;
     if (n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
     if (n_problems == 0) return MMGAP_OK;
@@ -614,8 +637,12 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, MMGAP_EINVAL, "bad jobs array");
-    for (int j = 0; j < n_jobs; ++j)
+    for (int j = 0; j < n_jobs; ++j) {
         if ((st = check_detect_job(ctx, jobs[j], true)) != MMGAP_OK) return st;
+        if (jobs[j].mapping == MMGAP_MAPPING_DIRECT && params->early_exit)
+            return fail(ctx, MMGAP_EUNSUPPORTED, "the direct mapping has no early exit");
+        if ((st = check_early_exit(ctx, params, jobs[j].n_t)) != MMGAP_OK) return st;
+    }
     CurrentDevice cd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const EulerConsts k = euler_consts(*params);
@@ -642,7 +669,7 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
         const float* L_pre = nullptr;
         const float* rho_pre = nullptr;
         const int32_t* chol_pre = nullptr;
-        if (!gc && J.chan_index && J.n_chan < J.n_problems) {
+        if (!gc && !J.guess_in && J.chan_index && J.n_chan < J.n_problems) {
             const size_t nc = (size_t)J.n_chan;
             const size_t lb = align_up(nc * 2 * J.n_t * J.n_t * sizeof(float)), rb = align_up(nc * 4);
             if (gc_bytes + lb + 3 * rb + per + 3 * kAlign <= ctx->ws_bytes) {
@@ -694,6 +721,8 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
             b.n_chan = J.chan_index ? J.n_chan : P;
             qam_kappa(J.mod_bits, &b.kappa, &b.kappa2);
             b.err = ctx->dev_err;
+            b.guess_mode = J.guess_in ? 2 : 0;
+            b.g_in = J.guess_in ? J.guess_in + (size_t)p0 * n : nullptr;
             b.Aq = Aq;
             b.hq = hq;
             b.g = g;
@@ -712,7 +741,7 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
             a.f_mvm = params->f_mvm;
             a.key0 = (uint32_t)J.seed;
             a.key1 = (uint32_t)(J.seed >> 32);
-            a.problem_offset = (uint64_t)p0;
+            a.problem_offset = J.problem_offset + (uint64_t)p0;
             a.k = k;
             a.d_out = J.offset_out ? J.offset_out + (size_t)p0 * n : nullptr;
             a.E_out = J.energy_out ? J.energy_out + p0 : nullptr;
@@ -721,6 +750,8 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
             a.sym_out = J.sym_out + (size_t)p0 * J.n_t;
             a.mod_bits = J.mod_bits;
             a.variant = ctx->variant[J.n_t];
+            a.early_exit = params->early_exit;
+            a.steps_out = J.steps_out ? J.steps_out + p0 : nullptr;
             e = dispatch_nt<OpSolve>(J.n_t, a, params->runs, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
             if (J.guess_out) {
@@ -741,8 +772,10 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
     mmgap_status st = check_params(ctx, params);
     if (st != MMGAP_OK) return st;
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, MMGAP_EINVAL, "bad jobs array");
-    for (int j = 0; j < n_jobs; ++j)
+    for (int j = 0; j < n_jobs; ++j) {
         if ((st = check_precode_job(ctx, jobs[j])) != MMGAP_OK) return st;
+        if ((st = check_early_exit(ctx, params, jobs[j].n_u)) != MMGAP_OK) return st;
+    }
     CurrentDevice cd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const EulerConsts k = euler_consts(*params);
@@ -803,6 +836,7 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
             a.E_out = J.energy_out ? J.energy_out + p0 : nullptr;
             a.ndiv_out = J.ndiv_out ? J.ndiv_out + p0 : nullptr;
             a.variant = ctx->variant[J.n_u];
+            a.early_exit = params->early_exit;
             e = dispatch_nt<OpSolve>(J.n_u, a, params->runs, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
             if ((st = timing_mark(ctx, 2, s)) != MMGAP_OK) return st;
@@ -863,6 +897,8 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
     if ((st = check_detect_job(ctx, *job, true)) != MMGAP_OK) return st;
     if (job->mapping != MMGAP_MAPPING_DELTA) return fail(ctx, MMGAP_EUNSUPPORTED, "MMGaP-E uses the delta mapping");
     if (job->n_t == 32) return fail(ctx, MMGAP_EUNSUPPORTED, "MMGaP-E: n_t up to 16");
+    if (job->guess_in) return fail(ctx, MMGAP_EUNSUPPORTED, "MMGaP-E makes its own guesses (guess_in must be NULL)");
+    if ((st = check_early_exit(ctx, params, job->n_t)) != MMGAP_OK) return st;
     if (stages < 1 || stages > 8) return fail(ctx, MMGAP_EINVAL, "stages=%d out of [1, 8]", stages);
     const mmgap_detect_job& J = *job;
     if (J.n_problems == 0) return MMGAP_OK;
@@ -915,10 +951,11 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
         a.n_problems = P;
         a.steps = params->steps;
         a.f_mvm = params->f_mvm;
-        a.problem_offset = (uint64_t)p0;
+        a.problem_offset = J.problem_offset + (uint64_t)p0;
         a.k = k;
         a.mod_bits = J.mod_bits;
         a.variant = ctx->variant[J.n_t];
+        a.early_exit = params->early_exit;
         cudaError_t e = cudaSuccess;
         for (int stg = 1; stg <= stages && e == cudaSuccess; ++stg)
             for (int inst = 0; inst < 2 && e == cudaSuccess; ++inst) {
@@ -981,6 +1018,7 @@ mmgap_status mmgap_anneal_spins(mmgap_ctx* ctx, const mmgap_params* params, int 
     if (n < 2 || (n & 1) || !nt_supported(n / 2))
         return fail(ctx, MMGAP_EUNSUPPORTED, "n=%d: supported 2, 4, 6, 8, 16, 32", n);
     if (n_problems < 0) return fail(ctx, MMGAP_EINVAL, "n_problems < 0");
+    if (params->early_exit) return fail(ctx, MMGAP_EUNSUPPORTED, "the integration study anneals all steps");
     if (n_problems == 0) return MMGAP_OK;
     if (!A_q || !h_q || !spins_out) return fail(ctx, MMGAP_EINVAL, "NULL A_q, h_q or spins_out");
     CurrentDevice cd(ctx->device);
@@ -1053,6 +1091,7 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
     a.f_mvm = params->f_mvm;
     a.key0 = 1;
     a.k = euler_consts(*params);
+    a.early_exit = params->early_exit;
     a.d_out = d;
     a.E_out = E;
     cudaEvent_t t0 = nullptr, t1 = nullptr;

@@ -61,20 +61,10 @@ const void* pick_build(int ntmax) {
 
 constexpr int kBatchWarps = 4;
 
-// Constants of the Euler discretisation of Eqs. 10-11, each computed in
-// double from the float parameters and rounded once to float (the same
-// values as the per-job entry points use).
+// Constants of the Euler discretisation of Eqs. 10-11 (the helper every
+// entry point uses, so the rounding is the same on every path).
 EulerConsts batch_consts(const mmgap_params& P) {
-    const double dt = P.dt, p = P.p, aa = P.a, zeta = P.zeta, eps = P.eps;
-    EulerConsts k;
-    k.c1 = (float)(1.0 + dt * (p - 1.0));
-    k.cdt = (float)(-dt);
-    k.cz = (float)(-(dt * zeta));
-    k.c2 = (float)(1.0 + (dt * zeta) * aa);
-    k.ce = (float)(eps * dt);
-    k.xs = (float)((double)P.sigma0 * 0x1p-23);
-    k.x_max = P.x_max;
-    return k;
+    return euler_consts(P.dt, P.p, P.a, P.zeta, P.eps, P.sigma0, P.x_max);
 }
 constexpr size_t kScratchAlign = 256;
 size_t salign(size_t v) { return (v + kScratchAlign - 1) / kScratchAlign * kScratchAlign; }
@@ -85,6 +75,7 @@ const char* BatchRunner::check_params(const mmgap_params& P) {
     if (P.runs != 32) return "batched launch runs 32 anneals per problem (one warp)";
     if (P.f_mvm != 1 && P.f_mvm != 2) return "batched launch supports f_mvm 1 or 2";
     if (P.steps < 0 || P.steps > (1 << 20) || !(P.dt > 0.0f) || !(P.x_max > 0.0f)) return "bad solver parameters";
+    if (P.early_exit != 0) return "batched launch runs every anneal for all steps (early_exit must be 0)";
     return nullptr;
 }
 
@@ -97,6 +88,7 @@ const char* BatchRunner::check_job(const mmgap_detect_job& J) {
     if (J.n_problems > 0 && !J.chan_index && J.n_chan < J.n_problems) return "chan_index NULL needs n_chan >= n";
     if (J.gram_precision != 0) return "batched launch builds the Gram in FP32 (gram_precision 0)";
     if (J.mapping != MMGAP_MAPPING_DELTA) return "batched launch uses the delta mapping";
+    if (J.steps_out) return "batched launch runs every anneal for all steps (steps_out must be NULL)";
     return nullptr;
 }
 
@@ -232,9 +224,9 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
             b.mod_bits = J.mod_bits;
             b.n_problems = J.n_problems;
             b.n_chan = J.chan_index ? J.n_chan : J.n_problems;
-            const double M = (double)(1 << J.mod_bits);
-            b.kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
-            b.kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
+            qam_kappa(J.mod_bits, &b.kappa, &b.kappa2);
+            b.guess_mode = J.guess_in ? 2 : 0;
+            b.g_in = J.guess_in;
             b.err = err_word_;
             b.Aq = (int16_t*)(scratch_ + off);
             b.hq = (int16_t*)(scratch_ + off + salign(P * n * n * 2));
@@ -249,6 +241,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
             a.n_problems = J.n_problems;
             a.key0 = (uint32_t)J.seed;
             a.key1 = (uint32_t)(J.seed >> 32);
+            a.problem_offset = J.problem_offset;
             a.d_out = J.offset_out;
             a.E_out = J.energy_out;
             a.ndiv_out = J.ndiv_out;
@@ -275,13 +268,14 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
             B.b.mod_bits = J.mod_bits;
             B.b.n_problems = J.n_problems;
             B.b.n_chan = J.chan_index ? J.n_chan : J.n_problems;
-            const double M = (double)(1 << J.mod_bits);
-            B.b.kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
-            B.b.kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
+            qam_kappa(J.mod_bits, &B.b.kappa, &B.b.kappa2);
+            B.b.guess_mode = J.guess_in ? 2 : 0;
+            B.b.g_in = J.guess_in;
             B.nt = J.n_t;
             B.kind = 0;
             B.key0 = (uint32_t)J.seed;
             B.key1 = (uint32_t)(J.seed >> 32);
+            B.poff = J.problem_offset;
             const size_t n = 2 * (size_t)J.n_t, P = (size_t)J.n_problems;
             if (off + scratch_bytes(J.n_t, J.n_problems) > scratch_bytes_) return -2;
             B.Aq = (int16_t*)(scratch_ + off);
@@ -315,6 +309,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
             B.kind = 1;
             B.key0 = (uint32_t)J.seed;
             B.key1 = (uint32_t)(J.seed >> 32);
+            B.poff = 0;
             B.Aq = R.Aq;
             B.hq = R.hq;
             B.g = nullptr;
@@ -335,6 +330,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
         if (!G.det) continue;
         const mmgap_detect_job& J = *G.det;
         if (!J.chan_index || J.n_chan >= J.n_problems || J.n_problems == 0) continue;
+        if (J.guess_in) continue;  // a caller-supplied guess needs no MMSE factor
         const size_t fb = factor_bytes(J.n_t, J.n_chan);
         if (off + fb > scratch_bytes_) continue;
         if (slot[i] < 0 && J.n_problems == 0) continue;  // (empty wide jobs are not staged)

@@ -23,6 +23,7 @@ struct BatchJob {
     int kind;               // 0 detection (built by the batch builder); 1 VPP, built before the
                             // batch: no clipping (guess 0), offsets to offset_out, no symbols
     uint32_t key0, key1;
+    unsigned long long poff;  // the job's problem_offset (Philox counter of its problem 0)
     long long first;        // batch index of the job's problem 0
     long long tile_first;   // tensor-core solver: index of the job's first 4-problem tile
     int16_t* Aq;            // scratch [P][n][n]
@@ -108,7 +109,8 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
     const int run = lane;
     float x1[n], x2[n], e1[n], e2[n], xa, ea = 1.0f;
     {
-        const uint32_t c2 = (uint32_t)p, c3 = 0u;
+        const unsigned long long pg = J.poff + (unsigned long long)p;
+        const uint32_t c2 = (uint32_t)pg, c3 = (uint32_t)(pg >> 32);
 #pragma unroll
         for (int b = 0; b < n / 4; ++b) {
             const U4 w1 = philox4x32_10(U4{(uint32_t)b, (uint32_t)run, c2, c3}, J.key0, J.key1);
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(128) batch_solve_umma_kernel(BatchArgs A) {
             u.hq = J.hq + (size_t)base * n;
             u.g = J.g ? J.g + (size_t)base * n : nullptr;
             u.n_live = live;
-            u.problem0 = (uint64_t)base;
+            u.problem0 = J.poff + (uint64_t)base;
             u.key0 = J.key0;
             u.key1 = J.key1;
             u.level_max = J.kind == 0 ? (1 << (J.b.mod_bits >> 1)) - 1 : 0;

@@ -180,7 +180,7 @@ __device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, in
 
     const int c = a.chan_index ? a.chan_index[p] : p;
     if (c < 0 || c >= a.n_chan) {  // bad channel index: flag it, emit an all-zero problem
-        if (lane == 0) atomicOr(a.err, kErrChanIndex);
+        if (lane == 0 && a.err) atomicOr(a.err, kErrChanIndex);
         if (o.Aq)
             for (int e = lane; e < n * n; e += 32) o.Aq[e] = 0;
         for (int e = lane; e < n; e += 32) {
@@ -213,11 +213,17 @@ __device__ __forceinline__ void build_problem_warp(const BuildArgs& a, int p, in
         return (float)(2 * (int)floorf(mulrn(xc, 0.5f)) + 1);
     };
     if (a.guess_mode == 2) {
-        // externally supplied guess (a previous stage's solution)
+        // externally supplied guess (a previous stage's solution, or the caller's); an entry that
+        // is not an alphabet point (odd, |g| <= sqrt(M) - 1) is used as given and flagged
+        bool bad = false;
         if (lane < NT) {
-            gv[lane] = (float)a.g_in[(size_t)p * n + lane];
-            gv[NT + lane] = (float)a.g_in[(size_t)p * n + NT + lane];
+            const int gr = a.g_in[(size_t)p * n + lane], gi = a.g_in[(size_t)p * n + NT + lane];
+            const int L = side - 1;
+            bad = !(gr & 1) || !(gi & 1) || gr > L || gr < -L || gi > L || gi < -L;
+            gv[lane] = (float)gr;
+            gv[NT + lane] = (float)gi;
         }
+        if (__any_sync(0xffffffffu, bad) && lane == 0 && a.err) atomicOr(a.err, kErrGuess);
         __syncwarp();
     } else {
         // Cholesky of B = G_c + rho I, rho = noise_var kappa^2 (cholesky_warp)

@@ -3,19 +3,17 @@
 // Some callers cannot allocate device memory.  A real-time slot loop may not
 // call cudaMalloc once it is running, because an allocation can synchronise
 // the device and blow a 0.5 ms slot; a plug-in hosted by an application that
-// owns every device allocation may not allocate at all; and code that records
-// its work into a CUDA graph cannot have an allocation inside the recorded
-// section.  This entry point serves them: it needs no context and takes its
-// per-problem scratch (the quantised couplings, field and guess between the
-// build and solve kernels) from a fixed array compiled into the library
-// instead of from a workspace.
+// owns every device allocation may not allocate at all.  This entry point
+// serves them: it needs no context and takes its per-problem scratch (the
+// quantised couplings, field and guess between the build and solve kernels)
+// from a fixed array compiled into the library instead of from a workspace.
 //
 // The scratch is a file-scope __device__ array of kStaticScratchBytes, so
 // every GPU that loads this library holds that much memory until the process
-// exits.  Host code only ever sees a host-side stand-in for the array's name;
-// its device address is looked up with cudaGetSymbolAddress once per device
-// (with that device current) and cached.
-#include <cmath>
+// exits (with lazy module loading, from the first call on that device).
+// Host code only ever sees a host-side stand-in for the array's name; its
+// device address is looked up with cudaGetSymbolAddress once per device (with
+// that device current) and cached, together with the device's SM count.
 #include <cstdio>
 #include <mutex>
 
@@ -32,32 +30,37 @@ constexpr size_t kStaticScratchBytes = (size_t)8 << 20;  // 8 MiB per device
 constexpr size_t kAlign = 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
-static __device__ __align__(256) int g_scratch_err[1];
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-struct DevicePtrs {
-    unsigned char* scratch = nullptr;
-    int* err = nullptr;
+struct DeviceInfo {
+    unsigned char* scratch = nullptr;  // device address of g_scratch on this device
+    int n_sm = 0;                      // SMs, for the small-call launch shapes
 };
 
 std::mutex g_mu;
-DevicePtrs g_ptrs[kMaxDevices];
+DeviceInfo g_info[kMaxDevices];
 
-// Device addresses of the static scratch on the current device (looked up on
-// the first call on that device).
-mmgap_status device_ptrs(int dev, DevicePtrs* out) {
+// Address of the static scratch and SM count of the current device `dev`
+// (looked up on the first call on that device, with it current).
+mmgap_status device_info(int dev, DeviceInfo* out) {
     std::lock_guard<std::mutex> lock(g_mu);
-    DevicePtrs& p = g_ptrs[dev];
-    if (!p.scratch) {
+    DeviceInfo& d = g_info[dev];
+    if (!d.scratch) {
         void* s = nullptr;
-        void* e = nullptr;
-        if (cudaGetSymbolAddress(&s, g_scratch) != cudaSuccess) return MMGAP_ECUDA;
-        if (cudaGetSymbolAddress(&e, g_scratch_err) != cudaSuccess) return MMGAP_ECUDA;
-        p.scratch = (unsigned char*)s;
-        p.err = (int*)e;
+        if (cudaGetSymbolAddress(&s, g_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return MMGAP_ECUDA;
+        }
+        int n_sm = 0;
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            n_sm = 0;  // unknown: the throughput shapes for every call
+        }
+        d.n_sm = n_sm;
+        d.scratch = (unsigned char*)s;
     }
-    *out = p;
+    *out = d;
     return MMGAP_OK;
 }
 
@@ -89,7 +92,8 @@ mmgap_status mmgap_detect_static(const mmgap_params* params, const mmgap_detect_
     if (!params || !job) return MMGAP_EINVAL;
     const mmgap_params& P = *params;
     if (!(P.runs == 32 || P.runs == 64 || P.runs == 96 || P.runs == 128)) return MMGAP_EUNSUPPORTED;
-    if (P.steps < 0 || P.steps > (1 << 20) || P.f_mvm < 1 || P.f_mvm > 64 || !(P.dt > 0.0f) || !(P.x_max > 0.0f))
+    if (P.steps < 0 || P.steps > (1 << 20) || P.f_mvm < 1 || P.f_mvm > 64 || !(P.dt > 0.0f) || !(P.x_max > 0.0f) ||
+        P.early_exit < 0)
         return MMGAP_EINVAL;
     const mmgap_detect_job& J = *job;
     if (!nt_ok(J.n_t) || J.n_r < 1 || J.n_r > kMaxNr || !(J.mod_bits == 2 || J.mod_bits == 4 || J.mod_bits == 6))
@@ -100,6 +104,7 @@ mmgap_status mmgap_detect_static(const mmgap_params* params, const mmgap_detect_
     if (!J.chan_index && J.n_chan < J.n_problems) return MMGAP_EINVAL;
     if (J.gram_precision != 0) return MMGAP_EUNSUPPORTED;  // the tensor-core Gram needs a workspace
     if (J.mapping != MMGAP_MAPPING_DELTA) return MMGAP_EUNSUPPORTED;  // the direct mapping has its own scratch layout
+    if (P.early_exit > 0 && J.n_t == 32) return MMGAP_EUNSUPPORTED;     // early exit: up to 16 users
 
     // scratch this job needs: A_q, h_q and g in three 256-B-aligned regions
     const int n = 2 * J.n_t;
@@ -115,15 +120,15 @@ mmgap_status mmgap_detect_static(const mmgap_params* params, const mmgap_detect_
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MMGAP_ECUDA;
-    DevicePtrs ptr;
-    mmgap_status st = device_ptrs(dev, &ptr);
+    DeviceInfo info;
+    mmgap_status st = device_info(dev, &info);
     if (st != MMGAP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // the error word is OR-ed by the build kernel; it starts from zero on every call
-    if (cudaMemsetAsync(ptr.err, 0, sizeof(int), s) != cudaSuccess) return MMGAP_ECUDA;
 
-    int16_t* Aq = (int16_t*)ptr.scratch;
-    int16_t* hq = (int16_t*)(ptr.scratch + align_up((size_t)J.n_problems * n * n * 2));
+    // Every region below is written in full by the build kernel before the
+    // solver reads it, so nothing left by an earlier call is ever read.
+    int16_t* Aq = (int16_t*)info.scratch;
+    int16_t* hq = (int16_t*)(info.scratch + align_up((size_t)J.n_problems * n * n * 2));
     int8_t* g = (int8_t*)((unsigned char*)hq + align_up((size_t)J.n_problems * n * 2));
 
     BuildArgs b{};
@@ -135,12 +140,10 @@ mmgap_status mmgap_detect_static(const mmgap_params* params, const mmgap_detect_
     b.mod_bits = J.mod_bits;
     b.n_problems = J.n_problems;
     b.n_chan = J.chan_index ? J.n_chan : J.n_problems;
-    {
-        const double M = (double)(1 << J.mod_bits);
-        b.kappa = (float)(1.0 / std::sqrt(2.0 * (M - 1.0) / 3.0));
-        b.kappa2 = (float)(1.0 / (2.0 * (M - 1.0) / 3.0));
-    }
-    b.err = ptr.err;
+    qam_kappa(J.mod_bits, &b.kappa, &b.kappa2);
+    b.err = nullptr;  // no error word: a bad channel index gives an all-zero problem, unreported
+    b.guess_mode = J.guess_in ? 2 : 0;
+    b.g_in = J.guess_in;
     b.Aq = Aq;
     b.hq = hq;
     b.g = g;
@@ -156,17 +159,11 @@ mmgap_status mmgap_detect_static(const mmgap_params* params, const mmgap_detect_
     a.f_mvm = P.f_mvm;
     a.key0 = (uint32_t)J.seed;
     a.key1 = (uint32_t)(J.seed >> 32);
-    a.problem_offset = 0;
-    {
-        const double dt = P.dt, p = P.p, aa = P.a, zeta = P.zeta, eps = P.eps;
-        a.k.c1 = (float)(1.0 + dt * (p - 1.0));
-        a.k.cdt = (float)(-dt);
-        a.k.cz = (float)(-(dt * zeta));
-        a.k.c2 = (float)(1.0 + (dt * zeta) * aa);
-        a.k.ce = (float)(eps * dt);
-        a.k.xs = (float)((double)P.sigma0 * 0x1p-23);
-        a.k.x_max = P.x_max;
-    }
+    a.problem_offset = J.problem_offset;
+    a.k = euler_consts(P.dt, P.p, P.a, P.zeta, P.eps, P.sigma0, P.x_max);
+    a.n_sm = info.n_sm;
+    a.early_exit = P.early_exit;
+    a.steps_out = J.steps_out;
     a.d_out = J.offset_out;
     a.E_out = J.energy_out;
     a.ndiv_out = J.ndiv_out;

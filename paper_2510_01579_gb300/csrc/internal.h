@@ -31,6 +31,12 @@ struct EulerConsts {
     float x_max;
 };
 
+// Host-side derivation of the constants above, shared by every entry point so
+// that all paths round them identically.
+EulerConsts euler_consts(float dt, float p, float a, float zeta, float eps, float sigma0, float x_max);
+// QAM normalisation kappa = 1/sqrt(2 (M-1)/3) and kappa^2, each rounded once to float.
+void qam_kappa(int mod_bits, float* kappa, float* kappa2);
+
 struct SolveArgs {
     const int16_t* Aq;   // [P][n][n]
     const int16_t* hq;   // [P][n]
@@ -55,6 +61,8 @@ struct SolveArgs {
     uint64_t* spins_out;       // [P][runs][2] final sign bits per anneal (plain kernel), or nullptr
     int* err;                  // device error word (bit 1: a tcgen05 wait expired), or nullptr
     int n_sm;                  // SMs of the device (0: unknown); picks latency shapes for small calls
+    int early_exit;            // K > 0: stop a problem's anneals at the first K-th refresh with no sign change
+    int32_t* steps_out;        // [P] Euler steps taken, or nullptr
 };
 
 // Launch shapes of the solver.  All produce bit-identical results.
@@ -259,5 +267,6 @@ constexpr int kMaxDevices = 64;  // devices whose per-kernel launch attributes a
 
 // Bits of the device error word.
 constexpr int kErrChanIndex = 1;
+constexpr int kErrGuess = 4;  // a caller-supplied guess entry is not an alphabet point
 
 }  // namespace mmgap

@@ -62,9 +62,40 @@ cudaError_t launch_umma(const SolveArgs& a, int runs, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The bit-identical tuned shapes with early exit (SolveArgs::early_exit > 0).
+template <int NT, int F>
+cudaError_t launch_tuned_early_exit(const SolveArgs& a, int runs, int variant, cudaStream_t s) {
+    switch (variant) {
+    case kVariantTpa1: cac_solve_tuned_kernel<NT, F, 1, false, false, false, true><<<a.n_problems, runs, 0, s>>>(a); break;
+    case kVariantTpa1Packed:
+        cac_solve_tuned_kernel<NT, F, 1, true, false, false, true><<<a.n_problems, runs, 0, s>>>(a);
+        break;
+    case kVariantTpa2Packed:
+        cac_solve_tuned_kernel<NT, F, 2, true, false, false, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
+        break;
+    case kVariantTpa4Packed:
+        if constexpr (NT >= 8) cac_solve_tuned_kernel<NT, F, 4, true, false, false, true><<<a.n_problems, 4 * runs, 0, s>>>(a);
+        else cac_solve_tuned_kernel<NT, F, 2, true, false, false, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
+        break;
+    case kVariantTpa8Packed:
+        if constexpr (NT >= 16) cac_solve_tuned_kernel<NT, F, 8, true, false, false, true><<<a.n_problems, 8 * runs, 0, s>>>(a);
+        else cac_solve_tuned_kernel<NT, F, 2, true, false, false, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
+        break;
+    case kVariantPairPacked:
+        cac_solve_tuned_kernel<NT, F, 1, true, false, true, true><<<a.n_problems, runs, 0, s>>>(a);
+        break;
+    case kVariantTensorCore:
+    case kVariantTensorCore2:
+    case kVariantUmma: return cudaErrorNotSupported;  // (the entry points refuse this combination first)
+    default: cac_solve_kernel<NT, F><<<a.n_problems, runs, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
 template <int NT, int F>
 cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t s) {
     if constexpr (tuned_size(NT)) {
+        if (a.early_exit > 0) return launch_tuned_early_exit<NT, F>(a, runs, variant, s);
         switch (variant) {
         case kVariantTpa1: cac_solve_tuned_kernel<NT, F, 1, false><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa1Packed: cac_solve_tuned_kernel<NT, F, 1, true><<<a.n_problems, runs, 0, s>>>(a); break;
@@ -135,7 +166,7 @@ cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
         // 32 users (n = 64): the row-block kernel (two anneals x 8 rows per thread, four warps per 32
         // anneals); f_mvm 1 and 2 compiled in, others at run time; no spin dump (129 spins do not fit
         // the 128-bit state words, and the API refuses it)
-        if (a.spins_out || a.f_mvm < 1 || runs % 32 != 0) return cudaErrorInvalidValue;
+        if (a.spins_out || a.early_exit || a.f_mvm < 1 || runs % 32 != 0) return cudaErrorInvalidValue;
         // latency: when the problems' 32-anneal groups fit the SMs, each problem is a cluster of
         // runs / 32 CTAs (same results: anneal indices and the arg-min key are the problem's)
         const int cl = runs / 32;

@@ -25,6 +25,39 @@ __device__ __forceinline__ void euler_spin(float& x, float& e, float mu, const E
     x = xn;
 }
 
+// Early exit (SolveArgs::early_exit = K > 0; a budget lever, not in the
+// paper, which anneals a fixed N_I steps): a problem's anneals advance
+// together, and at every K-th field refresh, t = j K f_mvm with 0 < t < S,
+// the signs [x >= 0] of all spins of all its anneals are compared with those
+// at the previous check point.  If none changed, every anneal of the problem
+// stops at t; its state there is final.  One CTA holds one problem, so the
+// decision is one CTA-wide vote (__syncthreads_or), uniform across the CTA.
+template <int M>
+__device__ __forceinline__ uint32_t sign_word(const float* x) {
+    static_assert(M <= 32, "one word per 32 spins");
+    uint32_t w = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) w |= (x[i] >= 0.0f ? 1u : 0u) << i;
+    return w;
+}
+
+// Sign words of x[0..M) compared with prev (updated); true if any sign changed.
+template <int M>
+__device__ __forceinline__ bool signs_changed(const float (&x)[M], uint32_t (&prev)[(M + 31) / 32]) {
+    bool changed = false;
+#pragma unroll
+    for (int b = 0; b < (M + 31) / 32; ++b) {
+        constexpr int W = 32;
+        uint32_t w = 0;
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            if (W * b + i < M) w |= (x[W * b + i] >= 0.0f ? 1u : 0u) << i;
+        changed = changed || w != prev[b];
+        prev[b] = w;
+    }
+    return changed;
+}
+
 template <int NT>
 struct SolveSmem {
     static constexpr int n = 2 * NT;
@@ -174,7 +207,29 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
     float mua;
     const int S = a.steps;
     int t = 0;
-    if constexpr (F > 0) {
+    int taken = S;
+    if (a.early_exit > 0) {
+        // refresh intervals one at a time, with the early-exit check before each K-th refresh
+        const int K = a.early_exit;
+        const int f = F > 0 ? F : a.f_mvm;
+        uint32_t prev[(N + 31) / 32];
+        signs_changed<N>(x, prev);
+        int c = K;
+#pragma unroll 1
+        for (; t < S; t += f) {
+            if (t > 0 && --c == 0) {
+                c = K;
+                const bool changed = signs_changed<N>(x, prev);
+                if (!__syncthreads_or(changed)) {
+                    taken = t;
+                    break;
+                }
+            }
+            coupling_mvm<n>(sm.A, sm.h, x, m, mua);
+            frozen_steps_rt<n>(sm.h, sm.nd, x, e, m, mua, S - t < f ? S - t : f, k);
+        }
+        t = S;  // (the tail below is part of the loop here)
+    } else if constexpr (F > 0) {
 #pragma unroll 1
         for (; t + F <= S; t += F) {
             coupling_mvm<n>(sm.A, sm.h, x, m, mua);
@@ -192,6 +247,8 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
         coupling_mvm<n>(sm.A, sm.h, x, m, mua);
         frozen_steps_rt<n>(sm.h, sm.nd, x, e, m, mua, S - t, k);
     }
+
+    if (a.steps_out && run == 0) a.steps_out[p] = taken;
 
     // spins -> offset d = s_a (s1 + s2) / 2, clipped to the alphabet
     bool valid = true;
@@ -703,13 +760,14 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
     }
 }
 
-template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false>
+template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false, bool EE = false>
 __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a) {
     constexpr int n = 2 * NT;
     constexpr int NS = n / TPA;
     static_assert(n % TPA == 0 && NS % 4 == 0, "rows per thread must be a multiple of 4");
     static_assert(F > 0, "compile-time refresh period");
     static_assert(!TC || (TPA <= 2 && PACKED && n % 16 == 0), "tensor-core refresh: 1 or 2 threads per anneal");
+    static_assert(!(TC && EE), "early exit runs on the bit-identical shapes");
     __shared__ __align__(16) SolveSmem<NT> sm;
     __shared__ long long skey[4 * TPA];
     __shared__ int sdiv[4 * TPA];
@@ -765,7 +823,36 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
 
     const int S = a.steps;
     int t = 0;
-    if constexpr (TC) {
+    int taken = S;
+    if constexpr (EE) {
+        // refresh intervals one at a time, with the early-exit check before each K-th refresh
+        // (this thread's spins: its rows of x1 and x2 and its copy of the auxiliary spin)
+        const int K = a.early_exit;
+        uint32_t p1 = sign_word<NS>(x1), p2 = sign_word<NS>(x2);
+        bool pa = xa >= 0.0f;
+        int c = K;
+#pragma unroll 1
+        for (; t < S; t += F) {
+            if (t > 0 && --c == 0) {
+                c = K;
+                const uint32_t w1 = sign_word<NS>(x1), w2 = sign_word<NS>(x2);
+                const bool wa = xa >= 0.0f;
+                const bool changed = (w1 != p1) || (w2 != p2) || (wa != pa);
+                p1 = w1;
+                p2 = w2;
+                pa = wa;
+                if (!__syncthreads_or(changed)) {
+                    taken = t;
+                    break;
+                }
+            }
+            if (t + F <= S)
+                tuned_block<n, NS, TPA, PACKED, F, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
+            else
+                tuned_block<n, NS, TPA, PACKED, 0, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t,
+                                                          k);
+        }
+    } else if constexpr (TC) {
         uint32_t* wsm = tc_ws + warp * TcShape<NT>::warp_words(32 / TPA);
         const float mscale = mulrn(k.ce, 0x1p-5f);  // eps dt, and the 2^5 of u
 #pragma unroll 1
@@ -779,6 +866,8 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
         if (t < S)
             tuned_block<n, NS, TPA, PACKED, 0, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
     }
+
+    if (a.steps_out && tid == 0) a.steps_out[p] = taken;
 
     // validity over the whole anneal
     bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);

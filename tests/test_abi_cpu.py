@@ -47,12 +47,33 @@ def test_default_params_from_library(lib_path):
     assert abs(p.dt - 0.02) < 1e-7 and abs(p.p - 1.2) < 1e-6 and p.zeta == 3.0 and p.eps == 0.5
 
 
-def test_struct_layouts_match_header(lib_path):
-    """ctypes mirrors of the ABI structs have the C sizes (x86-64 / aarch64 LP64)."""
+def _c_layout(struct, fields):
+    """sizeof and offsetof of an ABI struct as the host C compiler lays it out."""
+    import subprocess
+    import tempfile
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    body = "".join(f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src = ("#include <stddef.h>\n#include <stdio.h>\n#include \"mmgap.h\"\n"
+           f'int main(void) {{ printf("%zu\\n", sizeof({struct})); {body} return 0; }}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(root, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()]
+    return vals[0], dict(zip(fields, vals[1:]))
+
+
+@pytest.mark.parametrize("cname,pyname", [("mmgap_params", "_Params"), ("mmgap_detect_job", "_DetectJob"),
+                                          ("mmgap_precode_job", "_PrecodeJob"),
+                                          ("mmgap_server_config", "_ServerConfig"),
+                                          ("mmgap_job_info", "_JobInfo"), ("mmgap_serve_stats", "_ServerStats")])
+def test_struct_layouts_match_header(lib_path, cname, pyname):
+    """The ctypes mirrors of the ABI structs have the C compiler's sizes and
+    field offsets (LP64: x86-64 here, aarch64 on the GPU hosts)."""
     from paper_2510_01579_gb300 import binding
-    assert ctypes.sizeof(binding._Params) == 40
-    assert ctypes.sizeof(binding._DetectJob) == 5 * 4 + 4 + 4 * 8 + 8 + 5 * 8 + 8
-    assert binding._DetectJob.mapping.offset == binding._DetectJob.gram_precision.offset + 4
-    assert ctypes.sizeof(binding._PrecodeJob) == 6 * 4 + 3 * 8 + 8 + 5 * 8
-    assert ctypes.sizeof(binding._ServerConfig) == 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4
-    assert binding._PrecodeJob.inv_precision.offset == 20 and binding._PrecodeJob.chan_index.offset == 24
+    py = getattr(binding, pyname)
+    fields = [f for f, _ in py._fields_]
+    size, offs = _c_layout(cname, fields)
+    assert ctypes.sizeof(py) == size
+    for f in fields:
+        assert getattr(py, f).offset == offs[f], f

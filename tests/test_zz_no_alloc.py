@@ -2,11 +2,12 @@
 
 mmgap_detect_static is for callers that cannot allocate device memory: a
 real-time slot loop that must not call cudaMalloc once running (an
-allocation can synchronise the device and miss the slot), a plug-in inside an
-application that owns all device memory, or code being recorded into a CUDA
-graph.  It takes its scratch from a fixed array inside the library instead of
-a context workspace.  Its results must be the same bits as the context path's,
-call after call, although the array keeps the previous call's contents.
+allocation can synchronise the device and miss the slot), or a plug-in inside
+an application that owns all device memory.  It takes its scratch from a fixed
+array inside the library instead of a context workspace.  Its results must be
+the same bits as the context path's, call after call, although the array
+keeps the previous call's contents, and a repeated call must not change the
+device's free memory.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test.
@@ -51,6 +52,38 @@ def test_static_scratch_matches_context_path_two_calls_in_a_row():
             torch.cuda.synchronize()
             for k in ref:
                 assert torch.equal(got[k], ref[k]), (i, k)
+            # the same call again: same bits, and no device memory taken
+            free0 = torch.cuda.mem_get_info(DEV)[0]
+            again = _outputs(P, n_t)
+            ctx.detect_static(ctx.detect_job(H, y, nv, w["mod_bits"], 900 + i, again, ci), prm)
+            torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info(DEV)[0] == free0, i
+            for k in ref:
+                assert torch.equal(again[k], ref[k]), (i, k)
+
+
+def test_static_scratch_with_guess_and_early_exit():
+    """A caller-supplied guess, early exit and the steps output through the
+    static entry point equal the context path, on two calls in a row."""
+    import paper_2510_01579_gb300 as pkg
+    prm = pkg.Params.default(early_exit=3)
+    w = synth.uplink(65, 16, 16, 4, n_sub=30, n_sym=8, snr_db=15.0)
+    P = w["y"].shape[0]
+    side, L = 4, 3
+    sym = w["sym"].astype(int)
+    g = np.concatenate([2 * (sym // side) - L, 2 * (sym % side) - L], axis=1).astype(np.int8)
+    g[::3, 0] = np.where(g[::3, 0] > -L, g[::3, 0] - 2, g[::3, 0] + 2)
+    H, y, nv, ci, gt = _T(w["H"]), _T(w["y"]), _T(w["noise_var"]), _T(w["chan_index"]), _T(g)
+    with pkg.Context(0) as ctx:
+        ref = dict(_outputs(P, 16), steps=torch.full((P,), -1, dtype=torch.int32, device=DEV))
+        ctx.detect_jobs([ctx.detect_job(H, y, nv, 4, 5, ref, ci, guess=gt)], prm)
+        for _ in range(2):
+            got = dict(_outputs(P, 16), steps=torch.full((P,), -1, dtype=torch.int32, device=DEV))
+            ctx.detect_static(ctx.detect_job(H, y, nv, 4, 5, got, ci, guess=gt), prm)
+            torch.cuda.synchronize()
+            for k in ref:
+                assert torch.equal(got[k], ref[k]), k
+        assert bool((ref["steps"] < 200).any())
 
 
 def test_static_scratch_rejects_a_job_larger_than_the_array():
