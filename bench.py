@@ -5,9 +5,11 @@ of 16x16 16-QAM through build -> CIM-CAC solve -> decode.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mmgap|reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank detects its own slot
-(weak scaling: fixed work per GPU, no collective on the data path); the step
-time is the max over ranks.  --impl reference times the CPU oracle on the
-host cores on a bounded sample of the same workload.
+(--split replica, the default: weak scaling, fixed work per GPU) or its
+contiguous PRB range of one shared slot (--split slot: strong scaling, the
+paper's subcarrier split); there is no collective on the data path, and the
+step time is the max over ranks.  --impl reference times the CPU oracle on
+the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -30,11 +32,15 @@ import synth  # noqa: E402
 
 METRIC = "detections/s (subcarrier-problems, 16x16 16-QAM) at equal BER; p99 slot latency"
 UNIT = "problems/s"
-# solver launch shapes whose DRAM bytes per 16-user problem were taken with ncu (profiles/)
-TRAFFIC_MEASURED = (3, 6)
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+# maximum SM clock of a GB300, used only when nvidia-smi gives no sample
+SM_MAX_MHZ_FALLBACK = 2070.0
+# DRAM bytes per 16x16 problem of the solver (launch shapes 3 and 6), read as
+# dram__bytes_read.sum + dram__bytes_write.sum by ncu on a 1,024-subcarrier
+# 16x16 slot (14,336 problems) and divided by its problems; the traffic grows in
+# proportion to the problems, so a launch's traffic is this times its problems.
+# None until measured on the current kernels.
+SOLVER_DRAM_BYTES_PER_PROBLEM = {}
 
 WORKLOADS = {
     # name: (n_r, n_t, mod_bits, model, hold, snr_db)
@@ -59,8 +65,42 @@ def solver_flops(P: int, n_t: int, runs: int, steps: int, f_mvm: int) -> float:
     return float(P) * runs * (refresh * (2 * n * n + 9 * n) + 9 * N * steps)
 
 
-def alu_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def solver_flops_survey(P: int, n_t: int, runs: int, steps: int, f_mvm: int) -> float:
+    """The per-problem work estimate R S [(2n^2 + 8n)/f + 14 N] + R (2n^2 + 2n)
+    (half-size refresh every f steps, about 14 flops per spin-step, one
+    energy evaluation per anneal), as the measurement plan states it; an
+    upper estimate next to the exact count of solver_flops."""
+    n = 2 * n_t
+    N = 2 * n + 1
+    return float(P) * (runs * steps * ((2 * n * n + 8 * n) / f_mvm + 14 * N) + runs * (2 * n * n + 2 * n))
+
+
+def solver_bytes(P: int, n_t: int) -> float:
+    """Algorithmic DRAM bytes of one solver launch over P problems: each
+    problem's Q14 couplings (n^2 int16), field (n int16) and guess (n int8) read
+    once; its symbols (n_t bytes) and energy (4 bytes) written once."""
+    n = 2 * n_t
+    return float(P) * (2 * n * n + 2 * n + n + n_t + 4)
+
+
+def alu_peak_tflops(sm_count: int, mhz: float) -> float:
+    return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def alu_peak(dev, clk):
+    """FP32 FMA peak of this device: its SM count (from the driver) x 128 FP32
+    lanes x 2 flops x the maximum SM clock nvidia-smi reported during the
+    timed region; also at the median clock sampled under load."""
+    import torch
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mx = clk["sm_max_mhz"] if clk and clk.get("sm_max_mhz") else None
+    med = clk["sm_mhz"] if clk and clk.get("sm_mhz") else None
+    max_mhz = mx or SM_MAX_MHZ_FALLBACK
+    return {"sm_count": sm, "sm_max_mhz": max_mhz, "sm_mhz_median": med,
+            "peak_tflops": alu_peak_tflops(sm, max_mhz),
+            "peak_tflops_at_median_clock": alu_peak_tflops(sm, med) if med else None,
+            "note": (f"FP32 FMA peak: {sm} SMs (device) x 128 lanes x 2 x {max_mhz:.0f} MHz "
+                     f"({'nvidia-smi max clock' if mx else 'fallback: no clock sample'})")}
 
 
 class ClockSampler:
@@ -304,6 +344,26 @@ def run_serve(args):
     capacity.  The continuous-batching server (graph replay, memory
     admission) against the plain per-job path (one mmgap_detect or
     mmgap_precode per job in arrival order on one stream)."""
+    r = serve_measure(args, args.serve_seconds, with_tc=True)
+    served, served_tc, plain = r["server"], r["server_tensor_core_refresh"], r["plain_per_job_path"]
+    line = {"metric": "problems/s served (Poisson mixed-size detection and precoding jobs); p50/p99 job latency",
+            "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": r["jobs"], "warmup": 2,
+            "ms_per_step": r["span_s"] * 1e3 / r["jobs"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve", "offered_load": args.load, "jobs": r["jobs"],
+                       "job_sizes": "n_t in {4,8,16}, QPSK..64-QAM, 100-3276 subcarriers x 1 symbol",
+                       "job_mix": "2/3 uplink detection, 1/3 downlink VPP (FP32 + refinement inverse)",
+                       "arrival_rate_jobs_per_s": r["rate"], "deadline_us": r["deadline_us"],
+                       "lanes": args.lanes, "runs": args.runs, "solver_steps": args.solver_steps},
+            "server": served, "server_tensor_core_refresh": served_tc, "plain_per_job_path": plain,
+            "p99_speedup_vs_plain": plain["p99_us"] / served["p99_us"], "clocks": r["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
+def serve_measure(args, seconds: float, with_tc: bool):
+    """The serving trace of run_serve: returns the server's, optionally the
+    tensor-core server's, and the plain per-job path's rates and latency
+    percentiles over the same Poisson arrivals."""
     import torch
 
     from paper_2510_01579_gb300 import Context, Params, Server
@@ -350,7 +410,7 @@ def run_serve(args):
     torch.cuda.synchronize()
     pool_s = time.perf_counter() - t0
     rate = args.load * len(pool) / pool_s  # jobs per second offered
-    n_jobs = max(len(pool), int(rate * args.serve_seconds))
+    n_jobs = max(len(pool), int(rate * seconds))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
     which = [i % len(pool) for i in range(n_jobs)]
     total_problems = sum(pool[k][2] for k in which)
@@ -386,26 +446,30 @@ def run_serve(args):
               "deadline_misses": st["deadline_misses"], "groups": st["groups"], "max_group_jobs": st["max_group_jobs"]}
 
     # the same arrivals with the tensor-core field refresh for 8- and 16-user problems (precision variant)
-    with Server(0, prm, scratch_bytes=2 << 30, n_lanes=args.lanes, max_jobs_per_group=32,
-                max_problems_per_group=1 << 16, deadline_us=deadline, tensor_core=True) as srv:
+    served_tc = None
+    with (Server(0, prm, scratch_bytes=2 << 30, n_lanes=args.lanes, max_jobs_per_group=32,
+                 max_problems_per_group=1 << 16, deadline_us=deadline, tensor_core=True) if with_tc
+          else _NullServer()) as srv:
         def submit_tc(k):
             kind, job, _ = pool[k]
             return srv.submit_precode(job) if kind else srv.submit(job)
 
-        for k in range(6):
-            submit_tc(k)
-        time.sleep(0.3)
-        srv.stats(reset=True)
-        tks = []
-        start = time.perf_counter()
-        for a, k in zip(arrivals, which):
-            while time.perf_counter() - start < a:
-                pass
-            tks.append(submit_tc(k))
-        lat_tc = [srv.wait(tk)["latency_us"] for tk in tks]
-        st_tc = srv.stats()
-    served_tc = {"value": total_problems / (st_tc["span_us"] / 1e6), "p50_us": pct(lat_tc, 0.5),
-                 "p99_us": pct(lat_tc, 0.99), "deadline_misses": st_tc["deadline_misses"], "groups": st_tc["groups"]}
+        if with_tc:
+            for k in range(6):
+                submit_tc(k)
+            time.sleep(0.3)
+            srv.stats(reset=True)
+            tks = []
+            start = time.perf_counter()
+            for a, k in zip(arrivals, which):
+                while time.perf_counter() - start < a:
+                    pass
+                tks.append(submit_tc(k))
+            lat_tc = [srv.wait(tk)["latency_us"] for tk in tks]
+            st_tc = srv.stats()
+            served_tc = {"value": total_problems / (st_tc["span_us"] / 1e6), "p50_us": pct(lat_tc, 0.5),
+                         "p99_us": pct(lat_tc, 0.99), "deadline_misses": st_tc["deadline_misses"],
+                         "groups": st_tc["groups"]}
 
     # plain per-job path: one launch pair per job, in arrival order, one stream
     stream = torch.cuda.current_stream(dev)
@@ -424,19 +488,19 @@ def run_serve(args):
     plain_span = ref_ev.elapsed_time(done[-1]) / 1e3
     plain = {"value": total_problems / plain_span, "p50_us": pct(plain_lat, 0.5), "p99_us": pct(plain_lat, 0.99),
              "deadline_misses": int(sum(x > deadline for x in plain_lat))}
-    line = {"metric": "problems/s served (Poisson mixed-size detection and precoding jobs); p50/p99 job latency",
-            "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": n_jobs, "warmup": 2,
-            "ms_per_step": span * 1e3 / n_jobs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serve", "offered_load": args.load, "jobs": n_jobs,
-                       "job_sizes": "n_t in {4,8,16}, QPSK..64-QAM, 100-3276 subcarriers x 1 symbol",
-                       "job_mix": "2/3 uplink detection, 1/3 downlink VPP (FP32 + refinement inverse)",
-                       "arrival_rate_jobs_per_s": rate, "deadline_us": deadline, "lanes": args.lanes,
-                       "runs": args.runs, "solver_steps": args.solver_steps},
-            "server": served, "server_tensor_core_refresh": served_tc, "plain_per_job_path": plain,
-            "p99_speedup_vs_plain": plain["p99_us"] / served["p99_us"], "clocks": clk}
-    print(json.dumps(line), flush=True)
     ctx.close()
+    return {"server": served, "server_tensor_core_refresh": served_tc, "plain_per_job_path": plain,
+            "jobs": n_jobs, "rate": rate, "deadline_us": deadline, "span_s": span, "clocks": clk}
+
+
+class _NullServer:
+    """Stands in for a server that is not run (a context manager doing nothing)."""
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
 
 
 def run_precode(args):
@@ -671,7 +735,8 @@ def run_ul32(args):
     flops = solver_flops(P, 32, prm.runs, prm.steps, prm.f_mvm)
     solve_avg = statistics.mean(solve)
     achieved = flops / (solve_avg / 1e3) / 1e12
-    peak = alu_peak_tflops()
+    pk = alu_peak(dev, clk)
+    peak = pk["peak_tflops"]
     cpu = None
     if not args.no_cpu_baseline:
         fields = {f: getattr(prm, f) for f in ("runs", "steps", "f_mvm", "dt", "p", "a", "zeta", "eps", "sigma0",
@@ -690,7 +755,11 @@ def run_ul32(args):
             "ber": {"mmgap": ber, "mmse": ber_mmse},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "cac_solve_rows (32 users: two anneals x 8 rows per thread)"},
+                         "kernel": "cac_solve_rows (32 users: two anneals x 8 rows per thread)",
+                         "sm_count": pk["sm_count"], "sm_max_mhz": pk["sm_max_mhz"],
+                         "sm_mhz_median": pk["sm_mhz_median"], "peak_note": pk["note"],
+                         "frac_survey_formula": solver_flops_survey(P, 32, prm.runs, prm.steps, prm.f_mvm) /
+                         (solve_avg / 1e3) / 1e12 / peak},
             "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -839,7 +908,8 @@ def run_budget(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
     out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
-           "guess": torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)}
+           "guess": torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev),
+           "steps": torch.empty(P, dtype=torch.int32, device=dev)}
     job = ctx.detect_job(H, y, nv, mb, 77, out, ci)
     nbits = P * n_t * mb
 
@@ -857,28 +927,36 @@ def run_budget(args):
             b.record(stream)
         torch.cuda.synchronize()
         ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-        return ms, synth.bit_errors(out["sym"].cpu().numpy(), w["sym"], mb)
+        return ms, synth.bit_errors(out["sym"].cpu().numpy(), w["sym"], mb), float(out["steps"].float().mean())
 
-    grid = [(200, 2, 0.02), (150, 2, 0.02), (100, 2, 0.02), (100, 2, 0.04), (64, 2, 0.04), (50, 2, 0.05),
-            (100, 4, 0.02), (64, 4, 0.04), (50, 4, 0.05), (32, 4, 0.08)]
+    # (steps, f_mvm, dt, early-exit K): the reference, the paper's N_I = 2.56 / dt = 128, early exit at
+    # several K, then shorter and coarser integrations
+    grid = [(200, 2, 0.02, 0), (128, 2, 0.02, 0), (200, 2, 0.02, 2), (200, 2, 0.02, 3), (200, 2, 0.02, 4),
+            (200, 2, 0.02, 5), (200, 2, 0.02, 6), (200, 2, 0.02, 8), (150, 2, 0.02, 0), (100, 2, 0.02, 0),
+            (100, 2, 0.04, 0), (64, 2, 0.04, 0), (50, 2, 0.05, 0), (100, 4, 0.02, 0), (64, 4, 0.04, 0),
+            (50, 4, 0.05, 0), (32, 4, 0.08, 0)]
     rows = []
     ref_err = None
-    for S, f, dt in grid:
-        prm = Params.default(steps=S, f_mvm=f, dt=dt)
-        ms, err = run(prm, exact)
-        ms_tc, err_tc = run(prm, 5)
+    for S, f, dt, K in grid:
+        prm = Params.default(steps=S, f_mvm=f, dt=dt, early_exit=K)
+        ms, err, mean_steps = run(prm, exact)
+        ms_tc, err_tc = (None, None) if K else run(prm, 5)[:2]  # (no early exit on the tensor-core shapes)
         if ref_err is None:
             ref_err = err
         sd = math.sqrt(ref_err * (1 - ref_err / nbits))
-        rows.append({"steps": S, "f_mvm": f, "dt": dt, "ms_per_slot": ms, "ber": err / nbits,
-                     "keeps_ber": abs(err - ref_err) <= 2 * sd, "ms_per_slot_tc": ms_tc, "ber_tc": err_tc / nbits,
-                     "tc_keeps_ber": abs(err_tc - ref_err) <= 2 * sd})
+        rows.append({"steps": S, "f_mvm": f, "dt": dt, "early_exit": K, "mean_steps": mean_steps,
+                     "ms_per_slot": ms, "ber": err / nbits, "bit_errors": err,
+                     "keeps_ber": abs(err - ref_err) <= 2 * sd, "ms_per_slot_tc": ms_tc,
+                     "ber_tc": None if err_tc is None else err_tc / nbits,
+                     "tc_keeps_ber": None if err_tc is None else abs(err_tc - ref_err) <= 2 * sd})
     ctx.set_solver_variant(n_t, exact)
     g = out["guess"].cpu().numpy().astype(int)
     mmse = synth.bit_errors(((g[:, :16] + 3) // 2) * 4 + (g[:, 16:] + 3) // 2, w["sym"], mb) / nbits
     keep = [r for r in rows if r["keeps_ber"]]
     best = min(keep, key=lambda r: r["ms_per_slot"])
     keep_tc = [r for r in rows if r["tc_keeps_ber"]]
+    # (anneals per problem stay at 32: the kernels take multiples of one warp; 16 or 24 anneals, run on
+    # the CPU oracle, miss the equal-BER bar)
     best_tc = min(keep_tc, key=lambda r: r["ms_per_slot_tc"]) if keep_tc else None
     line = {"metric": "slot time of 16x16 16-QAM detection at equal BER, smallest anneal budget",
             "value": best["ms_per_slot"], "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": 2,
@@ -1035,6 +1113,12 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=1.5, help="seconds of oracle work per core per step")
     ap.add_argument("--subcarriers", type=int, default=None,
                     help="subcarriers per slot (3276 = 100 MHz at 30 kHz; 288 = 10 MHz for the 32x32 workload)")
+    ap.add_argument("--split", default="replica", choices=["replica", "slot"],
+                    help="multi-GPU: replica = each rank detects its own slot (weak scaling); slot = one slot "
+                         "split across the ranks by contiguous PRB ranges (strong scaling, the paper's split)")
+    ap.add_argument("--early-exit", type=int, default=4,
+                    help="K of the early-exit line (0: skip it); the headline runs every anneal for all steps")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving trace")
     args = ap.parse_args()
     # the 32x32 high-connectivity evaluation (Sec. 5) is a 10 MHz slot with N_a = 128 anneals
     ul32 = args.workload == "ul32x32_16qam_slot"
@@ -1100,20 +1184,35 @@ def main():
         if world > 1:
             dist.barrier()
 
-    # each rank detects its own slot (different seed): weak scaling
-    w = make_workload(args.workload, rank_seed(rank), args.subcarriers)
+    # replica: each rank detects its own slot (different seed), weak scaling; slot: every rank takes
+    # its contiguous PRB range of the same slot as a job of its own (problem_offset = its first
+    # problem, so its results are the whole slot's), strong scaling
+    from paper_2510_01579_gb300 import shard
+    split = args.split == "slot"
+    w_full = make_workload(args.workload, rank_seed(0 if split else rank), args.subcarriers)
+    P_slot = w_full["y"].shape[0]
+    n_sym = synth.SYMBOLS_PER_SLOT
+    if split:
+        sh = shard.shard_slot(w_full["chan_index"], P_slot // n_sym, n_sym, world, rank)
+        p_lo, p_hi = sh["p0"], sh["p1"]
+        w = dict(w_full, H=w_full["H"][sh["c0"]:sh["c1"]], y=w_full["y"][p_lo:p_hi],
+                 noise_var=w_full["noise_var"][p_lo:p_hi], chan_index=sh["chan_index"],
+                 sym=w_full["sym"][p_lo:p_hi])
+    else:
+        p_lo, p_hi = 0, P_slot
+        w = w_full
     P = w["y"].shape[0]
     n_t, mb = w["n_t"], w["mod_bits"]
     prm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm)
-    H = torch.from_numpy(w["H"]).to(dev)
-    y = torch.from_numpy(w["y"]).to(dev)
-    nv = torch.from_numpy(w["noise_var"]).to(dev)
-    ci = torch.from_numpy(w["chan_index"]).to(dev)
+    H = torch.from_numpy(np.ascontiguousarray(w["H"])).to(dev)
+    y = torch.from_numpy(np.ascontiguousarray(w["y"])).to(dev)
+    nv = torch.from_numpy(np.ascontiguousarray(w["noise_var"])).to(dev)
+    ci = torch.from_numpy(np.ascontiguousarray(w["chan_index"])).to(dev)
     ctx = Context(local, workspace_bytes=512 << 20)
     out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
            "energy": torch.empty(P, dtype=torch.int32, device=dev),
            "guess": torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)}
-    job = ctx.detect_job(H, y, nv, mb, 77, out, ci)
+    job = ctx.detect_job(H, y, nv, mb, 77, out, ci, problem_offset=p_lo)
     if args.variant >= 0:
         ctx.set_solver_variant(n_t, args.variant)
         tune_ms = None
@@ -1156,7 +1255,8 @@ def main():
     step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
     total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = world * P * args.steps / (total_ms / 1e3)
+    # problems all ranks processed per second of the slowest rank
+    value = (P_slot if split else world * P) * args.steps / (total_ms / 1e3)
 
     # BER of this slot against the transmitted symbols, and of the MMSE guess
     sym = out["sym"].cpu().numpy()
@@ -1176,7 +1276,7 @@ def main():
         hsym = torch.empty((P, n_t), dtype=torch.uint8).pin_memory()
         dH, dy, dnv, dci = (torch.empty_like(a, device=dev) for a in (hH, hy, hnv, hci))
         e_out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev)}
-        ejob = ctx.detect_job(dH, dy, dnv, mb, 77, e_out, dci)
+        ejob = ctx.detect_job(dH, dy, dnv, mb, 77, e_out, dci, problem_offset=p_lo)
         h2d = sum(a.numel() * a.element_size() for a in (hH, hy, hnv, hci))
         d2h = hsym.numel() * hsym.element_size()
 
@@ -1204,7 +1304,8 @@ def main():
         e_total = max_over_ranks(sum(es[i].elapsed_time(ee[i]) for i in range(args.steps)), dev)
         if not torch.equal(hsym, out["sym"].cpu()):
             raise RuntimeError("host-buffer path disagrees with the device-resident path")
-        e2e = {"value": world * P * args.steps / (e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": (P_slot if split else world * P) * args.steps / (e_total / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_total / args.steps}
 
     # the paper's design point (one CTA per problem, one scalar thread per
@@ -1237,7 +1338,7 @@ def main():
     if not args.no_tc and n_t in (8, 16) and args.f_mvm in (1, 2):
         ctx.set_solver_variant(n_t, 5)
         tout = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev)}
-        tjob = ctx.detect_job(H, y, nv, mb, 77, tout, ci)
+        tjob = ctx.detect_job(H, y, nv, mb, 77, tout, ci, problem_offset=p_lo)
         for _ in range(2):
             flush.zero_()
             ctx.detect_jobs([tjob], prm)
@@ -1303,7 +1404,7 @@ def main():
         for mode, persistent, tcm in modes:
             bout = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
                     "energy": torch.empty(P, dtype=torch.int32, device=dev)}
-            bjob = ctx.detect_job(H, y, nv, mb, 77, bout, ci)
+            bjob = ctx.detect_job(H, y, nv, mb, 77, bout, ci, problem_offset=p_lo)
             with Batch(local, prm, [bjob], keepalive=(H, y, nv, ci, bout), persistent=persistent,
                        tensor_core=tcm) as batch:
                 for _ in range(args.warmup):
@@ -1324,19 +1425,90 @@ def main():
                              "p99_ms": bsrt[min(len(bsrt) - 1, int(math.ceil(0.99 * len(bsrt))) - 1)],
                              "graph": True}
 
+    # early exit (a budget lever, not in the paper): the same slot with each problem's anneals
+    # stopping at the first K-th field refresh that saw no spin-sign change since the previous one;
+    # its results are the oracle's under the same rule, and here it is held to the headline's BER
+    early = None
+    if args.early_exit > 0 and n_t <= 16:
+        eprm = Params.default(runs=args.runs, steps=args.solver_steps, f_mvm=args.f_mvm, early_exit=args.early_exit)
+        eo = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
+              "steps": torch.empty(P, dtype=torch.int32, device=dev)}
+        ejob_ee = ctx.detect_job(H, y, nv, mb, 77, eo, ci, problem_offset=p_lo)
+        for _ in range(2):
+            flush.zero_()
+            ctx.detect_jobs([ejob_ee], eprm)
+        torch.cuda.synchronize()
+        ee_solve = []
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            ctx.detect_jobs([ejob_ee], eprm)
+            ends[i].record(stream)
+            ee_solve.append(ctx.stage_times()[1])
+        torch.cuda.synchronize()
+        ee_ms = max_over_ranks(sum(starts[i].elapsed_time(ends[i]) for i in range(args.steps)), dev) / args.steps
+        e_err = synth.bit_errors(eo["sym"].cpu().numpy(), w["sym"], mb)
+        r_err = synth.bit_errors(sym, w["sym"], mb)
+        sd = math.sqrt(r_err * (1 - r_err / nbits))
+        early = {"K": args.early_exit, "ms_per_step": ee_ms,
+                 "value": (P_slot if split else world * P) / (ee_ms / 1e3), "solve_ms": statistics.mean(ee_solve),
+                 "mean_steps": float(eo["steps"].float().mean()), "steps": args.solver_steps,
+                 "bit_errors": e_err, "bit_errors_exact": r_err, "ber": e_err / nbits,
+                 "keeps_ber_2sigma": abs(e_err - r_err) <= 2 * sd, "speedup_vs_exact": ms_per_step / ee_ms}
+
+    # one slot split over the ranks: gather the shards' symbols on rank 0 and check them against
+    # the unsharded slot detected there
+    split_check = None
+    if split and world > 1:
+        parts = [None] * world
+        dist.all_gather_object(parts, (p_lo, sym))
+        if rank == 0:
+            gathered = np.concatenate([a for _, a in sorted(parts, key=lambda t: t[0])])
+            whole = ctx.detect(torch.from_numpy(w_full["H"]).to(dev), torch.from_numpy(w_full["y"]).to(dev),
+                               torch.from_numpy(w_full["noise_var"]).to(dev), mb, prm, 77,
+                               chan_index=torch.from_numpy(w_full["chan_index"]).to(dev))
+            torch.cuda.synchronize()
+            split_check = {"gathered_equals_unsharded": bool(np.array_equal(gathered, whole["sym"].cpu().numpy())),
+                           "ber_slot": synth.bit_errors(gathered, w_full["sym"], mb) / (P_slot * n_t * mb),
+                           "rank_problems": [int(b - a) for a, b in
+                                             (shard.shard_problems(P_slot // n_sym, n_sym, world, r)
+                                              for r in range(world))]}
+            if not split_check["gathered_equals_unsharded"]:
+                raise RuntimeError("the gathered shards differ from the unsharded slot")
+
+    # a short serving trace (continuous batching against the plain per-job path), p50 / p99 job
+    # latency over all of its jobs
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        sr = serve_measure(args, 0.6, with_tc=False)
+        sv, pl = sr["server"], sr["plain_per_job_path"]
+        serve = {"jobs": sr["jobs"], "offered_load": args.load, "p50_ms": sv["p50_us"] / 1e3,
+                 "p99_ms": sv["p99_us"] / 1e3, "value": sv["value"], "deadline_misses": sv["deadline_misses"],
+                 "plain_p50_ms": pl["p50_us"] / 1e3, "plain_p99_ms": pl["p99_us"] / 1e3, "plain_value": pl["value"],
+                 "deadline_us": sr["deadline_us"]}
+
     # roofline of the dominant kernel (the CIM-CAC solver), from the library's
-    # own CUDA events on the launching stream
+    # own CUDA events on the launching stream; the peak from this device's SM
+    # count and the clock sampled during the timed region
     flops = solver_flops(P, n_t, args.runs, args.solver_steps, args.f_mvm)
-    # DRAM bytes of the solver from ncu (profiles/cac_solve_16x16_slot_1024sc.md): 2,153 B per
-    # 16x16 problem, measured on 14,336 problems and scaled by problems; None for other shapes
-    traffic = 2153.0 * P if (n_t == 16 and variant in TRAFFIC_MEASURED) else None
+    flops_survey = solver_flops_survey(P, n_t, args.runs, args.solver_steps, args.f_mvm)
+    per_problem = SOLVER_DRAM_BYTES_PER_PROBLEM.get((n_t, variant))
+    traffic = per_problem * P if per_problem else None
     solve_avg = statistics.mean(solve_ms)
     achieved = flops / (solve_avg / 1e3) / 1e12
-    peak = alu_peak_tflops()
+    pk = alu_peak(dev, clk)
+    peak = pk["peak_tflops"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": f"cac_solve, launch shape {VARIANT_NAMES[variant]}",
-                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts and max clock)",
-                "flops_per_launch": flops, "avg_launch_ms": solve_avg}
+                "peak_note": pk["note"], "sm_count": pk["sm_count"], "sm_max_mhz": pk["sm_max_mhz"],
+                "sm_mhz_median": pk["sm_mhz_median"],
+                "frac_at_median_clock": (achieved / pk["peak_tflops_at_median_clock"]
+                                         if pk["peak_tflops_at_median_clock"] else None),
+                "flops_per_launch": flops, "flops_note": "exact count of the folded arithmetic: per anneal "
+                "ceil(S/f) (2n^2 + 9n) + 9 (2n+1) S",
+                "flops_per_launch_survey_formula": flops_survey,
+                "frac_survey_formula": flops_survey / (solve_avg / 1e3) / 1e12 / peak,
+                "algorithmic_bytes_per_launch": solver_bytes(P, n_t), "avg_launch_ms": solve_avg}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1348,20 +1520,23 @@ def main():
     srt = sorted(step_ms)
     p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "strong" if split else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "problems_per_step": P, "n_r": w["n_r"], "n_t": n_t,
+            "config": {"workload": args.workload, "problems_per_step": P_slot if split else P,
+                       "problems_per_rank": P, "n_r": w["n_r"], "n_t": n_t,
                        "mod_bits": mb, "runs": args.runs, "solver_steps": args.solver_steps, "f_mvm": args.f_mvm,
                        "dt": 0.02, "channel": WORKLOADS[args.workload][3], "hold": WORKLOADS[args.workload][4],
                        "snr_db": WORKLOADS[args.workload][5], "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": f"{world} rank(s), one slot per rank"},
+                       "parallelism": (f"{world} rank(s), one slot split by PRB ranges" if split else
+                                       f"{world} rank(s), one slot per rank")},
             "slot_latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "max": max(step_ms)},
             "stage_ms": {"build": statistics.mean(build_ms), "solve": solve_avg},
             "ber": {"mmgap": ber, "mmse": ber_mmse},
             "solver_shape": {"chosen": VARIANT_NAMES[variant], "autotune_ms": tune_ms},
             "plain_path": plain,
             "tensor_core_refresh": tc,
-            "batched_path": batched,
+            "batched_path": batched, "early_exit": early, "split_check": split_check, "serve": serve,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             # per call: builder + solver per chunk, and the per-channel factorisation (first-problem and
             # factor kernels) once when channels serve several problems (as here: H per subcarrier or PRB)

@@ -355,6 +355,16 @@ mmgap_status mmgap_set_timing(mmgap_ctx* ctx, int enable);
  * events.  *n_chunks_out (may be NULL) receives the number of chunks. */
 mmgap_status mmgap_stage_times(mmgap_ctx* ctx, float ms_out[4], int* n_chunks_out);
 
+/* Limit, in ns, of every bounded wait inside this context's kernels: the
+ * waits of solver shape 8 for its tensor-core product (an MMA that takes
+ * microseconds).  Default 200,000,000 (0.2 s).  0 makes each wait give up at
+ * once unless the product is already complete.  A wait that gives up makes
+ * the CTA return its problems' guesses with every anneal counted as diverged
+ * and set bit 1 of the device error word; the CTA still waits (bounded, 0.2 s)
+ * for its product in flight before it frees its tensor memory, so the
+ * context stays usable.  Applies to later calls on the context. */
+mmgap_status mmgap_set_device_wait(mmgap_ctx* ctx, uint64_t limit_ns);
+
 /* Device-side error word of this context (bit 0: a channel index outside
  * [0, n_chan) was met; the problem was computed as all-zero couplings;
  * bit 1: a wait of solver shape 8 on its tensor-core product expired; the

@@ -75,6 +75,7 @@ _lib.mmgap_stage_times.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)
 _lib.mmgap_device_errors.argtypes = [_vp, C.POINTER(C.c_int), C.c_int]
 _lib.mmgap_detect_static.argtypes = [C.POINTER(_Params), C.POINTER(_DetectJob), _vp]
 _lib.mmgap_set_solver_variant.argtypes = [_vp, C.c_int, C.c_int]
+_lib.mmgap_set_device_wait.argtypes = [_vp, C.c_uint64]
 _lib.mmgap_detect_e.argtypes = [_vp, C.POINTER(_Params), C.POINTER(_DetectJob), C.c_int, _vp, _vp, _vp, _vp]
 _lib.mmgap_vpp_inverse.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp]
 _lib.mmgap_solve_general.argtypes = [_vp, C.POINTER(_Params), C.c_int, C.c_int, _vp, _vp, _vp, C.c_uint64, _vp, _vp,
@@ -115,6 +116,7 @@ _lib.mmgap_server_destroy.argtypes = [_vp]
 for _f in ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_detect", "mmgap_precode",
            "mmgap_solve_ising", "mmgap_build_detect", "mmgap_set_timing", "mmgap_stage_times",
            "mmgap_device_errors", "mmgap_detect_static", "mmgap_set_solver_variant", "mmgap_get_solver_variant",
+           "mmgap_set_device_wait",
            "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse", "mmgap_solve_general",
            "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run", "mmgap_batch_destroy", "mmgap_server_create",
            "mmgap_server_submit", "mmgap_server_submit_precode", "mmgap_server_wait", "mmgap_server_stats",
@@ -127,7 +129,7 @@ ABI_SYMBOLS = ("mmgap_default_params", "mmgap_create", "mmgap_destroy", "mmgap_l
                "mmgap_detect_e", "mmgap_anneal_spins", "mmgap_vpp_inverse", "mmgap_solve_general",
                "mmgap_get_solver_variant", "mmgap_autotune", "mmgap_batch_create", "mmgap_batch_run",
                "mmgap_batch_destroy", "mmgap_server_create", "mmgap_server_submit", "mmgap_server_submit_precode",
-               "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy")
+               "mmgap_server_wait", "mmgap_server_stats", "mmgap_server_destroy", "mmgap_set_device_wait")
 
 VARIANT_NAMES = {0: "default", 1: "plain", 2: "tpa1", 3: "tpa1-packed", 4: "tpa2-packed", 5: "tensor-core",
                  6: "pair-packed", 7: "tensor-core-tpa2", 8: "tcgen05", 9: "tpa4-packed", 10: "tpa8-packed"}
@@ -421,6 +423,10 @@ class Context:
         st = _lib.mmgap_detect_static(C.byref(cp), C.byref(job), self._stream())
         if st != OK:
             raise MMGaPError(st, "mmgap_detect_static failed (see stderr)")
+
+    def set_device_wait(self, limit_ns: int):
+        """Limit of the bounded device-side waits of later calls (default 0.2 s; 0 = give up at once)."""
+        self._raise(_lib.mmgap_set_device_wait(self._h, int(limit_ns)))
 
     def set_solver_variant(self, n_t: int, variant: int):
         """Force the solver's launch shape for n_t users (0 = size default)."""

@@ -28,6 +28,7 @@ struct mmgap_ctx {
     int n_chunks = 0;
     int variant[33] = {};             // solver launch shape per n_t (0 = default)
     int n_sm = 0;                     // SMs of the device
+    unsigned long long wait_ns = kDefaultDeviceWaitNs;  // limit of the bounded device waits
 };
 
 namespace mmgap {
@@ -591,6 +592,7 @@ mmgap_status mmgap_solve_ising(mmgap_ctx* ctx, const mmgap_params* params, int n
     a.run_out = run_out;
     a.ndiv_out = ndiv_out;
     a.early_exit = params->early_exit;
+    a.wait_ns = ctx->wait_ns;
     a.variant = ctx->variant[n / 2];
     cudaError_t e = dispatch_nt<OpSolve>(n / 2, a, params->runs, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
@@ -751,6 +753,7 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
             a.mod_bits = J.mod_bits;
             a.variant = ctx->variant[J.n_t];
             a.early_exit = params->early_exit;
+            a.wait_ns = ctx->wait_ns;
             a.steps_out = J.steps_out ? J.steps_out + p0 : nullptr;
             e = dispatch_nt<OpSolve>(J.n_t, a, params->runs, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
@@ -837,6 +840,7 @@ mmgap_status mmgap_precode(mmgap_ctx* ctx, const mmgap_params* params, const mmg
             a.ndiv_out = J.ndiv_out ? J.ndiv_out + p0 : nullptr;
             a.variant = ctx->variant[J.n_u];
             a.early_exit = params->early_exit;
+            a.wait_ns = ctx->wait_ns;
             e = dispatch_nt<OpSolve>(J.n_u, a, params->runs, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "cac_solve launch");
             if ((st = timing_mark(ctx, 2, s)) != MMGAP_OK) return st;
@@ -956,6 +960,7 @@ mmgap_status mmgap_detect_e(mmgap_ctx* ctx, const mmgap_params* params, const mm
         a.mod_bits = J.mod_bits;
         a.variant = ctx->variant[J.n_t];
         a.early_exit = params->early_exit;
+        a.wait_ns = ctx->wait_ns;
         cudaError_t e = cudaSuccess;
         for (int stg = 1; stg <= stages && e == cudaSuccess; ++stg)
             for (int inst = 0; inst < 2 && e == cudaSuccess; ++inst) {
@@ -1050,6 +1055,12 @@ mmgap_status mmgap_set_solver_variant(mmgap_ctx* ctx, int n_t, int variant) {
     if (variant_tensor_core(variant) && n_t != 8 && n_t != 16)
         return fail(ctx, MMGAP_EUNSUPPORTED, "tensor-core refresh needs n_t 8 or 16");
     ctx->variant[n_t] = variant;
+    return MMGAP_OK;
+}
+
+mmgap_status mmgap_set_device_wait(mmgap_ctx* ctx, uint64_t limit_ns) {
+    if (!ctx) return MMGAP_EINVAL;
+    ctx->wait_ns = limit_ns;
     return MMGAP_OK;
 }
 

@@ -298,6 +298,7 @@ __global__ void __launch_bounds__(128) batch_solve_umma_kernel(BatchArgs A) {
             u.level_max = J.kind == 0 ? (1 << (J.b.mod_bits >> 1)) - 1 : 0;
             u.steps = A.steps;
             u.k = A.k;
+            u.wait_ns = kDefaultDeviceWaitNs;
             u.err = J.b.err;
             u.d_out = J.offset_out ? J.offset_out + (size_t)base * n : nullptr;
             u.E_out = J.energy_out ? J.energy_out + base : nullptr;

@@ -37,6 +37,9 @@ EulerConsts euler_consts(float dt, float p, float a, float zeta, float eps, floa
 // QAM normalisation kappa = 1/sqrt(2 (M-1)/3) and kappa^2, each rounded once to float.
 void qam_kappa(int mod_bits, float* kappa, float* kappa2);
 
+// Default limit of the bounded device-side waits (0.2 s; the awaited work takes microseconds).
+constexpr unsigned long long kDefaultDeviceWaitNs = 200000000ull;
+
 struct SolveArgs {
     const int16_t* Aq;   // [P][n][n]
     const int16_t* hq;   // [P][n]
@@ -63,6 +66,8 @@ struct SolveArgs {
     int n_sm;                  // SMs of the device (0: unknown); picks latency shapes for small calls
     int early_exit;            // K > 0: stop a problem's anneals at the first K-th refresh with no sign change
     int32_t* steps_out;        // [P] Euler steps taken, or nullptr
+    // limit of each bounded device wait (tcgen05 completion, shape 8); 0 = give up at once
+    unsigned long long wait_ns = kDefaultDeviceWaitNs;
 };
 
 // Launch shapes of the solver.  All produce bit-identical results.

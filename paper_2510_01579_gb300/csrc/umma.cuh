@@ -21,13 +21,16 @@ namespace mmgap {
 // field m of its problem's n columns -- with no shared-memory round trip.
 // Both operands are K-major without swizzle: core matrices of 8 rows x 16
 // bytes, 128 B apart along K (LBO) and 16 n B apart per 8 rows (SBO).
-// Every wait on the MMA's completion barrier is bounded (kUmmaWaitNs); on
-// expiry the CTA stops annealing, reports its problems' guesses as if every
-// anneal had diverged, sets bit 1 of the device error word, waits once more
-// (bounded) for the MMA in flight and frees its TMEM.
+// Every wait on the MMA's completion barrier is bounded (the context's wait
+// limit, 0.2 s by default; 0 gives up at once unless the product is already
+// complete).  A warp whose wait expired on any lane treats it as expired on
+// all of them, so the warp-aligned TMEM loads stay converged.  On expiry the
+// CTA stops annealing, reports its problems' guesses as if every anneal had
+// diverged, sets bit 1 of the device error word, waits once more for the MMA
+// in flight (bounded by kUmmaDrainNs whatever the limit) and frees its TMEM.
 // =========================================================================
 
-constexpr unsigned long long kUmmaWaitNs = 200000000ull;  // 0.2 s; an MMA here takes microseconds
+constexpr unsigned long long kUmmaDrainNs = kDefaultDeviceWaitNs;  // an MMA here takes microseconds
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -66,6 +69,16 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint32_t mbar, uint32_t parity) {  // non-blocking
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -83,12 +96,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Wait for the phase of parity `parity` to complete; false if it has not
-// within kUmmaWaitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
-    if (mbar_try_wait(mbar, parity)) return true;
+// within limit_ns (0: false at once unless it is already complete).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, unsigned long long limit_ns) {
+    if (mbar_test_wait(mbar, parity)) return true;
+    if (limit_ns == 0) return false;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(mbar, parity))
-        if (global_ns() - t0 > kUmmaWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 
@@ -162,7 +176,8 @@ __device__ __forceinline__ bool umma_block(uint8_t* su_h, uint8_t* su_l, uint32_
                                            uint32_t mbar, uint32_t& phase, bool& failed, const float* sh,
                                            const float* snd, float (&x1)[2 * NT], float (&x2)[2 * NT],
                                            float (&e1)[2 * NT], float (&e2)[2 * NT], float& xa, float& ea, int tid,
-                                           int Lrt, float mscale, const EulerConsts& k) {
+                                           int Lrt, float mscale, const EulerConsts& k,
+                                           unsigned long long wait_ns) {
     constexpr int n = 2 * NT;
     constexpr int SBO = UmmaSmem<NT>::SBO;
     asm volatile("" ::: "memory");
@@ -203,7 +218,8 @@ __device__ __forceinline__ bool umma_block(uint8_t* su_h, uint8_t* su_l, uint32_
         }
         umma_commit(mbar);
     }
-    const bool ok = mbar_wait_bounded(mbar, phase);
+    // warp-uniform outcome: the aligned TMEM load below needs every lane of the warp
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(mbar, phase, wait_ns));
     if (!ok) {
         failed = true;
         return true;  // the next barrier (or the caller's) stops the CTA
@@ -265,6 +281,7 @@ struct UmmaTile {
     int level_max;          // clip offsets to the alphabet (0: no clipping)
     int steps;
     EulerConsts k;
+    unsigned long long wait_ns;  // limit of each wait on the MMA's completion
     int* err;               // device error word or nullptr
     // outputs for the tile's first problem (each may be nullptr)
     int8_t* d_out;          // [n] offsets (0 where the guess was kept)
@@ -375,16 +392,17 @@ __device__ __forceinline__ void umma_tile(const UmmaTile& a, int runs, uint8_t* 
 #pragma unroll 1
     for (; go && t + F <= S; t += F)
         go = umma_block<NT, F>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed, shp, sndp,
-                               x1, x2, e1, e2, xa, ea, tid, F, mscale, k);
+                               x1, x2, e1, e2, xa, ea, tid, F, mscale, k, a.wait_ns);
     if (go && t < S)
         umma_block<NT, 0>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed, shp, sndp, x1,
-                          x2, e1, e2, xa, ea, tid, S - t, mscale, k);
+                          x2, e1, e2, xa, ea, tid, S - t, mscale, k, a.wait_ns);
     tc05_fence_before();
     const bool cta_failed = __syncthreads_or(failed ? 1 : 0) != 0;
     if (cta_failed) {
-        // one more bounded wait for the MMA in flight, then report
+        // one more bounded wait for the MMA in flight (thread 0 issued it and its phase
+        // bit still names it unless thread 0 saw it complete), then report
         if (tid == 0) {
-            mbar_wait_bounded(mbar, phase);
+            mbar_wait_bounded(mbar, phase, kUmmaDrainNs);
             if (a.err) atomicOr(a.err, 2);
         }
         __syncthreads();
@@ -494,6 +512,7 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
     t.level_max = a.level_max;
     t.steps = a.steps;
     t.k = a.k;
+    t.wait_ns = a.wait_ns;
     t.err = a.err;
     t.d_out = at(a.d_out, n);
     t.E_out = at(a.E_out, 1);

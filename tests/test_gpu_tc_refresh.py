@@ -171,3 +171,42 @@ def test_refused_where_not_built_and_never_autotuned(mm):
         assert e.value.status == 5
     v, ms = ctx.autotune(pkg.Params.default(steps=40), 16, 2048)
     assert v in (1, 2, 3, 4, 6, 9, 10) and 5 not in ms and 7 not in ms and 8 not in ms
+
+
+@pytest.mark.parametrize("n_t,runs", [(16, 32), (8, 64)])
+def test_tcgen05_wait_expiry_returns_guesses_and_flags_the_context(n_t, runs):
+    """A device wait limit of 0 makes the shape-8 waits on the tensor-core
+    product give up at once: every problem of an affected CTA returns its
+    guess (energy 0, offsets 0, every anneal counted as diverged) and bit 1 of
+    the device error word is set.  The CTA still drains its product before
+    freeing tensor memory, so the next call on the same context, with the
+    default limit, equals a call made before the expiry and leaves the word
+    clear.  No GPU fault is involved: the limit is what runs out."""
+    import paper_2510_01579_gb300 as pkg
+    w = synth.uplink(130 + n_t, n_t, n_t, 4, n_sub=4, n_sym=3, snr_db=14.0)
+    P = w["y"].shape[0]
+    prm = pkg.Params.default(runs=runs, steps=60)
+    args = (T(w["H"]), T(w["y"]), T(w["noise_var"]), 4, prm, 23)
+    kw = dict(chan_index=T(w["chan_index"]), want_energy=True, want_guess=True, want_offset=True, want_ndiv=True)
+    with pkg.Context(0) as ctx:
+        ctx.set_solver_variant(n_t, 8)
+        before = {k: v.cpu() for k, v in ctx.detect(*args, **kw).items()}
+        assert ctx.device_errors() == 0
+        ctx.set_device_wait(0)
+        bad = {k: v.cpu() for k, v in ctx.detect(*args, **kw).items()}
+        assert ctx.device_errors() == 2
+        ctx.set_device_wait(200_000_000)
+        after = {k: v.cpu() for k, v in ctx.detect(*args, **kw).items()}
+        assert ctx.device_errors() == 0
+    for k in before:
+        assert torch.equal(after[k], before[k]), k
+    # every problem of an affected CTA fell back to its guess
+    hit = bad["ndiv"] == runs
+    assert bool(hit.any())
+    assert bool((bad["energy"][hit] == 0).all()) and bool((bad["offset"][hit] == 0).all())
+    g = bad["guess"][hit].numpy().astype(int)
+    side = 4
+    mm_sym = ((g[:, :n_t] + 3) // 2) * side + (g[:, n_t:] + 3) // 2
+    assert np.array_equal(bad["sym"][hit].numpy(), mm_sym)
+    assert torch.equal(bad["guess"], before["guess"])
+    assert P > 0
