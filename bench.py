@@ -46,6 +46,8 @@ WORKLOADS = {
     # name: (n_r, n_t, mod_bits, model, hold, snr_db)
     "ul16x16_16qam_slot": (16, 16, 4, "iid", "subcarrier", 16.0),
     "ul8x8_16qam_slot_kron_prb": (8, 8, 4, "kron", "prb", 15.0),
+    # small problems, where a persistent launch could pay for itself
+    "ul4x4_qpsk_slot": (4, 4, 2, "iid", "subcarrier", 10.0),
     # the high-connectivity evaluation (Sec. 5): its own timing mode, run_ul32
     "ul32x32_16qam_slot": (32, 32, 4, "iid", "subcarrier", 18.0),
 }

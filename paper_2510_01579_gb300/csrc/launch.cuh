@@ -96,6 +96,11 @@ template <int NT, int F>
 cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t s) {
     if constexpr (tuned_size(NT)) {
         if (a.early_exit > 0) return launch_tuned_early_exit<NT, F>(a, runs, variant, s);
+        if (a.steps_out && variant != kVariantPlain) {  // (the tuned kernels without early exit leave it)
+            fill_steps_kernel<<<(a.n_problems + 255) / 256, 256, 0, s>>>(a.steps_out, a.n_problems, a.steps);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
         switch (variant) {
         case kVariantTpa1: cac_solve_tuned_kernel<NT, F, 1, false><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa1Packed: cac_solve_tuned_kernel<NT, F, 1, true><<<a.n_problems, runs, 0, s>>>(a); break;
@@ -167,6 +172,11 @@ cudaError_t launch_solve_impl(const SolveArgs& a, int runs, cudaStream_t s) {
         // anneals); f_mvm 1 and 2 compiled in, others at run time; no spin dump (129 spins do not fit
         // the 128-bit state words, and the API refuses it)
         if (a.spins_out || a.early_exit || a.f_mvm < 1 || runs % 32 != 0) return cudaErrorInvalidValue;
+        if (a.steps_out) {  // (every anneal takes all steps here)
+            fill_steps_kernel<<<(a.n_problems + 255) / 256, 256, 0, s>>>(a.steps_out, a.n_problems, a.steps);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
         // latency: when the problems' 32-anneal groups fit the SMs, each problem is a cluster of
         // runs / 32 CTAs (same results: anneal indices and the arg-min key are the problem's)
         const int cl = runs / 32;

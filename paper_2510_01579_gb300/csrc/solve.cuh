@@ -58,6 +58,11 @@ __device__ __forceinline__ bool signs_changed(const float (&x)[M], uint32_t (&pr
     return changed;
 }
 
+// steps_out of a launch without early exit: every problem took all S steps.
+__global__ void fill_steps_kernel(int32_t* out, int n, int S) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = S;
+}
+
 template <int NT>
 struct SolveSmem {
     static constexpr int n = 2 * NT;
@@ -207,7 +212,6 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
     float mua;
     const int S = a.steps;
     int t = 0;
-    int taken = S;
     if (a.early_exit > 0) {
         // refresh intervals one at a time, with the early-exit check before each K-th refresh
         const int K = a.early_exit;
@@ -220,14 +224,12 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
             if (t > 0 && --c == 0) {
                 c = K;
                 const bool changed = signs_changed<N>(x, prev);
-                if (!__syncthreads_or(changed)) {
-                    taken = t;
-                    break;
-                }
+                if (!__syncthreads_or(changed)) break;
             }
             coupling_mvm<n>(sm.A, sm.h, x, m, mua);
             frozen_steps_rt<n>(sm.h, sm.nd, x, e, m, mua, S - t < f ? S - t : f, k);
         }
+        if (a.steps_out && run == 0) a.steps_out[p] = t < S ? t : S;
         t = S;  // (the tail below is part of the loop here)
     } else if constexpr (F > 0) {
 #pragma unroll 1
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
         frozen_steps_rt<n>(sm.h, sm.nd, x, e, m, mua, S - t, k);
     }
 
-    if (a.steps_out && run == 0) a.steps_out[p] = taken;
+    if (a.early_exit <= 0 && a.steps_out && run == 0) a.steps_out[p] = S;
 
     // spins -> offset d = s_a (s1 + s2) / 2, clipped to the alphabet
     bool valid = true;
@@ -823,7 +825,6 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
 
     const int S = a.steps;
     int t = 0;
-    int taken = S;
     if constexpr (EE) {
         // refresh intervals one at a time, with the early-exit check before each K-th refresh
         // (this thread's spins: its rows of x1 and x2 and its copy of the auxiliary spin)
@@ -841,10 +842,7 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
                 p1 = w1;
                 p2 = w2;
                 pa = wa;
-                if (!__syncthreads_or(changed)) {
-                    taken = t;
-                    break;
-                }
+                if (!__syncthreads_or(changed)) break;
             }
             if (t + F <= S)
                 tuned_block<n, NS, TPA, PACKED, F, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, F, k);
@@ -866,8 +864,6 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
         if (t < S)
             tuned_block<n, NS, TPA, PACKED, 0, PAIR>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, q, lane, S - t, k);
     }
-
-    if (a.steps_out && tid == 0) a.steps_out[p] = taken;
 
     // validity over the whole anneal
     bool valid = (fabsf(xa) <= k.x_max) && (ea > 0.0f);
@@ -947,6 +943,9 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
             if (a.E_out) a.E_out[p] = bestE;
             if (a.run_out) a.run_out[p] = best_run;
             if (a.ndiv_out) a.ndiv_out[p] = ndiv;
+            if constexpr (EE) {  // (without early exit the launcher fills steps_out with S)
+                if (a.steps_out) a.steps_out[p] = t < S ? t : S;
+            }
             if (a.x_out) {
 #pragma unroll
                 for (int i = 0; i < n; ++i)
