@@ -59,7 +59,7 @@ __device__ __forceinline__ bool signs_changed(const float (&x)[M], uint32_t (&pr
 }
 
 // steps_out of a launch without early exit: every problem took all S steps.
-__global__ void fill_steps_kernel(int32_t* out, int n, int S) {
+static __global__ void fill_steps_kernel(int32_t* out, int n, int S) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = S;
 }
 
