@@ -39,14 +39,14 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum by ncu on a 1,024-subcarrier
 # 16x16 slot (14,336 problems) and divided by its problems; the traffic grows in
 # proportion to the problems, so a launch's traffic is this times its problems.
-# None until measured on the current kernels.
-SOLVER_DRAM_BYTES_PER_PROBLEM = {}
+# Keyed by (users, launch shape); a shape absent here reports traffic None.
+SOLVER_DRAM_BYTES_PER_PROBLEM = {(16, 6): 30868736 / 14336}
 
 WORKLOADS = {
     # name: (n_r, n_t, mod_bits, model, hold, snr_db)
     "ul16x16_16qam_slot": (16, 16, 4, "iid", "subcarrier", 16.0),
     "ul8x8_16qam_slot_kron_prb": (8, 8, 4, "kron", "prb", 15.0),
-    # small problems, where a persistent launch could pay for itself
+    # small problems (short anneals: launch overheads weigh most here)
     "ul4x4_qpsk_slot": (4, 4, 2, "iid", "subcarrier", 10.0),
     # the high-connectivity evaluation (Sec. 5): its own timing mode, run_ul32
     "ul32x32_16qam_slot": (32, 32, 4, "iid", "subcarrier", 18.0),
@@ -276,7 +276,7 @@ def run_reference(args, rank: int):
 def run_mixed(args):
     """Three slots of different sizes (16x16 16-QAM, 16x16 64-QAM, 8x8 QPSK):
     per-job path (one build + one solve launch per job) against one batched
-    persistent launch replayed from a CUDA graph."""
+    launch replayed from a CUDA graph."""
     import torch
 
     from paper_2510_01579_gb300 import Batch, Context, Params
@@ -314,12 +314,11 @@ def run_mixed(args):
     ref = [o["sym"].clone() for o in outs]
     clocks = ClockSampler(0)
     modes = {}
-    for mode, persistent in (("grid", False), ("persistent", True)):
-        with Batch(0, prm, jobs, keepalive=keep, persistent=persistent) as batch:
-            modes[mode] = statistics.mean(timed(lambda: batch.run(use_graph=True)))
-        for o, r in zip(outs, ref):
-            if not torch.equal(o["sym"], r):
-                raise RuntimeError("batched and per-job paths disagree")
+    with Batch(0, prm, jobs, keepalive=keep) as batch:
+        modes["grid"] = statistics.mean(timed(lambda: batch.run(use_graph=True)))
+    for o, r in zip(outs, ref):
+        if not torch.equal(o["sym"], r):
+            raise RuntimeError("batched and per-job paths disagree")
     clk = clocks.stop()
     best = min(modes, key=modes.get)
     ms = modes[best]
@@ -976,7 +975,7 @@ def run_snr_sweep(args):
     """8x8 16-QAM 100 MHz slot, Kronecker rho = 0.5, H per PRB, SNR 0..30 dB in
     5 dB steps: BER of MMGaP and MMSE, and slot time of the plain per-problem
     kernel (one thread per anneal, the paper's design), the per-job path
-    (autotuned shape) and the batched CUDA-graph launch (grid and persistent),
+    (autotuned shape) and the batched CUDA-graph launch,
     all with identical results."""
     import torch
 
@@ -1018,23 +1017,20 @@ def run_snr_sweep(args):
         ctx.set_solver_variant(8, tuned)
         ms_job = timed(lambda: ctx.detect_jobs([job], prm))
         same = bool(torch.equal(sym_plain, out["sym"]))
-        batched = {}
-        for mode, pers in (("grid", False), ("persistent", True)):
-            bout = {"sym": torch.empty((P, 8), dtype=torch.uint8, device=dev)}
-            bjob = ctx.detect_job(H, y, nv, 4, 9, bout, ci)
-            with Batch(0, prm, [bjob], keepalive=(H, y, nv, ci, bout), persistent=pers) as b:
-                batched[mode] = timed(lambda: b.run(use_graph=True))
-            same = same and bool(torch.equal(bout["sym"], out["sym"]))
+        bout = {"sym": torch.empty((P, 8), dtype=torch.uint8, device=dev)}
+        bjob = ctx.detect_job(H, y, nv, 4, 9, bout, ci)
+        with Batch(0, prm, [bjob], keepalive=(H, y, nv, ci, bout)) as b:
+            ms_batched = timed(lambda: b.run(use_graph=True))
+        same = same and bool(torch.equal(bout["sym"], out["sym"]))
         nbits = P * 8 * 4
         g = out["guess"].cpu().numpy().astype(int)
         mmse = ((g[:, :8] + 3) // 2) * 4 + (g[:, 8:] + 3) // 2
         rows.append({"snr_db": snr, "ber_mmgap": synth.bit_errors(out["sym"].cpu().numpy(), w["sym"], 4) / nbits,
                      "ber_mmse": synth.bit_errors(mmse, w["sym"], 4) / nbits, "ms_plain": ms_plain,
-                     "ms_per_job": ms_job, "ms_batched_grid": batched["grid"],
-                     "ms_batched_persistent": batched["persistent"], "identical_results": same})
-    best = min(rows[-1]["ms_batched_grid"], rows[-1]["ms_batched_persistent"])
+                     "ms_per_job": ms_job, "ms_batched": ms_batched, "identical_results": same})
+    best = rows[-1]["ms_batched"]
     line = {"metric": "detections/s, 8x8 16-QAM Kronecker slot (batched graph launch), SNR sweep 0-30 dB",
-            "value": P / (statistics.mean(min(r["ms_batched_grid"], r["ms_batched_persistent"]) for r in rows) / 1e3),
+            "value": P / (statistics.mean(r["ms_batched"] for r in rows) / 1e3),
             "unit": "problems/s", "n_gpus": 1, "steps": args.steps, "warmup": 2, "ms_per_step": best,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "ul8x8_16qam_kron_prb_snr_sweep", "problems_per_step": P, "runs": args.runs,
@@ -1111,7 +1107,7 @@ def main():
                     help="solver launch shape (1 plain, 2-4, 6, 9, 10 exact; 5, 7, 8 tensor-core precision variants); default: autotuned at set-up")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-problem kernel")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core field refresh variant")
-    ap.add_argument("--no-batch", action="store_true", help="skip timing the batched persistent launch")
+    ap.add_argument("--no-batch", action="store_true", help="skip timing the batched graph launch")
     ap.add_argument("--ref-budget", type=float, default=1.5, help="seconds of oracle work per core per step")
     ap.add_argument("--subcarriers", type=int, default=None,
                     help="subcarriers per slot (3276 = 100 MHz at 30 kHz; 288 = 10 MHz for the 32x32 workload)")
@@ -1394,20 +1390,20 @@ def main():
                        (statistics.mean(sv_ms) / 1e3) / 1e12, "shape": label}
         tc["device_errors"] = ctx.device_errors()
 
-    # the batched persistent launch (fused build + anneal per warp, replayed
+    # the batched launch (one builder and one solver over the job table, replayed
     # from a CUDA graph) on the same slot
     batched = None
     if not args.no_batch:
         from paper_2510_01579_gb300 import Batch
         batched = {}
-        modes = [("grid", False, False), ("persistent", True, False)]
+        modes = [("grid", False)]
         if tc is not None:  # the tcgen05 tiles (precision variant): equal to per-job shape 8
-            modes.append(("tensor_core", False, True))
-        for mode, persistent, tcm in modes:
+            modes.append(("tensor_core", True))
+        for mode, tcm in modes:
             bout = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
                     "energy": torch.empty(P, dtype=torch.int32, device=dev)}
             bjob = ctx.detect_job(H, y, nv, mb, 77, bout, ci, problem_offset=p_lo)
-            with Batch(local, prm, [bjob], keepalive=(H, y, nv, ci, bout), persistent=persistent,
+            with Batch(local, prm, [bjob], keepalive=(H, y, nv, ci, bout),
                        tensor_core=tcm) as batch:
                 for _ in range(args.warmup):
                     flush.zero_()

@@ -423,8 +423,8 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
                             float ms_out[16]);
 
 /*
- * Batched persistent launch of mixed-size uplink jobs (no counterpart in the
- * paper, which launches one fixed-size grid per kernel).
+ * Batched launch of mixed-size uplink jobs (no counterpart in the paper,
+ * which launches one fixed-size grid per kernel).
  *
  * mmgap_batch_create validates the jobs (n_t in {4, 8, 16, 32}, n_r <= 64,
  * runs = 32, f_mvm in {1, 2}) and uploads a job table (largest users first).
@@ -435,10 +435,11 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
  * A run is one builder kernel over every problem of every job (the Sec. 3.2
  * pre-processing, one warp per resource element) into batch-owned scratch,
  * then one solver kernel that anneals each problem with 32 anneals on the 32
- * lanes of a warp (solver and post-processing): either one CTA per problem
- * (flags 0) or, with MMGAP_BATCH_PERSISTENT, a grid sized from the kernel's
- * occupancy whose warps pull problems from one atomic counter across all
- * jobs.  Outputs equal mmgap_detect's bit for bit.
+ * lanes of a warp (solver and post-processing), one 32-thread CTA per problem
+ * across all jobs (the hardware CTA scheduler balances the sizes).  Outputs
+ * equal mmgap_detect's bit for bit.  A problem's Philox stream, and so its
+ * result, depends only on its job's seed and problem_offset and its index in
+ * its job.  flags: 0, or MMGAP_BATCH_TENSOR_CORE; other bits: MMGAP_EINVAL.
  * Job arrays are the caller's device memory and must stay valid for the life
  * of the batch; their contents may change between runs.  The batch owns a
  * small device table (allocated at create).
@@ -447,10 +448,9 @@ mmgap_status mmgap_autotune(mmgap_ctx* ctx, const mmgap_params* params, int n_t,
  * a private stream) and this and later runs launch the graph on `stream`.
  */
 typedef struct mmgap_batch mmgap_batch;
-#define MMGAP_BATCH_PERSISTENT 1 /* flags: persistent solver warps on an atomic counter (else one CTA per problem) */
 #define MMGAP_BATCH_TENSOR_CORE 2 /* flags: tcgen05 field refresh for 8 and 16 users (solver shape 8: a
                                      precision variant, results as mmgap_detect with that shape; 128-thread
-                                     CTAs over tiles of 4 problems of one job; not persistent) */
+                                     CTAs over tiles of 4 problems of one job) */
 mmgap_status mmgap_batch_create(mmgap_batch** batch, int device, const mmgap_params* params,
                                 const mmgap_detect_job* jobs, int n_jobs, int flags);
 mmgap_status mmgap_batch_run(mmgap_batch* batch, int use_graph, void* stream);
@@ -492,7 +492,6 @@ typedef struct {
     double deadline_us;
     double inject_delay_us;
     int32_t use_graph;
-    int32_t persistent;             /* solver mode of each group, as MMGAP_BATCH_PERSISTENT */
     int32_t tensor_core;            /* as MMGAP_BATCH_TENSOR_CORE (precision variant) */
 } mmgap_server_config;
 typedef struct {

@@ -93,7 +93,7 @@ class _ServerConfig(C.Structure):
     _fields_ = [("n_lanes", C.c_int32), ("max_jobs_per_group", C.c_int32), ("max_problems_per_group", C.c_int64),
                 ("scratch_bytes", C.c_size_t), ("max_n_t", C.c_int32), ("max_n_r", C.c_int32),
                 ("deadline_us", C.c_double), ("inject_delay_us", C.c_double), ("use_graph", C.c_int32),
-                ("persistent", C.c_int32), ("tensor_core", C.c_int32)]
+                ("tensor_core", C.c_int32)]
 
 
 class _JobInfo(C.Structure):
@@ -464,19 +464,17 @@ class Context:
 class Batch:
     """mmgap_batch: a fixed set of uplink jobs of mixed sizes run by one
     builder and one solver launch (optionally replayed from a CUDA graph):
-    one CTA per problem, persistent warps (persistent=True), or tcgen05 tiles
-    of 4 problems for 8 and 16 users (tensor_core=True, the precision variant
-    of solver shape 8).  The jobs' tensors must stay alive (and at the same
+    one CTA per problem, or tcgen05 tiles of 4 problems for 8 and 16 users
+    (tensor_core=True, the precision variant of solver shape 8).  The jobs' tensors must stay alive (and at the same
     addresses) for the life of the batch; their contents may change between
     runs."""
 
-    def __init__(self, device: int, params: Params, jobs, keepalive=(), persistent: bool = False,
-                 tensor_core: bool = False):
+    def __init__(self, device: int, params: Params, jobs, keepalive=(), tensor_core: bool = False):
         self._keep = list(keepalive)
         arr = (_DetectJob * len(jobs))(*jobs)
         cp = params._c()
         h = C.c_void_p()
-        flags = (1 if persistent else 0) | (2 if tensor_core else 0)
+        flags = 2 if tensor_core else 0
         st = _lib.mmgap_batch_create(C.byref(h), device, C.byref(cp), arr, len(jobs), flags)
         if st != OK:
             raise MMGaPError(st, "mmgap_batch_create failed (see stderr)")
@@ -518,10 +516,9 @@ class Server:
     def __init__(self, device: int, params: Params, scratch_bytes: int = 1 << 30, n_lanes: int = 2,
                  max_jobs_per_group: int = 64, max_problems_per_group: int = 1 << 20, max_n_t: int = 16,
                  max_n_r: int = 16, deadline_us: float = 0.0, inject_delay_us: float = 0.0, use_graph: bool = True,
-                 persistent: bool = False, tensor_core: bool = False):
+                 tensor_core: bool = False):
         cfg = _ServerConfig(n_lanes, max_jobs_per_group, max_problems_per_group, scratch_bytes, max_n_t, max_n_r,
-                            deadline_us, inject_delay_us, 1 if use_graph else 0, 1 if persistent else 0,
-                            1 if tensor_core else 0)
+                            deadline_us, inject_delay_us, 1 if use_graph else 0, 1 if tensor_core else 0)
         cp = params._c()
         h = C.c_void_p()
         st = _lib.mmgap_server_create(C.byref(h), device, C.byref(cp), C.byref(cfg))

@@ -2,10 +2,10 @@
 //
 // A batch is a fixed set of detection jobs (device inputs and outputs).  One
 // run = job-table upload, one builder kernel over every problem of every job
-// and one persistent solver kernel whose warps pull problems across all jobs
-// from one atomic counter, largest problems first, so jobs of different sizes
-// share the GPU instead of one pair of grids per job.  The run can be captured
-// once into a CUDA graph and replayed.
+// and one solver kernel with a CTA per problem across all jobs, largest
+// problems first, so jobs of different sizes share the GPU instead of one pair
+// of grids per job.  The run can be captured once into a CUDA graph and
+// replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -35,19 +35,17 @@ int build_floats_for(int nt, int n_r) {
 }
 
 template <int NTMAX>
-const void* solve_ptr(int f, bool persistent, bool tc) {
+const void* solve_ptr(int f, bool tc) {
     if (tc)  // tcgen05 tiles of 4 problems (solver shape 8)
         return f == 1 ? (const void*)batch_solve_umma_kernel<NTMAX, 1> : (const void*)batch_solve_umma_kernel<NTMAX, 2>;
-    if (persistent)
-        return f == 1 ? (const void*)batch_solve_kernel<NTMAX, 1> : (const void*)batch_solve_kernel<NTMAX, 2>;
     return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1> : (const void*)batch_solve_grid_kernel<NTMAX, 2>;
 }
 
-const void* pick_solve(int ntmax, int f, bool persistent, bool tc) {
+const void* pick_solve(int ntmax, int f, bool tc) {
     switch (ntmax) {
-    case 16: return solve_ptr<16>(f, persistent, tc);
-    case 8: return solve_ptr<8>(f, persistent, tc);
-    default: return solve_ptr<4>(f, persistent, tc);
+    case 16: return solve_ptr<16>(f, tc);
+    case 8: return solve_ptr<8>(f, tc);
+    default: return solve_ptr<4>(f, tc);
     }
 }
 
@@ -59,7 +57,6 @@ const void* pick_build(int ntmax) {
     }
 }
 
-constexpr int kBatchWarps = 4;
 
 // Constants of the Euler discretisation of Eqs. 10-11 (the helper every
 // entry point uses, so the rounding is the same on every path).
@@ -122,11 +119,10 @@ size_t BatchRunner::scratch_bytes(int n_t, int n_problems) {
 }
 
 cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r,
-                              int ntmax, int* err_word, bool persistent, bool tensor_core) {
+                              int ntmax, int* err_word, bool tensor_core) {
     device_ = device;
     ntmax = std::min(ntmax, 16);  // the table's kernels; 32-user jobs run their own launches
     tc_ = tensor_core && ntmax >= 8;
-    persistent_ = persistent && !tc_;
     capacity_ = capacity_jobs;
     capacity_problems_ = capacity_problems;
     ntmax_ = ntmax;
@@ -147,15 +143,11 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
     if ((e = cudaFuncSetAttribute(pick_build(ntmax), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem_)) !=
         cudaSuccess)
         return e;
-    int per_sm = 0, sms = 0, bper_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_solve(ntmax, 2, true, false), kBatchWarps * 32, 0)) !=
-        cudaSuccess)
-        return e;
+    int sms = 0, bper_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bper_sm, pick_build(ntmax), kBuildWarps * 32,
                                                            build_smem_)) != cudaSuccess)
         return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
-    grid_ = std::max(1, per_sm) * sms;
     build_grid_max_ = std::max(1, bper_sm) * sms;
     if (tc_) {
         // the tiles resident on an SM share its 512 TMEM columns (128 per 16-user tile, 64 per
@@ -169,7 +161,7 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
         if (smem < floor_bytes) smem = (floor_bytes + 127) & ~(size_t)127;
         umma_smem_ = smem;
         for (int f : {1, 2})
-            if ((e = cudaFuncSetAttribute(pick_solve(ntmax, f, false, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if ((e = cudaFuncSetAttribute(pick_solve(ntmax, f, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem)) != cudaSuccess)
                 return e;
     }
@@ -361,7 +353,6 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
     h_head_->n_jobs = n_table;
     h_head_->pad = 0;
     h_head_->total = first;
-    h_head_->counter = 0;
     h_head_->tiles = tiles;
     return 0;
 }
@@ -470,7 +461,7 @@ void BatchRunner::grids(unsigned* build_grid, unsigned* solve_grid) const {
         *solve_grid = (unsigned)std::max(1LL, tiles);
         return;
     }
-    *solve_grid = persistent_ ? (unsigned)grid_ : (unsigned)std::max(1LL, total);
+    *solve_grid = (unsigned)std::max(1LL, total);
 }
 
 cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
@@ -493,7 +484,7 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3(bg), dim3(kBuildWarps * 32), args, build_smem_, s)) !=
         cudaSuccess)
         return e;
-    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, persistent_, tc_), dim3(sg), dim3(solve_block()), args,
+    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, tc_), dim3(sg), dim3(solve_block()), args,
                             solve_smem(), s);
 }
 
@@ -556,7 +547,7 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         kb.kernelParams = args;
         if ((e = cudaGraphExecKernelNodeSetParams(exec_, build_node_, &kb)) != cudaSuccess) return e;
         cudaKernelNodeParams ks{};
-        ks.func = (void*)pick_solve(ntmax_, P.f_mvm, persistent_, tc_);
+        ks.func = (void*)pick_solve(ntmax_, P.f_mvm, tc_);
         ks.gridDim = dim3(sg);
         ks.blockDim = dim3(solve_block());
         ks.sharedMemBytes = (unsigned)solve_smem();
@@ -583,6 +574,10 @@ mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_param
     if (!out) return MMGAP_EINVAL;
     *out = nullptr;
     if (!params || n_jobs < 1 || !jobs) return MMGAP_EINVAL;
+    if (flags & ~MMGAP_BATCH_TENSOR_CORE) {
+        fprintf(stderr, "mmgap_batch_create: unknown flags 0x%x\n", (unsigned)flags);
+        return MMGAP_EINVAL;
+    }
     if (BatchRunner::check_params(*params)) {
         fprintf(stderr, "mmgap_batch_create: %s\n", BatchRunner::check_params(*params));
         return MMGAP_EUNSUPPORTED;
@@ -616,7 +611,6 @@ mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_param
     if (cudaMalloc(&b->err_word, sizeof(int)) != cudaSuccess || cudaMemset(b->err_word, 0, sizeof(int)) != cudaSuccess)
         st = MMGAP_ENOMEM;
     if (st == MMGAP_OK && b->runner.init(device, n_jobs, total, scratch, max_n_r, ntmax, b->err_word,
-                                         (flags & MMGAP_BATCH_PERSISTENT) != 0,
                                          (flags & MMGAP_BATCH_TENSOR_CORE) != 0) != cudaSuccess)
         st = MMGAP_ENOMEM;
     if (st == MMGAP_OK) {

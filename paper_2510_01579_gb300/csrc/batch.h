@@ -1,5 +1,5 @@
-// Internal runner of the batched persistent launch (shared by the batch
-// objects and the serving loop).  Not part of the ABI.
+// Internal runner of the batched launch (shared by the batch objects and the
+// serving loop).  Not part of the ABI.
 #pragma once
 #include <cstring>
 #include <vector>
@@ -38,12 +38,11 @@ class BatchRunner {
     // problems with n_r <= max_n_r and n_t <= ntmax (the table's kernels are
     // sized for min(ntmax, 16); 32-user jobs stay outside the table), `scratch`
     // bytes of coupling scratch; err_word receives out-of-range channel indices.
-    // persistent: the solver runs warps that pull problems from an atomic
-    // counter; otherwise one 32-thread CTA per problem.  tensor_core: the
-    // field refresh of 8- and 16-user problems as tcgen05 MMAs (solver shape
+    // The solver runs one 32-thread CTA per problem; tensor_core: the field
+    // refresh of 8- and 16-user problems as tcgen05 MMAs instead (solver shape
     // 8, a precision variant; 128-thread CTAs over 4-problem tiles).
     cudaError_t init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r, int ntmax,
-                     int* err_word, bool persistent, bool tensor_core = false);
+                     int* err_word, bool tensor_core = false);
     void release();
     // Fill the pinned host table with jobs[order[i]] (order may be NULL);
     // returns 0, or < 0 if the jobs exceed the table, scratch or problem capacity.
@@ -54,7 +53,6 @@ class BatchRunner {
     // solve, then the batch of the other jobs (table upload, builder,
     // solver; or the graph of them), then each precoding job's output kernel.
     cudaError_t run(const mmgap_params& P, cudaStream_t s, bool use_graph);
-    int grid() const { return grid_; }
 
   private:
     struct Precode {  // a staged precoding job and its scratch
@@ -86,10 +84,9 @@ class BatchRunner {
     std::vector<Wide> wide_;
     cudaError_t wide_before(const mmgap_params& P, cudaStream_t s);
     void grids(unsigned* build_grid, unsigned* solve_grid) const;
-    unsigned solve_block() const { return tc_ ? 128u : (persistent_ ? 4u * 32u : 32u); }
+    unsigned solve_block() const { return tc_ ? 128u : 32u; }
     size_t solve_smem() const { return tc_ ? umma_smem_ : 0; }
-    int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0, grid_ = 0, build_grid_max_ = 1;
-    bool persistent_ = false;
+    int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0, build_grid_max_ = 1;
     bool tc_ = false;  // tcgen05 field refresh for 8 and 16 users (4-problem tiles)
     size_t umma_smem_ = 0;  // dynamic shared memory of the tcgen05 solver
     long long capacity_problems_ = 0;

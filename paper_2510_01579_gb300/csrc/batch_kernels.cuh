@@ -1,5 +1,5 @@
-// Batched launch of mixed-size jobs: builder over the job table, grid / persistent
-// solvers and the tcgen05 tile solver.
+// Batched launch of mixed-size jobs: builder over the job table, the grid solver
+// and the tcgen05 tile solver.
 #pragma once
 #include "build.cuh"
 #include "solve.cuh"
@@ -10,12 +10,12 @@ namespace mmgap {
 // =========================================================================
 // Batched launch of mixed-size uplink jobs, in two kernels replayed as one
 // graph.  The builder runs one warp per problem over the whole batch (all
-// jobs, all sizes) into batch scratch; the solver is persistent: warps pull
-// problems from one atomic counter over a device job table (largest users
-// first), stage the problem's Q14 couplings in shared memory and anneal it
-// with 32 anneals on the warp's 32 lanes (one thread per anneal, packed
-// FP32).  Results equal the per-job path bit for bit: the Philox counters use
-// each problem's index within its own job.
+// jobs, all sizes) into batch scratch; the solver runs one 32-thread CTA per
+// problem over a device job table (largest users first), stages the problem's
+// Q14 couplings in shared memory and anneals it with 32 anneals on the warp's
+// 32 lanes (one thread per anneal, packed FP32).  Results equal the per-job
+// path bit for bit: the Philox counters use each problem's index within its
+// own job.
 // =========================================================================
 struct BatchJob {
     BuildArgs b;            // inputs, n_r, mod_bits, n_problems, n_chan, kappa, err
@@ -40,7 +40,6 @@ struct BatchHeader {
     int n_jobs;
     int pad;
     long long total;             // problems in the batch
-    unsigned long long counter;  // next problem to hand out (reset before each run)
     long long tiles;             // 4-problem tiles of the tensor-core solver (no tile spans two jobs)
 };
 
@@ -230,32 +229,6 @@ __global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
         if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, ssm);
     } else {
         batch_solve_problem<4, F>(A, J, p, lane, ssm);
-    }
-}
-
-// Persistent solver over the batch: one warp per problem, problems handed
-// out by an atomic counter.
-template <int NTMAX, int F>
-__global__ void __launch_bounds__(128) batch_solve_kernel(BatchArgs A) {
-    __shared__ __align__(16) unsigned char ssm[4 * batch_solve_bytes<NTMAX>()];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* mine = ssm + (size_t)warp * batch_solve_bytes<NTMAX>();
-    const int n_jobs = A.head->n_jobs;
-    const long long total = A.head->total;
-    for (;;) {
-        unsigned long long w = 0;
-        if (lane == 0) w = atomicAdd(&A.head->counter, 1ULL);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        if ((long long)w >= total) break;
-        const BatchJob& J = A.jobs[batch_find_job(A.jobs, n_jobs, (long long)w)];
-        const int p = (int)((long long)w - J.first);
-        if (J.nt == 16) {
-            if constexpr (NTMAX >= 16) batch_solve_problem<16, F>(A, J, p, lane, mine);
-        } else if (J.nt == 8) {
-            if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, mine);
-        } else {
-            batch_solve_problem<4, F>(A, J, p, lane, mine);
-        }
     }
 }
 

@@ -240,7 +240,7 @@ mmgap_status mmgap_server_create(mmgap_server** out, int device, const mmgap_par
         if (st != MMGAP_OK) break;
         if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess) st = MMGAP_ECUDA;
         else if (L.runner.init(device, s->lane_jobs, s->lane_problems, s->lane_scratch, cfg->max_n_r, cfg->max_n_t,
-                               s->err_word, cfg->persistent != 0, cfg->tensor_core != 0) != cudaSuccess)
+                               s->err_word, cfg->tensor_core != 0) != cudaSuccess)
             st = MMGAP_ENOMEM;
     }
     if (st != MMGAP_OK) {

@@ -34,8 +34,8 @@ SPECS = [(16, 4, 300, "iid", "subcarrier"), (8, 2, 1200, "kron", "prb"), (4, 6, 
          (16, 4, 64, "kron", "prb"), (8, 6, 333, "iid", "problem")]
 
 
-@pytest.mark.parametrize("persistent", [False, True])
-def test_each_job_same_alone_and_in_the_mix(persistent):
+@pytest.mark.parametrize("graph", [True, False])
+def test_each_job_same_alone_and_in_the_mix(graph):
     import paper_2510_01579_gb300 as pkg
     prm = pkg.Params.default(steps=80)
     with pkg.Context(0) as ctx:
@@ -47,7 +47,7 @@ def test_each_job_same_alone_and_in_the_mix(persistent):
             refs.append(r)
         torch.cuda.synchronize()
         # in the mix: all submitted at once; a budget that forces several groups per lane
-        with pkg.Server(0, prm, scratch_bytes=8 << 20, n_lanes=2, max_jobs_per_group=3, persistent=persistent) as srv:
+        with pkg.Server(0, prm, scratch_bytes=8 << 20, n_lanes=2, max_jobs_per_group=3, use_graph=graph) as srv:
             tickets = [srv.submit(job) for _, _, _, job in jobs]
             infos = [srv.wait(tk, timeout_us=60_000_000) for tk in tickets]
             st = srv.stats()
@@ -113,8 +113,8 @@ def _precode_jobs(ctx, specs):
     return out
 
 
-@pytest.mark.parametrize("persistent", [False, True])
-def test_precoding_jobs_in_the_mix_equal_mmgap_precode(persistent):
+@pytest.mark.parametrize("graph", [True, False])
+def test_precoding_jobs_in_the_mix_equal_mmgap_precode(graph):
     """Detection and VPP jobs of several sizes, both inverse precisions, submitted together: every
     precoding output (v, x, power, energy, divergence count) equals mmgap_precode's alone, and every
     detection output equals mmgap_detect's."""
@@ -133,7 +133,7 @@ def test_precoding_jobs_in_the_mix_equal_mmgap_precode(persistent):
                                        want_ndiv=True, inv_precision=ip))
         torch.cuda.synchronize()
         with pkg.Server(0, prm, scratch_bytes=16 << 20, n_lanes=2, max_jobs_per_group=3, max_n_r=16,
-                        persistent=persistent) as srv:
+                        use_graph=graph) as srv:
             tickets = []
             for i in range(max(len(det), len(pre))):  # interleaved arrivals
                 if i < len(det):
