@@ -273,6 +273,69 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def secondary_measurements(ctx, dev, flush, steps: int = 5):
+    """Short timings of the workloads next to the headline, so that one default
+    run records them too (each with CUDA events on the current stream, L2 flushed
+    between steps): the 8x8 16-QAM Kronecker PRB-held slot, the 16x16 16-QAM VPP
+    slot with the FP32 + refinement inverse, and the paper's 32x32 16-QAM 10 MHz
+    slot with 128 anneals."""
+    import torch
+
+    from paper_2510_01579_gb300 import Params
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, n):
+        for _ in range(2):
+            flush.zero_()
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        out = None
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev), out
+
+    res = {}
+    # 8x8 16-QAM, Kronecker rho = 0.5, H per PRB, 15 dB
+    w = make_workload("ul8x8_16qam_slot_kron_prb", rank_seed(0))
+    H, y, nv, ci = (torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index"))
+    ms, out = timed(lambda: ctx.detect(H, y, nv, 4, Params.default(), 77, chan_index=ci, want_guess=True), steps)
+    P = w["y"].shape[0]
+    g = out["guess"].cpu().numpy().astype(int)
+    nbits = P * 8 * 4
+    res["ul8x8_16qam_slot_kron_prb"] = {
+        "problems": P, "ms_per_slot": ms, "problems_per_s": P / (ms / 1e3),
+        "ber": synth.bit_errors(out["sym"].cpu().numpy(), w["sym"], 4) / nbits,
+        "ber_mmse": synth.bit_errors(((g[:, :8] + 3) // 2) * 4 + (g[:, 8:] + 3) // 2, w["sym"], 4) / nbits}
+    # downlink VPP, 16x16 16-QAM, 3,276 subcarriers, FP32 + refinement inverse; power against zero forcing
+    d = synth.downlink(4016, 16, 16, 4)
+    H, u, ci = (torch.from_numpy(d[k]).to(dev) for k in ("H", "u_sym", "chan_index"))
+    ms, out = timed(lambda: ctx.precode(H, u, 4, Params.default(), 5, chan_index=ci, inv_precision=1), steps)
+    ul = (2 * (d["u_sym"].astype(int) // 4) - 3) + 1j * (2 * (d["u_sym"].astype(int) % 4) - 3)
+    Hh = d["H"].astype(np.complex128)
+    zf = np.array([np.linalg.norm(Hh[c].conj().T @ np.linalg.solve(Hh[c] @ Hh[c].conj().T, ul[p])) ** 2
+                   for p, c in enumerate(d["chan_index"])])
+    res["precode_16x16_16qam_slot"] = {
+        "problems": int(u.shape[0]), "ms_per_slot": ms, "problems_per_s": u.shape[0] / (ms / 1e3),
+        "inverse": "fp32 + refinement", "mean_power_over_zf": float(np.mean(out["power"].cpu().numpy() / zf))}
+    # the paper's high-connectivity case: 32x32 16-QAM, 10 MHz (288 x 14 problems), 128 anneals, 18 dB
+    w = synth.uplink(rank_seed(0) + 320, 32, 32, 4, n_sub=synth.SUBCARRIERS_10MHZ_30KHZ, snr_db=18.0)
+    H, y, nv, ci = (torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index"))
+    prm = Params.default(runs=128)
+    ms, out = timed(lambda: ctx.detect(H, y, nv, 4, prm, 3, chan_index=ci, want_guess=True), max(2, steps // 2))
+    P = w["y"].shape[0]
+    g = out["guess"].cpu().numpy().astype(int)
+    nbits = P * 32 * 4
+    res["ul32x32_16qam_10mhz_slot"] = {
+        "problems": P, "runs": 128, "ms_per_slot": ms, "problems_per_s": P / (ms / 1e3),
+        "ber": synth.bit_errors(out["sym"].cpu().numpy(), w["sym"], 4) / nbits,
+        "ber_mmse": synth.bit_errors(((g[:, :32] + 3) // 2) * 4 + (g[:, 32:] + 3) // 2, w["sym"], 4) / nbits}
+    return res
+
+
 def run_mixed(args):
     """Three slots of different sizes (16x16 16-QAM, 16x16 64-QAM, 8x8 QPSK):
     per-job path (one build + one solve launch per job) against one batched
@@ -1117,6 +1180,8 @@ def main():
     ap.add_argument("--early-exit", type=int, default=4,
                     help="K of the early-exit line (0: skip it); the headline runs every anneal for all steps")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving trace")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the short 8x8 Kronecker, 16x16 VPP and 32x32 slot timings")
     args = ap.parse_args()
     # the 32x32 high-connectivity evaluation (Sec. 5) is a 10 MHz slot with N_a = 128 anneals
     ul32 = args.workload == "ul32x32_16qam_slot"
@@ -1485,6 +1550,12 @@ def main():
                  "plain_p50_ms": pl["p50_us"] / 1e3, "plain_p99_ms": pl["p99_us"] / 1e3, "plain_value": pl["value"],
                  "deadline_us": sr["deadline_us"]}
 
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary and args.workload == "ul16x16_16qam_slot":
+        ctx.set_timing(False)
+        secondary = secondary_measurements(ctx, dev, flush)
+        ctx.set_timing(True)
+
     # roofline of the dominant kernel (the CIM-CAC solver), from the library's
     # own CUDA events on the launching stream; the peak from this device's SM
     # count and the clock sampled during the timed region
@@ -1535,6 +1606,7 @@ def main():
             "plain_path": plain,
             "tensor_core_refresh": tc,
             "batched_path": batched, "early_exit": early, "split_check": split_check, "serve": serve,
+            "secondary_workloads": secondary,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             # per call: builder + solver per chunk, and the per-channel factorisation (first-problem and
             # factor kernels) once when channels serve several problems (as here: H per subcarrier or PRB)
