@@ -1518,28 +1518,6 @@ def main():
                  "mean_steps": float(eo["steps"].float().mean()), "steps": args.solver_steps,
                  "bit_errors": e_err, "bit_errors_exact": r_err, "ber": e_err / nbits,
                  "keeps_ber_2sigma": abs(e_err - r_err) <= 2 * sd, "speedup_vs_exact": ms_per_step / ee_ms}
-        # the same rule on the tcgen05 shape (precision variant: each problem of a tile frozen at its stop)
-        if not args.no_tc and n_t in (8, 16) and args.f_mvm in (1, 2) and args.runs != 96:
-            ctx.set_solver_variant(n_t, 8)
-            for _ in range(2):
-                flush.zero_()
-                ctx.detect_jobs([ejob_ee], eprm)
-            torch.cuda.synchronize()
-            t_solve = []
-            for i in range(args.steps):
-                flush.zero_()
-                starts[i].record(stream)
-                ctx.detect_jobs([ejob_ee], eprm)
-                ends[i].record(stream)
-                t_solve.append(ctx.stage_times()[1])
-            torch.cuda.synchronize()
-            ctx.set_solver_variant(n_t, variant)
-            t_ms = max_over_ranks(sum(starts[i].elapsed_time(ends[i]) for i in range(args.steps)), dev) / args.steps
-            t_err = synth.bit_errors(eo["sym"].cpu().numpy(), w["sym"], mb)
-            early["tcgen05"] = {"ms_per_step": t_ms, "value": (P_slot if split else world * P) / (t_ms / 1e3),
-                                "solve_ms": statistics.mean(t_solve), "mean_steps": float(eo["steps"].float().mean()),
-                                "bit_errors": t_err, "keeps_ber_2sigma": abs(t_err - r_err) <= 2 * sd,
-                                "speedup_vs_exact": ms_per_step / t_ms, "device_errors": ctx.device_errors()}
 
     # one slot split over the ranks: gather the shards' symbols on rank 0 and check them against
     # the unsharded slot detected there

@@ -141,15 +141,12 @@ mmgap_status check_params(mmgap_ctx* ctx, const mmgap_params* P) {
     return MMGAP_OK;
 }
 
-// Early exit runs on the bit-identical solver shapes and the tcgen05 shape 8
-// (not at 96 anneals, which shape 8 hands to shape 5), up to 16 users.
+// Early exit runs on the bit-identical solver shapes up to 16 users.
 mmgap_status check_early_exit(mmgap_ctx* ctx, const mmgap_params* P, int n_t) {
     if (P->early_exit == 0) return MMGAP_OK;
     if (n_t > 16) return fail(ctx, MMGAP_EUNSUPPORTED, "early exit: up to 16 users");
-    const int v = resolve_variant(n_t, P->f_mvm, ctx->variant[n_t]);
-    if (v == kVariantTensorCore || v == kVariantTensorCore2 || (v == kVariantUmma && P->runs == 96))
-        return fail(ctx, MMGAP_EUNSUPPORTED, "early exit runs on the bit-identical shapes and shape 8 (not 5, 7, "
-                    "or 8 at 96 anneals)");
+    if (variant_tensor_core(resolve_variant(n_t, P->f_mvm, ctx->variant[n_t])))
+        return fail(ctx, MMGAP_EUNSUPPORTED, "early exit runs on the bit-identical solver shapes, not 5, 7 or 8");
     return MMGAP_OK;
 }
 

@@ -42,7 +42,7 @@ __host__ __device__ constexpr bool tuned_size(int NT) { return NT == 4 || NT == 
 // Shape 8: CTAs of 128 anneals.  The CTAs resident on an SM share its 512
 // TMEM columns, so shared memory is padded where needed to keep at most
 // 512 / ncols of them on one SM (registers already allow fewer here).
-template <int NT, int F, bool EE = false>
+template <int NT, int F>
 cudaError_t launch_umma(const SolveArgs& a, int runs, cudaStream_t s) {
     const int pp = 128 / runs;
     const int N = pp * 2 * NT;
@@ -55,10 +55,10 @@ cudaError_t launch_umma(const SolveArgs& a, int runs, cudaStream_t s) {
     size_t smem = (size_t)UmmaSmem<NT>(pp).bytes();
     const size_t floor_bytes = (size_t)smem_sm / (size_t)(max_ctas + 1) + 1;  // (max_ctas + 1) CTAs no longer fit
     if (smem < floor_bytes) smem = (floor_bytes + 127) & ~(size_t)127;
-    err = ensure_dynamic_smem<cac_solve_umma_kernel<NT, F, EE>>(smem);
+    err = ensure_dynamic_smem<cac_solve_umma_kernel<NT, F>>(smem);
     if (err != cudaSuccess) return err;
     const int blocks = (a.n_problems + pp - 1) / pp;
-    cac_solve_umma_kernel<NT, F, EE><<<blocks, 128, smem, s>>>(a, runs);
+    cac_solve_umma_kernel<NT, F><<<blocks, 128, smem, s>>>(a, runs);
     return cudaGetLastError();
 }
 
@@ -84,13 +84,9 @@ cudaError_t launch_tuned_early_exit(const SolveArgs& a, int runs, int variant, c
     case kVariantPairPacked:
         cac_solve_tuned_kernel<NT, F, 1, true, false, true, true><<<a.n_problems, runs, 0, s>>>(a);
         break;
-    case kVariantUmma:  // tcgen05 tiles, each problem frozen at its own stop (not for 96 anneals)
-        if constexpr (NT % 8 == 0) {
-            if (runs != 96) return launch_umma<NT, F, true>(a, runs, s);
-        }
-        return cudaErrorNotSupported;
     case kVariantTensorCore:
-    case kVariantTensorCore2: return cudaErrorNotSupported;  // (the entry points refuse these first)
+    case kVariantTensorCore2:
+    case kVariantUmma: return cudaErrorNotSupported;  // (the entry points refuse this combination first)
     default: cac_solve_kernel<NT, F><<<a.n_problems, runs, 0, s>>>(a); break;
     }
     return cudaGetLastError();

@@ -169,11 +169,7 @@ struct UmmaSmem {
 
 // Refresh through the tensor cores + L frozen Euler steps (L == 0: runtime
 // Lrt).  Returns false, without stepping, once any thread of the CTA has met
-// an expired wait (the decision is CTA-uniform).  A thread of a problem that
-// early exit has stopped (`frozen`, uniform over the problem's whole warps)
-// leaves its row of U^T stale, still takes part in the barrier and the
-// bounded wait (so every thread tracks the same barrier phase), and then
-// skips the TMEM load and the Euler steps.
+// an expired wait (the decision is CTA-uniform).
 template <int NT, int L>
 __device__ __forceinline__ bool umma_block(uint8_t* su_h, uint8_t* su_l, uint32_t a_h, uint32_t a_l, uint32_t c_h,
                                            uint32_t c_l, uint32_t idesc, uint32_t d_tmem, uint32_t my_cols,
@@ -181,14 +177,13 @@ __device__ __forceinline__ bool umma_block(uint8_t* su_h, uint8_t* su_l, uint32_
                                            const float* snd, float (&x1)[2 * NT], float (&x2)[2 * NT],
                                            float (&e1)[2 * NT], float (&e2)[2 * NT], float& xa, float& ea, int tid,
                                            int Lrt, float mscale, const EulerConsts& k,
-                                           unsigned long long wait_ns, bool frozen = false) {
+                                           unsigned long long wait_ns) {
     constexpr int n = 2 * NT;
     constexpr int SBO = UmmaSmem<NT>::SBO;
     asm volatile("" ::: "memory");
     // u = x1 + x2, mu_a = b^T u (FP32, ascending j), FP16 split of 2^5 u into row tid of U^T
     float mua = 0.0f;
     const int rowoff = (tid >> 3) * SBO + (tid & 7) * 16;
-    if (!frozen) {
 #pragma unroll
     for (int c = 0; c < n / 8; ++c) {
         uint32_t hv[4], lv[4];
@@ -205,7 +200,6 @@ __device__ __forceinline__ bool umma_block(uint8_t* su_h, uint8_t* su_l, uint32_
         }
         *reinterpret_cast<uint4*>(su_h + rowoff + 128 * c) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
         *reinterpret_cast<uint4*>(su_l + rowoff + 128 * c) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-    }
     }
     fence_async_smem();  // the generic-proxy rows become visible to the tensor cores
     tc05_fence_before();
@@ -231,7 +225,6 @@ __device__ __forceinline__ bool umma_block(uint8_t* su_h, uint8_t* su_l, uint32_
         return true;  // the next barrier (or the caller's) stops the CTA
     }
     phase ^= 1u;
-    if (frozen) return true;
     tc05_fence_after();
     float m[n];
     tmem_ld_row(my_cols, m);
@@ -289,10 +282,8 @@ struct UmmaTile {
     int steps;
     EulerConsts k;
     unsigned long long wait_ns;  // limit of each wait on the MMA's completion
-    int early_exit;         // K > 0 (EE instantiation): a problem stops at the first K-th refresh with no sign change
     int* err;               // device error word or nullptr
     // outputs for the tile's first problem (each may be nullptr)
-    int32_t* steps_out;     // Euler steps each problem took (EE instantiation)
     int8_t* d_out;          // [n] offsets (0 where the guess was kept)
     int32_t* E_out;
     int32_t* run_out;
@@ -303,7 +294,7 @@ struct UmmaTile {
     int mod_bits;
 };
 
-template <int NT, int F, bool EE = false>
+template <int NT, int F>
 __device__ __forceinline__ void umma_tile(const UmmaTile& a, int runs, uint8_t* usm) {
     constexpr int n = 2 * NT;
     static_assert(n % 16 == 0 && F > 0, "tcgen05 refresh: n a multiple of 16, compile-time refresh period");
@@ -311,7 +302,6 @@ __device__ __forceinline__ void umma_tile(const UmmaTile& a, int runs, uint8_t* 
     __shared__ uint32_t tmem_slot;
     __shared__ long long skey[4];
     __shared__ int sdiv[4];
-    __shared__ int schg[4];  // early exit: a sign of this warp's anneals changed since the last check
     const int PP = 128 / runs;
     const UmmaSmem<NT> L(PP);
     const int N = PP * n;
@@ -399,54 +389,13 @@ __device__ __forceinline__ void umma_tile(const UmmaTile& a, int runs, uint8_t* 
     const int S = a.steps;
     int t = 0;
     bool go = true;
-    int stop_t = S;  // early exit: where this thread's problem stopped
-    if constexpr (EE) {
-        // Early exit per problem, with the rule of the exact shapes: every K-th refresh point
-        // compares all spin signs of the problem's anneals with the previous check point; a
-        // problem that saw no change is frozen there (its threads skip their TMEM loads and Euler
-        // steps from then on); the tile ends when all of its problems are frozen.
-        const int K = a.early_exit;
-        uint32_t p1 = sign_word<n>(x1), p2 = sign_word<n>(x2);
-        bool pa = xa >= 0.0f, frozen = false;
-        const int wpp = runs / 32, w0 = pl * wpp;  // this problem's warps
-        int c = K;
 #pragma unroll 1
-        for (; go && t < S; t += F) {
-            if (t > 0 && --c == 0) {
-                c = K;
-                const uint32_t w1 = sign_word<n>(x1), w2 = sign_word<n>(x2);
-                const bool wa = xa >= 0.0f;
-                const bool changed = (w1 != p1) || (w2 != p2) || (wa != pa);
-                p1 = w1;
-                p2 = w2;
-                pa = wa;
-                const bool any = __any_sync(0xffffffffu, changed);
-                if (lane == 0) schg[warp] = any ? 1 : 0;
-                __syncthreads();
-                bool chg = false;
-                for (int w = 0; w < wpp; ++w) chg = chg || schg[w0 + w] != 0;
-                if (!frozen && !chg) {
-                    frozen = true;
-                    stop_t = t;
-                }
-                if (__syncthreads_and(frozen ? 1 : 0)) break;  // every problem of the tile stopped
-            }
-            if (t + F <= S)
-                go = umma_block<NT, F>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed,
-                                       shp, sndp, x1, x2, e1, e2, xa, ea, tid, F, mscale, k, a.wait_ns, frozen);
-            else
-                go = umma_block<NT, 0>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed,
-                                       shp, sndp, x1, x2, e1, e2, xa, ea, tid, S - t, mscale, k, a.wait_ns, frozen);
-        }
-    } else {
-#pragma unroll 1
-        for (; go && t + F <= S; t += F)
-            go = umma_block<NT, F>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed, shp,
-                                   sndp, x1, x2, e1, e2, xa, ea, tid, F, mscale, k, a.wait_ns);
-        if (go && t < S)
-            umma_block<NT, 0>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed, shp, sndp,
-                              x1, x2, e1, e2, xa, ea, tid, S - t, mscale, k, a.wait_ns);
-    }
+    for (; go && t + F <= S; t += F)
+        go = umma_block<NT, F>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed, shp, sndp,
+                               x1, x2, e1, e2, xa, ea, tid, F, mscale, k, a.wait_ns);
+    if (go && t < S)
+        umma_block<NT, 0>(su_h, su_l, a_h, a_l, c_h, c_l, idesc, tmem, my_cols, mbar, phase, failed, shp, sndp, x1,
+                          x2, e1, e2, xa, ea, tid, S - t, mscale, k, a.wait_ns);
     tc05_fence_before();
     const bool cta_failed = __syncthreads_or(failed ? 1 : 0) != 0;
     if (cta_failed) {
@@ -524,9 +473,6 @@ __device__ __forceinline__ void umma_tile(const UmmaTile& a, int runs, uint8_t* 
         if (a.E_out) a.E_out[p] = bestE;
         if (a.run_out) a.run_out[p] = best_run;
         if (a.ndiv_out) a.ndiv_out[p] = ndiv;
-        if constexpr (EE) {
-            if (a.steps_out) a.steps_out[p] = stop_t;
-        }
         if (a.x_out) {
 #pragma unroll
             for (int i = 0; i < n; ++i) a.x_out[(size_t)p * n + i] = (int8_t)((int)g[i] + 2 * (keep ? d[i] : 0));
@@ -548,7 +494,7 @@ __device__ __forceinline__ void umma_tile(const UmmaTile& a, int runs, uint8_t* 
     }
 }
 
-template <int NT, int F, bool EE = false>
+template <int NT, int F>
 __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int runs) {
     constexpr int n = 2 * NT;
     extern __shared__ __align__(128) uint8_t usm[];
@@ -567,9 +513,7 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
     t.steps = a.steps;
     t.k = a.k;
     t.wait_ns = a.wait_ns;
-    t.early_exit = a.early_exit;
     t.err = a.err;
-    t.steps_out = at(a.steps_out, 1);
     t.d_out = at(a.d_out, n);
     t.E_out = at(a.E_out, 1);
     t.run_out = at(a.run_out, 1);
@@ -578,7 +522,7 @@ __global__ void __launch_bounds__(128) cac_solve_umma_kernel(SolveArgs a, int ru
     t.guess_out = nullptr;
     t.sym_out = at(a.sym_out, NT);
     t.mod_bits = a.mod_bits;
-    umma_tile<NT, F, EE>(t, runs, usm);
+    umma_tile<NT, F>(t, runs, usm);
 }
 
 }  // namespace mmgap
