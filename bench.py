@@ -336,6 +336,60 @@ def secondary_measurements(ctx, dev, flush, steps: int = 5):
     return res
 
 
+def small_jobs_measurement(ctx, dev, flush, steps: int = 10, n_jobs: int = 96, seed: int = 11):
+    """Many small uplink jobs of uneven sizes (one OFDM symbol of 100-400
+    subcarriers each; 4, 8 or 16 users; QPSK to 64-QAM; PRB-held Kronecker or
+    i.i.d. channels), as a slot scheduler hands them over: the plain per-job
+    path (one mmgap_detect call over the job list: per job its factorisation,
+    builder and solver launches) against one batched launch replayed from a CUDA
+    graph.  Small grids leave most SMs idle per job; the batch fills the GPU
+    once.  Outputs must be equal."""
+    import torch
+
+    from paper_2510_01579_gb300 import Batch, Params
+    rng = np.random.default_rng(seed)
+    prm = Params.default()
+    keep, jobs, outs, total = [], [], [], 0
+    for i in range(n_jobs):
+        n_t = int(rng.choice([4, 8, 16]))
+        mb = int(rng.choice([2, 4, 6]))
+        n_sub = int(rng.integers(100, 401))
+        model = str(rng.choice(["iid", "kron"]))
+        w = synth.uplink(7000 + i, n_t, n_t, mb, n_sub=n_sub, n_sym=1, snr_db=float(rng.uniform(8, 24)),
+                         model=model, hold="prb")
+        t = [torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index")]
+        o = {"sym": torch.empty((n_sub, n_t), dtype=torch.uint8, device=dev)}
+        keep += t + [o["sym"]]
+        outs.append(o)
+        jobs.append(ctx.detect_job(t[0], t[1], t[2], mb, 90 + i, o, t[3]))
+        total += n_sub
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(2):
+            flush.zero_()
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    per_job = timed(lambda: ctx.detect_jobs(jobs, prm))
+    ref = [o["sym"].clone() for o in outs]
+    with Batch(dev.index or 0, prm, jobs, keepalive=keep) as batch:
+        batched = timed(lambda: batch.run(use_graph=True))
+    same = all(torch.equal(o["sym"], r) for o, r in zip(outs, ref))
+    if not same:
+        raise RuntimeError("batched and per-job paths disagree on the small jobs")
+    return {"jobs": n_jobs, "problems": total, "per_job_ms": per_job, "batched_ms": batched,
+            "speedup_batched_vs_per_job": per_job / batched, "identical_results": same,
+            "batched_problems_per_s": total / (batched / 1e3)}
+
+
 def run_mixed(args):
     """Three slots of different sizes (16x16 16-QAM, 16x16 64-QAM, 8x8 QPSK):
     per-job path (one build + one solve launch per job) against one batched
@@ -395,7 +449,7 @@ def run_mixed(args):
             "batched_modes_ms": modes, "batched_mode": best,
             "per_job_path": {"ms_per_step": statistics.mean(per_job), "launches_per_step": 2 * len(jobs)},
             "speedup_batched_vs_per_job": statistics.mean(per_job) / ms, "gpu_launches": 2 * args.steps,
-            "clocks": clk}
+            "clocks": clk, "small_jobs": small_jobs_measurement(ctx, dev, flush, steps=args.steps)}
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -1554,6 +1608,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_secondary and args.workload == "ul16x16_16qam_slot":
         ctx.set_timing(False)
         secondary = secondary_measurements(ctx, dev, flush)
+        if not args.no_batch:
+            secondary["batched_small_jobs"] = small_jobs_measurement(ctx, dev, flush)
         ctx.set_timing(True)
 
     # roofline of the dominant kernel (the CIM-CAC solver), from the library's
