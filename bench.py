@@ -161,6 +161,17 @@ def max_over_ranks(x: float, device=None) -> float:
     return float(t.item())
 
 
+def gather_shards(p_lo: int, rows) -> np.ndarray:
+    """Concatenate every rank's shard rows (its first problem p_lo and its
+    result rows) in problem order; the identity without a process group."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return np.asarray(rows)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, (int(p_lo), np.asarray(rows)))
+    return np.concatenate([r for _, r in sorted(parts, key=lambda t: t[0])])
+
+
 def rank_seed(rank: int) -> int:
     """Each rank detects its own slot (own channels, symbols and noise)."""
     return 2025 + rank
@@ -1577,10 +1588,8 @@ def main():
     # the unsharded slot detected there
     split_check = None
     if split and world > 1:
-        parts = [None] * world
-        dist.all_gather_object(parts, (p_lo, sym))
+        gathered = gather_shards(p_lo, sym)
         if rank == 0:
-            gathered = np.concatenate([a for _, a in sorted(parts, key=lambda t: t[0])])
             whole = ctx.detect(torch.from_numpy(w_full["H"]).to(dev), torch.from_numpy(w_full["y"]).to(dev),
                                torch.from_numpy(w_full["noise_var"]).to(dev), mb, prm, 77,
                                chan_index=torch.from_numpy(w_full["chan_index"]).to(dev))

@@ -1,6 +1,7 @@
 """The benchmark's multi-rank path on CPU with gloo (world size 2): each rank
-detects its own slot (weak scaling, no collective on the data path) and the
-step time is the slowest rank's."""
+detects its own slot (weak scaling, no collective on the data path), the step
+time is the slowest rank's, and the --split slot gather puts the ranks' PRB
+shards back in problem order."""
 import os
 import socket
 
@@ -22,10 +23,16 @@ def _worker(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
+    from paper_2510_01579_gb300 import shard
     local = 10.0 + 5.0 * rank  # ms: rank 1 is the slow one
     m = bench.max_over_ranks(local)
     w = bench.make_workload("ul16x16_16qam_slot", bench.rank_seed(rank), n_sub=4)
-    q.put((rank, m, float(np.abs(w["y"]).sum())))
+    # the --split slot gather: each rank contributes the result rows of its PRB range; every rank
+    # gets them all back, ordered by first problem
+    sh = shard.shard_slot(np.repeat(np.arange(30), 2), 30, 2, world, rank)
+    rows = np.arange(sh["p0"], sh["p1"]) * 10
+    g = bench.gather_shards(sh["p0"], rows)
+    q.put((rank, m, float(np.abs(w["y"]).sum()), g.tolist()))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -43,6 +50,7 @@ def test_two_ranks_take_the_slowest_step_and_own_slots():
         assert p.exitcode == 0
     assert [r[1] for r in res] == [15.0, 15.0]
     assert res[0][2] != res[1][2]  # different slots per rank
+    assert res[0][3] == res[1][3] == list(range(0, 600, 10))  # shards gathered in problem order
 
 
 def test_single_process_is_identity():
