@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(128) cac_solve_kernel(SolveArgs a) {
         // refresh intervals one at a time, with the early-exit check before each K-th refresh
         const int K = a.early_exit;
         const int f = F > 0 ? F : a.f_mvm;
-        uint32_t prev[(N + 31) / 32];
-        signs_changed<N>(x, prev);
+        uint32_t prev[(N + 31) / 32] = {};
+        signs_changed<N>(x, prev);  // (records the initial signs)
         int c = K;
 #pragma unroll 1
         for (; t < S; t += f) {

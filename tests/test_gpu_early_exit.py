@@ -136,6 +136,43 @@ def test_early_exit_sampled_full_slot_16x16(mm):
     assert 0.05 < np.mean(s < 200) < 1.0
 
 
+@pytest.mark.parametrize("shape", [1, 3, 6])
+def test_early_exit_without_a_check_point_is_the_plain_call(mm, shape):
+    """steps = 0, or no check point before S: the outputs equal the call
+    without early exit, and every problem reports all S steps."""
+    pkg, ctx = mm
+    w = synth.uplink(77, 16, 16, 4, n_sub=6, n_sym=3, snr_db=15.0)
+    args = (T(w["H"]), T(w["y"]), T(w["noise_var"]), 4)
+    kw = dict(chan_index=T(w["chan_index"]), want_energy=True, want_offset=True, want_ndiv=True, want_steps=True)
+    ctx.set_solver_variant(16, shape)
+    try:
+        for steps, K in ((0, 2), (7, 4), (40, 20)):
+            a = ctx.detect(*args, pkg.Params.default(steps=steps), 3, **kw)
+            b = ctx.detect(*args, pkg.Params.default(steps=steps, early_exit=K), 3, **kw)
+            torch.cuda.synchronize()
+            for k in ("sym", "energy", "offset", "ndiv", "steps"):
+                assert torch.equal(a[k], b[k]), (steps, K, k)
+            assert bool((b["steps"] == steps).all())
+    finally:
+        ctx.set_solver_variant(16, 0)
+
+
+def test_mmgap_e_early_exit_bit_exact(mm):
+    """MMGaP-E's stages anneal with the same early-exit rule (both instances of
+    every stage), bit-exact against the oracle's detect_e under it."""
+    pkg, ctx = mm
+    w = synth.uplink(88, 8, 8, 6, n_sub=6, n_sym=2, snr_db=22.0, hold="problem")
+    prm = pkg.Params.default(steps=160, early_exit=3)
+    out = ctx.detect_e(T(w["H"]), T(w["y"]), T(w["noise_var"]), 6, prm, 17, stages=2,
+                       chan_index=T(w["chan_index"]), want_candidates=True)
+    torch.cuda.synchronize()
+    cands = out["candidates"].cpu().numpy()
+    for p in range(w["y"].shape[0]):
+        r = oracle.detect_e(w["H"][p], w["y"][p], w["noise_var"][p], 6, 2, oparams(prm), 17, p)
+        assert np.array_equal(cands[:, p, :], r["candidates"].astype(np.int8)), p
+        assert int(out["best"][p]) == r["best"] and np.array_equal(out["sym"][p].cpu().numpy(), r["sym"]), p
+
+
 def test_early_exit_refusals(mm):
     """Shapes and calls without early exit refuse K > 0 before launching."""
     pkg, ctx = mm
