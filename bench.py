@@ -14,6 +14,7 @@ the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -1339,7 +1340,8 @@ def main():
     ctx = Context(local, workspace_bytes=512 << 20)
     out = {"sym": torch.empty((P, n_t), dtype=torch.uint8, device=dev),
            "energy": torch.empty(P, dtype=torch.int32, device=dev),
-           "guess": torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev)}
+           "guess": torch.empty((P, 2 * n_t), dtype=torch.int8, device=dev),
+           "ndiv": torch.empty(P, dtype=torch.int32, device=dev)}
     job = ctx.detect_job(H, y, nv, mb, 77, out, ci, problem_offset=p_lo)
     if args.variant >= 0:
         ctx.set_solver_variant(n_t, args.variant)
@@ -1667,6 +1669,9 @@ def main():
             "slot_latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "max": max(step_ms)},
             "stage_ms": {"build": statistics.mean(build_ms), "solve": solve_avg},
             "ber": {"mmgap": ber, "mmse": ber_mmse},
+            # anneals that diverged (non-finite, |x| > x_max or e <= 0) over the slot, and a hash that
+            # identifies the configuration of the line
+            "diverged_anneals": int(out["ndiv"].sum().item()),
             "solver_shape": {"chosen": VARIANT_NAMES[variant], "autotune_ms": tune_ms},
             "plain_path": plain,
             "tensor_core_refresh": tc,
@@ -1677,6 +1682,7 @@ def main():
             # factor kernels) once when channels serve several problems (as here: H per subcarrier or PRB)
             "gpu_launches": 2 * chunks + (2 * args.steps if w["H"].shape[0] < P else 0), "clocks": clk,
             "wall_s": wall}
+    line["config_hash"] = hashlib.sha256(json.dumps(line["config"], sort_keys=True).encode()).hexdigest()[:16]
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
