@@ -674,7 +674,7 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
         if (!gc && !J.guess_in && J.chan_index && J.n_chan < J.n_problems) {
             const size_t nc = (size_t)J.n_chan;
             const size_t lb = align_up(nc * 2 * J.n_t * J.n_t * sizeof(float)), rb = align_up(nc * 4);
-            if (gc_bytes + lb + 3 * rb + per + 3 * kAlign <= ctx->ws_bytes) {
+            if (gc_bytes + 2 * lb + 3 * rb + per + 3 * kAlign <= ctx->ws_bytes) {
                 char* fb = ctx->ws + gc_bytes;
                 ChanFactorArgs f{};
                 f.H = J.H;
@@ -688,12 +688,14 @@ mmgap_status mmgap_detect(mmgap_ctx* ctx, const mmgap_params* params, const mmga
                 f.rho_out = (float*)(fb + lb);
                 f.chol_out = (int32_t*)(fb + lb + rb);
                 f.first = (int32_t*)(fb + lb + 2 * rb);
+                f.G_out = (float*)(fb + lb + 3 * rb);
                 cudaError_t e = dispatch_nt<OpFactor>(J.n_t, f, s);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "chan_factor launch");
                 L_pre = f.L_out;
                 rho_pre = f.rho_out;
                 chol_pre = f.chol_out;
-                fac_bytes = lb + 3 * rb;
+                gc = f.G_out;  // each channel's Gram, made once (read by channel index, as the tensor-core Gram)
+                fac_bytes = 2 * lb + 3 * rb;
             }
         }
         char* base = ctx->ws + gc_bytes + fac_bytes;

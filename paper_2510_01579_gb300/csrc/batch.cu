@@ -110,7 +110,7 @@ size_t BatchRunner::precode_scratch_bytes(const mmgap_precode_job& J) {
 
 size_t BatchRunner::factor_bytes(int n_t, int n_chan) {
     const size_t nc = (size_t)std::max(0, n_chan);
-    return salign(nc * 2 * n_t * n_t * sizeof(float)) + 3 * salign(nc * 4);
+    return 2 * salign(nc * 2 * n_t * n_t * sizeof(float)) + 3 * salign(nc * 4);
 }
 
 size_t BatchRunner::scratch_bytes(int n_t, int n_problems) {
@@ -345,6 +345,8 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
         f.rho_out = (float*)(base + lb);
         f.chol_out = (int32_t*)(base + lb + rb);
         f.first = (int32_t*)(base + lb + 2 * rb);
+        f.G_out = (float*)(base + lb + 3 * rb);
+        B.Gc_pre = f.G_out;
         B.L_pre = f.L_out;
         B.rho_pre = f.rho_out;
         B.chol_pre = f.chol_out;

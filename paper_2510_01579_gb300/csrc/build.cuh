@@ -418,6 +418,10 @@ __global__ void __launch_bounds__(kBuildWarps * 32) chan_factor_kernel(ChanFacto
     __syncwarp();
     gram_mf_warp<NT>(Hs, yv, n_r, Gc, mv, 0, NT * NT, lane);
     __syncwarp();
+    if (a.G_out) {  // the channel's Gram, for every problem of the channel (the same function, the same bits)
+        float* Gg = a.G_out + (size_t)c * 2 * NT * NT;
+        for (int e = lane; e < 2 * NT * NT; e += 32) Gg[e] = Gc[e];
+    }
     const float rho = mulrn(a.noise_var[p0], a.kappa2);
     cholesky_warp<NT>(Gc, rho, false, Lc, flag, perm, dg, lane);
     float* Lg = a.L_out + (size_t)c * 2 * NT * NT;

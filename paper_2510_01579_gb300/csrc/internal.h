@@ -137,6 +137,7 @@ struct ChanFactorArgs {
     float* L_out;              // complex [n_chan][n_t][n_t]
     float* rho_out;            // [n_chan] (NaN for a channel no problem uses)
     int32_t* chol_out;         // [n_chan] 1 if a pivot failed
+    float* G_out;              // complex [n_chan][n_t][n_t]: the Gram of kappa H (the builder's Gc_pre), or nullptr
 };
 
 // Direct (binary-weighted) spin mapping: the delta build's MMSE guess, Gram
