@@ -68,6 +68,17 @@ def solver_flops(P: int, n_t: int, runs: int, steps: int, f_mvm: int) -> float:
     return float(P) * runs * (refresh * (2 * n * n + 9 * n) + 9 * N * steps)
 
 
+def solver_fp32_ops(P: int, n_t: int, runs: int, steps: int, f_mvm: int) -> float:
+    """FP32 pipe operations of the anneals, every FMA, MUL and ADD counted once
+    (the FP32 pipe takes one lane-operation of either kind per lane and cycle):
+    per anneal ceil(S/f) (n^2 + 5n) for the refreshes (u, m = A u, b^T u, c,
+    mu1, mu2) and 6 per spin-step for the Euler updates."""
+    n = 2 * n_t
+    N = 2 * n + 1
+    refresh = math.ceil(steps / f_mvm) if steps else 0
+    return float(P) * runs * (refresh * (n * n + 5 * n) + 6 * N * steps)
+
+
 def solver_flops_survey(P: int, n_t: int, runs: int, steps: int, f_mvm: int) -> float:
     """The per-problem work estimate R S [(2n^2 + 8n)/f + 14 N] + R (2n^2 + 2n)
     (half-size refresh every f steps, about 14 flops per spin-step, one
@@ -1644,6 +1655,10 @@ def main():
                 "ceil(S/f) (2n^2 + 9n) + 9 (2n+1) S",
                 "flops_per_launch_survey_formula": flops_survey,
                 "frac_survey_formula": flops_survey / (solve_avg / 1e3) / 1e12 / peak,
+                # the FP32 pipe's own capacity: one lane-operation (FMA, MUL or ADD) per lane and cycle
+                "fp32_ops_per_launch": solver_fp32_ops(P, n_t, args.runs, args.solver_steps, args.f_mvm),
+                "frac_fp32_pipe": solver_fp32_ops(P, n_t, args.runs, args.solver_steps, args.f_mvm) /
+                (solve_avg / 1e3) / (pk["peak_tflops"] * 1e12 / 2),
                 "algorithmic_bytes_per_launch": solver_bytes(P, n_t), "avg_launch_ms": solve_avg}
 
     cpu = None
