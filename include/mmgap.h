@@ -72,8 +72,10 @@ typedef enum {
  *   selection proceeds as usual.  Results stay bit-exact with the CPU oracle
  *   under the same rule.  Supported by mmgap_detect (delta mapping, up to 16
  *   users, the bit-identical solver shapes), mmgap_detect_e, mmgap_precode,
- *   mmgap_solve_ising (n <= 32) and mmgap_detect_static; the other calls and
- *   the tensor-core shapes 5, 7 and 8 return MMGAP_EUNSUPPORTED when K > 0.
+ *   mmgap_solve_ising (n <= 32), mmgap_detect_static, the batched launch and
+ *   the server (without MMGAP_BATCH_TENSOR_CORE / tensor_core, up to 16
+ *   users); the other calls and the tensor-core shapes 5, 7 and 8 return
+ *   MMGAP_EUNSUPPORTED when K > 0.
  */
 typedef struct {
     int32_t runs;
@@ -114,9 +116,7 @@ typedef struct {
  *   offset_out: int8 [n_problems][2 n_t] selected offset d in {-1, 0, 1}
  *   ndiv_out:   int32 [n_problems] diverged anneals
  *   steps_out:  int32 [n_problems] Euler steps the problem's anneals took
- *               (params->steps unless early exit stopped them); mmgap_detect
- *               and mmgap_detect_static only (the batch and the server
- *               refuse it)
+ *               (params->steps unless early exit stopped them)
  * guess_in: int8 [n_problems][2 n_t] (re block, im block) lattice guess that
  *   replaces the MMSE guess (Sec. 3.2: the guess is an input of the
  *   pre-processing); NULL = MMSE.  Each entry must be an alphabet point, odd

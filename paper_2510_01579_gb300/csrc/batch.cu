@@ -35,17 +35,20 @@ int build_floats_for(int nt, int n_r) {
 }
 
 template <int NTMAX>
-const void* solve_ptr(int f, bool tc) {
+const void* solve_ptr(int f, bool tc, bool ee) {
     if (tc)  // tcgen05 tiles of 4 problems (solver shape 8)
         return f == 1 ? (const void*)batch_solve_umma_kernel<NTMAX, 1> : (const void*)batch_solve_umma_kernel<NTMAX, 2>;
+    if (ee)  // the early-exit rule of the per-job solver
+        return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1, true>
+                      : (const void*)batch_solve_grid_kernel<NTMAX, 2, true>;
     return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1> : (const void*)batch_solve_grid_kernel<NTMAX, 2>;
 }
 
-const void* pick_solve(int ntmax, int f, bool tc) {
+const void* pick_solve(int ntmax, int f, bool tc, bool ee = false) {
     switch (ntmax) {
-    case 16: return solve_ptr<16>(f, tc);
-    case 8: return solve_ptr<8>(f, tc);
-    default: return solve_ptr<4>(f, tc);
+    case 16: return solve_ptr<16>(f, tc, ee);
+    case 8: return solve_ptr<8>(f, tc, ee);
+    default: return solve_ptr<4>(f, tc, ee);
     }
 }
 
@@ -72,7 +75,16 @@ const char* BatchRunner::check_params(const mmgap_params& P) {
     if (P.runs != 32) return "batched launch runs 32 anneals per problem (one warp)";
     if (P.f_mvm != 1 && P.f_mvm != 2) return "batched launch supports f_mvm 1 or 2";
     if (P.steps < 0 || P.steps > (1 << 20) || !(P.dt > 0.0f) || !(P.x_max > 0.0f)) return "bad solver parameters";
-    if (P.early_exit != 0) return "batched launch runs every anneal for all steps (early_exit must be 0)";
+    if (P.early_exit < 0) return "early_exit must be >= 0";
+    return nullptr;
+}
+
+const char* BatchRunner::check_early_exit(const mmgap_params& P, const mmgap_detect_job* jobs, int n_jobs,
+                                          bool tensor_core) {
+    if (P.early_exit <= 0) return nullptr;
+    if (tensor_core) return "early exit runs on the exact solver, not the tcgen05 tiles";
+    for (int i = 0; i < n_jobs; ++i)
+        if (jobs[i].n_t == 32) return "early exit: up to 16 users (a 32-user job)";
     return nullptr;
 }
 
@@ -85,7 +97,6 @@ const char* BatchRunner::check_job(const mmgap_detect_job& J) {
     if (J.n_problems > 0 && !J.chan_index && J.n_chan < J.n_problems) return "chan_index NULL needs n_chan >= n";
     if (J.gram_precision != 0) return "batched launch builds the Gram in FP32 (gram_precision 0)";
     if (J.mapping != MMGAP_MAPPING_DELTA) return "batched launch uses the delta mapping";
-    if (J.steps_out) return "batched launch runs every anneal for all steps (steps_out must be NULL)";
     return nullptr;
 }
 
@@ -237,6 +248,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
             a.d_out = J.offset_out;
             a.E_out = J.energy_out;
             a.ndiv_out = J.ndiv_out;
+            a.steps_out = J.steps_out;
             a.sym_out = J.sym_out;
             a.mod_bits = J.mod_bits;
             W.guess_out = J.guess_out;
@@ -279,6 +291,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
             B.guess_out = J.guess_out;
             B.offset_out = J.offset_out;
             B.ndiv_out = J.ndiv_out;
+            B.steps_out = J.steps_out;
             first += J.n_problems;
             tiles += (J.n_problems + 3) / 4;
         } else {
@@ -478,6 +491,7 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     a.jobs = d_jobs_;
     a.head = d_head_;
     a.steps = P.steps;
+    a.early_exit = P.early_exit;
     a.k = batch_consts(P);
     a.build_floats = build_floats_;
     void* args[] = {&a};
@@ -486,7 +500,7 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3(bg), dim3(kBuildWarps * 32), args, build_smem_, s)) !=
         cudaSuccess)
         return e;
-    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, tc_), dim3(sg), dim3(solve_block()), args,
+    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, tc_, P.early_exit > 0), dim3(sg), dim3(solve_block()), args,
                             solve_smem(), s);
 }
 
@@ -549,7 +563,7 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         kb.kernelParams = args;
         if ((e = cudaGraphExecKernelNodeSetParams(exec_, build_node_, &kb)) != cudaSuccess) return e;
         cudaKernelNodeParams ks{};
-        ks.func = (void*)pick_solve(ntmax_, P.f_mvm, tc_);
+        ks.func = (void*)pick_solve(ntmax_, P.f_mvm, tc_, P.early_exit > 0);
         ks.gridDim = dim3(sg);
         ks.blockDim = dim3(solve_block());
         ks.sharedMemBytes = (unsigned)solve_smem();
@@ -579,6 +593,10 @@ mmgap_status mmgap_batch_create(mmgap_batch** out, int device, const mmgap_param
     if (flags & ~MMGAP_BATCH_TENSOR_CORE) {
         fprintf(stderr, "mmgap_batch_create: unknown flags 0x%x\n", (unsigned)flags);
         return MMGAP_EINVAL;
+    }
+    if (const char* why = BatchRunner::check_early_exit(*params, jobs, n_jobs, (flags & MMGAP_BATCH_TENSOR_CORE) != 0)) {
+        fprintf(stderr, "mmgap_batch_create: %s\n", why);
+        return MMGAP_EUNSUPPORTED;
     }
     if (BatchRunner::check_params(*params)) {
         fprintf(stderr, "mmgap_batch_create: %s\n", BatchRunner::check_params(*params));

@@ -24,6 +24,9 @@ class BatchRunner {
     static const char* check_params(const mmgap_params& P);
     static const char* check_job(const mmgap_detect_job& J);
     static const char* check_precode(const mmgap_precode_job& J);
+    // Early exit (params.early_exit > 0) needs the exact solver and jobs of at most 16 users.
+    static const char* check_early_exit(const mmgap_params& P, const mmgap_detect_job* jobs, int n_jobs,
+                                        bool tensor_core);
 
     // Scratch bytes (Q14 couplings, field, guess) of one job.
     static size_t scratch_bytes(int n_t, int n_problems);

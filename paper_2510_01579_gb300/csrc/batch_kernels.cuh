@@ -34,6 +34,7 @@ struct BatchJob {
     int8_t* guess_out;
     int8_t* offset_out;
     int32_t* ndiv_out;
+    int32_t* steps_out;     // Euler steps each problem took, or nullptr
 };
 
 struct BatchHeader {
@@ -47,6 +48,7 @@ struct BatchArgs {
     const BatchJob* jobs;
     BatchHeader* head;
     int steps;
+    int early_exit;         // K > 0: the early-exit rule of the per-job solver (grid solver only)
     EulerConsts k;
     int build_floats;       // builder shared memory per warp (floats)
 };
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 8) batch_build_kernel(BatchA
 }
 
 // Anneal one problem already built into sm (Aq, hq, g) with one warp.
-template <int NT, int F>
+template <int NT, int F, bool EE = false>
 __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const BatchJob& J, int p, int lane,
                                                  SolveSmem<NT>& sm) {
     constexpr int n = 2 * NT;
@@ -128,9 +130,32 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
     }
     const int S = A.steps;
     int t = 0;
-    {
-        // 16 users: the paired refresh (faster there, same bits); fewer users: one anneal per lane
-        constexpr bool kPair = NT == 16;
+    // 16 users: the paired refresh (faster there, same bits); fewer users: one anneal per lane
+    constexpr bool kPair = NT == 16;
+    if constexpr (EE) {
+        // early exit, the per-job solver's rule: the problem is this warp, so one warp vote decides
+        const int K = A.early_exit;
+        uint32_t p1 = sign_word<n>(x1), p2 = sign_word<n>(x2);
+        bool pa = xa >= 0.0f;
+        int c = K;
+#pragma unroll 1
+        for (; t < S; t += F) {
+            if (t > 0 && --c == 0) {
+                c = K;
+                const uint32_t w1 = sign_word<n>(x1), w2 = sign_word<n>(x2);
+                const bool wa = xa >= 0.0f;
+                const bool changed = (w1 != p1) || (w2 != p2) || (wa != pa);
+                p1 = w1;
+                p2 = w2;
+                pa = wa;
+                if (!__any_sync(0xffffffffu, changed)) break;
+            }
+            if (t + F <= S)
+                tuned_block<n, n, 1, true, F, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, F, k);
+            else
+                tuned_block<n, n, 1, true, 0, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, S - t, k);
+        }
+    } else {
 #pragma unroll 1
         for (; t + F <= S; t += F)
             tuned_block<n, n, 1, true, F, kPair>(sm.A, sm.h, sm.nd, x1, x2, e1, e2, xa, ea, 0, lane, F, k);
@@ -176,6 +201,7 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
         const int bestE = (int)((key - (long long)best_run) / 4294967296LL);
         if (J.energy_out) J.energy_out[p] = bestE;
         if (J.ndiv_out) J.ndiv_out[p] = ndiv;
+        if (J.steps_out) J.steps_out[p] = EE && t < S ? t : S;
         if (J.offset_out) {
 #pragma unroll
             for (int i = 0; i < n; ++i) J.offset_out[(size_t)p * n + i] = keep ? (int8_t)d[i] : (int8_t)0;
@@ -198,7 +224,7 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
     __syncwarp();  // the warp's shared memory is reused by its next problem
 }
 
-template <int NT, int F>
+template <int NT, int F, bool EE = false>
 __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const BatchJob& J, int p, int lane,
                                                     unsigned char* solve_mem) {
     constexpr int n = 2 * NT;
@@ -210,12 +236,12 @@ __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const Ba
         sm.g[i] = J.g ? J.g[(size_t)p * n + i] : (int8_t)0;
     }
     __syncwarp();
-    batch_solve_warp<NT, F>(A, J, p, lane, sm);
+    batch_solve_warp<NT, F, EE>(A, J, p, lane, sm);
 }
 
 // Grid solver over the batch: one 32-thread CTA per problem (the hardware
 // CTA scheduler balances sizes); CTAs past the staged total exit.
-template <int NTMAX, int F>
+template <int NTMAX, int F, bool EE = false>
 __global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
     __shared__ __align__(16) unsigned char ssm[batch_solve_bytes<NTMAX>()];
     const long long w = blockIdx.x;
@@ -224,11 +250,11 @@ __global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
     const int p = (int)(w - J.first);
     const int lane = threadIdx.x;
     if (J.nt == 16) {
-        if constexpr (NTMAX >= 16) batch_solve_problem<16, F>(A, J, p, lane, ssm);
+        if constexpr (NTMAX >= 16) batch_solve_problem<16, F, EE>(A, J, p, lane, ssm);
     } else if (J.nt == 8) {
-        if constexpr (NTMAX >= 8) batch_solve_problem<8, F>(A, J, p, lane, ssm);
+        if constexpr (NTMAX >= 8) batch_solve_problem<8, F, EE>(A, J, p, lane, ssm);
     } else {
-        batch_solve_problem<4, F>(A, J, p, lane, ssm);
+        batch_solve_problem<4, F, EE>(A, J, p, lane, ssm);
     }
 }
 

@@ -213,6 +213,10 @@ mmgap_status mmgap_server_create(mmgap_server** out, int device, const mmgap_par
         fprintf(stderr, "mmgap_server_create: %s\n", BatchRunner::check_params(*params));
         return MMGAP_EUNSUPPORTED;
     }
+    if (const char* why = BatchRunner::check_early_exit(*params, nullptr, 0, cfg->tensor_core != 0)) {
+        fprintf(stderr, "mmgap_server_create: %s\n", why);
+        return MMGAP_EUNSUPPORTED;
+    }
     if (cfg->n_lanes < 1 || cfg->n_lanes > 16 || cfg->scratch_bytes == 0 || cfg->max_jobs_per_group < 1 ||
         cfg->max_problems_per_group < 1 || cfg->max_n_r < 1 || cfg->max_n_r > 64 ||
         !(cfg->max_n_t == 4 || cfg->max_n_t == 8 || cfg->max_n_t == 16 || cfg->max_n_t == 32))
@@ -263,6 +267,10 @@ mmgap_status mmgap_server_create(mmgap_server** out, int device, const mmgap_par
 mmgap_status mmgap_server_submit(mmgap_server* s, const mmgap_detect_job* job, uint64_t* ticket) {
     if (!s || !job || !ticket) return MMGAP_EINVAL;
     if (const char* why = BatchRunner::check_job(*job)) {
+        fprintf(stderr, "mmgap_server_submit: %s\n", why);
+        return MMGAP_EUNSUPPORTED;
+    }
+    if (const char* why = BatchRunner::check_early_exit(s->params, job, 1, false)) {
         fprintf(stderr, "mmgap_server_submit: %s\n", why);
         return MMGAP_EUNSUPPORTED;
     }

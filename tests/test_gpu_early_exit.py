@@ -196,10 +196,60 @@ def test_early_exit_refusals(mm):
     with pytest.raises(pkg.MMGaPError) as e:
         ctx.anneal_spins(T(A), T(h), prm, 1)
     assert e.value.status == 5
-    o = {"sym": torch.empty((w["y"].shape[0], 16), dtype=torch.uint8, device=DEV)}
-    job = ctx.detect_job(T(w["H"]), T(w["y"]), T(w["noise_var"]), 4, 1, o, T(w["chan_index"]))
-    with pytest.raises(pkg.MMGaPError):
-        pkg.Batch(0, prm, [job])
     with pytest.raises(pkg.MMGaPError) as e:
         ctx.detect(*args[:4], pkg.Params.default(early_exit=-1), 1, chan_index=T(w["chan_index"]))
     assert e.value.status == 1
+
+
+def test_batch_and_server_early_exit_equal_the_per_job_path(mm):
+    """The batched launch and the server anneal with the same early-exit rule:
+    every job's symbols, energies, divergence counts and steps equal the
+    per-job call's, across 4-, 8- and 16-user jobs."""
+    pkg, ctx = mm
+    prm = pkg.Params.default(steps=160, early_exit=3)
+    specs = [(16, 4, 20, "subcarrier"), (8, 2, 36, "prb"), (4, 6, 30, "problem"), (8, 4, 24, "subcarrier")]
+    keep, jobs, outs, refs = [], [], [], []
+    for i, (nt, mb, n_sub, hold) in enumerate(specs):
+        w = synth.uplink(150 + i, nt, nt, mb, n_sub=n_sub, n_sym=4, snr_db=14.0, model="kron", hold=hold)
+        t = [T(w[k]) for k in ("H", "y", "noise_var", "chan_index")]
+        P = w["y"].shape[0]
+
+        def outs_of():
+            return {"sym": torch.full((P, nt), 255, dtype=torch.uint8, device=DEV),
+                    "energy": torch.full((P,), 3, dtype=torch.int32, device=DEV),
+                    "ndiv": torch.full((P,), -1, dtype=torch.int32, device=DEV),
+                    "steps": torch.full((P,), -1, dtype=torch.int32, device=DEV)}
+        r = outs_of()
+        ctx.detect_jobs([ctx.detect_job(t[0], t[1], t[2], mb, 20 + i, r, t[3])], prm)
+        o = outs_of()
+        keep.append(t)
+        outs.append(o)
+        refs.append(r)
+        jobs.append(ctx.detect_job(t[0], t[1], t[2], mb, 20 + i, o, t[3]))
+    torch.cuda.synchronize()
+    assert any(bool((r["steps"] < 160).any()) for r in refs)
+    with pkg.Batch(0, prm, jobs, keepalive=(keep, outs)) as b:
+        b.run(use_graph=True)
+        torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        for k in o:
+            assert torch.equal(o[k], r[k]), k
+    for o in outs:
+        for v in o.values():
+            v.fill_(-7)
+    with pkg.Server(0, prm, scratch_bytes=32 << 20, n_lanes=2, max_jobs_per_group=2) as srv:
+        for tk in [srv.submit(j) for j in jobs]:
+            srv.wait(tk, timeout_us=60_000_000)
+    for o, r in zip(outs, refs):
+        for k in o:
+            assert torch.equal(o[k], r[k]), k
+    # refused: the tcgen05 tiles, and a 32-user job
+    with pytest.raises(pkg.MMGaPError):
+        pkg.Batch(0, prm, jobs[:1], tensor_core=True)
+    with pytest.raises(pkg.MMGaPError):
+        pkg.Server(0, prm, tensor_core=True)
+    w32 = synth.uplink(160, 32, 32, 4, n_sub=1, n_sym=2)
+    o32 = {"sym": torch.empty((2, 32), dtype=torch.uint8, device=DEV)}
+    t32 = [T(w32[k]) for k in ("H", "y", "noise_var", "chan_index")]
+    with pytest.raises(pkg.MMGaPError):
+        pkg.Batch(0, prm, [ctx.detect_job(t32[0], t32[1], t32[2], 4, 1, o32, t32[3])])
