@@ -52,9 +52,11 @@ def test_static_scratch_matches_context_path_two_calls_in_a_row():
             torch.cuda.synchronize()
             for k in ref:
                 assert torch.equal(got[k], ref[k]), (i, k)
-            # the same call again: same bits, and no device memory taken
-            free0 = torch.cuda.mem_get_info(DEV)[0]
+            # the same call again: same bits, and no device memory taken (the outputs are allocated
+            # before the free memory is read)
             again = _outputs(P, n_t)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info(DEV)[0]
             ctx.detect_static(ctx.detect_job(H, y, nv, w["mod_bits"], 900 + i, again, ci), prm)
             torch.cuda.synchronize()
             assert torch.cuda.mem_get_info(DEV)[0] == free0, i
