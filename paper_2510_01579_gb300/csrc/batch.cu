@@ -511,6 +511,14 @@ cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_gra
     if (e != cudaSuccess) return e;
     if ((e = wide_before(P, s)) != cudaSuccess) return e;
     if (h_head_->n_jobs > 0 && (e = run_batch(P, s, use_graph)) != cudaSuccess) return e;
+    if (P.early_exit <= 0) {  // every problem of the table's jobs took all the steps
+        for (int j = 0; j < h_head_->n_jobs; ++j) {
+            const BatchJob& B = h_jobs_[j];
+            if (!B.steps_out || B.b.n_problems <= 0) continue;
+            fill_steps_kernel<<<(B.b.n_problems + 255) / 256, 256, 0, s>>>(B.steps_out, B.b.n_problems, P.steps);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
     return precode_after(s);
 }
 

@@ -201,7 +201,9 @@ __device__ __forceinline__ void batch_solve_warp(const BatchArgs& A, const Batch
         const int bestE = (int)((key - (long long)best_run) / 4294967296LL);
         if (J.energy_out) J.energy_out[p] = bestE;
         if (J.ndiv_out) J.ndiv_out[p] = ndiv;
-        if (J.steps_out) J.steps_out[p] = EE && t < S ? t : S;
+        if constexpr (EE) {  // (without early exit the runner fills steps_out with S)
+            if (J.steps_out) J.steps_out[p] = t < S ? t : S;
+        }
         if (J.offset_out) {
 #pragma unroll
             for (int i = 0; i < n; ++i) J.offset_out[(size_t)p * n + i] = keep ? (int8_t)d[i] : (int8_t)0;
