@@ -154,12 +154,6 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
     if ((e = cudaFuncSetAttribute(pick_build(ntmax), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem_)) !=
         cudaSuccess)
         return e;
-    int sms = 0, bper_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bper_sm, pick_build(ntmax), kBuildWarps * 32,
-                                                           build_smem_)) != cudaSuccess)
-        return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
-    build_grid_max_ = std::max(1, bper_sm) * sms;
     if (tc_) {
         // the tiles resident on an SM share its 512 TMEM columns (128 per 16-user tile, 64 per
         // 8-user tile): pad shared memory so that no more of them fit
@@ -470,7 +464,7 @@ cudaError_t BatchRunner::precode_after(cudaStream_t s) {
 void BatchRunner::grids(unsigned* build_grid, unsigned* solve_grid) const {
     const long long total = h_head_ ? h_head_->total : capacity_problems_;
     const long long bb = (std::max(1LL, total) + kBuildWarps - 1) / kBuildWarps;
-    *build_grid = (unsigned)std::min<long long>(bb, build_grid_max_);
+    *build_grid = (unsigned)bb;  // one warp per problem
     if (tc_) {  // tiles of 4 problems, at most one partial tile per job
         const long long tiles = h_head_ ? h_head_->tiles : (capacity_problems_ + 3) / 4 + capacity_;
         *solve_grid = (unsigned)std::max(1LL, tiles);

@@ -89,7 +89,7 @@ class BatchRunner {
     void grids(unsigned* build_grid, unsigned* solve_grid) const;
     unsigned solve_block() const { return tc_ ? 128u : 32u; }
     size_t solve_smem() const { return tc_ ? umma_smem_ : 0; }
-    int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0, build_grid_max_ = 1;
+    int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0;
     bool tc_ = false;  // tcgen05 field refresh for 8 and 16 users (4-problem tiles)
     size_t umma_smem_ = 0;  // dynamic shared memory of the tcgen05 solver
     long long capacity_problems_ = 0;

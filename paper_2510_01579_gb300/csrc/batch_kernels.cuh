@@ -68,31 +68,40 @@ __device__ __forceinline__ int batch_find_job(const BatchJob* jobs, int n_jobs, 
     return lo;
 }
 
-// Builder over the whole batch: warp w of the grid builds problem w.
+// Builder over the whole batch: warp w of the grid builds problem w, as the
+// per-job builder does.  The job's arguments are staged in shared memory and
+// read from there: unlike a reference into the job table, they cannot alias the
+// builder's global stores, and unlike a register copy they cost no registers
+// (the per-job builder reads them from the kernel parameters).
 template <int NTMAX>
-__global__ void __launch_bounds__(kBuildWarps * 32, 8) batch_build_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(kBuildWarps * 32) batch_build_kernel(BatchArgs A) {
     extern __shared__ __align__(16) float bws[];
+    __shared__ __align__(16) BuildArgs sargs[kBuildWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long total = A.head->total;
-    const int n_jobs = A.head->n_jobs;
-    float* ws = bws + warp * A.build_floats;
-    for (long long w = (long long)blockIdx.x * kBuildWarps + warp; w < total;
-         w += (long long)gridDim.x * kBuildWarps) {
-        const BatchJob& J = A.jobs[batch_find_job(A.jobs, n_jobs, w)];
-        if (J.kind != 0) continue;  // built before the batch
-        const int p = (int)(w - J.first);
-        const int n = 2 * J.nt;
-        BuildOut o{J.Aq + (size_t)p * n * n, J.hq + (size_t)p * n, J.g + (size_t)p * n, nullptr, nullptr, nullptr};
-        // a register copy of the job's arguments: read through the reference, every field would be
-        // reloaded from global memory after each of the builder's global stores
-        const BuildArgs b = J.b;
-        if (J.nt == 16) {
-            if constexpr (NTMAX >= 16) build_problem_warp<16>(b, p, lane, ws, o);
-        } else if (J.nt == 8) {
-            if constexpr (NTMAX >= 8) build_problem_warp<8>(b, p, lane, ws, o);
-        } else {
-            build_problem_warp<4>(b, p, lane, ws, o);
-        }
+    const long long w = (long long)blockIdx.x * kBuildWarps + warp;
+    if (w >= A.head->total) return;  // warp-uniform; no block-wide barrier below
+    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
+    if (J.kind != 0) return;  // built before the batch
+    static_assert(sizeof(BuildArgs) % 4 == 0, "copied as words");
+    const int* src = reinterpret_cast<const int*>(&J.b);
+    int* dst = reinterpret_cast<int*>(&sargs[warp]);
+    for (int i = lane; i < (int)(sizeof(BuildArgs) / 4); i += 32) dst[i] = src[i];
+    __syncwarp();
+    const BuildArgs& b = sargs[warp];
+    const int p = (int)(w - J.first);
+    const int nt = J.nt, n = 2 * nt;
+    BuildOut o{J.Aq + (size_t)p * n * n, J.hq + (size_t)p * n, J.g + (size_t)p * n, nullptr, nullptr, nullptr};
+    // the host rounds the stride to 4 floats; saying so lets the compiler vectorise the
+    // builder's shared-memory accesses as in the per-job builder (there the stride is a
+    // compile-time multiple of 4): with an unknown alignment every access is split into
+    // 4-byte loads
+    float* ws = bws + warp * (A.build_floats & ~3);
+    if (nt == 16) {
+        if constexpr (NTMAX >= 16) build_problem_warp<16>(b, p, lane, ws, o);
+    } else if (nt == 8) {
+        if constexpr (NTMAX >= 8) build_problem_warp<8>(b, p, lane, ws, o);
+    } else {
+        build_problem_warp<4>(b, p, lane, ws, o);
     }
 }
 
