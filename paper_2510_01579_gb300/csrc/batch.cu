@@ -146,7 +146,6 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
     scratch_bytes_ = scratch;
     cudaError_t e;
     if ((e = cudaMalloc(&d_jobs_, sizeof(BatchJob) * (size_t)std::max(1, capacity_jobs))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&d_head_, sizeof(BatchHeader))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&scratch_, std::max<size_t>(scratch, 256))) != cudaSuccess) return e;
     if ((e = cudaMallocHost(&h_jobs_, sizeof(BatchJob) * (size_t)std::max(1, capacity_jobs))) != cudaSuccess)
         return e;
@@ -179,7 +178,6 @@ void BatchRunner::release() {
     if (exec_) cudaGraphExecDestroy(exec_);
     if (graph_) cudaGraphDestroy(graph_);
     if (d_jobs_) cudaFree(d_jobs_);
-    if (d_head_) cudaFree(d_head_);
     if (scratch_) cudaFree(scratch_);
     scratch_ = nullptr;
     if (h_jobs_) cudaFreeHost(h_jobs_);
@@ -187,7 +185,7 @@ void BatchRunner::release() {
     exec_ = nullptr;
     graph_ = nullptr;
     d_jobs_ = h_jobs_ = nullptr;
-    d_head_ = h_head_ = nullptr;
+    h_head_ = nullptr;
 }
 
 int BatchRunner::stage(const mmgap_detect_job* jobs, const int* order, int n_jobs) {
@@ -478,12 +476,12 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     if ((e = cudaMemcpyAsync(d_jobs_, h_jobs_, sizeof(BatchJob) * (size_t)std::max(1, capacity_),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;
-    if ((e = cudaMemcpyAsync(d_head_, h_head_, sizeof(BatchHeader), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return e;
     BatchArgs& a = args_;
     a = BatchArgs{};
     a.jobs = d_jobs_;
-    a.head = d_head_;
+    a.n_jobs = h_head_->n_jobs;
+    a.total = h_head_->total;
+    a.tiles = h_head_->tiles;
     a.steps = P.steps;
     a.early_exit = P.early_exit;
     a.k = batch_consts(P);
@@ -553,9 +551,12 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         }
         if (!build_node_ || !solve_node_) return cudaErrorInvalidValue;
     } else {
-        // grids follow the staged total; the kernel arguments are unchanged
+        // grids and counts follow the staged header; the other kernel arguments are unchanged
         unsigned bg, sg;
         grids(&bg, &sg);
+        args_.n_jobs = h_head_->n_jobs;
+        args_.total = h_head_->total;
+        args_.tiles = h_head_->tiles;
         void* args[] = {&args_};
         cudaKernelNodeParams kb{};
         kb.func = (void*)pick_build(ntmax_);

@@ -98,7 +98,6 @@ class BatchRunner {
     int* err_word_ = nullptr;
     BatchJob* d_jobs_ = nullptr;
     BatchJob* h_jobs_ = nullptr;
-    BatchHeader* d_head_ = nullptr;
     BatchHeader* h_head_ = nullptr;
     cudaStream_t cap_stream_ = nullptr;
     cudaGraph_t graph_ = nullptr;

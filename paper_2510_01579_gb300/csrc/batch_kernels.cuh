@@ -46,7 +46,11 @@ struct BatchHeader {
 
 struct BatchArgs {
     const BatchJob* jobs;
-    BatchHeader* head;
+    // the staged header's counts, as kernel arguments (a graph replay updates them with the grids):
+    // read from the constant bank, they add no dependent load ahead of each warp's job lookup
+    int n_jobs;
+    long long total;
+    long long tiles;
     int steps;
     int early_exit;         // K > 0: the early-exit rule of the per-job solver (grid solver only)
     EulerConsts k;
@@ -79,8 +83,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) batch_build_kernel(BatchArgs
     __shared__ __align__(16) BuildArgs sargs[kBuildWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long w = (long long)blockIdx.x * kBuildWarps + warp;
-    if (w >= A.head->total) return;  // warp-uniform; no block-wide barrier below
-    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
+    if (w >= A.total) return;  // warp-uniform; no block-wide barrier below
+    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.n_jobs, w)];
     if (J.kind != 0) return;  // built before the batch
     static_assert(sizeof(BuildArgs) % 4 == 0, "copied as words");
     const int* src = reinterpret_cast<const int*>(&J.b);
@@ -256,8 +260,8 @@ template <int NTMAX, int F, bool EE = false>
 __global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
     __shared__ __align__(16) unsigned char ssm[batch_solve_bytes<NTMAX>()];
     const long long w = blockIdx.x;
-    if (w >= A.head->total) return;
-    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.head->n_jobs, w)];
+    if (w >= A.total) return;
+    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.n_jobs, w)];
     const int p = (int)(w - J.first);
     const int lane = threadIdx.x;
     if (J.nt == 16) {
@@ -284,8 +288,8 @@ template <int NTMAX, int F>
 __global__ void __launch_bounds__(128) batch_solve_umma_kernel(BatchArgs A) {
     extern __shared__ __align__(128) uint8_t usm[];
     const long long t = blockIdx.x;
-    if (t >= A.head->tiles) return;
-    int lo = 0, hi = A.head->n_jobs - 1;  // last job whose tiles start at or before t
+    if (t >= A.tiles) return;
+    int lo = 0, hi = A.n_jobs - 1;  // last job whose tiles start at or before t
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (A.jobs[mid].tile_first <= t) lo = mid;
