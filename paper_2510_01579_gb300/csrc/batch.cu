@@ -34,21 +34,36 @@ int build_floats_for(int nt, int n_r) {
     }
 }
 
-template <int NTMAX>
-const void* solve_ptr(int f, bool tc, bool ee) {
-    if (tc)  // tcgen05 tiles of 4 problems (solver shape 8)
-        return f == 1 ? (const void*)batch_solve_umma_kernel<NTMAX, 1> : (const void*)batch_solve_umma_kernel<NTMAX, 2>;
-    if (ee)  // the early-exit rule of the per-job solver
-        return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1, true>
-                      : (const void*)batch_solve_grid_kernel<NTMAX, 2, true>;
-    return f == 1 ? (const void*)batch_solve_grid_kernel<NTMAX, 1> : (const void*)batch_solve_grid_kernel<NTMAX, 2>;
+// tcgen05 tiles of 4 problems (solver shape 8) over every size up to ntmax
+const void* umma_solve(int ntmax, int f) {
+    switch (ntmax) {
+    case 16: return f == 1 ? (const void*)batch_solve_umma_kernel<16, 1> : (const void*)batch_solve_umma_kernel<16, 2>;
+    case 8: return f == 1 ? (const void*)batch_solve_umma_kernel<8, 1> : (const void*)batch_solve_umma_kernel<8, 2>;
+    default: return f == 1 ? (const void*)batch_solve_umma_kernel<4, 1> : (const void*)batch_solve_umma_kernel<4, 2>;
+    }
 }
 
-const void* pick_solve(int ntmax, int f, bool tc, bool ee = false) {
+template <int NT>
+const void* class_solve_nt(int f, bool ee) {
+    if (ee)  // the early-exit rule of the per-job solver
+        return f == 1 ? (const void*)batch_solve_grid_kernel<NT, 1, true> : (const void*)batch_solve_grid_kernel<NT, 2, true>;
+    return f == 1 ? (const void*)batch_solve_grid_kernel<NT, 1> : (const void*)batch_solve_grid_kernel<NT, 2>;
+}
+
+// the grid solver of size class c (batch_class)
+const void* class_solve(int c, int f, bool ee) {
+    switch (c) {
+    case 0: return class_solve_nt<16>(f, ee);
+    case 1: return class_solve_nt<8>(f, ee);
+    default: return class_solve_nt<4>(f, ee);
+    }
+}
+
+const void* pick_factor(int ntmax) {
     switch (ntmax) {
-    case 16: return solve_ptr<16>(f, tc, ee);
-    case 8: return solve_ptr<8>(f, tc, ee);
-    default: return solve_ptr<4>(f, tc, ee);
+    case 16: return (const void*)batch_factor_kernel<16>;
+    case 8: return (const void*)batch_factor_kernel<8>;
+    default: return (const void*)batch_factor_kernel<4>;
     }
 }
 
@@ -151,7 +166,12 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
         return e;
     if ((e = cudaMallocHost(&h_head_, sizeof(BatchHeader))) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(pick_build(ntmax), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem_)) !=
-        cudaSuccess)
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(pick_factor(ntmax), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)build_smem_)) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&d_fac_, sizeof(FactorJob) * (size_t)std::max(1, capacity_jobs))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&h_fac_, sizeof(FactorJob) * (size_t)std::max(1, capacity_jobs))) != cudaSuccess)
         return e;
     if (tc_) {
         // the tiles resident on an SM share its 512 TMEM columns (128 per 16-user tile, 64 per
@@ -165,19 +185,34 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
         if (smem < floor_bytes) smem = (floor_bytes + 127) & ~(size_t)127;
         umma_smem_ = smem;
         for (int f : {1, 2})
-            if ((e = cudaFuncSetAttribute(pick_solve(ntmax, f, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if ((e = cudaFuncSetAttribute(umma_solve(ntmax, f), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem)) != cudaSuccess)
                 return e;
     }
-    return cudaSuccess;
+    for (int i = 0; i < 2; ++i)
+        if ((e = cudaStreamCreateWithFlags(&side_[i], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&join_[i], cudaEventDisableTiming)) != cudaSuccess)
+            return e;
+    return cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming);
 }
 
 void BatchRunner::release() {
     if (cap_stream_) cudaStreamDestroy(cap_stream_);
     cap_stream_ = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        if (side_[i]) cudaStreamDestroy(side_[i]);
+        if (join_[i]) cudaEventDestroy(join_[i]);
+        side_[i] = nullptr;
+        join_[i] = nullptr;
+    }
+    if (fork_) cudaEventDestroy(fork_);
+    fork_ = nullptr;
     if (exec_) cudaGraphExecDestroy(exec_);
     if (graph_) cudaGraphDestroy(graph_);
     if (d_jobs_) cudaFree(d_jobs_);
+    if (d_fac_) cudaFree(d_fac_);
+    if (h_fac_) cudaFreeHost(h_fac_);
+    d_fac_ = h_fac_ = nullptr;
     if (scratch_) cudaFree(scratch_);
     scratch_ = nullptr;
     if (h_jobs_) cudaFreeHost(h_jobs_);
@@ -199,12 +234,19 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
     if (n_jobs > capacity_) return -1;
     pre_.clear();
     wide_.clear();
+    // the table groups its jobs by size class (16, then 8, then 4 users; 32-user jobs stay outside
+    // it), so that each class's problems are contiguous for the class's solver kernel; within a
+    // class the given order holds
+    std::vector<int> ord((size_t)std::max(0, n_jobs));
+    for (int i = 0; i < n_jobs; ++i) ord[(size_t)i] = order ? order[i] : i;
+    auto class_key = [&](int j) { return jobs[j].n_t() == 32 ? -1 : batch_class(jobs[j].n_t()); };
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return class_key(x) < class_key(y); });
     long long first = 0, tiles = 0;
     size_t off = 0;
     int n_table = 0;
     std::vector<int> slot((size_t)std::max(0, n_jobs));  // table index, or -1 - (index into wide_)
     for (int i = 0; i < n_jobs; ++i) {
-        const GroupJob& G = jobs[order ? order[i] : i];
+        const GroupJob& G = jobs[ord[(size_t)i]];
         if (G.det && G.det->n_t == 32) {
             const mmgap_detect_job& J = *G.det;
             const size_t n = 64, P = (size_t)J.n_problems;
@@ -323,7 +365,7 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
     // several problems, as far as the remaining scratch allows
     fac_.clear();
     for (int i = 0; i < n_jobs; ++i) {
-        const GroupJob& G = jobs[order ? order[i] : i];
+        const GroupJob& G = jobs[ord[(size_t)i]];
         if (!G.det) continue;
         const mmgap_detect_job& J = *G.det;
         if (!J.chan_index || J.n_chan >= J.n_problems || J.n_problems == 0) continue;
@@ -357,8 +399,27 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
         B.chol_pre = f.chol_out;
         fac_.push_back(F);
     }
+    n_fac_ = 0;
+    fac_chan_ = fac_prob_ = 0;
+    for (const Factor& F : fac_) {
+        if (F.n_t == 32) continue;  // (their own launches)
+        FactorJob& Q = h_fac_[n_fac_++];
+        Q.a = F.args;
+        Q.nt = F.n_t;
+        Q.chan_first = fac_chan_;
+        Q.prob_first = fac_prob_;
+        fac_chan_ += F.args.n_chan;
+        fac_prob_ += F.args.n_problems;
+    }
     h_head_->n_jobs = n_table;
     h_head_->pad = 0;
+    for (int c = 0; c < 3; ++c) cls_first_[c] = cls_count_[c] = 0;
+    for (int j = 0; j < n_table; ++j) {
+        const BatchJob& B = h_jobs_[j];
+        const int c = batch_class(B.nt);
+        if (cls_count_[c] == 0) cls_first_[c] = B.first;
+        cls_count_[c] += B.b.n_problems;
+    }
     h_head_->total = first;
     h_head_->tiles = tiles;
     return 0;
@@ -402,17 +463,24 @@ cudaError_t BatchRunner::wide_before(const mmgap_params& P, cudaStream_t s) {
 }
 
 cudaError_t BatchRunner::factor_before(cudaStream_t s) {
-    for (const Factor& F : fac_) {
-        cudaError_t e;
-        switch (F.n_t) {
-        case 32: e = launch_chan_factor<32>(F.args, s); break;
-        case 16: e = launch_chan_factor<16>(F.args, s); break;
-        case 8: e = launch_chan_factor<8>(F.args, s); break;
-        default: e = launch_chan_factor<4>(F.args, s); break;
-        }
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    cudaError_t e;
+    for (const Factor& F : fac_)
+        if (F.n_t == 32 && (e = launch_chan_factor<32>(F.args, s)) != cudaSuccess) return e;
+    if (n_fac_ == 0) return cudaSuccess;
+    // every other job's channels in three launches (one launch per job and kernel left the GPU
+    // idle between small jobs' launches)
+    if ((e = cudaMemcpyAsync(d_fac_, h_fac_, sizeof(FactorJob) * (size_t)n_fac_, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return e;
+    FactorBatch F{d_fac_, n_fac_, fac_chan_, fac_prob_, build_floats_};
+    auto blocks = [](long long n) { return (unsigned)std::min<long long>(std::max(1LL, (n + 255) / 256), 4096); };
+    batch_factor_init_kernel<<<blocks(fac_chan_), 256, 0, s>>>(F);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    batch_factor_first_kernel<<<blocks(fac_prob_), 256, 0, s>>>(F);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    void* args[] = {&F};
+    return cudaLaunchKernel(pick_factor(ntmax_), dim3((unsigned)((fac_chan_ + kBuildWarps - 1) / kBuildWarps)),
+                            dim3(kBuildWarps * 32), args, build_smem_, s);
 }
 
 cudaError_t BatchRunner::precode_before(cudaStream_t s) {
@@ -459,17 +527,17 @@ cudaError_t BatchRunner::precode_after(cudaStream_t s) {
     return cudaSuccess;
 }
 
-void BatchRunner::grids(unsigned* build_grid, unsigned* solve_grid) const {
-    const long long total = h_head_ ? h_head_->total : capacity_problems_;
-    const long long bb = (std::max(1LL, total) + kBuildWarps - 1) / kBuildWarps;
-    *build_grid = (unsigned)bb;  // one warp per problem
-    if (tc_) {  // tiles of 4 problems, at most one partial tile per job
-        const long long tiles = h_head_ ? h_head_->tiles : (capacity_problems_ + 3) / 4 + capacity_;
-        *solve_grid = (unsigned)std::max(1LL, tiles);
-        return;
-    }
-    *solve_grid = (unsigned)std::max(1LL, total);
+unsigned BatchRunner::build_grid() const {  // one warp per problem
+    return (unsigned)((std::max(1LL, h_head_->total) + kBuildWarps - 1) / kBuildWarps);
 }
+
+unsigned BatchRunner::umma_grid() const {  // tiles of 4 problems, at most one partial tile per job
+    return (unsigned)std::max(1LL, h_head_->tiles);
+}
+
+unsigned BatchRunner::class_grid(int c) const { return (unsigned)std::max(1LL, cls_count_[c]); }
+
+int BatchRunner::class_lo() const { return batch_class(ntmax_); }
 
 cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     cudaError_t e;
@@ -486,14 +554,34 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     a.early_exit = P.early_exit;
     a.k = batch_consts(P);
     a.build_floats = build_floats_;
+    for (int c = 0; c < 3; ++c) {
+        a.cls_first[c] = cls_first_[c];
+        a.cls_count[c] = cls_count_[c];
+    }
     void* args[] = {&a};
-    unsigned bg, sg;
-    grids(&bg, &sg);
-    if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3(bg), dim3(kBuildWarps * 32), args, build_smem_, s)) !=
-        cudaSuccess)
+    if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3(build_grid()), dim3(kBuildWarps * 32), args, build_smem_,
+                              s)) != cudaSuccess)
         return e;
-    return cudaLaunchKernel(pick_solve(ntmax_, P.f_mvm, tc_, P.early_exit > 0), dim3(sg), dim3(solve_block()), args,
-                            solve_smem(), s);
+    if (tc_) return cudaLaunchKernel(umma_solve(ntmax_, P.f_mvm), dim3(umma_grid()), dim3(128), args, umma_smem_, s);
+    // one solver kernel per size class; with more than one class they are independent branches
+    // (fork from s through an event, the other classes on the side streams, joined back into s)
+    const int c0 = class_lo(), nside = 2 - c0;
+    if (nside > 0) {
+        if ((e = cudaEventRecord(fork_, s)) != cudaSuccess) return e;
+        for (int i = 0; i < nside; ++i)
+            if ((e = cudaStreamWaitEvent(side_[i], fork_, 0)) != cudaSuccess) return e;
+    }
+    for (int c = c0; c < 3; ++c) {
+        cudaStream_t cs = c == c0 ? s : side_[c - c0 - 1];
+        if ((e = cudaLaunchKernel(class_solve(c, P.f_mvm, P.early_exit > 0), dim3(class_grid(c)), dim3(32), args, 0,
+                                  cs)) != cudaSuccess)
+            return e;
+    }
+    for (int i = 0; i < nside; ++i) {
+        if ((e = cudaEventRecord(join_[i], side_[i])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, join_[i], 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t BatchRunner::run(const mmgap_params& P, cudaStream_t s, bool use_graph) {
@@ -535,8 +623,10 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         if (e != cudaSuccess) return e;
         if ((e = cudaGraphInstantiate(&exec_, graph_, 0)) != cudaSuccess) return e;
         graph_params_ = P;
-        // remember the two kernel nodes so each replay can size their grids
-        build_node_ = solve_node_ = nullptr;
+        // remember the kernel nodes so each replay can size their grids: the builder, and the
+        // solver (tcgen05 tiles) or one solver per size class
+        build_node_ = nullptr;
+        for (cudaGraphNode_t& nd : solve_nodes_) nd = nullptr;
         size_t count = 0;
         if ((e = cudaGraphGetNodes(graph_, nullptr, &count)) != cudaSuccess) return e;
         std::vector<cudaGraphNode_t> nodes(count);
@@ -547,31 +637,48 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
             cudaKernelNodeParams kp;
             if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
             if (kp.func == pick_build(ntmax_)) build_node_ = nd;
-            else solve_node_ = nd;
+            else if (tc_) solve_nodes_[0] = nd;
+            else
+                for (int c = class_lo(); c < 3; ++c)
+                    if (kp.func == class_solve(c, P.f_mvm, P.early_exit > 0)) solve_nodes_[c] = nd;
         }
-        if (!build_node_ || !solve_node_) return cudaErrorInvalidValue;
+        if (!build_node_) return cudaErrorInvalidValue;
+        for (int c = tc_ ? 0 : class_lo(); c < (tc_ ? 1 : 3); ++c)
+            if (!solve_nodes_[c]) return cudaErrorInvalidValue;
     } else {
         // grids and counts follow the staged header; the other kernel arguments are unchanged
-        unsigned bg, sg;
-        grids(&bg, &sg);
         args_.n_jobs = h_head_->n_jobs;
         args_.total = h_head_->total;
         args_.tiles = h_head_->tiles;
+        for (int c = 0; c < 3; ++c) {
+            args_.cls_first[c] = cls_first_[c];
+            args_.cls_count[c] = cls_count_[c];
+        }
         void* args[] = {&args_};
         cudaKernelNodeParams kb{};
         kb.func = (void*)pick_build(ntmax_);
-        kb.gridDim = dim3(bg);
+        kb.gridDim = dim3(build_grid());
         kb.blockDim = dim3(kBuildWarps * 32);
         kb.sharedMemBytes = (unsigned)build_smem_;
         kb.kernelParams = args;
         if ((e = cudaGraphExecKernelNodeSetParams(exec_, build_node_, &kb)) != cudaSuccess) return e;
         cudaKernelNodeParams ks{};
-        ks.func = (void*)pick_solve(ntmax_, P.f_mvm, tc_, P.early_exit > 0);
-        ks.gridDim = dim3(sg);
-        ks.blockDim = dim3(solve_block());
-        ks.sharedMemBytes = (unsigned)solve_smem();
         ks.kernelParams = args;
-        if ((e = cudaGraphExecKernelNodeSetParams(exec_, solve_node_, &ks)) != cudaSuccess) return e;
+        if (tc_) {
+            ks.func = (void*)umma_solve(ntmax_, P.f_mvm);
+            ks.gridDim = dim3(umma_grid());
+            ks.blockDim = dim3(128);
+            ks.sharedMemBytes = (unsigned)umma_smem_;
+            if ((e = cudaGraphExecKernelNodeSetParams(exec_, solve_nodes_[0], &ks)) != cudaSuccess) return e;
+        } else {
+            for (int c = class_lo(); c < 3; ++c) {
+                ks.func = (void*)class_solve(c, P.f_mvm, P.early_exit > 0);
+                ks.gridDim = dim3(class_grid(c));
+                ks.blockDim = dim3(32);
+                ks.sharedMemBytes = 0;
+                if ((e = cudaGraphExecKernelNodeSetParams(exec_, solve_nodes_[c], &ks)) != cudaSuccess) return e;
+            }
+        }
     }
     return cudaGraphLaunch(exec_, s);
 }

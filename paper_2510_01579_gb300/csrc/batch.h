@@ -69,12 +69,18 @@ class BatchRunner {
     cudaError_t enqueue(const mmgap_params& P, cudaStream_t s);
     cudaError_t run_batch(const mmgap_params& P, cudaStream_t s, bool use_graph);
     cudaError_t precode_before(cudaStream_t s);
-    cudaError_t factor_before(cudaStream_t s);  // per-channel factorisation of the staged jobs
+    // per-channel factorisation of the staged jobs: 32-user jobs one launch each, the others in
+    // three launches over the factor table
+    cudaError_t factor_before(cudaStream_t s);
     struct Factor {
         int n_t;
         ChanFactorArgs args;
     };
     std::vector<Factor> fac_;
+    FactorJob* h_fac_ = nullptr;  // pinned factor table (jobs of up to 16 users)
+    FactorJob* d_fac_ = nullptr;
+    int n_fac_ = 0;
+    long long fac_chan_ = 0, fac_prob_ = 0;  // channels and problems of the factor table
     cudaError_t precode_after(cudaStream_t s);
     std::vector<Precode> pre_;
     // 32-user detection jobs: outside the job table (the mixed-size kernels
@@ -86,9 +92,10 @@ class BatchRunner {
     };
     std::vector<Wide> wide_;
     cudaError_t wide_before(const mmgap_params& P, cudaStream_t s);
-    void grids(unsigned* build_grid, unsigned* solve_grid) const;
-    unsigned solve_block() const { return tc_ ? 128u : 32u; }
-    size_t solve_smem() const { return tc_ ? umma_smem_ : 0; }
+    unsigned build_grid() const;
+    unsigned umma_grid() const;
+    unsigned class_grid(int c) const;  // grid of size class c's solver (at least 1 CTA)
+    int class_lo() const;              // the runner's first size class: batch_class(ntmax_)
     int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0;
     bool tc_ = false;  // tcgen05 field refresh for 8 and 16 users (4-problem tiles)
     size_t umma_smem_ = 0;  // dynamic shared memory of the tcgen05 solver
@@ -99,9 +106,14 @@ class BatchRunner {
     BatchJob* d_jobs_ = nullptr;
     BatchJob* h_jobs_ = nullptr;
     BatchHeader* h_head_ = nullptr;
+    // the grid solver's size classes (batch_class): first problem and count of each in the table
+    long long cls_first_[3] = {0, 0, 0}, cls_count_[3] = {0, 0, 0};
+    // side streams and events of the classes' concurrent solver launches (fork and join)
+    cudaStream_t side_[2] = {nullptr, nullptr};
+    cudaEvent_t fork_ = nullptr, join_[2] = {nullptr, nullptr};
     cudaStream_t cap_stream_ = nullptr;
     cudaGraph_t graph_ = nullptr;
-    cudaGraphNode_t build_node_ = nullptr, solve_node_ = nullptr;
+    cudaGraphNode_t build_node_ = nullptr, solve_nodes_[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t exec_ = nullptr;
     mmgap_params graph_params_{};
     BatchArgs args_{};

@@ -51,6 +51,10 @@ struct BatchArgs {
     int n_jobs;
     long long total;
     long long tiles;
+    // the grid solver's size classes (16, 8 and 4 users, batch_class): the table holds each class's
+    // jobs contiguously, class c's problems being [cls_first[c], cls_first[c] + cls_count[c])
+    long long cls_first[3];
+    long long cls_count[3];
     int steps;
     int early_exit;         // K > 0: the early-exit rule of the per-job solver (grid solver only)
     EulerConsts k;
@@ -254,23 +258,91 @@ __device__ __forceinline__ void batch_solve_problem(const BatchArgs& A, const Ba
     batch_solve_warp<NT, F, EE>(A, J, p, lane, sm);
 }
 
-// Grid solver over the batch: one 32-thread CTA per problem (the hardware
-// CTA scheduler balances sizes); CTAs past the staged total exit.
-template <int NTMAX, int F, bool EE = false>
-__global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
-    __shared__ __align__(16) unsigned char ssm[batch_solve_bytes<NTMAX>()];
-    const long long w = blockIdx.x;
-    if (w >= A.total) return;
-    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.n_jobs, w)];
-    const int p = (int)(w - J.first);
-    const int lane = threadIdx.x;
-    if (J.nt == 16) {
-        if constexpr (NTMAX >= 16) batch_solve_problem<16, F, EE>(A, J, p, lane, ssm);
-    } else if (J.nt == 8) {
-        if constexpr (NTMAX >= 8) batch_solve_problem<8, F, EE>(A, J, p, lane, ssm);
-    } else {
-        batch_solve_problem<4, F, EE>(A, J, p, lane, ssm);
+// Per-channel MMSE factorisations of the staged detection jobs (chan_factor_warp)
+// in three launches for all jobs: the jobs' channels are numbered one after
+// another from chan_first, their problems from prob_first.
+struct FactorJob {
+    ChanFactorArgs a;
+    int nt;
+    long long chan_first;
+    long long prob_first;
+};
+
+struct FactorBatch {
+    const FactorJob* jobs;
+    int n_jobs;
+    long long n_chan;      // channels of all jobs
+    long long n_problems;  // problems of all jobs
+    int build_floats;      // shared memory per warp of the factor kernel (floats, a multiple of 4)
+};
+
+// Last job whose channels (CHAN) or problems start at or before v.
+template <bool CHAN>
+__device__ __forceinline__ int factor_find_job(const FactorJob* jobs, int n_jobs, long long v) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((CHAN ? jobs[mid].chan_first : jobs[mid].prob_first) <= v) lo = mid;
+        else hi = mid - 1;
     }
+    return lo;
+}
+
+// Every channel's first-problem slot to a value above any problem index.
+static __global__ void batch_factor_init_kernel(FactorBatch F) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < F.n_chan;
+         g += (long long)gridDim.x * blockDim.x) {
+        const FactorJob& J = F.jobs[factor_find_job<true>(F.jobs, F.n_jobs, g)];
+        J.a.first[g - J.chan_first] = 0x7fffffff;
+    }
+}
+
+// First problem of each channel of every job (atomic minimum over the job's problems).
+static __global__ void batch_factor_first_kernel(FactorBatch F) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < F.n_problems;
+         g += (long long)gridDim.x * blockDim.x) {
+        const FactorJob& J = F.jobs[factor_find_job<false>(F.jobs, F.n_jobs, g)];
+        const int p = (int)(g - J.prob_first);
+        const int c = J.a.chan_index[p];
+        if (c >= 0 && c < J.a.n_chan) atomicMin(J.a.first + c, p);
+    }
+}
+
+// One warp per channel of every job.
+template <int NTMAX>
+__global__ void __launch_bounds__(kBuildWarps * 32) batch_factor_kernel(FactorBatch F) {
+    extern __shared__ __align__(16) float fws[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long g = (long long)blockIdx.x * kBuildWarps + warp;
+    if (g >= F.n_chan) return;  // warp-uniform
+    const FactorJob& J = F.jobs[factor_find_job<true>(F.jobs, F.n_jobs, g)];
+    const int c = (int)(g - J.chan_first);
+    float* ws = fws + warp * (F.build_floats & ~3);  // (a multiple of 4: vectorised accesses)
+    if (J.nt == 16) {
+        if constexpr (NTMAX >= 16) chan_factor_warp<16>(J.a, c, lane, ws);
+    } else if (J.nt == 8) {
+        if constexpr (NTMAX >= 8) chan_factor_warp<8>(J.a, c, lane, ws);
+    } else {
+        chan_factor_warp<4>(J.a, c, lane, ws);
+    }
+}
+
+// Size class of a table job's user count: 0 for 16 users, 1 for 8, 2 for 4.
+__host__ __device__ constexpr int batch_class(int nt) { return nt == 16 ? 0 : (nt == 8 ? 1 : 2); }
+
+// Grid solver of one size class: one 32-thread CTA per problem of the class's
+// jobs.  Each class is its own kernel, with its own size's registers and
+// shared memory (one kernel over all sizes ran every problem at the 16-user
+// footprint); the classes' kernels are independent and may run concurrently.
+// CTAs past the class's count exit.
+template <int NT, int F, bool EE = false>
+__global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
+    __shared__ __align__(16) unsigned char ssm[batch_solve_bytes<NT>()];
+    constexpr int c = batch_class(NT);
+    if ((long long)blockIdx.x >= A.cls_count[c]) return;
+    const long long w = A.cls_first[c] + blockIdx.x;
+    const BatchJob& J = A.jobs[batch_find_job(A.jobs, A.n_jobs, w)];
+    batch_solve_problem<NT, F, EE>(A, J, (int)(w - J.first), threadIdx.x, ssm);
 }
 
 // Batched tensor-core solver (tcgen05, solver shape 8): one 128-thread CTA

@@ -385,23 +385,19 @@ __global__ void chan_first_kernel(ChanFactorArgs a) {
     }
 }
 
-// One warp per channel: Hs = kappa H, the Gram and the MMSE Cholesky factor
-// with rho of the channel's first problem -- the same functions and shared
-// memory layout as build_problem_warp, so a problem with that rho finds the
-// bits its own factorisation would give.
+// Channel c of `a` with one warp: Hs = kappa H, the Gram and the MMSE Cholesky
+// factor with rho of the channel's first problem -- the same functions and
+// shared memory layout as build_problem_warp, so a problem with that rho finds
+// the bits its own factorisation would give.  ws: build_smem_floats<NT>(n_r)
+// floats of this warp's shared memory.
 template <int NT>
-__global__ void __launch_bounds__(kBuildWarps * 32) chan_factor_kernel(ChanFactorArgs a) {
-    extern __shared__ __align__(16) float smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * kBuildWarps + warp;
-    if (c >= a.n_chan) return;  // warp-uniform
+__device__ __forceinline__ void chan_factor_warp(const ChanFactorArgs& a, int c, int lane, float* ws) {
     const int p0 = a.first[c];
     if (p0 < 0 || p0 >= a.n_problems) {
         if (lane == 0) a.rho_out[c] = __int_as_float(0x7fc00000);  // NaN: no problem compares equal
         return;
     }
     const int n_r = a.n_r;
-    float* ws = smem + warp * build_smem_floats<NT>(n_r);
     float* Hs = ws;
     float* Gc = Hs + 2 * n_r * NT;
     float* Lc = Gc + 2 * NT * NT;
@@ -430,6 +426,16 @@ __global__ void __launch_bounds__(kBuildWarps * 32) chan_factor_kernel(ChanFacto
         a.rho_out[c] = rho;
         a.chol_out[c] = flag[0];
     }
+}
+
+// One warp per channel (chan_factor_warp).
+template <int NT>
+__global__ void __launch_bounds__(kBuildWarps * 32) chan_factor_kernel(ChanFactorArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kBuildWarps + warp;
+    if (c >= a.n_chan) return;  // warp-uniform
+    chan_factor_warp<NT>(a, c, lane, smem + warp * build_smem_floats<NT>(a.n_r));
 }
 
 }  // namespace mmgap
