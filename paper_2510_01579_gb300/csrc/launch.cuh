@@ -36,6 +36,45 @@ cudaError_t launch_chan_factor_impl(const ChanFactorArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Latency: when few problems would leave SMs idle, each problem of a shape with
+// TPA threads per anneal runs as a cluster of CL CTAs (4 or 2), each with
+// runs / CL of its anneals on its own SM; the same bits (the anneals keep their
+// indices in the problem).  Returns the cluster size to use, 1 for none.
+template <int TPA>
+int tuned_cluster_size(const SolveArgs& a, int runs) {
+    if (a.n_sm <= 0 || a.n_problems <= 0) return 1;
+    for (int cl : {4, 2})
+        if (runs % cl == 0 && (runs / cl * TPA) % 32 == 0 && (long long)a.n_problems * cl <= a.n_sm) return cl;
+    return 1;
+}
+
+template <int NT, int F, int TPA, int CL>
+cudaError_t launch_tuned_cluster(const SolveArgs& a, int runs, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(a.n_problems * CL));
+    cfg.blockDim = dim3((unsigned)(runs / CL * TPA));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cac_solve_tuned_kernel<NT, F, TPA, true, false, false, false, CL>, a);
+}
+
+// A TPA-threads-per-anneal shape, as a cluster per problem when few problems leave SMs idle.
+template <int NT, int F, int TPA>
+cudaError_t launch_tuned_latency(const SolveArgs& a, int runs, cudaStream_t s) {
+    const int cl = tuned_cluster_size<TPA>(a, runs);
+    if (cl == 4) return launch_tuned_cluster<NT, F, TPA, 4>(a, runs, s);
+    if (cl == 2) return launch_tuned_cluster<NT, F, TPA, 2>(a, runs, s);
+    cac_solve_tuned_kernel<NT, F, TPA, true><<<a.n_problems, TPA * runs, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // Tuned kernels exist for n_t in {4, 8, 16} and f_mvm in {1, 2}.
 __host__ __device__ constexpr bool tuned_size(int NT) { return NT == 4 || NT == 8 || NT == 16; }
 
@@ -106,11 +145,11 @@ cudaError_t launch_tuned(const SolveArgs& a, int runs, int variant, cudaStream_t
         case kVariantTpa1Packed: cac_solve_tuned_kernel<NT, F, 1, true><<<a.n_problems, runs, 0, s>>>(a); break;
         case kVariantTpa2Packed: cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a); break;
         case kVariantTpa4Packed:  // (smaller sizes are resolved to shape 4 before launch)
-            if constexpr (NT >= 8) cac_solve_tuned_kernel<NT, F, 4, true><<<a.n_problems, 4 * runs, 0, s>>>(a);
+            if constexpr (NT >= 8) return launch_tuned_latency<NT, F, 4>(a, runs, s);
             else cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
             break;
         case kVariantTpa8Packed:
-            if constexpr (NT >= 16) cac_solve_tuned_kernel<NT, F, 8, true><<<a.n_problems, 8 * runs, 0, s>>>(a);
+            if constexpr (NT >= 16) return launch_tuned_latency<NT, F, 8>(a, runs, s);
             else cac_solve_tuned_kernel<NT, F, 2, true><<<a.n_problems, 2 * runs, 0, s>>>(a);
             break;
         case kVariantPairPacked:

@@ -1,6 +1,8 @@
 // CIM-CAC solver (Eqs. 10-11, Sec. 3.2.1): the one-thread-per-anneal kernel, the
 // bit-identical tuned launch shapes and the mma.sync tensor-core refresh (shapes 5, 7).
 #pragma once
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace mmgap {
@@ -762,7 +764,12 @@ __device__ __forceinline__ void tc_block(const uint32_t* sAf, const float* sh, c
     }
 }
 
-template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false, bool EE = false>
+// CL > 1 (latency: few problems): a cluster of CL CTAs per problem, each with
+// R / CL of its anneals on its own SM.  The anneals keep their indices in the
+// problem (Philox streams and arg-min key), so the results are the same bits;
+// the arg-min and the divergence count are combined through distributed
+// shared memory.
+template <int NT, int F, int TPA, bool PACKED, bool TC = false, bool PAIR = false, bool EE = false, int CL = 1>
 __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a) {
     constexpr int n = 2 * NT;
     constexpr int NS = n / TPA;
@@ -770,14 +777,16 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
     static_assert(F > 0, "compile-time refresh period");
     static_assert(!TC || (TPA <= 2 && PACKED && n % 16 == 0), "tensor-core refresh: 1 or 2 threads per anneal");
     static_assert(!(TC && EE), "early exit runs on the bit-identical shapes");
+    static_assert(CL == 1 || (!TC && !EE), "clusters: the exact shapes without early exit");
     __shared__ __align__(16) SolveSmem<NT> sm;
     __shared__ long long skey[4 * TPA];
     __shared__ int sdiv[4 * TPA];
     __shared__ __align__(16) uint32_t tc_af[TC ? TcShape<NT>::AF_WORDS : 1];
     extern __shared__ __align__(16) uint32_t tc_ws[];  // TC: TcShape<NT>::warp_words(32 / TPA) per warp (dynamic)
-    const int p = blockIdx.x;
+    const int p = blockIdx.x / CL;
     const int tid = threadIdx.x, T = blockDim.x;
-    const int q = tid % TPA, run = tid / TPA;
+    const int crank = CL > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+    const int q = tid % TPA, run = crank * (T / TPA) + tid / TPA;  // the anneal's index in the problem
     const int lane = tid & 31, warp = tid >> 5;
     const int row0 = q * NS;
     const EulerConsts k = a.k;
@@ -931,6 +940,25 @@ __global__ void __launch_bounds__(128 * TPA) cac_solve_tuned_kernel(SolveArgs a)
     for (int w = 1; w < T / 32; ++w) {
         best = skey[w] < best ? skey[w] : best;
         ndiv += sdiv[w];
+    }
+    if constexpr (CL > 1) {
+        __shared__ long long ckey;
+        __shared__ int cdiv;
+        cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+        if (tid == 0) {
+            ckey = best;
+            cdiv = ndiv;
+        }
+        cluster.sync();
+        best = 0x7fffffffffffffffLL;
+        ndiv = 0;
+#pragma unroll
+        for (int r = 0; r < CL; ++r) {
+            const long long kr = *cluster.map_shared_rank(&ckey, (unsigned)r);
+            best = kr < best ? kr : best;
+            ndiv += *cluster.map_shared_rank(&cdiv, (unsigned)r);
+        }
+        cluster.sync();  // no CTA leaves while another still reads its shared memory
     }
     const int best_run = (int)(best & 0xffffffffLL);
     if (run == best_run) {
