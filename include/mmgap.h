@@ -389,7 +389,10 @@ mmgap_status mmgap_device_errors(mmgap_ctx* ctx, int* flags_out, int clear);
  *     by lane pairs (each coupling read once for two anneals)
  *   9 tuned kernel, four threads per anneal, packed (n_t 8 and 16; 4 runs 4)
  *  10 tuned kernel, eight threads per anneal, packed (n_t 16; 8 runs 9,
- *     4 runs 4) -- shapes for latency, when few problems leave SMs idle
+ *     4 runs 4) -- shapes for latency, when few problems leave SMs idle;
+ *     with at most a quarter (half) as many problems as SMs, each problem
+ *     runs as a cluster of 4 (2) CTAs with a quarter (half) of its anneals
+ *     each (the same results)
  * Shapes 2-4, 6, 9 and 10 exist for n_t in {4, 8, 16} with f_mvm in {1, 2};
  * elsewhere 1 runs.  Shape 5 is a precision variant, not bit-identical: shape 3 with
  * the coupling field of a warp's 32 anneals computed on the tensor cores
