@@ -419,6 +419,40 @@ def test_solver_shapes_bit_exact(mm, nt, variant, f_mvm, steps, runs):
     assert np.array_equal(got["ndiv"].cpu().numpy(), ref["n_div"])
 
 
+def _cluster_sizes():
+    """Call sizes at the edges of the latency shapes' clusters on this device:
+    a cluster of 4 CTAs per problem up to n_sm / 4 problems, of 2 up to
+    n_sm / 2, none above."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    return [1, n_sm // 4, n_sm // 4 + 1, n_sm // 2, n_sm // 2 + 1]
+
+
+@pytest.mark.parametrize("nt,runs", [(16, 32), (16, 96), (8, 32), (8, 64)])
+def test_latency_clusters_are_bit_identical(mm, nt, runs):
+    """The latency shapes (8 threads per anneal for 16 users, 4 for 8) run a
+    small call's problems as clusters of 4 or 2 CTAs; at every cluster size
+    every output of every problem equals the throughput shape's, and sampled
+    problems equal the oracle's."""
+    pkg, ctx = mm
+    prm = pkg.Params.default(runs=runs, steps=50)
+    for P in _cluster_sizes():
+        w = synth.uplink(690 + nt + P, nt, nt, 4, n_sub=P, n_sym=1, snr_db=14.0)
+        ctx.set_solver_variant(nt, 10 if nt == 16 else 9)
+        try:
+            lat = _detect(ctx, w, prm, 5)
+            ctx.set_solver_variant(nt, 6 if nt == 16 else 3)
+            thr = _detect(ctx, w, prm, 5)
+        finally:
+            ctx.set_solver_variant(nt, 0)
+        for k in ("sym", "energy", "offset", "ndiv", "guess"):
+            assert np.array_equal(lat[k], thr[k]), (P, k)
+        for p in sorted({0, P - 1}):
+            c = int(w["chan_index"][p])
+            bld = oracle.build_detect32(w["H"][c], w["y"][p], w["noise_var"][p], 4)
+            r = oracle.cac_solve(bld["Aq"], bld["hq"], bld["g"], 3, oparams(prm), 5, p)
+            assert lat["energy"][p] == r["E"] and lat["ndiv"][p] == r["n_div"], (P, p)
+
+
 @pytest.mark.parametrize("nt,P", [(16, 5), (16, 200), (16, 400), (8, 5), (8, 200), (8, 400)])
 def test_default_shape_by_call_size_is_bit_identical(mm, nt, P):
     """The default shape depends on the call's size (latency shapes when SMs
