@@ -41,7 +41,7 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 # 16x16 slot (14,336 problems) and divided by its problems; the traffic grows in
 # proportion to the problems, so a launch's traffic is this times its problems.
 # Keyed by (users, launch shape); a shape absent here reports traffic None.
-SOLVER_DRAM_BYTES_PER_PROBLEM = {(16, 6): 30868736 / 14336}
+SOLVER_DRAM_BYTES_PER_PROBLEM = {(16, 6): 30983680 / 14336}
 
 WORKLOADS = {
     # name: (n_r, n_t, mod_bits, model, hold, snr_db)
