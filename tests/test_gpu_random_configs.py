@@ -193,3 +193,72 @@ def test_random_job_groups_batched_equal_per_job(mm, i):
             for j in range(n_jobs):
                 for k in refs[j]:
                     assert torch.equal(outs[j][k], refs[j][k]), (sizes, j, k, graph, ee)
+
+
+@pytest.mark.parametrize("i", range(16))
+def test_random_detect_e_bit_exact(mm, i):
+    """MMGaP-E (MMSE and MMSE-SIC guesses, 1-3 stages, early exit at times):
+    every candidate, the chosen candidate, its objective and the symbols equal
+    the oracle's."""
+    pkg, ctx = mm
+    rng = np.random.default_rng(94000 + i)
+    n_t = int(rng.choice([1, 2, 3, 4, 8, 16]))
+    n_r = int(rng.integers(n_t, n_t + 9))
+    mb = int(rng.choice([2, 4, 6]))
+    stages = int(rng.integers(1, 4))
+    prm = pkg.Params.default(runs=int(rng.choice([32, 64])), steps=int(rng.integers(0, 101)),
+                             f_mvm=int(rng.integers(1, 4)), early_exit=int(rng.choice([0, 0, 3])))
+    w = synth.uplink(int(rng.integers(0, 100000)), n_r, n_t, mb, n_sub=int(rng.choice([1, 4, 9])),
+                     n_sym=int(rng.choice([1, 3])), snr_db=float(rng.uniform(5, 28)),
+                     hold=str(rng.choice(["problem", "subcarrier", "prb"])))
+    seed = int(rng.integers(0, 2 ** 31))
+    out = ctx.detect_e(T(w["H"]), T(w["y"]), T(w["noise_var"]), mb, prm, seed, stages=stages,
+                       chan_index=T(w["chan_index"]), want_candidates=True)
+    torch.cuda.synchronize()
+    cands = out["candidates"].cpu().numpy()
+    case = (n_t, n_r, mb, stages, prm.runs, prm.steps, prm.f_mvm, prm.early_exit)
+    for p in range(w["y"].shape[0]):
+        c = int(w["chan_index"][p])
+        r = oracle.detect_e(w["H"][c], w["y"][p], w["noise_var"][p], mb, stages, oparams(prm), seed, p)
+        assert np.array_equal(cands[:, p, :], r["candidates"].astype(np.int8)), (case, p)
+        assert int(out["best"][p]) == r["best"], (case, p)
+        assert float(out["obj"][p]) == np.float32(r["obj"]), (case, p)
+        assert np.array_equal(out["sym"][p].cpu().numpy(), r["sym"]), (case, p)
+
+
+@pytest.mark.parametrize("i", range(16))
+def test_random_static_entry_equals_context_path(mm, i):
+    """The allocation-free entry point gives the context path's bits on
+    random jobs (1-32 users, early exit and caller guesses at times), twice in
+    a row (its scratch keeps the previous call's contents)."""
+    pkg, ctx = mm
+    rng = np.random.default_rng(95000 + i)
+    n_t = int(rng.choice([1, 3, 4, 8, 16, 32]))
+    n_r = n_t if n_t == 32 else int(rng.integers(n_t, n_t + 9))
+    mb = int(rng.choice([2, 4, 6]))
+    prm = pkg.Params.default(runs=int(rng.choice([32, 64, 128])), steps=int(rng.integers(1, 121)),
+                             f_mvm=int(rng.integers(1, 3)),
+                             early_exit=0 if n_t == 32 else int(rng.choice([0, 0, 2])))
+    w = synth.uplink(int(rng.integers(0, 100000)), n_r, n_t, mb,
+                     n_sub=int(rng.choice([1, 6, 40])) if n_t < 32 else 2,
+                     n_sym=int(rng.choice([1, 14])) if n_t < 32 else 1, snr_db=float(rng.uniform(5, 28)),
+                     hold=str(rng.choice(["problem", "subcarrier", "prb"])))
+    P = w["y"].shape[0]
+    guess = None
+    if rng.integers(0, 3) == 0:
+        L = (1 << (mb // 2)) - 1
+        guess = T((2 * rng.integers(0, L + 1, size=(P, 2 * n_t)) - L).astype(np.int8))
+    t = (T(w["H"]), T(w["y"]), T(w["noise_var"]), T(w["chan_index"]))
+    seed = int(rng.integers(0, 2 ** 31))
+    ref, out = _outs(P, n_t), _outs(P, n_t)
+    ctx.detect_jobs([ctx.detect_job(*t[:3], mb, seed, ref, t[3], guess=guess)], prm)
+    job = ctx.detect_job(*t[:3], mb, seed, out, t[3], guess=guess)
+    for _ in range(2):
+        for v in out.values():
+            v.fill_(5)
+        ctx.detect_static(job, prm)
+        torch.cuda.synchronize()
+        for k in ref:
+            if guess is not None and k == "guess":
+                continue
+            assert torch.equal(out[k], ref[k]), (n_t, n_r, mb, prm.runs, prm.steps, prm.early_exit, k)
