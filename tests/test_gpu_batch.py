@@ -1,5 +1,5 @@
-"""Batched launch (mixed sizes in one kernel, CUDA-graph replay)
-against the per-job path, bit for bit."""
+"""Batched launch (mixed sizes in one graph: one solver kernel per size
+class, CUDA-graph replay) against the per-job path, bit for bit."""
 import numpy as np
 import pytest
 import torch
