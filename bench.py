@@ -1563,6 +1563,7 @@ def main():
                 raise RuntimeError("batched and per-job paths disagree")
             bsrt = sorted(bt)
             batched[mode] = {"ms_per_step": statistics.mean(bt), "value": world * P / (statistics.mean(bt) / 1e3),
+                             "p50_ms": statistics.median(bt),
                              "p99_ms": bsrt[min(len(bsrt) - 1, int(math.ceil(0.99 * len(bsrt))) - 1)],
                              "graph": True}
 
