@@ -41,13 +41,17 @@ class BatchRunner {
     // problems with n_r <= max_n_r and n_t <= ntmax (the table's kernels are
     // sized for min(ntmax, 16); 32-user jobs stay outside the table), `scratch`
     // bytes of coupling scratch; err_word receives out-of-range channel indices.
-    // The solver runs one 32-thread CTA per problem; tensor_core: the field
-    // refresh of 8- and 16-user problems as tcgen05 MMAs instead (solver shape
-    // 8, a precision variant; 128-thread CTAs over 4-problem tiles).
+    // The solver runs one 32-thread CTA per problem, one kernel per size class
+    // (the classes concurrently, on the runner's side streams); tensor_core: the
+    // field refresh of 8- and 16-user problems as tcgen05 MMAs instead (solver
+    // shape 8, a precision variant; 128-thread CTAs over 4-problem tiles).
+    // Creates the side streams and events of the class launches.
     cudaError_t init(int device, int capacity_jobs, long long capacity_problems, size_t scratch, int max_n_r, int ntmax,
                      int* err_word, bool tensor_core = false);
     void release();
-    // Fill the pinned host table with jobs[order[i]] (order may be NULL);
+    // Fill the pinned host table with jobs[order[i]] (order may be NULL),
+    // grouped by size class (16, 8, 4 users) with the given order kept within
+    // each class, and the factor table of the jobs' per-channel factorisations;
     // returns 0, or < 0 if the jobs exceed the table, scratch or problem capacity.
     int stage(const mmgap_detect_job* jobs, const int* order, int n_jobs);
     int stage(const GroupJob* jobs, const int* order, int n_jobs);
