@@ -300,8 +300,8 @@ def secondary_measurements(ctx, dev, flush, steps: int = 5):
     """Short timings of the workloads next to the headline, so that one default
     run records them too (each with CUDA events on the current stream, L2 flushed
     between steps): the 8x8 16-QAM Kronecker PRB-held slot, the 16x16 16-QAM VPP
-    slot with the FP32 + refinement inverse, and the paper's 32x32 16-QAM 10 MHz
-    slot with 128 anneals."""
+    slot with the FP32 + refinement inverse, the paper's 32x32 16-QAM 10 MHz
+    slot with 128 anneals, and one 8x8 and one 16x16 problem alone (critical path)."""
     import torch
 
     from paper_2510_01579_gb300 import Params
@@ -356,6 +356,28 @@ def secondary_measurements(ctx, dev, flush, steps: int = 5):
         "problems": P, "runs": 128, "ms_per_slot": ms, "problems_per_s": P / (ms / 1e3),
         "ber": synth.bit_errors(out["sym"].cpu().numpy(), w["sym"], 4) / nbits,
         "ber_mmse": synth.bit_errors(((g[:, :32] + 3) // 2) * 4 + (g[:, 32:] + 3) // 2, w["sym"], 4) / nbits}
+    # critical path: one problem alone, the default (latency) launch shape, CUDA events around each
+    # call without an L2 flush (device time of build + solve and the launch gaps between them)
+    # (a context of its own: its shapes are the defaults, which pick the latency shapes for one problem)
+    from paper_2510_01579_gb300 import Context
+    crit = {}
+    with Context(dev.index or 0, workspace_bytes=16 << 20) as cctx:
+        for n_t in (8, 16):
+            w = synth.uplink(rank_seed(0) + 300 + n_t + 4, n_t, n_t, 4, n_sub=1, n_sym=1, snr_db=20.0)
+            H, y, nv, ci = (torch.from_numpy(w[k]).to(dev) for k in ("H", "y", "noise_var", "chan_index"))
+            o = {"sym": torch.empty((1, n_t), dtype=torch.uint8, device=dev)}
+            job = cctx.detect_job(H, y, nv, 4, 11, o, ci)
+            for _ in range(3):
+                cctx.detect_jobs([job], Params.default())
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+            for a, b in ev:
+                a.record(stream)
+                cctx.detect_jobs([job], Params.default())
+                b.record(stream)
+            torch.cuda.synchronize()
+            ts = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)
+            crit[f"{n_t}x{n_t}_16qam_us"] = {"median": ts[len(ts) // 2], "min": ts[0], "max": ts[-1]}
+    res["critical_path_one_problem"] = crit
     return res
 
 
