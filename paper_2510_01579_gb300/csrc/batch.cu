@@ -34,11 +34,11 @@ int build_floats_for(int nt, int n_r) {
     }
 }
 
-// tcgen05 tiles of 4 problems (solver shape 8) over every size up to ntmax
-const void* umma_solve(int ntmax, int f) {
-    switch (ntmax) {
-    case 16: return f == 1 ? (const void*)batch_solve_umma_kernel<16, 1> : (const void*)batch_solve_umma_kernel<16, 2>;
-    case 8: return f == 1 ? (const void*)batch_solve_umma_kernel<8, 1> : (const void*)batch_solve_umma_kernel<8, 2>;
+// tcgen05 tiles of 4 problems (solver shape 8) of size class c (batch_class)
+const void* umma_solve(int c, int f) {
+    switch (c) {
+    case 0: return f == 1 ? (const void*)batch_solve_umma_kernel<16, 1> : (const void*)batch_solve_umma_kernel<16, 2>;
+    case 1: return f == 1 ? (const void*)batch_solve_umma_kernel<8, 1> : (const void*)batch_solve_umma_kernel<8, 2>;
     default: return f == 1 ? (const void*)batch_solve_umma_kernel<4, 1> : (const void*)batch_solve_umma_kernel<4, 2>;
     }
 }
@@ -179,15 +179,19 @@ cudaError_t BatchRunner::init(int device, int capacity_jobs, long long capacity_
         int smem_sm = 0;
         if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device)) != cudaSuccess)
             return e;
-        const int ncols = ntmax >= 16 ? 128 : 64;
-        size_t smem = ntmax >= 16 ? batch_umma_bytes<16>() : batch_umma_bytes<8>();
-        const size_t floor_bytes = (size_t)smem_sm / (size_t)(512 / ncols + 1) + 1;
-        if (smem < floor_bytes) smem = (floor_bytes + 127) & ~(size_t)127;
-        umma_smem_ = smem;
-        for (int f : {1, 2})
-            if ((e = cudaFuncSetAttribute(umma_solve(ntmax, f), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem)) != cudaSuccess)
-                return e;
+        for (int c = class_lo(); c < 3; ++c) {
+            const int ncols = c == 0 ? 128 : (c == 1 ? 64 : 0);  // (4-user tiles take no tensor memory)
+            size_t smem = c == 0 ? batch_umma_bytes<16>() : (c == 1 ? batch_umma_bytes<8>() : batch_umma_bytes<4>());
+            if (ncols > 0) {
+                const size_t floor_bytes = (size_t)smem_sm / (size_t)(512 / ncols + 1) + 1;
+                if (smem < floor_bytes) smem = (floor_bytes + 127) & ~(size_t)127;
+            }
+            umma_smem_[c] = smem;
+            for (int f : {1, 2})
+                if ((e = cudaFuncSetAttribute(umma_solve(c, f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)) != cudaSuccess)
+                    return e;
+        }
     }
     for (int i = 0; i < 2; ++i)
         if ((e = cudaStreamCreateWithFlags(&side_[i], cudaStreamNonBlocking)) != cudaSuccess ||
@@ -413,12 +417,14 @@ int BatchRunner::stage(const GroupJob* jobs, const int* order, int n_jobs) {
     }
     h_head_->n_jobs = n_table;
     h_head_->pad = 0;
-    for (int c = 0; c < 3; ++c) cls_first_[c] = cls_count_[c] = 0;
+    for (int c = 0; c < 3; ++c) cls_first_[c] = cls_count_[c] = cls_tile_first_[c] = cls_tiles_[c] = 0;
     for (int j = 0; j < n_table; ++j) {
         const BatchJob& B = h_jobs_[j];
         const int c = batch_class(B.nt);
         if (cls_count_[c] == 0) cls_first_[c] = B.first;
+        if (cls_tiles_[c] == 0) cls_tile_first_[c] = B.tile_first;
         cls_count_[c] += B.b.n_problems;
+        cls_tiles_[c] += (B.b.n_problems + 3) / 4;
     }
     h_head_->total = first;
     h_head_->tiles = tiles;
@@ -531,11 +537,13 @@ unsigned BatchRunner::build_grid() const {  // one warp per problem
     return (unsigned)((std::max(1LL, h_head_->total) + kBuildWarps - 1) / kBuildWarps);
 }
 
-unsigned BatchRunner::umma_grid() const {  // tiles of 4 problems, at most one partial tile per job
-    return (unsigned)std::max(1LL, h_head_->tiles);
+const void* BatchRunner::solver_fn(int c, const mmgap_params& P) const {
+    return tc_ ? umma_solve(c, P.f_mvm) : class_solve(c, P.f_mvm, P.early_exit > 0);
 }
 
-unsigned BatchRunner::class_grid(int c) const { return (unsigned)std::max(1LL, cls_count_[c]); }
+unsigned BatchRunner::solver_grid(int c) const {  // a CTA per problem, or per tile of 4 problems of one job
+    return (unsigned)std::max(1LL, tc_ ? cls_tiles_[c] : cls_count_[c]);
+}
 
 int BatchRunner::class_lo() const { return batch_class(ntmax_); }
 
@@ -557,12 +565,13 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     for (int c = 0; c < 3; ++c) {
         a.cls_first[c] = cls_first_[c];
         a.cls_count[c] = cls_count_[c];
+        a.cls_tile_first[c] = cls_tile_first_[c];
+        a.cls_tiles[c] = cls_tiles_[c];
     }
     void* args[] = {&a};
     if ((e = cudaLaunchKernel(pick_build(ntmax_), dim3(build_grid()), dim3(kBuildWarps * 32), args, build_smem_,
                               s)) != cudaSuccess)
         return e;
-    if (tc_) return cudaLaunchKernel(umma_solve(ntmax_, P.f_mvm), dim3(umma_grid()), dim3(128), args, umma_smem_, s);
     // one solver kernel per size class; with more than one class they are independent branches
     // (fork from s through an event, the other classes on the side streams, joined back into s)
     const int c0 = class_lo(), nside = 2 - c0;
@@ -573,7 +582,7 @@ cudaError_t BatchRunner::enqueue(const mmgap_params& P, cudaStream_t s) {
     }
     for (int c = c0; c < 3; ++c) {
         cudaStream_t cs = c == c0 ? s : side_[c - c0 - 1];
-        if ((e = cudaLaunchKernel(class_solve(c, P.f_mvm, P.early_exit > 0), dim3(class_grid(c)), dim3(32), args, 0,
+        if ((e = cudaLaunchKernel(solver_fn(c, P), dim3(solver_grid(c)), dim3(solver_block()), args, solver_smem(c),
                                   cs)) != cudaSuccess)
             return e;
     }
@@ -623,8 +632,8 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         if (e != cudaSuccess) return e;
         if ((e = cudaGraphInstantiate(&exec_, graph_, 0)) != cudaSuccess) return e;
         graph_params_ = P;
-        // remember the kernel nodes so each replay can size their grids: the builder, and the
-        // solver (tcgen05 tiles) or one solver per size class
+        // remember the kernel nodes so each replay can size their grids: the builder and one
+        // solver per size class
         build_node_ = nullptr;
         for (cudaGraphNode_t& nd : solve_nodes_) nd = nullptr;
         size_t count = 0;
@@ -637,13 +646,12 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
             cudaKernelNodeParams kp;
             if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
             if (kp.func == pick_build(ntmax_)) build_node_ = nd;
-            else if (tc_) solve_nodes_[0] = nd;
             else
                 for (int c = class_lo(); c < 3; ++c)
-                    if (kp.func == class_solve(c, P.f_mvm, P.early_exit > 0)) solve_nodes_[c] = nd;
+                    if (kp.func == solver_fn(c, P)) solve_nodes_[c] = nd;
         }
         if (!build_node_) return cudaErrorInvalidValue;
-        for (int c = tc_ ? 0 : class_lo(); c < (tc_ ? 1 : 3); ++c)
+        for (int c = class_lo(); c < 3; ++c)
             if (!solve_nodes_[c]) return cudaErrorInvalidValue;
     } else {
         // grids and counts follow the staged header; the other kernel arguments are unchanged
@@ -653,6 +661,8 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         for (int c = 0; c < 3; ++c) {
             args_.cls_first[c] = cls_first_[c];
             args_.cls_count[c] = cls_count_[c];
+            args_.cls_tile_first[c] = cls_tile_first_[c];
+            args_.cls_tiles[c] = cls_tiles_[c];
         }
         void* args[] = {&args_};
         cudaKernelNodeParams kb{};
@@ -664,20 +674,12 @@ cudaError_t BatchRunner::run_batch(const mmgap_params& P, cudaStream_t s, bool u
         if ((e = cudaGraphExecKernelNodeSetParams(exec_, build_node_, &kb)) != cudaSuccess) return e;
         cudaKernelNodeParams ks{};
         ks.kernelParams = args;
-        if (tc_) {
-            ks.func = (void*)umma_solve(ntmax_, P.f_mvm);
-            ks.gridDim = dim3(umma_grid());
-            ks.blockDim = dim3(128);
-            ks.sharedMemBytes = (unsigned)umma_smem_;
-            if ((e = cudaGraphExecKernelNodeSetParams(exec_, solve_nodes_[0], &ks)) != cudaSuccess) return e;
-        } else {
-            for (int c = class_lo(); c < 3; ++c) {
-                ks.func = (void*)class_solve(c, P.f_mvm, P.early_exit > 0);
-                ks.gridDim = dim3(class_grid(c));
-                ks.blockDim = dim3(32);
-                ks.sharedMemBytes = 0;
-                if ((e = cudaGraphExecKernelNodeSetParams(exec_, solve_nodes_[c], &ks)) != cudaSuccess) return e;
-            }
+        for (int c = class_lo(); c < 3; ++c) {
+            ks.func = (void*)solver_fn(c, P);
+            ks.gridDim = dim3(solver_grid(c));
+            ks.blockDim = dim3(solver_block());
+            ks.sharedMemBytes = (unsigned)solver_smem(c);
+            if ((e = cudaGraphExecKernelNodeSetParams(exec_, solve_nodes_[c], &ks)) != cudaSuccess) return e;
         }
     }
     return cudaGraphLaunch(exec_, s);

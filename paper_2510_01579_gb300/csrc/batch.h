@@ -97,12 +97,15 @@ class BatchRunner {
     std::vector<Wide> wide_;
     cudaError_t wide_before(const mmgap_params& P, cudaStream_t s);
     unsigned build_grid() const;
-    unsigned umma_grid() const;
-    unsigned class_grid(int c) const;  // grid of size class c's solver (at least 1 CTA)
-    int class_lo() const;              // the runner's first size class: batch_class(ntmax_)
+    int class_lo() const;  // the runner's first size class: batch_class(ntmax_)
+    // size class c's solver: the grid kernel (CTA per problem) or the tcgen05 tiles
+    const void* solver_fn(int c, const mmgap_params& P) const;
+    unsigned solver_grid(int c) const;  // (at least 1 CTA)
+    unsigned solver_block() const { return tc_ ? 128u : 32u; }
+    size_t solver_smem(int c) const { return tc_ ? umma_smem_[c] : 0; }
     int device_ = 0, capacity_ = 0, ntmax_ = 16, build_floats_ = 0;
     bool tc_ = false;  // tcgen05 field refresh for 8 and 16 users (4-problem tiles)
-    size_t umma_smem_ = 0;  // dynamic shared memory of the tcgen05 solver
+    size_t umma_smem_[3] = {0, 0, 0};  // dynamic shared memory of each class's tcgen05 solver
     long long capacity_problems_ = 0;
     size_t build_smem_ = 0, scratch_bytes_ = 0;
     char* scratch_ = nullptr;
@@ -112,6 +115,7 @@ class BatchRunner {
     BatchHeader* h_head_ = nullptr;
     // the grid solver's size classes (batch_class): first problem and count of each in the table
     long long cls_first_[3] = {0, 0, 0}, cls_count_[3] = {0, 0, 0};
+    long long cls_tile_first_[3] = {0, 0, 0}, cls_tiles_[3] = {0, 0, 0};  // the tcgen05 solver's tiles
     // side streams and events of the classes' concurrent solver launches (fork and join)
     cudaStream_t side_[2] = {nullptr, nullptr};
     cudaEvent_t fork_ = nullptr, join_[2] = {nullptr, nullptr};

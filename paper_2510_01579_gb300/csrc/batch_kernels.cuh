@@ -55,6 +55,8 @@ struct BatchArgs {
     // jobs contiguously, class c's problems being [cls_first[c], cls_first[c] + cls_count[c])
     long long cls_first[3];
     long long cls_count[3];
+    long long cls_tile_first[3];  // the tcgen05 solver's 4-problem tiles of each class, likewise
+    long long cls_tiles[3];
     int steps;
     int early_exit;         // K > 0: the early-exit rule of the per-job solver (grid solver only)
     EulerConsts k;
@@ -345,22 +347,24 @@ __global__ void __launch_bounds__(32) batch_solve_grid_kernel(BatchArgs A) {
     batch_solve_problem<NT, F, EE>(A, J, (int)(w - J.first), threadIdx.x, ssm);
 }
 
-// Batched tensor-core solver (tcgen05, solver shape 8): one 128-thread CTA
-// per tile of 4 consecutive problems of one job; 8- and 16-user tiles run
-// umma_tile (the same tiles as mmgap_detect with shape 8, so the same bits),
-// 4-user tiles one exact warp per problem.
-template <int NTMAX>
+// Batched tensor-core solver (tcgen05, solver shape 8) of one size class: one
+// 128-thread CTA per tile of 4 consecutive problems of one job of the class
+// (the table holds each class's tiles contiguously: [cls_tile_first[c],
+// cls_tile_first[c] + cls_tiles[c])).  8- and 16-user tiles run umma_tile (the
+// same tiles as mmgap_detect with shape 8, so the same bits), 4-user tiles one
+// exact warp per problem.  Each class is its own kernel, with its own size's
+// registers and shared memory, and the classes may run concurrently.
+template <int NT>
 __host__ __device__ constexpr size_t batch_umma_bytes() {
-    constexpr size_t u = NTMAX >= 8 ? (size_t)UmmaSmem<NTMAX >= 16 ? 16 : 8>(4).bytes() : 0;
-    constexpr size_t w = 4 * batch_solve_bytes<4>();
-    return u > w ? u : w;
+    return NT >= 8 ? (size_t)UmmaSmem<NT >= 16 ? 16 : 8>(4).bytes() : 4 * batch_solve_bytes<4>();
 }
 
-template <int NTMAX, int F>
+template <int NT, int F>
 __global__ void __launch_bounds__(128) batch_solve_umma_kernel(BatchArgs A) {
     extern __shared__ __align__(128) uint8_t usm[];
-    const long long t = blockIdx.x;
-    if (t >= A.tiles) return;
+    constexpr int c = batch_class(NT);
+    if ((long long)blockIdx.x >= A.cls_tiles[c]) return;
+    const long long t = A.cls_tile_first[c] + blockIdx.x;
     int lo = 0, hi = A.n_jobs - 1;  // last job whose tiles start at or before t
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -370,36 +374,30 @@ __global__ void __launch_bounds__(128) batch_solve_umma_kernel(BatchArgs A) {
     const BatchJob& J = A.jobs[lo];
     const int base = (int)(t - J.tile_first) * 4;
     const int live = min(4, J.b.n_problems - base);
-    if (J.nt >= 8) {
-        if constexpr (NTMAX >= 8) {
-            const int nt = J.nt, n = 2 * nt;
-            UmmaTile u;
-            u.Aq = J.Aq + (size_t)base * n * n;
-            u.hq = J.hq + (size_t)base * n;
-            u.g = J.g ? J.g + (size_t)base * n : nullptr;
-            u.n_live = live;
-            u.problem0 = J.poff + (uint64_t)base;
-            u.key0 = J.key0;
-            u.key1 = J.key1;
-            u.level_max = J.kind == 0 ? (1 << (J.b.mod_bits >> 1)) - 1 : 0;
-            u.steps = A.steps;
-            u.k = A.k;
-            u.wait_ns = kDefaultDeviceWaitNs;
-            u.err = J.b.err;
-            u.d_out = J.offset_out ? J.offset_out + (size_t)base * n : nullptr;
-            u.E_out = J.energy_out ? J.energy_out + base : nullptr;
-            u.run_out = nullptr;
-            u.ndiv_out = J.ndiv_out ? J.ndiv_out + base : nullptr;
-            u.x_out = nullptr;
-            u.guess_out = J.guess_out ? J.guess_out + (size_t)base * n : nullptr;
-            u.sym_out = J.sym_out ? J.sym_out + (size_t)base * nt : nullptr;
-            u.mod_bits = J.b.mod_bits;
-            if (nt == 16) {
-                if constexpr (NTMAX >= 16) umma_tile<16, F>(u, 32, usm);
-            } else {
-                umma_tile<8, F>(u, 32, usm);
-            }
-        }
+    if constexpr (NT >= 8) {
+        constexpr int n = 2 * NT;
+        UmmaTile u;
+        u.Aq = J.Aq + (size_t)base * n * n;
+        u.hq = J.hq + (size_t)base * n;
+        u.g = J.g ? J.g + (size_t)base * n : nullptr;
+        u.n_live = live;
+        u.problem0 = J.poff + (uint64_t)base;
+        u.key0 = J.key0;
+        u.key1 = J.key1;
+        u.level_max = J.kind == 0 ? (1 << (J.b.mod_bits >> 1)) - 1 : 0;
+        u.steps = A.steps;
+        u.k = A.k;
+        u.wait_ns = kDefaultDeviceWaitNs;
+        u.err = J.b.err;
+        u.d_out = J.offset_out ? J.offset_out + (size_t)base * n : nullptr;
+        u.E_out = J.energy_out ? J.energy_out + base : nullptr;
+        u.run_out = nullptr;
+        u.ndiv_out = J.ndiv_out ? J.ndiv_out + base : nullptr;
+        u.x_out = nullptr;
+        u.guess_out = J.guess_out ? J.guess_out + (size_t)base * n : nullptr;
+        u.sym_out = J.sym_out ? J.sym_out + (size_t)base * NT : nullptr;
+        u.mod_bits = J.b.mod_bits;
+        umma_tile<NT, F>(u, 32, usm);
     } else {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (warp < live) batch_solve_problem<4, F>(A, J, base + warp, lane, usm + warp * batch_solve_bytes<4>());
