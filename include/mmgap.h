@@ -545,7 +545,8 @@ mmgap_status mmgap_server_destroy(mmgap_server* server);
  * 14,900 of 8 users); a larger job returns MMGAP_ENOMEM (with a message on
  * stderr) and launches nothing.  Split it.
  * The first call on a device looks up the array's device address and the
- * device's SM count (with that device current).
+ * device's SM count (with that device current); make that first call before
+ * any stream capture.
  * Every call shares the one array, which keeps the last call's contents (each
  * call writes every byte it reads before reading it), so calls whose work
  * overlaps on the GPU (other streams, other host threads) race: serialise
